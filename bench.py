@@ -1,0 +1,525 @@
+#!/usr/bin/env python
+"""Benchmark of the batched (a:b)HOPH query path on GB300.
+
+Workload (one step): sketch a batch of 1,024 query sets (K1, OPH/HOPH
+sketching) and compare them with (1:2)HOPH, k = 256, k' = 64, T = 0.7,
+eps = 1e-4 against a device-resident collection of 10,000,000 sketches
+(10.24 GB; sets of lognormal size, median 300, sigma 1, clipped to
+[10, 20000], uniform IDs over D = 2^20).  10% of the queries are planted
+near duplicates (Jaccard 0.6-0.95) of collection rows, the rest are fresh
+random sets.  value = (query, row) sketch-pair comparisons per second.
+
+Also reported on the same line: batched sketching of 1,000,000 sets
+(lognormal sizes, Zipf(1.1) IDs, k = 256 OPH) as sets/s and GB/s, the
+roofline fraction of the dominant kernel from live CUDA events, the CPU
+oracle timed on this host, an end-to-end number through host buffers,
+recall/precision of the planted near duplicates against exact Jaccard and
+the one-query-per-launch full-scan OPH baseline.
+
+--impl reference times the CPU oracle itself on a bounded sample per step.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HOPH sketch-pair comparisons/sec + sets sketched/sec, % HBM roofline, equal recall"
+UNIT = "pair-comparisons/s"
+D = 1 << 20
+K, KG, AB = 256, 64, (1, 2)
+T, EPS = (7, 10), 1e-4
+PERM_SEED, COLL_SEED, Q_SEED, PLANT_SEED = 1, 11, 12, 13
+SKETCH_SEED = 21
+
+# dram read+write bytes per scan-kernel launch from an ncu capture, keyed by
+# the sha256 of the query kernel source it was taken on (null once the
+# source changes)
+NCU_TRAFFIC = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--rows", type=int, default=10_000_000)
+    p.add_argument("--queries", type=int, default=1024)
+    p.add_argument("--sketch-sets", type=int, default=1_000_000)
+    p.add_argument("--e2e-steps", type=int, default=100)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-extras", action="store_true", help="skip sketch/OPH/CPU legs")
+    p.add_argument("--profile", action="store_true", help="few launches, for ncu")
+    return p.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def src_sha(name):
+    with open(os.path.join(ROOT, "paper_1805_11254_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+
+def collection_host(n_rows, rank):
+    from paper_1805_11254_gb300 import synth
+    sizes = synth.counter_collection_sizes(n_rows, COLL_SEED + 1000 * rank)
+    return synth.offsets_from_sizes(sizes), COLL_SEED + rank
+
+
+def query_sets(n_q, off, coll_seed):
+    from paper_1805_11254_gb300 import synth
+    return synth.query_batch(n_q, 0.1, D, coll_seed, off, 0.6, 0.95, Q_SEED, PLANT_SEED)
+
+
+def to_dev(a, dev):
+    import torch
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).to(dev)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z):
+    """One bounded CPU step: oracle sketches of the query batch and the
+    (1:2)HOPH comparison against `rows` collection rows.  The sample rows'
+    sketches are prepared outside the timing (the collection is resident on
+    both sides).  Returns (seconds, pairs)."""
+    from oracle import oracle_c as oc
+    from paper_1805_11254_gb300 import synth
+    ids = synth.counter_ids(coll_seed, 0, int(off[rows]), D)
+    c_sk = oc.sketch(ids, off[:rows + 1], lo, perm=perm, threads=threads)
+    t0 = time.perf_counter()
+    q_sk = oc.sketch(qw["q_ids"], qw["q_off"], lo, perm=perm, threads=threads)
+    oc.query("hoph", q_sk, c_sk, KG, T[0], T[1], EPS, z=z, threads=threads)
+    return time.perf_counter() - t0, len(qw["q_off"]) - 1
+
+
+def cpu_baseline(qw, off, coll_seed, target_s, n_rows):
+    from oracle import oracle_c as oc
+    threads = os.cpu_count() or 1
+    lo = oc.layout(D, K, KG, *AB)
+    perm = oc.permutation(D, PERM_SEED)
+    z = np.diff(lo[::KG]).astype(np.uint64)
+    probe = min(2000, n_rows)
+    t, nq = cpu_oracle_pass(qw, off, coll_seed, probe, threads, lo, perm, z)
+    rows = int(min(n_rows, max(probe, probe * target_s / max(t, 1e-6))))
+    t, nq = cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z)
+    return {"value": nq * rows / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "oracle sketches of the %d query sets + (1:2)HOPH comparison against "
+                      "collection rows 0..%d (%d pairs, %.1f s)" % (nq, rows - 1, nq * rows, t)}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    from oracle import oracle_c as oc
+    oc.build()
+    off, coll_seed = collection_host(args.rows, 0)
+    qw = query_sets(args.queries, off, coll_seed)
+    threads = os.cpu_count() or 1
+    lo = oc.layout(D, K, KG, *AB)
+    perm = oc.permutation(D, PERM_SEED)
+    z = np.diff(lo[::KG]).astype(np.uint64)
+    budget = 150.0 / max(1, args.steps + args.warmup)  # seconds per step
+    probe = 256
+    t, nq = cpu_oracle_pass(qw, off, coll_seed, probe, threads, lo, perm, z)
+    rows = int(min(args.rows, max(16, probe * budget / max(t, 1e-6))))
+    for _ in range(args.warmup):
+        cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z)
+    total = 0.0
+    for _ in range(args.steps):
+        t, nq = cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z)
+        total += t
+    value = nq * rows * args.steps / total
+    sample = ("per step: oracle sketches of %d query sets + (1:2)HOPH comparison against "
+              "collection rows 0..%d (%d pairs)" % (nq, rows - 1, nq * rows))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": workload_config(args, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, world):
+    return {"workload": "batched (1:2)HOPH query: %d query sets (10%% planted, J 0.6-0.95) "
+                        "sketched and compared against %d resident k=256 sketches per GPU"
+                        % (args.queries, args.rows),
+            "D": D, "k": K, "k_group": KG, "a_b": "1:2", "T": "7/10", "eps": EPS,
+            "queries": args.queries, "rows_per_gpu": args.rows,
+            "set_size": "lognormal(median 300, sigma 1.0) clipped [10, 20000]",
+            "ids": "uniform over D", "l2": "inputs larger than L2 (2.56 GB plane per pass)",
+            "parallelism": "rows sharded, %d GPU(s), no data-path collective" % world}
+
+
+# ---------------------------------------------------------------------------
+# native
+# ---------------------------------------------------------------------------
+
+def run_native(args):
+    import torch
+    from paper_1805_11254_gb300 import build_lib, hoph, synth
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build_lib.build()
+    hoph.load()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- collection (setup, untimed)
+    off, coll_seed = collection_host(args.rows, rank)
+    n_ids = int(off[-1])
+    plan = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
+    d_off = to_dev(off, dev)
+    d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+    hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
+    planes = plan.sketch(d_ids, d_off, args.rows)
+    plan.check()
+    del d_ids
+    torch.cuda.empty_cache()
+
+    # ---- query batch
+    qw = query_sets(args.queries, off, coll_seed)
+    nq = args.queries
+    dq_ids = to_dev(qw["q_ids"], dev)
+    dq_off = to_dev(qw["q_off"], dev)
+    q_planes = torch.empty((plan.G, nq, KG), dtype=torch.int32, device=dev)
+    cap = 1 << 20
+    out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def step():
+        hoph.oph_build_sketches(plan.handle, dq_ids, dq_off, nq, q_planes, stream)
+        hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_HOPH, q_planes, nq, planes, args.rows,
+                              out, cap, cnt, None, stream)
+
+    if args.profile:
+        for _ in range(max(1, args.warmup)):
+            step()
+        plan.check()
+        return
+
+    for _ in range(args.warmup):
+        step()
+    plan.check()
+    st = torch.zeros(hoph.STATS_WORDS, dtype=torch.int64, device=dev)
+    hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_HOPH, q_planes, nq, planes, args.rows, out,
+                          cap, cnt, st, stream)
+    stats = hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes())
+    n_acc = int(cnt.item())
+    pairs = out[:min(n_acc, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+
+    # ---- timed region
+    clocks = Clocks(local)
+    hoph.hoph_plan_enable_timing(plan.handle, True)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    phase_ms, calls, launches = hoph.hoph_plan_read_timing(plan.handle)
+    hoph.hoph_plan_enable_timing(plan.handle, False)
+    plan.check()
+    ms = max_over_ranks(ms)
+    pairs_per_step = nq * args.rows
+    value = pairs_per_step * world * args.steps / (ms / 1e3)
+
+    peaks, peak_kind = measured_peaks()
+    scan_ms = phase_ms[1] / max(calls, 1)
+    alg_bytes = int(stats.sketch_bytes)
+    achieved = alg_bytes / (scan_ms / 1e3) / 1e9
+    traffic = NCU_TRAFFIC.get(src_sha("query.cu"))
+    roofline = {"bound": "hbm", "kernel": "scan_kernel (join strategy, first group)",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy)",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel_ms_per_launch": scan_ms,
+                "phases_ms_per_step": {"join_index": phase_ms[0] / max(calls, 1),
+                                       "scan": scan_ms, "sort_stats": phase_ms[2] / max(calls, 1)}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": workload_config(args, world), "roofline": roofline,
+            "gpu_launches": int(launches) + args.steps * 1,  # + one sketch kernel per step
+            "clocks": clk,
+            "stats": {"accepted": n_acc, "survivors_entering_group": list(stats.entering[:4]),
+                      "accepted_per_group": list(stats.accepted[:4]),
+                      "rejected_per_group": list(stats.rejected[:4]),
+                      "join_hits": int(stats.join_hits), "strategy": int(stats.strategy)}}
+
+    if rank == 0 and not args.no_extras:
+        line["e2e"] = e2e_leg(args, plan, qw, planes, dev, stream)
+        line["quality"] = quality(qw, pairs, off, coll_seed, args)
+        line["sketch"] = sketch_leg(dev, stream, peaks)
+        line["oph_full_scan_baseline"] = oph_baseline_leg(args, off, coll_seed, qw, dev, stream,
+                                                          value)
+        line["cpu_baseline"] = cpu_baseline(qw, off, coll_seed, args.cpu_seconds, args.rows)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e_leg(args, plan, qw, planes, dev, stream):
+    """Same step through the public API from pinned host buffers: H2D of the
+    query sets, sketch, query, D2H of the count and the accepted pairs."""
+    import torch
+    from paper_1805_11254_gb300 import hoph
+    nq = args.queries
+    h_ids = torch.from_numpy(np.ascontiguousarray(qw["q_ids"]).view(np.int32)).pin_memory()
+    h_off = torch.from_numpy(np.ascontiguousarray(qw["q_off"])).pin_memory()
+    d_ids = torch.empty_like(h_ids, device=dev)
+    d_off = torch.empty_like(h_off, device=dev)
+    q_planes = torch.empty((plan.G, nq, KG), dtype=torch.int32, device=dev)
+    cap = 1 << 20
+    out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    h_cnt = torch.zeros(1, dtype=torch.int64).pin_memory()
+    h_out = torch.empty((cap, 2), dtype=torch.int64).pin_memory()
+    d2h = 0
+
+    def once():
+        nonlocal d2h
+        d_ids.copy_(h_ids, non_blocking=True)
+        d_off.copy_(h_off, non_blocking=True)
+        hoph.oph_build_sketches(plan.handle, d_ids, d_off, nq, q_planes, stream)
+        hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_HOPH, q_planes, nq, planes, args.rows,
+                              out, cap, cnt, None, stream)
+        h_cnt.copy_(cnt, non_blocking=True)
+        stream.synchronize()
+        n = min(int(h_cnt.item()), cap)
+        h_out[:n].copy_(out[:n], non_blocking=True)
+        stream.synchronize()
+        d2h = 8 + 16 * n
+
+    for _ in range(3):
+        once()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        once()
+    dt = (time.perf_counter() - t0) / args.e2e_steps
+    return {"value": nq * args.rows / dt, "unit": UNIT,
+            "h2d_bytes_per_step": int(h_ids.numel() * 4 + h_off.numel() * 8),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
+            "path": "pinned host sets -> oph_build_sketches -> hoph_query_batch -> host pairs"}
+
+
+def quality(qw, pairs, off, coll_seed, args):
+    """Recall and precision against exact Jaccard >= T: planted pairs (known
+    sources) and every reported pair, exact Jaccard from the CPU oracle."""
+    from oracle import oracle_c as oc
+    from paper_1805_11254_gb300 import synth
+    rep = {(int(p["query"]), int(p["row"])) for p in pairs}
+    planted = {(int(q), int(r)) for q, r in enumerate(qw["src"]) if r >= 0}
+    cand = sorted(rep | planted)
+    rows = sorted({r for _, r in cand})
+    sets = [synth.counter_ids(coll_seed, int(off[r]), int(off[r + 1] - off[r]), D) for r in rows]
+    c_ids, c_off = synth.pack_sets(sets)
+    ridx = {r: i for i, r in enumerate(rows)}
+    pa = np.asarray([q for q, _ in cand], dtype=np.int64)
+    pb = np.asarray([ridx[r] for _, r in cand], dtype=np.int64)
+    inter, uni = oc.jaccard_pairs(qw["q_ids"], qw["q_off"], c_ids, c_off, pa, pb)
+    truth = {c for c, i, u in zip(cand, inter, uni) if u and i * T[1] >= T[0] * u}
+    tp = len(rep & truth)
+    return {"reported": len(rep), "truly_similar_among_planted_and_reported": len(truth),
+            "precision": tp / len(rep) if rep else 1.0,
+            "recall": tp / len(truth) if truth else 1.0,
+            "ground_truth": "exact Jaccard (CPU oracle) of planted and reported pairs; random "
+                            "pairs of this workload have Jaccard ~2e-4"}
+
+
+def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
+    """Batched OPH sketching: 10^6 sets, lognormal sizes, Zipf(1.1) IDs over
+    2^20, k = 256 (one plane)."""
+    import torch
+    from paper_1805_11254_gb300 import hoph, synth
+    sizes = synth.lognormal_sizes(n_sets, 300, 1.0, 10, 20000, SKETCH_SEED)
+    off = synth.offsets_from_sizes(sizes)
+    n_ids = int(off[-1])
+    cdf = synth.zipf_cdf(D, 1.1)
+    d_cdf = torch.from_numpy(cdf).to(dev)
+    d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+    hoph.hoph_synth_ids(SKETCH_SEED, 0, n_ids, D, 1, d_cdf, len(cdf), d_ids)
+    d_off = to_dev(off, dev)
+    with hoph.Plan(D, K, K, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
+        out = torch.empty((1, n_sets, K), dtype=torch.int32, device=dev)
+        for _ in range(3):
+            plan.sketch(d_ids, d_off, n_sets, out=out, stream=stream)
+        plan.check()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.sketch(d_ids, d_off, n_sets, out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.check()
+        ms = e0.elapsed_time(e1) / steps
+    bytes_ = 4 * n_ids + 8 * (n_sets + 1) + 4 * K * n_sets
+    gbs = bytes_ / (ms / 1e3) / 1e9
+    return {"sets_per_s": n_sets / (ms / 1e3), "ms_per_launch": ms,
+            "workload": "1,000,000 sets, lognormal(300, 1.0) [10, 20000], Zipf(1.1) IDs over 2^20,"
+                        " k = 256 OPH",
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                         "algorithmic_bytes_per_launch": bytes_}}
+
+
+def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, n_launch=8):
+    """Plain OPH over all 256 bins, one query per launch (the dense scan),
+    on a uniform-OPH sketch of the same collection."""
+    import torch
+    from paper_1805_11254_gb300 import hoph
+    n_ids = int(off[-1])
+    with hoph.Plan(D, K, K, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
+        d_off = to_dev(off, dev)
+        d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+        hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
+        planes = plan.sketch(d_ids, d_off, args.rows)
+        del d_ids
+        torch.cuda.empty_cache()
+        dq_ids = to_dev(qw["q_ids"], dev)
+        dq_off = to_dev(qw["q_off"], dev)
+        nq = len(qw["q_off"]) - 1
+        q_planes = plan.sketch(dq_ids, dq_off, nq)
+        plan.check()
+        plan.set_exec(strategy=0)
+        cap = 1 << 16
+        out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        planted = [q for q in range(nq) if qw["src"][q] >= 0][:n_launch]
+        for q in planted[:2]:
+            hoph.hoph_query_batch(plan.handle, 0, q_planes[:, q:q + 1].contiguous(), 1, planes,
+                                  args.rows, out, cap, cnt, None, stream)
+        torch.cuda.synchronize()
+        qs = [q_planes[:, q:q + 1].contiguous() for q in planted]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for qp in qs:
+            hoph.hoph_query_batch(plan.handle, 0, qp, 1, planes, args.rows, out, cap, cnt, None,
+                                  stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.check()
+        ms = e0.elapsed_time(e1) / len(qs)
+        del planes
+        torch.cuda.empty_cache()
+    v = args.rows / (ms / 1e3)
+    return {"value": v, "unit": UNIT, "ms_per_query_launch": ms,
+            "hoph_speedup": hoph_value / v,
+            "how": "mode OPH_FULL, dense scan of all 256 bins (10.24 GB), one query per launch, "
+                   "%d launches" % len(qs)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * hoph.h - C ABI of the GB300 library for One Permutation Hashing (OPH),
+ * group-based OPH (GOPH) and hierarchical (a:b) OPH (HOPH) near-duplicate
+ * detection, with MinWise as the baseline.
+ *
+ * Method: Zhang et al., "Hierarchical One Permutation Hashing: Efficient
+ * Multimedia Near Duplicate Detection" (arXiv 1805.11254).  Section,
+ * equation and algorithm numbers are the paper's.
+ *
+ * Conventions for every entry point
+ *   - Device pointers ("d_" prefix) are CUDA device memory owned by the
+ *     caller.  The library never frees or reallocates caller memory.
+ *   - `stream` is a cudaStream_t passed as void*.  Work is enqueued on it
+ *     and the call returns without synchronising, except where stated.
+ *   - Return value: HOPH_OK (0) or a negative HOPH_ERR_* code.  Argument
+ *     errors are returned before anything is enqueued.  Errors found on the
+ *     device (an ID >= D, a full output buffer, a bounded wait that gave up)
+ *     are recorded in the plan's device status word; hoph_sync_status()
+ *     synchronises the stream and returns and clears that word.
+ *   - A plan owns its permutation table, bin layout, decision thresholds and
+ *     scratch memory.  Calls that use one plan must be ordered on one stream
+ *     (they share its scratch); use one plan per concurrent stream.
+ */
+#ifndef HOPH_H
+#define HOPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HOPH_OK 0
+#define HOPH_ERR_PARAM (-1)       /* invalid argument or parameter set       */
+#define HOPH_ERR_ID_RANGE (-2)    /* an input ID was >= D (element skipped)  */
+#define HOPH_ERR_CAPACITY (-3)    /* more accepted pairs than out_capacity   */
+#define HOPH_ERR_TIMEOUT (-4)     /* a bounded device wait gave up           */
+#define HOPH_ERR_CUDA (-5)        /* a CUDA runtime call failed              */
+#define HOPH_ERR_NOMEM (-6)       /* host or device allocation failed        */
+#define HOPH_ERR_UNSUPPORTED (-7) /* valid parameters this build cannot run  */
+
+/* ---- enumerations ------------------------------------------------------ */
+/* comparison modes of hoph_query_batch */
+#define HOPH_MODE_OPH_FULL 0     /* Eq. 6 over all k bins, no early exit       */
+#define HOPH_MODE_GOPH 1         /* Algorithm 1, equal groups of k' bins       */
+#define HOPH_MODE_HOPH 2         /* Algorithm 2, (a:b) hierarchical groups     */
+#define HOPH_MODE_MINWISE_FULL 3 /* MinWise: matching minima / k >= T          */
+
+/* how psi is realised */
+#define HOPH_PERM_TABLE 0  /* explicit Fisher-Yates table of D entries       */
+#define HOPH_PERM_HASH61 1 /* ((a x + b) mod (2^61 - 1)) >> 29, D = 2^32     */
+
+/* which bins count in a group's denominator K_j */
+#define HOPH_EMPTY_BOTH 0   /* drop bins empty in both sketches (Eq. 5)     */
+#define HOPH_EMPTY_EITHER 1 /* drop bins empty in either sketch             */
+#define HOPH_EMPTY_NONE 2   /* keep all k' bins (Algorithms 1-2 literally)  */
+
+/* HOPH remaining-requirement rule */
+#define HOPH_WEIGHT_SPACE 0 /* groups weighted by their share of V (a:b)   */
+
+#define HOPH_MAX_GROUPS 16
+#define HOPH_EMPTY_VALUE 0xFFFFFFFFu /* the empty-bin marker in a sketch */
+
+/*
+ * Method parameters (Sec. 3.1-4.1 and Table 1).
+ *   universe_D  size of the vocabulary V; IDs are 0..D-1.  1 <= D <= 2^32.
+ *               HOPH_PERM_HASH61 requires D = 2^32.
+ *   k           bins per sketch; k_group (k') bins per group; k % k' == 0,
+ *               G = k / k' <= HOPH_MAX_GROUPS.
+ *   a, b        (a:b)HOPH split of the space (Sec. 4.1); a = b = 0 gives the
+ *               equal bins of OPH / GOPH (Sec. 3.2-3.3).  Every HOPH group
+ *               must hold at least k' values of V.
+ *   perm_kind   HOPH_PERM_TABLE or HOPH_PERM_HASH61.
+ *   minwise_k   number of MinWise permutations to build (0 = none); table t
+ *               is the Fisher-Yates table of seed + t.
+ *   seed        seed of psi.
+ *   thr_num/thr_den  the similarity threshold T as an exact fraction
+ *               (0 < T <= 1, thr_den <= 65535).
+ *   epsilon     the error tolerance of Definition 1, 0 <= eps.
+ *   empty_rule  HOPH_EMPTY_*.
+ *   weighting   HOPH_WEIGHT_SPACE.
+ */
+typedef struct {
+    uint64_t universe_D;
+    uint32_t k;
+    uint32_t k_group;
+    uint32_t a, b;
+    uint32_t perm_kind;
+    uint32_t minwise_k;
+    uint64_t seed;
+    uint32_t thr_num, thr_den;
+    double epsilon;
+    uint32_t empty_rule;
+    uint32_t weighting;
+} hoph_params;
+
+/* One accepted (query, row) pair (the result set O of Algorithms 1-2). */
+typedef struct {
+    int64_t row;      /* collection row index                          */
+    uint32_t query;   /* query index                                   */
+    uint16_t groups;  /* groups compared before the decision           */
+    uint16_t matches; /* matched bins over those groups                */
+} hoph_pair;
+
+/* Optional per-call statistics, accumulated (the caller zeroes it). */
+typedef struct {
+    int64_t entering[HOPH_MAX_GROUPS]; /* pairs still open when group g starts */
+    int64_t accepted[HOPH_MAX_GROUPS]; /* pairs accepted after group g         */
+    int64_t rejected[HOPH_MAX_GROUPS]; /* pairs rejected after group g         */
+    int64_t sketch_bytes;              /* sketch bytes read from HBM (model)   */
+    int64_t join_hits;                 /* (row value, query) join matches      */
+    int64_t strategy;                  /* 0 dense scan, 1 value join            */
+    int64_t reserved;
+} hoph_stats;
+
+/* Read-only facts about a plan (for tests and tooling). */
+typedef struct {
+    uint32_t groups;                    /* G                                  */
+    uint32_t key_bits;                  /* packed psi table: bits of offset   */
+    int64_t upper_limit;                /* U = min{j : P(X >= j) <= eps}      */
+    int64_t lower_limit;                /* L = max{j : P(X < j) <= eps}       */
+    uint64_t group_size[HOPH_MAX_GROUPS]; /* z_g, the values of V in group g  */
+} hoph_plan_info;
+
+/* Execution knobs (never change results).  0 = library default. */
+typedef struct {
+    int32_t strategy;        /* -1 auto, 0 dense, 1 value join            */
+    int32_t tile_rows;       /* rows per shared-memory tile               */
+    int32_t consumer_warps;  /* scoring warps per CTA                     */
+    int32_t ctas_per_sm;     /* resident CTAs per SM for the scan         */
+    int32_t stages;          /* TMA pipeline depth                        */
+    int32_t reserved[3];
+} hoph_exec;
+
+typedef struct hoph_plan hoph_plan;
+
+/*
+ * Create a plan: validate the parameters, build psi (Sec. 3.2; Fisher-Yates
+ * over D driven by SplitMix64(seed), or the 2-universal hash), the bin
+ * layout (Sec. 3.2 equal bins or Sec. 4.1 a:b groups), the packed psi ->
+ * (bin, offset) table in device memory, the MinWise tables if requested,
+ * and the exact integer decision thresholds derived from the binomial tails
+ * of Definition 1 (Eq. 10-11).  Synchronous; uses the current CUDA device.
+ * *out receives the plan (NULL on error).
+ */
+int hoph_plan_create(const hoph_params *params, hoph_plan **out);
+
+/* As hoph_plan_create, with psi given as a host table of D entries
+ * (host_perm[x] = psi(x), a permutation of 0..D-1).  Copied; the caller
+ * keeps ownership of host_perm. */
+int hoph_plan_create_with_perm(const hoph_params *params, const uint32_t *host_perm,
+                               hoph_plan **out);
+
+/* Free a plan and everything it owns (synchronises the device). */
+void hoph_plan_destroy(hoph_plan *plan);
+
+/* Copy read-only facts about a plan into *out. */
+int hoph_plan_get_info(const hoph_plan *plan, hoph_plan_info *out);
+
+/* Set execution knobs (exec = NULL restores the defaults). */
+int hoph_plan_set_exec(hoph_plan *plan, const hoph_exec *exec);
+
+/*
+ * OPH / HOPH sketches of n_sets sets (Sec. 3.2 "One Permutation Hashing",
+ * Sec. 4.1 construction): for every bin, the smallest psi-value of the set
+ * that falls in it minus the bin's lower bound, or HOPH_EMPTY_VALUE.
+ *   d_ids       uint32 IDs of all sets back to back (duplicates allowed).
+ *   d_offsets   int64[n_sets + 1]; set i is d_ids[d_offsets[i] .. d_offsets[i+1]).
+ *   d_planes    uint32[G][n_sets][k'] output, group-major: plane g holds
+ *               bins g*k' .. (g+1)*k'-1 of every set.
+ * IDs >= D are skipped and flag HOPH_ERR_ID_RANGE in the status word.
+ */
+int oph_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
+                       int64_t n_sets, uint32_t *d_planes, void *stream);
+
+/*
+ * MinWise sketches (Sec. 1, the baseline): d_sketches[n_sets][minwise_k],
+ * entry t = min over the set of psi_t(x); HOPH_EMPTY_VALUE for an empty set.
+ * Needs a plan created with minwise_k > 0.  Same input layout as above.
+ */
+int minwise_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
+                           int64_t n_sets, uint32_t *d_sketches, void *stream);
+
+/*
+ * Compare every query with every collection row and return the similar
+ * pairs (Algorithm 1 for HOPH_MODE_GOPH, Algorithm 2 for HOPH_MODE_HOPH,
+ * Eq. 6 over all bins for HOPH_MODE_OPH_FULL, MinWise for
+ * HOPH_MODE_MINWISE_FULL).
+ *   d_query_planes  uint32[G][n_queries][k'] (MinWise: [n_queries][minwise_k]).
+ *   d_coll_planes   uint32[G][n_rows][k']    (MinWise: [n_rows][minwise_k]).
+ *   d_out           hoph_pair[out_capacity]; receives the accepted pairs
+ *                   sorted by (query, row).
+ *   d_out_count     int64 on the device; receives the number of accepted
+ *                   pairs.  If it exceeds out_capacity, only out_capacity
+ *                   pairs (an unspecified subset) are written, the status
+ *                   word gets HOPH_ERR_CAPACITY, and the call can be repeated
+ *                   with a larger buffer.
+ *   d_stats         nullable; hoph_stats accumulated on the device.
+ * Mode GOPH and OPH_FULL need an equal-bin plan (a = b = 0); mode HOPH an
+ * (a:b) plan; MINWISE_FULL a plan with minwise_k > 0.
+ * Plane pointers must be 16-byte aligned.
+ */
+int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_planes,
+                     int64_t n_queries, const uint32_t *d_coll_planes, int64_t n_rows,
+                     hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
+                     hoph_stats *d_stats, void *stream);
+
+/*
+ * Per-pair, per-group bin counts (Eq. 2-5) of every (query, row) pair with
+ * no early exit: d_counts[n_queries][n_rows][G][3] uint16 holding
+ * (matched bins, bins empty in both, bins empty in exactly one).
+ */
+int hoph_pair_counts(hoph_plan *plan, const uint32_t *d_query_planes, int64_t n_queries,
+                     const uint32_t *d_coll_planes, int64_t n_rows, uint16_t *d_counts,
+                     void *stream);
+
+/*
+ * Seeded synthetic IDs on the device (benchmark inputs, no method
+ * arithmetic): element e (0 <= e < n_ids) receives
+ *   h = SplitMix64 output number e+1 of the stream seeded with `seed`,
+ *   kind 0: ((h >> 32) * D) >> 32 (uniform over 0..D-1);
+ *   kind 1: the first index i with u < d_cdf[i], u = (h >> 11) * 2^-53
+ *           (inverse-CDF sampling from the float64 table d_cdf[n_cdf]).
+ */
+int hoph_synth_ids(uint64_t seed, int64_t first, int64_t n_ids, uint64_t D, uint32_t kind,
+                   const double *d_cdf, int64_t n_cdf, uint32_t *d_ids, void *stream);
+
+/*
+ * Optional phase timing of hoph_query_batch (for benchmarks; no paper
+ * counterpart).  While enabled, every call records CUDA events on its stream
+ * around (0) the join-index build, (1) the scan kernel and (2) the sort and
+ * statistics kernels.  hoph_plan_read_timing waits for the last event, writes
+ * the summed milliseconds of the three phases to ms[0..2], the number of
+ * recorded calls to *calls and the number of kernels launched by library
+ * calls on this plan to *launches (both nullable), then resets the counters.
+ */
+int hoph_plan_enable_timing(hoph_plan *plan, int enable);
+int hoph_plan_read_timing(hoph_plan *plan, double *ms, int64_t *calls, int64_t *launches);
+
+/* Synchronise `stream`, then return and clear the plan's device status word
+ * (HOPH_OK if no device-side error was recorded). */
+int hoph_sync_status(hoph_plan *plan, void *stream);
+
+/* Text for a status code (static storage). */
+const char *hoph_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOPH_H */

@@ -1,0 +1,401 @@
+// Plan creation: parameter validation, psi (Sec. 3.2), the bin layout
+// (Sec. 3.2 equal bins, Sec. 4.1 a:b groups), the packed psi table, the
+// MinWise tables, and the small-probability limits of Definition 1.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+int hoph_cuda_fail(cudaError_t e) {
+    (void)e;
+    cudaGetLastError();  // clear a sticky-free error so later calls are not poisoned
+    return HOPH_ERR_CUDA;
+}
+
+namespace {
+
+// SplitMix64 (Steele, Lea, Flood 2014): seeds the Fisher-Yates shuffle.
+struct SplitMix {
+    uint64_t s;
+    uint64_t next() {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+};
+
+// psi over {0..D-1}: Fisher-Yates from the identity, i = D-1 down to 1,
+// swap with j = next() mod (i+1).
+void fisher_yates(uint64_t D, uint64_t seed, uint32_t *out) {
+    for (uint64_t i = 0; i < D; ++i) out[i] = (uint32_t)i;
+    SplitMix g{seed};
+    for (uint64_t i = D - 1; i >= 1; --i) {
+        const uint64_t j = g.next() % (i + 1);
+        std::swap(out[i], out[j]);
+    }
+}
+
+const uint64_t kP61 = (1ull << 61) - 1;
+
+int ceil_log2(uint64_t v) {
+    int b = 0;
+    while ((1ull << b) < v) ++b;
+    return b;
+}
+
+// Bounds of the k bins.  Equal bins (a = b = 0): lo_j = ceil(j D / k).
+// (a:b): G - 1 splits give floor(rem a / (a + b)) to the next group, the
+// last group keeps the remainder; group g's k' bins start at
+// s_g + ceil(i z_g / k').
+bool build_layout(const hoph_params &p, std::vector<uint64_t> &lo, uint64_t *z) {
+    const uint32_t k = p.k, kg = p.k_group, G = k / kg;
+    lo.assign(k + 1, 0);
+    if (p.a == 0 && p.b == 0) {
+        if (p.universe_D < k) return false;
+        for (uint32_t j = 0; j <= k; ++j)
+            lo[j] = (uint64_t)(((unsigned __int128)j * p.universe_D + k - 1) / k);
+    } else {
+        uint64_t rem = p.universe_D, start = 0;
+        for (uint32_t g = 0; g < G; ++g) {
+            const uint64_t zg =
+                (g + 1 < G) ? (uint64_t)(((unsigned __int128)rem * p.a) / ((uint64_t)p.a + p.b))
+                            : rem;
+            if (zg < kg) return false;
+            for (uint32_t i = 0; i < kg; ++i)
+                lo[(size_t)g * kg + i] = start + ((uint64_t)i * zg + kg - 1) / kg;
+            start += zg;
+            rem -= zg;
+        }
+        lo[k] = p.universe_D;
+    }
+    for (uint32_t g = 0; g < G; ++g) z[g] = lo[(size_t)(g + 1) * kg] - lo[(size_t)g * kg];
+    return true;
+}
+
+// X ~ Bin(k', T): U = min{j : P(X >= j) <= eps}, L = max{j : P(X < j) <= eps}
+// (Definition 1 with the two tails of Eq. 11).  The pmf comes from the
+// ratio recurrence p_{i+1} = p_i (k'-i)/(i+1) T/(1-T) in long double.
+void small_probability_limits(uint32_t kg, int64_t tn, int64_t td, double eps, int64_t *U,
+                              int64_t *L, int32_t *always) {
+    *always = eps >= 1.0;
+    std::vector<long double> pmf(kg + 1, 0.0L);
+    if (tn == td) {
+        pmf[kg] = 1.0L;
+    } else {
+        const long double T = (long double)tn / (long double)td;
+        const long double ratio = T / (1.0L - T);
+        long double v = powl(1.0L - T, (long double)kg);
+        for (uint32_t i = 0; i <= kg; ++i) {
+            pmf[i] = v;
+            v = v * (long double)(kg - i) / (long double)(i + 1) * ratio;
+        }
+    }
+    // upper(j) = sum_{i >= j} pmf_i, lower(j) = sum_{i < j} pmf_i
+    std::vector<long double> upper(kg + 2, 0.0L), lower(kg + 2, 0.0L);
+    for (int j = (int)kg; j >= 0; --j) upper[j] = upper[j + 1] + pmf[j];
+    for (uint32_t j = 1; j <= kg + 1; ++j) lower[j] = lower[j - 1] + pmf[j - 1];
+    const long double e = (long double)eps;
+    int64_t u = kg + 1;
+    for (uint32_t j = 0; j <= kg + 1; ++j)
+        if (upper[j] <= e) { u = j; break; }
+    int64_t l = 0;
+    for (uint32_t j = 0; j <= kg + 1; ++j)
+        if (lower[j] <= e) l = j;
+    *U = u;
+    *L = l;
+}
+
+int validate(const hoph_params &p) {
+    if (p.universe_D == 0 || p.universe_D > (1ull << 32)) return HOPH_ERR_PARAM;
+    if (p.k == 0 || p.k_group == 0 || p.k % p.k_group) return HOPH_ERR_PARAM;
+    if (p.k > 65535) return HOPH_ERR_PARAM;
+    if (p.k / p.k_group > HOPH_MAX_GROUPS) return HOPH_ERR_PARAM;
+    if ((p.a == 0) != (p.b == 0)) return HOPH_ERR_PARAM;
+    if (p.thr_den == 0 || p.thr_den > 65535 || p.thr_num == 0 || p.thr_num > p.thr_den)
+        return HOPH_ERR_PARAM;
+    if (!(p.epsilon >= 0.0) || !isfinite(p.epsilon)) return HOPH_ERR_PARAM;
+    if (p.empty_rule > HOPH_EMPTY_NONE) return HOPH_ERR_PARAM;
+    if (p.weighting != HOPH_WEIGHT_SPACE) return HOPH_ERR_UNSUPPORTED;
+    if (p.perm_kind == HOPH_PERM_TABLE) {
+        if (p.universe_D > (1ull << 30)) return HOPH_ERR_UNSUPPORTED;
+    } else if (p.perm_kind == HOPH_PERM_HASH61) {
+        if (p.universe_D != (1ull << 32)) return HOPH_ERR_PARAM;
+        if (p.minwise_k) return HOPH_ERR_UNSUPPORTED;
+    } else {
+        return HOPH_ERR_PARAM;
+    }
+    if (p.minwise_k > 4096 || (uint64_t)p.minwise_k * p.universe_D > (1ull << 31))
+        return HOPH_ERR_UNSUPPORTED;
+    // exact HOPH decisions need products of up to G effective-bin counts to
+    // stay inside __int128 next to T's denominator and the space sizes
+    if (p.a != 0 && 58 + (p.k / p.k_group) * ceil_log2((uint64_t)p.k_group + 1) > 126)
+        return HOPH_ERR_UNSUPPORTED;
+    return HOPH_OK;
+}
+
+void plan_free(hoph_plan *pl) {
+    if (!pl) return;
+    for (cudaEvent_t e : pl->events) cudaEventDestroy(e);
+    for (int m = 0; m < 4; ++m) cudaFree(pl->d_table[m]);
+    cudaFree(pl->d_key);
+    cudaFree(pl->d_lo);
+    cudaFree(pl->d_minwise);
+    cudaFree(pl->d_status);
+    cudaFree(pl->d_scratch);
+    if (pl->h_status) cudaFreeHost(pl->h_status);
+    delete pl;
+}
+
+int plan_create(const hoph_params *params, const uint32_t *host_perm, hoph_plan **out) {
+    if (!out) return HOPH_ERR_PARAM;
+    *out = nullptr;
+    if (!params) return HOPH_ERR_PARAM;
+    const hoph_params p = *params;
+    int rc = validate(p);
+    if (rc) return rc;
+    if (host_perm && p.perm_kind != HOPH_PERM_TABLE) return HOPH_ERR_PARAM;
+
+    hoph_plan *pl = new (std::nothrow) hoph_plan();
+    if (!pl) return HOPH_ERR_NOMEM;
+    pl->P = p;
+    pl->G = p.k / p.k_group;
+    if (!build_layout(p, pl->lo, pl->z)) {
+        delete pl;
+        return HOPH_ERR_PARAM;
+    }
+    uint64_t max_width = 0;
+    for (uint32_t j = 0; j < p.k; ++j) max_width = std::max(max_width, pl->lo[j + 1] - pl->lo[j]);
+    if (max_width >= (1ull << 32)) {  // an offset could collide with the empty marker
+        delete pl;
+        return HOPH_ERR_PARAM;
+    }
+
+    // decision parameters shared by GOPH / HOPH
+    DecideParams &dp = pl->dp;
+    dp.mode = (p.a == 0) ? HOPH_MODE_GOPH : HOPH_MODE_HOPH;
+    dp.rule = p.empty_rule;
+    dp.G = pl->G;
+    dp.kg = p.k_group;
+    dp.tn = p.thr_num;
+    dp.td = p.thr_den;
+    small_probability_limits(p.k_group, p.thr_num, p.thr_den, p.epsilon, &dp.U, &dp.L,
+                             &dp.always_stop);
+    dp.zsuf[pl->G] = 0;
+    for (int g = (int)pl->G - 1; g >= 0; --g) {
+        dp.z[g] = pl->z[g];
+        dp.zsuf[g] = dp.zsuf[g + 1] + pl->z[g];
+    }
+
+    cudaError_t e = cudaGetDevice(&pl->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(pl->d_status, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&pl->h_status, sizeof(int32_t));
+    if (e != cudaSuccess) {
+        plan_free(pl);
+        return hoph_cuda_fail(e);
+    }
+
+    if (p.perm_kind == HOPH_PERM_TABLE) {
+        const uint64_t D = p.universe_D;
+        std::vector<uint32_t> perm;
+        const uint32_t *psi = host_perm;
+        if (!psi) {
+            try {
+                perm.resize(D);
+            } catch (...) {
+                plan_free(pl);
+                return HOPH_ERR_NOMEM;
+            }
+            fisher_yates(D, p.seed, perm.data());
+            psi = perm.data();
+        }
+        // packed key: (bin << key_bits) | (psi(x) - lo[bin])
+        const int bin_bits = ceil_log2(p.k);
+        pl->key_bits = 32 - bin_bits;
+        if (pl->key_bits < 32 && max_width > (1ull << pl->key_bits)) {
+            plan_free(pl);
+            return HOPH_ERR_UNSUPPORTED;
+        }
+        std::vector<uint32_t> key(D);
+        std::vector<uint8_t> seen(host_perm ? D : 0, 0);
+        for (uint64_t x = 0; x < D; ++x) {
+            const uint64_t v = psi[x];
+            if (v >= D || (host_perm && seen[v]++)) {  // not a permutation of 0..D-1
+                plan_free(pl);
+                return HOPH_ERR_PARAM;
+            }
+            const uint32_t bin = (uint32_t)(std::upper_bound(pl->lo.begin(), pl->lo.end(), v) -
+                                            pl->lo.begin() - 1);
+            key[x] = (uint32_t)(((uint64_t)bin << pl->key_bits) | (v - pl->lo[bin]));
+        }
+        e = cudaMalloc(&pl->d_key, D * sizeof(uint32_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(pl->d_key, key.data(), D * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && p.minwise_k) {
+            const uint32_t mk = p.minwise_k;
+            std::vector<uint32_t> tab((size_t)D * mk), one(D);
+            for (uint32_t t = 0; t < mk; ++t) {
+                fisher_yates(D, p.seed + t, one.data());
+                for (uint64_t x = 0; x < D; ++x) tab[(size_t)x * mk + t] = one[x];
+            }
+            e = cudaMalloc(&pl->d_minwise, tab.size() * sizeof(uint32_t));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(pl->d_minwise, tab.data(), tab.size() * sizeof(uint32_t),
+                               cudaMemcpyHostToDevice);
+        }
+    } else {
+        // 2-universal hash parameters from the seed: a = 1 + next() mod (p-1), b = next() mod p
+        SplitMix g{p.seed};
+        pl->hash_a = 1 + g.next() % (kP61 - 1);
+        pl->hash_b = g.next() % kP61;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_lo, (p.k + 1) * sizeof(uint64_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pl->d_lo, pl->lo.data(), (p.k + 1) * sizeof(uint64_t),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        plan_free(pl);
+        return hoph_cuda_fail(e);
+    }
+    pl->exec.strategy = -1;
+    *out = pl;
+    return HOPH_OK;
+}
+
+}  // namespace
+
+void *hoph_scratch(hoph_plan *plan, size_t bytes) {
+    if (bytes <= plan->scratch_bytes) return plan->d_scratch;
+    size_t want = std::max(bytes, plan->scratch_bytes * 2);
+    want = (want + 255) & ~(size_t)255;
+    if (plan->d_scratch) {
+        cudaDeviceSynchronize();  // a previous launch may still read the old buffer
+        cudaFree(plan->d_scratch);
+        plan->d_scratch = nullptr;
+        plan->scratch_bytes = 0;
+    }
+    if (cudaMalloc(&plan->d_scratch, want) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    plan->scratch_bytes = want;
+    return plan->d_scratch;
+}
+
+void hoph_timing_mark(hoph_plan *plan, int which, cudaStream_t s) {
+    if (!plan->timing) return;
+    const size_t idx = plan->events_used + (size_t)which;
+    while (plan->events.size() <= idx) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        plan->events.push_back(e);
+    }
+    cudaEventRecord(plan->events[idx], s);
+    if (which == 3) plan->events_used += 4;
+}
+
+extern "C" {
+
+int hoph_plan_enable_timing(hoph_plan *plan, int enable) {
+    if (!plan) return HOPH_ERR_PARAM;
+    plan->timing = enable != 0;
+    plan->events_used = 0;
+    plan->launches = 0;
+    return HOPH_OK;
+}
+
+int hoph_plan_read_timing(hoph_plan *plan, double *ms, int64_t *calls, int64_t *launches) {
+    if (!plan || !ms) return HOPH_ERR_PARAM;
+    for (int i = 0; i < 3; ++i) ms[i] = 0.0;
+    const size_t n = plan->events_used / 4;
+    if (n) HOPH_CUDA_TRY(cudaEventSynchronize(plan->events[plan->events_used - 1]));
+    for (size_t c = 0; c < n; ++c)
+        for (int i = 0; i < 3; ++i) {
+            float t = 0.f;
+            HOPH_CUDA_TRY(cudaEventElapsedTime(&t, plan->events[4 * c + i], plan->events[4 * c + i + 1]));
+            ms[i] += t;
+        }
+    if (calls) *calls = (int64_t)n;
+    if (launches) *launches = plan->launches;
+    plan->events_used = 0;
+    plan->launches = 0;
+    return HOPH_OK;
+}
+
+int hoph_plan_create(const hoph_params *params, hoph_plan **out) {
+    return plan_create(params, nullptr, out);
+}
+
+int hoph_plan_create_with_perm(const hoph_params *params, const uint32_t *host_perm,
+                               hoph_plan **out) {
+    if (!host_perm) return HOPH_ERR_PARAM;
+    return plan_create(params, host_perm, out);
+}
+
+void hoph_plan_destroy(hoph_plan *plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    plan_free(plan);
+}
+
+int hoph_plan_get_info(const hoph_plan *plan, hoph_plan_info *out) {
+    if (!plan || !out) return HOPH_ERR_PARAM;
+    memset(out, 0, sizeof *out);
+    out->groups = plan->G;
+    out->key_bits = plan->key_bits;
+    out->upper_limit = plan->dp.always_stop ? 0 : plan->dp.U;
+    out->lower_limit = plan->dp.always_stop ? (int64_t)plan->P.k_group + 1 : plan->dp.L;
+    for (uint32_t g = 0; g < plan->G; ++g) out->group_size[g] = plan->z[g];
+    return HOPH_OK;
+}
+
+int hoph_plan_set_exec(hoph_plan *plan, const hoph_exec *exec) {
+    if (!plan) return HOPH_ERR_PARAM;
+    if (!exec) {
+        memset(&plan->exec, 0, sizeof plan->exec);
+        plan->exec.strategy = -1;
+        return HOPH_OK;
+    }
+    if (exec->strategy < -1 || exec->strategy > 1 || exec->tile_rows < 0 ||
+        exec->tile_rows > 256 || exec->consumer_warps < 0 || exec->consumer_warps > 16 ||
+        exec->ctas_per_sm < 0 || exec->ctas_per_sm > 8 || exec->stages < 0 || exec->stages > 8)
+        return HOPH_ERR_PARAM;
+    plan->exec = *exec;
+    return HOPH_OK;
+}
+
+int hoph_sync_status(hoph_plan *plan, void *stream) {
+    if (!plan) return HOPH_ERR_PARAM;
+    cudaStream_t s = (cudaStream_t)stream;
+    HOPH_CUDA_TRY(cudaMemcpyAsync(plan->h_status, plan->d_status, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, s));
+    HOPH_CUDA_TRY(cudaMemsetAsync(plan->d_status, 0, sizeof(int32_t), s));
+    HOPH_CUDA_TRY(cudaStreamSynchronize(s));
+    return *plan->h_status;
+}
+
+const char *hoph_status_string(int status) {
+    switch (status) {
+        case HOPH_OK: return "ok";
+        case HOPH_ERR_PARAM: return "invalid argument or parameter set";
+        case HOPH_ERR_ID_RANGE: return "an input ID was >= D";
+        case HOPH_ERR_CAPACITY: return "more accepted pairs than the output capacity";
+        case HOPH_ERR_TIMEOUT: return "a bounded device wait gave up";
+        case HOPH_ERR_CUDA: return "a CUDA runtime call failed";
+        case HOPH_ERR_NOMEM: return "allocation failed";
+        case HOPH_ERR_UNSUPPORTED: return "parameters not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,1112 @@
+// Comparison of query sketches against a device-resident collection:
+// GOPH (Algorithm 1), (a:b)HOPH (Algorithm 2), plain OPH (Eq. 6) and MinWise.
+//
+// One persistent launch streams the first group's plane (or every plane for
+// the full-scan modes) through shared memory: a producer warp issues 3-D
+// TMA tile loads (cp.async.bulk.tensor) into a ring of stages guarded by
+// mbarriers, consumer warps score the tile against the whole query batch.
+// Two scoring strategies give identical results:
+//   dense  - for every (query, row) pair, lanes compare 32 bins at a time and
+//            __popc of __ballot_sync gives matched / both-empty / one-empty
+//            counts;
+//   join   - an exact value join: the batch's first-group query values are
+//            indexed (bitmap + CSR over the group's psi-space), each streamed
+//            row value is looked up once, and per-query match counts build
+//            up in per-warp shared-memory counters.  Pairs without a match are
+//            rejected for every possible denominator (checked on the host
+//            before the join is chosen), so only hit pairs are evaluated.
+// The first-group decision is a table lookup on (matched, effective bins).
+// Pairs that continue are compacted into a per-warp shared-memory list and
+// resolved lane-parallel: each lane gathers only its pair's later groups
+// from HBM and applies the exact integer rule group by group.  Accepted
+// pairs are appended with an atomic cursor and finally sorted by
+// (query, row) by a single-CTA sort, so the output is deterministic.
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kSurvCap = 32;        // per-warp survivor list (one entry per lane)
+constexpr int kMaxW = 1024;         // scanned bins per row
+constexpr int kStatWords = 3 * HOPH_MAX_GROUPS + 4;
+constexpr uint32_t kMaxJoinKeys = 1u << 22;
+constexpr uint32_t kSmemBitmapBytes = 96 * 1024;
+
+struct Survivor {
+    int64_t row;
+    uint32_t q;
+    uint16_t m1, k1;
+};
+
+struct ScanArgs {
+    const uint32_t *coll;
+    int64_t cstride;  // elements between collection planes
+    const uint32_t *qry;
+    int64_t qstride;  // elements between query planes
+    int64_t n_rows;
+    int32_t n_q;
+    int32_t kg, Gs, W, G;
+    uint32_t rule;
+    int32_t join;
+    int32_t use_tma;
+    int32_t tile_rows;
+    int32_t stages;
+    int32_t n_cons;      // consumer warps
+    int64_t n_tiles;
+    uint32_t stage_bytes;  // bytes of one tile (the TMA transaction size)
+    uint32_t stage_stride; // stage_bytes rounded up to 128
+    const uint16_t *thr; // rej[W+1] then acc[W+1]
+    DecideParams dp;
+    // join
+    const uint32_t *bitmap;
+    uint32_t bitmap_words;
+    int32_t bitmap_in_smem;
+    const uint32_t *csr_off;
+    const uint16_t *csr_q;
+    const uint64_t *binbase;  // bin lower bounds; key = binbase[w] + value
+    const uint32_t *q_emask;  // [n_q][mask_words]
+    int32_t mask_words;
+    const int32_t *allempty;  // queries whose scanned bins are all empty
+    const uint32_t *n_allempty;
+    // output
+    hoph_pair *out;
+    int64_t cap;
+    unsigned long long *out_count;
+    unsigned long long *stat;  // kStatWords counters
+    int32_t *status;
+};
+
+struct SmemLayout {
+    uint32_t bars, abort_flag, thr, toff, qoff, binbase, bitmap, counters, rowmask, surv, nsurv,
+        stats, stages, total;
+};
+
+__host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
+
+__host__ __device__ inline SmemLayout smem_layout(const ScanArgs &a) {
+    SmemLayout L;
+    uint32_t o = 0;
+    L.bars = o;        o += 16 * 8;                         // full[8], empty[8]
+    L.abort_flag = o;  o += 16;
+    L.thr = o;         o = align_up(o + 2 * (a.W + 1) * 2, 16);
+    L.toff = o;        o = align_up(o + a.W * 4, 16);
+    L.qoff = o;        o = align_up(o + a.W * 8, 16);
+    L.binbase = o;     o = align_up(o + (a.join ? a.W * 4 : 0), 16);
+    L.bitmap = o;      o = align_up(o + (a.join && a.bitmap_in_smem ? a.bitmap_words * 4 : 0), 16);
+    L.counters = o;    o = align_up(o + (a.join ? a.n_cons * ((a.n_q + 1) / 2) * 4 : 0), 16);
+    L.rowmask = o;     o = align_up(o + (a.join ? a.n_cons * a.mask_words * 4 : 0), 16);
+    L.surv = o;        o = align_up(o + a.n_cons * kSurvCap * (uint32_t)sizeof(Survivor), 16);
+    L.nsurv = o;       o = align_up(o + a.n_cons * 4, 16);
+    L.stats = o;       o = align_up(o + kStatWords * 8, 128);
+    L.stages = o;      o += a.stages * a.stage_stride;
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ void emit_pair(const ScanArgs &a, uint32_t q, int64_t row, int groups,
+                                          int matches) {
+    const unsigned long long idx = atomicAdd(a.out_count, 1ull);
+    if (idx < (unsigned long long)a.cap) {
+        hoph_pair p;
+        p.row = row;
+        p.query = q;
+        p.groups = (uint16_t)groups;
+        p.matches = (uint16_t)matches;
+        a.out[idx] = p;
+    }
+}
+
+// stats layout: [0..15] entering, [16..31] accepted, [32..47] rejected,
+// [48] sketch bytes, [49] join hits
+__device__ __forceinline__ void stat_add(unsigned long long *s, int idx, unsigned long long v) {
+    if (v) atomicAdd(s + idx, v);
+}
+
+// Lane-parallel resolution of the warp's survivor list: lane j finishes
+// entry j by comparing the later groups of its pair one at a time.
+__device__ void resolve_survivors(const ScanArgs &a, Survivor *list, uint32_t *nsurv,
+                                  unsigned long long *s_stats) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    const uint32_t n = min(*nsurv, (uint32_t)kSurvCap);
+    if ((uint32_t)lane < n) {
+        const Survivor sv = list[lane];
+        int32_t Ms[HOPH_MAX_GROUPS], Ks[HOPH_MAX_GROUPS];
+        Ms[0] = sv.m1;
+        Ks[0] = sv.k1;
+        int matches = sv.m1;
+        for (int l = 2; l <= a.G; ++l) {
+            const int g = l - 1;
+            const uint32_t *rp = a.coll + (int64_t)g * a.cstride + sv.row * a.kg;
+            const uint32_t *qp = a.qry + (int64_t)g * a.qstride + (int64_t)sv.q * a.kg;
+            int32_t m = 0, both = 0, one = 0;
+            for (int b = 0; b < a.kg; ++b) {
+                const uint32_t rv = __ldg(rp + b), qv = __ldg(qp + b);
+                const bool er = rv == HOPH_EMPTY_VALUE, eq = qv == HOPH_EMPTY_VALUE;
+                m += (!eq && rv == qv);
+                both += (er && eq);
+                one += (er != eq);
+            }
+            Ms[g] = m;
+            Ks[g] = hoph_effective(a.rule, a.kg, both, one);
+            matches += m;
+            atomicAdd(s_stats + g, 1ull);
+            atomicAdd(s_stats + 48, (unsigned long long)a.kg * 8);
+            const int d = hoph_decide(a.dp, l, Ms, Ks);
+            if (d == HOPH_ACCEPT) {
+                atomicAdd(s_stats + 16 + g, 1ull);
+                emit_pair(a, sv.q, sv.row, l, matches);
+                break;
+            }
+            if (d == HOPH_REJECT) {
+                atomicAdd(s_stats + 32 + g, 1ull);
+                break;
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) *nsurv = 0;
+    __syncwarp();
+}
+
+// Append one survivor from one lane (the caller guarantees room).
+__device__ __forceinline__ bool push_survivor(Survivor *list, uint32_t *nsurv, uint32_t q,
+                                              int64_t row, int m1, int k1) {
+    const uint32_t slot = atomicAdd(nsurv, 1u);
+    if (slot >= (uint32_t)kSurvCap) {
+        atomicSub(nsurv, 1u);
+        return false;
+    }
+    Survivor s;
+    s.row = row;
+    s.q = q;
+    s.m1 = (uint16_t)m1;
+    s.k1 = (uint16_t)k1;
+    list[slot] = s;
+    return true;
+}
+
+__device__ __forceinline__ int table_decide(const uint16_t *thr, int W, int m, int K) {
+    return m < thr[K] ? HOPH_REJECT : (m >= thr[W + 1 + K] ? HOPH_ACCEPT : HOPH_CONTINUE);
+}
+
+// ---------------------------------------------------------------------------
+// Dense scoring of one tile: every (query, row) pair, lanes over bins.
+// ---------------------------------------------------------------------------
+__device__ void score_tile_dense(const ScanArgs &a, const uint32_t *tile, int rows_here,
+                                 int64_t row0, const int32_t *s_toff, const int64_t *s_qoff,
+                                 const uint16_t *s_thr, Survivor *list, uint32_t *nsurv,
+                                 unsigned long long *s_stats, int cw, unsigned long long &acc0,
+                                 unsigned long long &cont0) {
+    const int lane = threadIdx.x & 31;
+    const int nch = (a.W + 31) >> 5;
+    const int64_t n_pairs = (int64_t)rows_here * a.n_q;
+    for (int64_t p = cw; p < n_pairs; p += a.n_cons) {
+        const int q = (int)(p / rows_here);
+        const int rl = (int)(p - (int64_t)q * rows_here);
+        const uint32_t *qb = a.qry + (int64_t)q * a.kg;
+        int m = 0, both = 0, one = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int w = (c << 5) + lane;
+            const bool valid = w < a.W;
+            uint32_t rv = 0, qv = 0;
+            if (valid) {
+                rv = tile[s_toff[w] + rl * a.kg];
+                qv = __ldg(qb + s_qoff[w]);
+            }
+            const bool er = rv == HOPH_EMPTY_VALUE, eq = qv == HOPH_EMPTY_VALUE;
+            m += __popc(__ballot_sync(0xFFFFFFFFu, valid && !eq && rv == qv));
+            both += __popc(__ballot_sync(0xFFFFFFFFu, valid && er && eq));
+            one += __popc(__ballot_sync(0xFFFFFFFFu, valid && er != eq));
+        }
+        const int K = hoph_effective(a.rule, a.W, both, one);
+        const int d = table_decide(s_thr, a.W, m, K);
+        if (d == HOPH_ACCEPT) {
+            ++acc0;
+            if (lane == 0) emit_pair(a, q, row0 + rl, 1, m);
+        } else if (d == HOPH_CONTINUE) {
+            ++cont0;
+            if (*nsurv >= (uint32_t)kSurvCap) resolve_survivors(a, list, nsurv, s_stats);
+            if (lane == 0) push_survivor(list, nsurv, q, row0 + rl, m, K);
+            __syncwarp();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Join scoring of one tile: one warp per row.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool bitmap_has(const ScanArgs &a, const uint32_t *s_bitmap,
+                                           uint32_t key) {
+    const uint32_t w = a.bitmap_in_smem ? s_bitmap[key >> 5] : __ldg(a.bitmap + (key >> 5));
+    return (w >> (key & 31)) & 1u;
+}
+
+__device__ void score_tile_join(const ScanArgs &a, const uint32_t *tile, int rows_here,
+                                int64_t row0, const int32_t *s_toff, const uint32_t *s_binbase,
+                                const uint32_t *s_bitmap, const uint16_t *s_thr, uint32_t *cnt,
+                                uint32_t *rowmask, Survivor *list, uint32_t *nsurv,
+                                unsigned long long *s_stats, int cw, unsigned long long &acc0,
+                                unsigned long long &cont0, unsigned long long &hits) {
+    const int lane = threadIdx.x & 31;
+    const int nch = (a.W + 31) >> 5;
+    const int n_allempty = a.join ? (int)*a.n_allempty : 0;
+    // a pair of all-empty scans has M = 0 and K = the rule's effective bins
+    const int d00 = table_decide(s_thr, a.W, 0, hoph_effective(a.rule, a.W, a.W, 0));
+    for (int rl = cw; rl < rows_here; rl += a.n_cons) {
+        const int64_t row = row0 + rl;
+        // pass 1: row empty mask and match counts per query
+        bool all_empty = true;
+        for (int c = 0; c < nch; ++c) {
+            const int w = (c << 5) + lane;
+            const bool valid = w < a.W;
+            const uint32_t v = valid ? tile[s_toff[w] + rl * a.kg] : HOPH_EMPTY_VALUE;
+            const bool e = v == HOPH_EMPTY_VALUE;
+            const uint32_t em = __ballot_sync(0xFFFFFFFFu, valid && e);
+            const uint32_t vm = __ballot_sync(0xFFFFFFFFu, valid);
+            all_empty = all_empty && (em == vm);
+            if (lane == 0) rowmask[c] = em;
+            if (!e) {
+                const uint32_t key = s_binbase[w] + v;
+                if (bitmap_has(a, s_bitmap, key)) {
+                    const uint32_t o1 = __ldg(a.csr_off + key), o2 = __ldg(a.csr_off + key + 1);
+                    for (uint32_t i = o1; i < o2; ++i) {
+                        const uint32_t q = __ldg(a.csr_q + i);
+                        atomicAdd(cnt + (q >> 1), 1u << ((q & 1) * 16));
+                    }
+                    hits += o2 - o1;
+                }
+            }
+        }
+        __syncwarp();
+        // pass 2: each distinct hit query is taken by the first lane that
+        // clears its counter; resumable so a full survivor list can drain
+        int c = 0;
+        uint32_t i = 0, iend = 0;
+        bool done = false;
+        while (true) {
+            while (!done) {
+                if (i == iend) {
+                    // next chunk of this lane with a bitmap hit
+                    bool found = false;
+                    for (; c < nch && !found; ++c) {
+                        const int w = (c << 5) + lane;
+                        if (w >= a.W) continue;
+                        const uint32_t v = tile[s_toff[w] + rl * a.kg];
+                        if (v == HOPH_EMPTY_VALUE) continue;
+                        const uint32_t key = s_binbase[w] + v;
+                        if (!bitmap_has(a, s_bitmap, key)) continue;
+                        i = __ldg(a.csr_off + key);
+                        iend = __ldg(a.csr_off + key + 1);
+                        found = i < iend;
+                    }
+                    if (!found) {
+                        done = true;
+                        break;
+                    }
+                }
+                const uint32_t q = __ldg(a.csr_q + i);
+                const uint32_t sh = (q & 1) * 16;
+                const uint32_t old = atomicAnd(cnt + (q >> 1), ~(0xFFFFu << sh));
+                const int m = (int)((old >> sh) & 0xFFFFu);
+                if (m) {
+                    int both = 0, one = 0;
+                    const uint32_t *qm = a.q_emask + (int64_t)q * a.mask_words;
+                    for (int j = 0; j < a.mask_words; ++j) {
+                        const uint32_t x = __ldg(qm + j), y = rowmask[j];
+                        both += __popc(x & y);
+                        one += __popc(x ^ y);
+                    }
+                    const int K = hoph_effective(a.rule, a.W, both, one);
+                    const int d = table_decide(s_thr, a.W, m, K);
+                    if (d == HOPH_ACCEPT) {
+                        ++acc0;
+                        emit_pair(a, q, row, 1, m);
+                    } else if (d == HOPH_CONTINUE) {
+                        if (!push_survivor(list, nsurv, q, row, m, K)) {
+                            atomicAdd(cnt + (q >> 1), (uint32_t)m << sh);  // retry later
+                            break;
+                        }
+                        ++cont0;
+                    }
+                }
+                ++i;
+            }
+            const bool all_done = __all_sync(0xFFFFFFFFu, done);
+            __syncwarp();
+            if (*nsurv >= (uint32_t)kSurvCap / 2 || !all_done)
+                resolve_survivors(a, list, nsurv, s_stats);
+            if (all_done) break;
+        }
+        // pairs whose scanned bins are empty on both sides (effective bins 0)
+        if (all_empty && n_allempty > 0 && d00 != HOPH_REJECT) {
+            for (int base = 0; base < n_allempty; base += 32) {
+                if (*nsurv + 32 > (uint32_t)kSurvCap) resolve_survivors(a, list, nsurv, s_stats);
+                if (base + lane < n_allempty) {
+                    const uint32_t q = (uint32_t)a.allempty[base + lane];
+                    if (d00 == HOPH_ACCEPT) {
+                        ++acc0;
+                        emit_pair(a, q, row, 1, 0);
+                    } else {
+                        ++cont0;
+                        push_survivor(list, nsurv, q, row, 0, 0);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The persistent scan kernel
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32 * 17) scan_kernel(const __grid_constant__ ScanArgs a,
+                                                       const __grid_constant__ CUtensorMap map) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const SmemLayout L = smem_layout(a);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
+    uint64_t *empty = full + 8;
+    volatile int32_t *abort_flag = reinterpret_cast<volatile int32_t *>(smem + L.abort_flag);
+    uint16_t *s_thr = reinterpret_cast<uint16_t *>(smem + L.thr);
+    int32_t *s_toff = reinterpret_cast<int32_t *>(smem + L.toff);
+    int64_t *s_qoff = reinterpret_cast<int64_t *>(smem + L.qoff);
+    uint32_t *s_binbase = reinterpret_cast<uint32_t *>(smem + L.binbase);
+    uint32_t *s_bitmap = reinterpret_cast<uint32_t *>(smem + L.bitmap);
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + L.counters);
+    uint32_t *s_rowmask = reinterpret_cast<uint32_t *>(smem + L.rowmask);
+    Survivor *s_surv = reinterpret_cast<Survivor *>(smem + L.surv);
+    uint32_t *s_nsurv = reinterpret_cast<uint32_t *>(smem + L.nsurv);
+    unsigned long long *s_stats = reinterpret_cast<unsigned long long *>(smem + L.stats);
+    unsigned char *stages = smem + L.stages;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int R = a.tile_rows;
+
+    // set-up: tables into shared memory
+    for (int i = tid; i < 2 * (a.W + 1); i += blockDim.x) s_thr[i] = a.thr[i];
+    for (int w = tid; w < a.W; w += blockDim.x) {
+        const int g = w / a.kg, b = w - g * a.kg;
+        s_toff[w] = (g * R) * a.kg + b;
+        s_qoff[w] = (int64_t)g * a.qstride + b;
+        if (a.join) s_binbase[w] = (uint32_t)a.binbase[w];
+    }
+    if (a.join && a.bitmap_in_smem)
+        for (uint32_t i = tid; i < a.bitmap_words; i += blockDim.x) s_bitmap[i] = a.bitmap[i];
+    if (a.join)
+        for (int i = tid; i < a.n_cons * ((a.n_q + 1) / 2); i += blockDim.x) s_cnt[i] = 0;
+    for (int i = tid; i < a.n_cons; i += blockDim.x) s_nsurv[i] = 0;
+    for (int i = tid; i < kStatWords; i += blockDim.x) s_stats[i] = 0;
+    if (tid == 0) {
+        *abort_flag = 0;
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, a.n_cons);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == a.n_cons) {
+        // ---------------- producer warp ----------------
+        if (a.use_tma && lane == 0) {
+            tma_prefetch_desc(&map);
+            int64_t it = 0;
+            for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+                const int s = (int)(it % a.stages);
+                const uint32_t use = (uint32_t)(it / a.stages);
+                if (use > 0 && !mbar_wait_bounded(empty + s, (use - 1) & 1, abort_flag)) {
+                    hoph_flag(a.status, HOPH_ERR_TIMEOUT);
+                    *abort_flag = 1;
+                    break;
+                }
+                mbar_arrive_expect_tx(full + s, a.stage_bytes);
+                tma_load_3d(stages + (size_t)s * a.stage_stride, &map, full + s, 0,
+                            (int32_t)(tile * R), 0);
+            }
+            // let every copy this warp issued land before it leaves
+            const int64_t issued = it;
+            for (int64_t j = (issued > a.stages ? issued - a.stages : 0); j < issued; ++j) {
+                const int s = (int)(j % a.stages);
+                if (!mbar_wait_bounded(full + s, (uint32_t)(j / a.stages) & 1, abort_flag)) {
+                    // consumers gave up; give the copy a last bounded chance
+                    const uint64_t t0 = global_ns();
+                    while (!mbar_try_wait(full + s, (uint32_t)(j / a.stages) & 1) &&
+                           global_ns() - t0 < 1000000000ull) {
+                    }
+                }
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumer warps ----------------
+    const int cw = warp;
+    Survivor *list = s_surv + cw * kSurvCap;
+    uint32_t *nsurv = s_nsurv + cw;
+    uint32_t *cnt = s_cnt + cw * ((a.n_q + 1) / 2);
+    uint32_t *rowmask = s_rowmask + cw * a.mask_words;
+    unsigned long long acc0 = 0, cont0 = 0, hits = 0;
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+        const int s = a.use_tma ? (int)(it % a.stages) : 0;
+        const uint32_t *tp = reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride);
+        const int64_t row0 = tile * R;
+        const int rows_here = (int)min((long long)R, (long long)(a.n_rows - row0));
+        if (a.use_tma) {
+            if (!mbar_wait_bounded(full + s, (uint32_t)(it / a.stages) & 1, abort_flag)) {
+                hoph_flag(a.status, HOPH_ERR_TIMEOUT);
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+        } else {
+            // plain cooperative load of the tile ([Gs][R][k'] layout)
+            uint32_t *dst = reinterpret_cast<uint32_t *>(stages);
+            const int per_plane = rows_here * a.kg;
+            for (int idx = cw * 32 + lane; idx < a.Gs * per_plane; idx += a.n_cons * 32) {
+                const int g = idx / per_plane, rem = idx - g * per_plane;
+                dst[g * R * a.kg + rem] = a.coll[(int64_t)g * a.cstride + row0 * a.kg + rem];
+            }
+            named_bar_sync(1, a.n_cons * 32);
+        }
+        if (a.join)
+            score_tile_join(a, tp, rows_here, row0, s_toff, s_binbase, s_bitmap, s_thr, cnt,
+                            rowmask, list, nsurv, s_stats, cw, acc0, cont0, hits);
+        else
+            score_tile_dense(a, tp, rows_here, row0, s_toff, s_qoff, s_thr, list, nsurv, s_stats,
+                             cw, acc0, cont0);
+        __syncwarp();
+        if (a.use_tma) {
+            if (lane == 0) mbar_arrive(empty + s);
+        } else {
+            named_bar_sync(1, a.n_cons * 32);
+        }
+    }
+    if (ok && *nsurv) resolve_survivors(a, list, nsurv, s_stats);
+    // warp totals (dense counts are warp-uniform; join counts are per lane)
+    if (!a.join) {
+        if (lane != 0) acc0 = cont0 = 0;
+    }
+    for (int o = 16; o; o >>= 1) {
+        acc0 += __shfl_xor_sync(0xFFFFFFFFu, acc0, o);
+        cont0 += __shfl_xor_sync(0xFFFFFFFFu, cont0, o);
+        hits += __shfl_xor_sync(0xFFFFFFFFu, hits, o);
+    }
+    if (lane == 0) {
+        stat_add(s_stats, 16, acc0);
+        stat_add(s_stats, 49, hits);
+    }
+    named_bar_sync(1, a.n_cons * 32);
+    if (cw == 0)
+        for (int i = lane; i < kStatWords; i += 32)
+            if (s_stats[i]) atomicAdd(a.stat + i, s_stats[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Join index over the batch's scanned query bins
+// ---------------------------------------------------------------------------
+struct IndexArgs {
+    const uint32_t *qry;
+    int64_t qstride;
+    int32_t n_q, kg, W, mask_words;
+    const uint64_t *binbase;
+    uint32_t *counts;    // [keys + 1]
+    uint32_t *bitmap;
+    uint32_t *q_emask;   // [n_q][mask_words]
+    int32_t *allempty;
+    uint32_t *n_allempty;
+};
+
+// warp per query: empty masks, all-empty list, key counts and the bitmap
+__global__ void join_count_kernel(const IndexArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= a.n_q) return;
+    bool all_empty = true;
+    for (int c = 0; c < a.mask_words; ++c) {
+        const int w = (c << 5) + lane;
+        const bool valid = w < a.W;
+        uint32_t v = HOPH_EMPTY_VALUE;
+        if (valid) {
+            const int g = w / a.kg, b = w - g * a.kg;
+            v = a.qry[(int64_t)g * a.qstride + q * a.kg + b];
+        }
+        const bool e = v == HOPH_EMPTY_VALUE;
+        const uint32_t em = __ballot_sync(0xFFFFFFFFu, valid && e);
+        const uint32_t vm = __ballot_sync(0xFFFFFFFFu, valid);
+        all_empty = all_empty && em == vm;
+        if (lane == 0) a.q_emask[q * a.mask_words + c] = em;
+        if (valid && !e) {
+            const uint32_t key = (uint32_t)(a.binbase[w] + v);
+            atomicAdd(a.counts + key, 1u);
+            atomicOr(a.bitmap + (key >> 5), 1u << (key & 31));
+        }
+    }
+    if (lane == 0 && all_empty) a.allempty[atomicAdd(a.n_allempty, 1u)] = (int32_t)q;
+}
+
+__global__ void join_fill_kernel(const IndexArgs a, const uint32_t *csr_off, uint16_t *csr_q) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= a.n_q) return;
+    for (int w = lane; w < a.W; w += 32) {
+        const int g = w / a.kg, b = w - g * a.kg;
+        const uint32_t v = a.qry[(int64_t)g * a.qstride + q * a.kg + b];
+        if (v == HOPH_EMPTY_VALUE) continue;
+        const uint32_t key = (uint32_t)(a.binbase[w] + v);
+        const uint32_t pos = csr_off[key] + atomicSub(a.counts + key, 1u) - 1u;
+        csr_q[pos] = (uint16_t)q;
+    }
+}
+
+// exclusive scan of n uint32 values in three launches: block sums, scan of
+// the sums, scan inside each block plus its offset
+constexpr int kScanBlock = 1024;
+constexpr int kScanPer = 8;  // items per thread
+constexpr int kScanChunk = kScanBlock * kScanPer;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *tmp, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < (int)(blockDim.x >> 5) ? tmp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+            if (lane >= o) s += y;
+        }
+        tmp[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t excl = x - v + (warp ? tmp[warp - 1] : 0);
+    if (total) *total = tmp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return excl;
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_sums_kernel(const uint32_t *in, int64_t n,
+                                                               uint32_t *sums) {
+    __shared__ uint32_t tmp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    uint32_t s = 0;
+    for (int j = 0; j < kScanPer; ++j) {
+        const int64_t i = base + (int64_t)threadIdx.x * kScanPer + j;
+        if (i < n) s += in[i];
+    }
+    uint32_t tot;
+    block_exclusive_scan(s, tmp, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_top_kernel(uint32_t *sums, int64_t nb) {
+    __shared__ uint32_t tmp[32];
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += kScanBlock) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? sums[i] : 0;
+        uint32_t tot;
+        const uint32_t e = block_exclusive_scan(v, tmp, &tot);
+        if (i < nb) sums[i] = e + carry;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_apply_kernel(const uint32_t *in, int64_t n,
+                                                                const uint32_t *sums,
+                                                                uint32_t *out) {
+    __shared__ uint32_t tmp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+    uint32_t v[kScanPer], s = 0;
+    for (int j = 0; j < kScanPer; ++j) {
+        v[j] = base + j < n ? in[base + j] : 0;
+        s += v[j];
+    }
+    uint32_t run = block_exclusive_scan(s, tmp, nullptr) + sums[blockIdx.x];
+    for (int j = 0; j < kScanPer; ++j) {
+        if (base + j < n) out[base + j] = run;
+        run += v[j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic output order: sort the accepted pairs by (query, row)
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 1024;
+constexpr int kSortSmem = 8192;  // records sorted in shared memory at once
+
+__device__ __forceinline__ unsigned long long pair_key(const hoph_pair &p) {
+    return ((unsigned long long)p.query << 40) | (unsigned long long)p.row;
+}
+
+__device__ void bitonic_smem(ulonglong2 *v, int m) {
+    for (int size = 2; size <= m; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < m / 2; i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const ulonglong2 x = v[lo], y = v[hi];
+                if ((x.x > y.x) == up) {
+                    v[lo] = y;
+                    v[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__device__ int64_t lower_bound_key(const ulonglong2 *a, int64_t n, unsigned long long k) {
+    int64_t l = 0, h = n;
+    while (l < h) {
+        const int64_t m = (l + h) >> 1;
+        if (a[m].x < k) l = m + 1; else h = m;
+    }
+    return l;
+}
+
+__global__ void __launch_bounds__(kSortThreads) sort_pairs_kernel(
+    hoph_pair *out, const unsigned long long *count, int64_t cap, ulonglong2 *bufA,
+    ulonglong2 *bufB, int32_t *status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    ulonglong2 *sv = reinterpret_cast<ulonglong2 *>(smem);
+    const unsigned long long total = *count;
+    if (total > (unsigned long long)cap && threadIdx.x == 0) hoph_flag(status, HOPH_ERR_CAPACITY);
+    const int64_t n = (int64_t)min(total, (unsigned long long)cap);
+    if (n <= 1) return;
+    // sort runs of kSortSmem records in shared memory into bufA
+    for (int64_t base = 0; base < n; base += kSortSmem) {
+        const int cnt = (int)min((long long)kSortSmem, (long long)(n - base));
+        int m = 1;
+        while (m < cnt) m <<= 1;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            if (i < cnt) {
+                const hoph_pair p = out[base + i];
+                sv[i] = make_ulonglong2(pair_key(p),
+                                        ((unsigned long long)p.groups << 16) | p.matches);
+            } else {
+                sv[i] = make_ulonglong2(~0ull, 0ull);
+            }
+        }
+        __syncthreads();
+        bitonic_smem(sv, m);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) bufA[base + i] = sv[i];
+        __syncthreads();
+    }
+    // merge sorted runs (keys are unique: rank = own index + rank in the other run)
+    ulonglong2 *src = bufA, *dst = bufB;
+    for (int64_t run = kSortSmem; run < n; run <<= 1) {
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const int64_t pairbase = (i / (2 * run)) * (2 * run);
+            const int64_t a0 = pairbase, a1 = min(pairbase + run, n);
+            const int64_t b0 = a1, b1 = min(pairbase + 2 * run, n);
+            int64_t pos;
+            if (i < a1)
+                pos = pairbase + (i - a0) + lower_bound_key(src + b0, b1 - b0, src[i].x);
+            else
+                pos = pairbase + (i - b0) + lower_bound_key(src + a0, a1 - a0, src[i].x);
+            dst[pos] = src[i];
+        }
+        __syncthreads();
+        ulonglong2 *t = src;
+        src = dst;
+        dst = t;
+    }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const ulonglong2 r = src[i];
+        hoph_pair p;
+        p.query = (uint32_t)(r.x >> 40);
+        p.row = (int64_t)(r.x & ((1ull << 40) - 1));
+        p.groups = (uint16_t)(r.y >> 16);
+        p.matches = (uint16_t)(r.y & 0xFFFFu);
+        out[i] = p;
+    }
+}
+
+// fold the call's counters into the caller's hoph_stats
+__global__ void stats_fold_kernel(const unsigned long long *st, int64_t pairs, int G, int Gs,
+                                  int64_t first_pass_bytes, int strategy, hoph_stats *out) {
+    if (threadIdx.x != 0 || !out) return;
+    out->entering[0] += pairs;
+    const int64_t acc0 = (int64_t)st[16], cont = (Gs < G) ? (int64_t)st[1] : 0;
+    out->accepted[0] += acc0;
+    out->rejected[0] += pairs - acc0 - cont;
+    for (int g = 1; g < G && Gs < G; ++g) {
+        out->entering[g] += (int64_t)st[g];
+        out->accepted[g] += (int64_t)st[16 + g];
+        out->rejected[g] += (int64_t)st[32 + g];
+    }
+    out->sketch_bytes += first_pass_bytes + (int64_t)st[48];
+    out->join_hits += (int64_t)st[49];
+    out->strategy = strategy;
+}
+
+// ---------------------------------------------------------------------------
+// Per-pair counts (no early exit): warp per pair, lanes over bins
+// ---------------------------------------------------------------------------
+__global__ void pair_counts_kernel(const uint32_t *qry, int64_t qstride, int64_t n_q,
+                                   const uint32_t *coll, int64_t cstride, int64_t n_rows, int kg,
+                                   int G, uint16_t *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = wid; p < n_q * n_rows; p += nw) {
+        const int64_t q = p / n_rows, r = p - q * n_rows;
+        for (int g = 0; g < G; ++g) {
+            int m = 0, both = 0, one = 0;
+            for (int b0 = 0; b0 < kg; b0 += 32) {
+                const int b = b0 + lane;
+                const bool valid = b < kg;
+                const uint32_t qv = valid ? qry[g * qstride + q * kg + b] : 0;
+                const uint32_t rv = valid ? coll[g * cstride + r * kg + b] : 0;
+                const bool eq = qv == HOPH_EMPTY_VALUE, er = rv == HOPH_EMPTY_VALUE;
+                m += __popc(__ballot_sync(0xFFFFFFFFu, valid && !eq && qv == rv));
+                both += __popc(__ballot_sync(0xFFFFFFFFu, valid && eq && er));
+                one += __popc(__ballot_sync(0xFFFFFFFFu, valid && eq != er));
+            }
+            if (lane == 0) {
+                uint16_t *o = out + (p * G + g) * 3;
+                o[0] = (uint16_t)m;
+                o[1] = (uint16_t)both;
+                o[2] = (uint16_t)one;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// First-pass decision table for W scanned bins under `dp` after `l` groups.
+bool build_table(const DecideParams &dp, int W, int l, std::vector<uint16_t> &tab) {
+    tab.assign(2 * (W + 1), 0);
+    for (int K = 0; K <= W; ++K) {
+        int rej = K + 1, acc = K + 1;
+        for (int m = 0; m <= K; ++m) {
+            int32_t M[1] = {m}, Kk[1] = {K};
+            const int d = hoph_decide(dp, l, M, Kk);
+            if (d != HOPH_REJECT && rej == K + 1) rej = m;
+            if (d == HOPH_ACCEPT && acc == K + 1) acc = m;
+        }
+        // check the monotone shape the table relies on
+        for (int m = 0; m <= K; ++m) {
+            int32_t M[1] = {m}, Kk[1] = {K};
+            const int d = hoph_decide(dp, l, M, Kk);
+            const int want = m < rej ? HOPH_REJECT : (m >= acc ? HOPH_ACCEPT : HOPH_CONTINUE);
+            if (d != want) return false;
+        }
+        tab[K] = (uint16_t)rej;
+        tab[W + 1 + K] = (uint16_t)acc;
+    }
+    return true;
+}
+
+struct Bump {
+    unsigned char *base;
+    size_t off = 0;
+    void *take(size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_planes,
+                     int64_t n_queries, const uint32_t *d_coll_planes, int64_t n_rows,
+                     hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
+                     hoph_stats *d_stats, void *stream) {
+    if (!plan || !d_out_count || n_queries < 0 || n_rows < 0 || out_capacity < 0)
+        return HOPH_ERR_PARAM;
+    if (out_capacity > 0 && !d_out) return HOPH_ERR_PARAM;
+    if (n_queries > 65535 || n_rows >= (1ll << 40)) return HOPH_ERR_UNSUPPORTED;
+    const hoph_params &P = plan->P;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // mode -> scanned planes and the rule of the first pass
+    DecideParams dp = plan->dp;
+    int kg = (int)P.k_group, G = (int)plan->G, Gs = 1;
+    if (mode == HOPH_MODE_GOPH || mode == HOPH_MODE_OPH_FULL) {
+        if (P.a != 0) return HOPH_ERR_PARAM;
+    } else if (mode == HOPH_MODE_HOPH) {
+        if (P.a == 0) return HOPH_ERR_PARAM;
+    } else if (mode == HOPH_MODE_MINWISE_FULL) {
+        if (!P.minwise_k) return HOPH_ERR_PARAM;
+    } else {
+        return HOPH_ERR_PARAM;
+    }
+    DecideParams fp = dp;  // rule of the first pass
+    if (mode == HOPH_MODE_OPH_FULL) {
+        Gs = G;
+        fp.mode = HOPH_MODE_GOPH;
+        fp.G = 1;
+        fp.kg = P.k;
+        G = 1;
+    } else if (mode == HOPH_MODE_MINWISE_FULL) {
+        kg = (int)P.minwise_k;
+        G = 1;
+        fp.mode = HOPH_MODE_GOPH;
+        fp.G = 1;
+        fp.kg = P.minwise_k;
+        fp.rule = HOPH_EMPTY_NONE;
+    }
+    const int W = Gs * kg;
+    if (W > kMaxW) return HOPH_ERR_UNSUPPORTED;
+
+    HOPH_CUDA_TRY(cudaMemsetAsync(d_out_count, 0, sizeof(int64_t), s));
+    if (n_queries == 0 || n_rows == 0) return HOPH_OK;
+    if (!d_query_planes || !d_coll_planes) return HOPH_ERR_PARAM;
+
+    if (plan->table_W[mode] != W) {
+        plan->table_ok[mode] = build_table(fp, W, 1, plan->h_table[mode]);
+        plan->table_W[mode] = W;
+        cudaFree(plan->d_table[mode]);
+        plan->d_table[mode] = nullptr;
+        if (plan->table_ok[mode]) {
+            const size_t b = plan->h_table[mode].size() * 2;
+            HOPH_CUDA_TRY(cudaMalloc(&plan->d_table[mode], b));
+            HOPH_CUDA_TRY(cudaMemcpy(plan->d_table[mode], plan->h_table[mode].data(), b,
+                                     cudaMemcpyHostToDevice));
+        }
+    }
+    if (!plan->table_ok[mode]) return HOPH_ERR_UNSUPPORTED;
+    const std::vector<uint16_t> &tab = plan->h_table[mode];
+
+    // strategy: the join needs "no match => reject" for every K >= 1, a
+    // small key space and a rule whose K == 0 pairs are the all-empty ones
+    const uint64_t keys = (mode == HOPH_MODE_MINWISE_FULL) ? ~0ull : plan->lo[W];
+    bool join_ok = mode != HOPH_MODE_MINWISE_FULL && fp.rule != HOPH_EMPTY_EITHER &&
+                   keys < kMaxJoinKeys && n_queries <= 4096;
+    for (int K = 1; K <= W && join_ok; ++K) join_ok = tab[K] >= 1;
+    int strategy = plan->exec.strategy;
+    if (strategy == 1 && !join_ok) return HOPH_ERR_UNSUPPORTED;
+    if (strategy < 0) strategy = (join_ok && n_queries >= 16) ? 1 : 0;
+
+    // launch shape
+    const int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 8;
+    int R = plan->exec.tile_rows > 0 ? plan->exec.tile_rows : 0;
+    if (R == 0) {
+        R = (int)std::max<int64_t>(1, std::min<int64_t>(256, 8192 / (W * 4)));
+        if (R >= 8) R &= ~7;
+    }
+    const int mask_words = (W + 31) / 32;
+    const bool tma_ok = (kg % 4 == 0) && kg <= 256 && Gs <= 256 &&
+                        ((uintptr_t)d_coll_planes & 15) == 0 && get_encode_fn() != nullptr;
+    const int stages = tma_ok ? (plan->exec.stages > 0 ? plan->exec.stages : 4) : 1;
+
+    // scratch
+    Bump bump{nullptr};
+    const size_t st_b = kStatWords * 8;
+    size_t need = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        bump.off = 0;
+        bump.take(st_b);
+        if (strategy == 1) {
+            bump.take((keys + 1) * 4);                       // counts
+            bump.take((keys + 1) * 4);                       // csr_off
+            bump.take(((keys + 1 + kScanChunk - 1) / kScanChunk) * 4);  // block sums
+            bump.take((keys / 32 + 1) * 4);                  // bitmap
+            bump.take((size_t)n_queries * W * 2);            // csr_q
+            bump.take((size_t)n_queries * mask_words * 4);   // q_emask
+            bump.take((size_t)n_queries * 4 + 4);            // allempty + count
+        }
+        bump.take((size_t)std::max<int64_t>(out_capacity, 1) * 16);  // sort A
+        bump.take((size_t)std::max<int64_t>(out_capacity, 1) * 16);  // sort B
+        if (pass == 0) {
+            need = bump.off;
+            unsigned char *base = (unsigned char *)hoph_scratch(plan, need);
+            if (!base) return HOPH_ERR_NOMEM;
+            bump.base = base;
+        }
+    }
+    bump.off = 0;
+    unsigned long long *st = (unsigned long long *)bump.take(st_b);
+    const uint16_t *d_thr = plan->d_table[mode];
+    uint32_t *counts = nullptr, *csr_off = nullptr, *sums = nullptr, *bitmap = nullptr,
+             *q_emask = nullptr, *n_allempty = nullptr;
+    uint16_t *csr_q = nullptr;
+    int32_t *allempty = nullptr;
+    if (strategy == 1) {
+        counts = (uint32_t *)bump.take((keys + 1) * 4);
+        csr_off = (uint32_t *)bump.take((keys + 1) * 4);
+        sums = (uint32_t *)bump.take(((keys + 1 + kScanChunk - 1) / kScanChunk) * 4);
+        bitmap = (uint32_t *)bump.take((keys / 32 + 1) * 4);
+        csr_q = (uint16_t *)bump.take((size_t)n_queries * W * 2);
+        q_emask = (uint32_t *)bump.take((size_t)n_queries * mask_words * 4);
+        allempty = (int32_t *)bump.take((size_t)n_queries * 4 + 4);
+        n_allempty = (uint32_t *)(allempty + n_queries);
+    }
+    ulonglong2 *sortA = (ulonglong2 *)bump.take((size_t)std::max<int64_t>(out_capacity, 1) * 16);
+    ulonglong2 *sortB = (ulonglong2 *)bump.take((size_t)std::max<int64_t>(out_capacity, 1) * 16);
+
+    HOPH_CUDA_TRY(cudaMemsetAsync(st, 0, st_b, s));
+
+    const int64_t qstride = n_queries * (int64_t)kg;
+    const int64_t cstride = n_rows * (int64_t)kg;
+    hoph_timing_mark(plan, 0, s);
+    if (strategy == 1) {
+        IndexArgs ia;
+        ia.qry = d_query_planes;
+        ia.qstride = qstride;
+        ia.n_q = (int32_t)n_queries;
+        ia.kg = kg;
+        ia.W = W;
+        ia.mask_words = mask_words;
+        ia.binbase = plan->d_lo;
+        ia.counts = counts;
+        ia.bitmap = bitmap;
+        ia.q_emask = q_emask;
+        ia.allempty = allempty;
+        ia.n_allempty = n_allempty;
+        HOPH_CUDA_TRY(cudaMemsetAsync(counts, 0, (keys + 1) * 4, s));
+        HOPH_CUDA_TRY(cudaMemsetAsync(bitmap, 0, (keys / 32 + 1) * 4, s));
+        HOPH_CUDA_TRY(cudaMemsetAsync(n_allempty, 0, 4, s));
+        const unsigned qb = (unsigned)((n_queries * 32 + 255) / 256);
+        join_count_kernel<<<qb, 256, 0, s>>>(ia);
+        const int64_t n_scan = (int64_t)keys + 1;
+        const int64_t nb = (n_scan + kScanChunk - 1) / kScanChunk;
+        scan_sums_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, n_scan, sums);
+        scan_top_kernel<<<1, kScanBlock, 0, s>>>(sums, nb);
+        scan_apply_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, n_scan, sums, csr_off);
+        join_fill_kernel<<<qb, 256, 0, s>>>(ia, csr_off, csr_q);
+        HOPH_CUDA_TRY(cudaGetLastError());
+        plan->launches += 5;
+    }
+
+    ScanArgs a;
+    a.coll = d_coll_planes;
+    a.cstride = cstride;
+    a.qry = d_query_planes;
+    a.qstride = qstride;
+    a.n_rows = n_rows;
+    a.n_q = (int32_t)n_queries;
+    a.kg = kg;
+    a.Gs = Gs;
+    a.W = W;
+    a.G = G;
+    a.rule = fp.rule;
+    a.join = strategy;
+    a.use_tma = tma_ok ? 1 : 0;
+    a.tile_rows = R;
+    a.stages = stages;
+    a.n_cons = n_cons;
+    a.n_tiles = (n_rows + R - 1) / R;
+    a.stage_bytes = (uint32_t)Gs * R * kg * 4;
+    a.stage_stride = align_up(a.stage_bytes, 128);
+    a.thr = d_thr;
+    a.dp = dp;
+    a.bitmap = bitmap;
+    a.bitmap_words = (uint32_t)(strategy == 1 ? keys / 32 + 1 : 0);
+    a.bitmap_in_smem = a.bitmap_words * 4 <= kSmemBitmapBytes;
+    a.csr_off = csr_off;
+    a.csr_q = csr_q;
+    a.binbase = plan->d_lo;
+    a.q_emask = q_emask;
+    a.mask_words = mask_words;
+    a.allempty = allempty;
+    a.n_allempty = n_allempty;
+    a.out = d_out;
+    a.cap = out_capacity;
+    a.out_count = reinterpret_cast<unsigned long long *>(d_out_count);
+    a.stat = st;
+    a.status = plan->d_status;
+
+    CUtensorMap map;
+    memset(&map, 0, sizeof map);
+    if (tma_ok) {
+        const cuuint64_t gdim[3] = {(cuuint64_t)kg, (cuuint64_t)n_rows, (cuuint64_t)Gs};
+        const cuuint64_t gstride[2] = {(cuuint64_t)kg * 4, (cuuint64_t)cstride * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)kg, (cuuint32_t)R, (cuuint32_t)Gs};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        const CUresult r = get_encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
+                                           (void *)d_coll_planes, gdim, gstride, box, estr,
+                                           CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                           CU_TENSOR_MAP_SWIZZLE_NONE,
+                                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            a.use_tma = 0;
+            a.stages = 1;
+        }
+    }
+    const SmemLayout L = smem_layout(a);
+    if (L.total > 227 * 1024) return HOPH_ERR_UNSUPPORTED;
+    HOPH_CUDA_TRY(
+        cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    const int threads = 32 * (n_cons + 1);
+    int per_sm = 0;
+    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, threads, L.total));
+    if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
+    if (plan->exec.ctas_per_sm > 0) per_sm = std::min(per_sm, plan->exec.ctas_per_sm);
+    const int64_t grid = std::min<int64_t>(a.n_tiles, (int64_t)plan->num_sms * per_sm);
+    hoph_timing_mark(plan, 1, s);
+    scan_kernel<<<(unsigned)grid, threads, L.total, s>>>(a, map);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    hoph_timing_mark(plan, 2, s);
+
+    HOPH_CUDA_TRY(cudaFuncSetAttribute(sort_pairs_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSortSmem * 16));
+    sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(
+        d_out, a.out_count, out_capacity, sortA, sortB, plan->d_status);
+    const int64_t fp_bytes = n_rows * (int64_t)W * 4 + n_queries * (int64_t)W * 4;
+    stats_fold_kernel<<<1, 32, 0, s>>>(st, n_queries * n_rows, G, Gs, fp_bytes, strategy, d_stats);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    hoph_timing_mark(plan, 3, s);
+    plan->launches += 3;
+    return HOPH_OK;
+}
+
+int hoph_pair_counts(hoph_plan *plan, const uint32_t *d_query_planes, int64_t n_queries,
+                     const uint32_t *d_coll_planes, int64_t n_rows, uint16_t *d_counts,
+                     void *stream) {
+    if (!plan || n_queries < 0 || n_rows < 0) return HOPH_ERR_PARAM;
+    if (n_queries == 0 || n_rows == 0) return HOPH_OK;
+    if (!d_query_planes || !d_coll_planes || !d_counts) return HOPH_ERR_PARAM;
+    const int kg = (int)plan->P.k_group, G = (int)plan->G;
+    const int64_t pairs = n_queries * n_rows;
+    const int64_t blocks = std::min<int64_t>((pairs * 32 + 255) / 256, (int64_t)plan->num_sms * 32);
+    pair_counts_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+        d_query_planes, n_queries * kg, n_queries, d_coll_planes, n_rows * kg, n_rows, kg, G,
+        d_counts);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    return HOPH_OK;
+}
+
+}  // extern "C"

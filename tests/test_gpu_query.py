@@ -1,0 +1,217 @@
+"""GPU comparison (hoph_query_batch, hoph_pair_counts) against the CPU
+oracle: accepted pairs, groups compared, matched bins and per-group
+decision counts must be identical."""
+import numpy as np
+import pytest
+
+from gpu_helpers import (device, oracle_tuples, pairs_tuples, planes_to_rows, rows_to_planes,
+                         to_dev, torch)  # noqa: F401
+from oracle import oracle_c as oc
+from paper_1805_11254_gb300 import hoph, synth
+
+pytestmark = pytest.mark.gpu
+
+T = (7, 10)
+EPS = 1e-4
+
+
+@pytest.fixture(scope="module")
+def small():
+    return synth.small_parity_workload()
+
+
+def _sketch_both(plan, w, dev):
+    c = plan.sketch(to_dev(w["ids"], dev), to_dev(w["off"], dev), len(w["off"]) - 1)
+    q = plan.sketch(to_dev(w["q_ids"], dev), to_dev(w["q_off"], dev), len(w["q_off"]) - 1)
+    plan.check()
+    return q, c
+
+
+def _oracle_query(mode, q_rows, c_rows, kg, z, eps=EPS, rule="both", thr=T):
+    return oc.query(mode, q_rows, c_rows, kg, thr[0], thr[1], eps, rule=rule,
+                    z=np.asarray(z, dtype=np.uint64))
+
+
+def _compare(plan, mode, q, c, nq, nr, want, strategy, G):
+    """Run one strategy and compare with the oracle.  The value join is only
+    offered when a pair without any match is rejected for every possible
+    denominator; otherwise forcing it must fail with UNSUPPORTED."""
+    plan.set_exec(strategy=strategy)
+    try:
+        pairs, n, st = plan.query(mode, q, nq, c, nr, capacity=1 << 16, stats=True)
+    except hoph.HophError as e:
+        assert strategy == 1 and e.code == hoph.HOPH_ERR_UNSUPPORTED
+        return None
+    assert n == want["count"]
+    assert pairs_tuples(pairs) == oracle_tuples(want)
+    hist = want["hist"]  # [groups compared][decision]
+    for g in range(G):
+        assert st.accepted[g] == hist[g + 1][1], ("accepted", g)
+        assert st.rejected[g] == hist[g + 1][2], ("rejected", g)
+    assert st.entering[0] == nq * nr
+    return st
+
+
+@pytest.mark.parametrize("strategy", [0, 1, -1])
+@pytest.mark.parametrize("mode,ab,kg", [("goph", (0, 0), 32), ("hoph", (1, 1), 32),
+                                        ("oph_full", (0, 0), 32), ("hoph", (1, 2), 32)])
+def test_small_workload_parity(small, mode, ab, kg, strategy):
+    """N = 5,000 sets over D = 2^16, k = 128, 50 planted queries, T = 0.7."""
+    dev = device()
+    D, k = small["D"], 128
+    with hoph.Plan(D, k, kg, *ab, seed=1, thr=T, epsilon=EPS) as plan:
+        q, c = _sketch_both(plan, small, dev)
+        nq, nr = q.shape[1], c.shape[1]
+        z = [plan.info.group_size[g] for g in range(plan.G)]
+        want = _oracle_query(mode, planes_to_rows(q), planes_to_rows(c), kg, z)
+        assert want["count"] > 0
+        G = plan.G if mode in ("goph", "hoph") else 1
+        _compare(plan, mode, q, c, nq, nr, want, strategy, G)
+
+
+def test_minwise_query_parity(small):
+    dev = device()
+    D, mk = small["D"], 128
+    with hoph.Plan(D, 128, 32, minwise_k=mk, seed=1, thr=T) as plan:
+        c = plan.minwise(to_dev(small["ids"], dev), to_dev(small["off"], dev),
+                         len(small["off"]) - 1)
+        q = plan.minwise(to_dev(small["q_ids"], dev), to_dev(small["q_off"], dev),
+                         len(small["q_off"]) - 1)
+        plan.check()
+        want = oc.query("minwise_full", q.cpu().numpy().view(np.uint32),
+                        c.cpu().numpy().view(np.uint32), mk, T[0], T[1], EPS)
+        pairs, n, _ = plan.query("minwise_full", q, q.shape[0], c, c.shape[0])
+        assert n == want["count"] > 0
+        assert pairs_tuples(pairs) == oracle_tuples(want)
+
+
+def _mixed_sets(rng, n, D, empty_every=7):
+    """Sets with many empty bins: tiny sets, empty sets, near duplicates."""
+    base = []
+    for i in range(n):
+        s = 0 if i % empty_every == 0 else int(rng.integers(1, 40))
+        base.append(rng.choice(D, s, replace=False).astype(np.uint32))
+    out = list(base)
+    for b in base[: n // 2]:
+        if len(b) > 2:
+            keep = b[: max(1, len(b) * 4 // 5)]
+            out.append(np.concatenate([keep, rng.choice(D, 2).astype(np.uint32)]))
+    return out
+
+
+@pytest.mark.parametrize("rule", ["both", "either", "none"])
+@pytest.mark.parametrize("eps", [0.0, 1e-3, 1.0])
+@pytest.mark.parametrize("mode,ab", [("goph", (0, 0)), ("hoph", (1, 1)), ("oph_full", (0, 0))])
+def test_rules_eps_and_empty_bins(mode, ab, rule, eps):
+    dev = device()
+    rng = np.random.default_rng(hash((mode, rule, eps)) & 0xFFFF)
+    D, k, kg = 4096, 64, 16
+    sets = _mixed_sets(rng, 120, D)
+    ids, off = synth.pack_sets(sets)
+    thr = (3, 5)
+    with hoph.Plan(D, k, kg, *ab, seed=9, thr=thr, epsilon=eps, empty_rule=rule) as plan:
+        d_ids, d_off = to_dev(ids, dev), to_dev(off, dev)
+        c = plan.sketch(d_ids, d_off, len(sets))
+        plan.check()
+        rows = planes_to_rows(c)
+        z = [plan.info.group_size[g] for g in range(plan.G)]
+        want = _oracle_query(mode, rows, rows, kg, z, eps=eps, rule=rule, thr=thr)
+        G = plan.G if mode != "oph_full" else 1
+        for strategy in (0, -1, 1):
+            _compare(plan, mode, c, c, len(sets), len(sets), want, strategy, G)
+
+
+@pytest.mark.parametrize("n_rows", [1, 2, 31, 33, 257, 1001])
+@pytest.mark.parametrize("n_q", [1, 3, 40])
+def test_ragged_tiles_and_batch_sizes(small, n_rows, n_q):
+    dev = device()
+    D, k, kg = small["D"], 128, 32
+    with hoph.Plan(D, k, kg, 1, 1, seed=1, thr=T) as plan:
+        q, c = _sketch_both(plan, small, dev)
+        # planted rows first so there are accepted pairs in range
+        src = small["src"][:n_q]
+        rows = planes_to_rows(c)
+        sel = np.concatenate([src, np.arange(n_rows)])[:n_rows]
+        c_rows = rows[sel]
+        q_rows = planes_to_rows(q)[:n_q]
+        z = [plan.info.group_size[g] for g in range(plan.G)]
+        want = _oracle_query("hoph", q_rows, c_rows, kg, z)
+        for strategy in (0, 1):
+            _compare(plan, "hoph", rows_to_planes(q_rows, kg, dev), rows_to_planes(c_rows, kg, dev),
+                     n_q, n_rows, want, strategy, plan.G)
+
+
+def test_empty_inputs_and_capacity_overflow(small):
+    dev = device()
+    D, k, kg = small["D"], 128, 32
+    with hoph.Plan(D, k, kg, seed=1, thr=(1, 100), epsilon=EPS) as plan:
+        q, c = _sketch_both(plan, small, dev)
+        pairs, n, _ = plan.query("goph", q, 0, c, c.shape[1])
+        assert n == 0
+        pairs, n, _ = plan.query("goph", q, q.shape[1], c, 0)
+        assert n == 0
+        # T = 0.01 accepts nearly everything: more pairs than the buffer holds
+        out = torch.empty((4, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        rows, qrows = planes_to_rows(c)[:100], planes_to_rows(q)[:10]
+        hoph.hoph_query_batch(plan.handle, "goph", rows_to_planes(qrows, kg, dev), 10,
+                              rows_to_planes(rows, kg, dev), 100, out, 4, cnt)
+        assert hoph.hoph_sync_status(plan.handle) == hoph.HOPH_ERR_CAPACITY
+        want = oc.query("goph", qrows, rows, kg, 1, 100, EPS)
+        assert int(cnt.item()) == want["count"] > 4
+        got = set(pairs_tuples(out.cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)))
+        assert got <= set(oracle_tuples(want))  # the 4 kept pairs are genuine
+
+
+def test_goph_example_1_sketches_on_gpu():
+    """Sec. 3.3 Example 1 (k'=100, n=10, T=0.6, eps=1e-4): matches 65, 5, 10,
+    10 reject the pair after the fourth group; an identical pair is accepted
+    when the remaining requirement falls into the lower tail."""
+    from fractions import Fraction
+    from oracle import hoph_ref as hr
+    dev = device()
+    kg, n = 100, 10
+    s = np.zeros((1, kg * n), dtype=np.uint32)
+    t = np.ones((2, kg * n), dtype=np.uint32)
+    for g, m in enumerate([65, 5, 10, 10]):
+        t[0, g * kg:g * kg + m] = 0
+    t[1, :] = 0
+    want0 = hr.goph_compare(s[0].tolist(), t[0].tolist(), kg, Fraction(3, 5), 1e-4)
+    want1 = hr.goph_compare(s[0].tolist(), t[1].tolist(), kg, Fraction(3, 5), 1e-4)
+    assert want0 == (hr.REJECT, 4, 90)
+    assert want1[0] == hr.ACCEPT
+    with hoph.Plan(100000, kg * n, kg, seed=1, thr=(3, 5), epsilon=1e-4) as plan:
+        for strategy in (0, -1):
+            plan.set_exec(strategy=strategy)
+            pairs, cnt, st = plan.query("goph", rows_to_planes(s, kg, dev), 1,
+                                        rows_to_planes(t, kg, dev), 2, stats=True)
+            assert pairs_tuples(pairs) == [(0, 1, want1[1], want1[2])]
+            assert st.rejected[3] == 1 and st.entering[3] == 2
+
+
+def test_pair_counts_parity(small):
+    dev = device()
+    D, k, kg = small["D"], 128, 32
+    with hoph.Plan(D, k, kg, 1, 1, seed=1) as plan:
+        q, c = _sketch_both(plan, small, dev)
+        nr = 700
+        cr = planes_to_rows(c)[:nr]
+        qr = planes_to_rows(q)
+        out = torch.empty((qr.shape[0], nr, plan.G, 3), dtype=torch.int16, device=dev)
+        hoph.hoph_pair_counts(plan.handle, rows_to_planes(qr, kg, dev), qr.shape[0],
+                              rows_to_planes(cr, kg, dev), nr, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint16)
+        assert np.array_equal(got, oc.pair_counts(qr, cr, kg))
+
+
+def test_identical_sets_always_accepted(small):
+    dev = device()
+    D, k, kg = small["D"], 128, 32
+    with hoph.Plan(D, k, kg, 1, 1, seed=1, thr=(1, 1), epsilon=EPS) as plan:
+        q, c = _sketch_both(plan, small, dev)
+        rows = planes_to_rows(c)[:300]
+        d = rows_to_planes(rows, kg, dev)
+        pairs, n, _ = plan.query("hoph", d, 300, d, 300)
+        got = {(int(p["query"]), int(p["row"])) for p in pairs}
+        assert {(i, i) for i in range(300)} <= got

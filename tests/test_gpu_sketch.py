@@ -1,0 +1,156 @@
+"""GPU sketches (oph_build_sketches, minwise_build_sketches, hoph_synth_ids)
+against the CPU oracle, bit for bit, through the C ABI."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import device, planes_to_rows, to_dev, torch  # noqa: F401
+from oracle import oracle_c as oc
+from paper_1805_11254_gb300 import hoph, synth
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gpu_sketch(plan, ids, off, dev):
+    d_ids = to_dev(ids if len(ids) else np.zeros(1, np.uint32), dev)
+    d_off = to_dev(off, dev)
+    planes = plan.sketch(d_ids, d_off, len(off) - 1)
+    plan.check()
+    return planes_to_rows(planes)
+
+
+@pytest.fixture(scope="module")
+def small():
+    return synth.small_parity_workload()
+
+
+@pytest.mark.parametrize("ab,kg", [((0, 0), 32), ((1, 1), 32), ((1, 2), 16), ((2, 1), 64)])
+def test_oph_hoph_sketch_parity_small_workload(small, ab, kg):
+    dev = device()
+    D, k = small["D"], 128
+    with hoph.Plan(D, k, kg, *ab, seed=1) as plan:
+        got = _gpu_sketch(plan, small["ids"], small["off"], dev)
+    perm = oc.permutation(D, 1)
+    want = oc.sketch(small["ids"], small["off"], oc.layout(D, k, kg, *ab), perm=perm)
+    assert np.array_equal(got, want)
+    qgot = None
+    with hoph.Plan(D, k, kg, *ab, seed=1) as plan:
+        qgot = _gpu_sketch(plan, small["q_ids"], small["q_off"], dev)
+    qwant = oc.sketch(small["q_ids"], small["q_off"], oc.layout(D, k, kg, *ab), perm=perm)
+    assert np.array_equal(qgot, qwant)
+
+
+def test_ragged_sizes_unaligned_offsets_and_empty_sets():
+    dev = device()
+    D, k, kg = 1 << 12, 64, 16
+    rng = np.random.default_rng(3)
+    sizes = [0, 1, 2, 3, 4, 5, 7, 31, 32, 33, 127, 128, 129, 130, 1000, 0, 4095, 20000, 9]
+    sets = [rng.integers(0, D, s).astype(np.uint32) for s in sizes]  # duplicates allowed
+    ids, off = synth.pack_sets(sets)
+    perm = oc.permutation(D, 5)
+    for ab in ((0, 0), (1, 1)):
+        with hoph.Plan(D, k, kg, *ab, seed=5) as plan:
+            got = _gpu_sketch(plan, ids, off, dev)
+        want = oc.sketch(ids, off, oc.layout(D, k, kg, *ab), perm=perm)
+        assert np.array_equal(got, want)
+        assert (got[0] == hoph.HOPH_EMPTY_VALUE).all()
+
+
+def test_size_sorted_work_list_path():
+    """Enough sets to switch on the size-bucket work list (> 2 per resident warp)."""
+    dev = device()
+    D, k, kg = 1 << 20, 256, 64
+    n = 60000
+    sizes = synth.lognormal_sizes(n, 60, 1.0, 1, 3000, 21)
+    off = synth.offsets_from_sizes(sizes)
+    cdf = synth.zipf_cdf(D, 1.1)
+    ids = synth.counter_zipf_ids(7, 0, int(off[-1]), cdf)
+    perm = oc.permutation(D, 1)
+    with hoph.Plan(D, k, kg, 1, 2, seed=1) as plan:
+        got = _gpu_sketch(plan, ids, off, dev)
+    want = oc.sketch(ids, off, oc.layout(D, k, kg, 1, 2), perm=perm)
+    assert np.array_equal(got, want)
+
+
+def test_id_out_of_range_is_flagged_and_skipped():
+    dev = device()
+    D, k, kg = 1000, 8, 8
+    ids = np.asarray([5, 999, 1000, 77, 123456], dtype=np.uint32)
+    off = np.asarray([0, 2, 5], dtype=np.int64)
+    with hoph.Plan(D, k, kg, seed=2) as plan:
+        planes = plan.sketch(to_dev(ids, dev), to_dev(off, dev), 2)
+        assert hoph.hoph_sync_status(plan.handle) == hoph.HOPH_ERR_ID_RANGE
+        assert hoph.hoph_sync_status(plan.handle) == hoph.HOPH_OK  # cleared
+    got = planes_to_rows(planes)
+    ok_ids = np.asarray([5, 999, 77], dtype=np.uint32)
+    want = oc.sketch(ok_ids, np.asarray([0, 2, 3]), oc.layout(D, k, kg), perm=oc.permutation(D, 2))
+    assert np.array_equal(got, want)
+
+
+def test_hash_permutation_sketch_parity():
+    """D = 2^32 through psi(x) = ((a x + b) mod 2^61-1) >> 29, (2:1)HOPH, k = 512."""
+    dev = device()
+    D, k, kg = 1 << 32, 512, 128
+    rng = np.random.default_rng(4)
+    sizes = [0, 1, 1000, 2345, 50000, 7, 100000]
+    sets = [rng.integers(0, 1 << 32, s, dtype=np.uint64).astype(np.uint32) for s in sizes]
+    ids, off = synth.pack_sets(sets)
+    with hoph.Plan(D, k, kg, 2, 1, perm_kind=hoph.HOPH_PERM_HASH61, seed=1) as plan:
+        got = _gpu_sketch(plan, ids, off, dev)
+    want = oc.sketch(ids, off, oc.layout(D, k, kg, 2, 1), D=D, hash_ab=oc.hash_params(1))
+    assert np.array_equal(got, want)
+
+
+def test_minwise_parity():
+    dev = device()
+    D, mk = 1 << 12, 64
+    rng = np.random.default_rng(6)
+    sets = [rng.choice(D, s, replace=False).astype(np.uint32) for s in (0, 1, 40, 300, 33)]
+    ids, off = synth.pack_sets(sets)
+    with hoph.Plan(D, 64, 64, minwise_k=mk, seed=3) as plan:
+        got = plan.minwise(to_dev(ids, dev), to_dev(off, dev), len(sets))
+        plan.check()
+    perms = np.stack([oc.permutation(D, 3 + t) for t in range(mk)])
+    want = oc.minwise(ids, off, perms)
+    assert np.array_equal(got.cpu().numpy().view(np.uint32), want)
+
+
+def test_paper_examples_on_gpu():
+    """Sec. 3.2 and Sec. 4.1 worked examples with psi = identity."""
+    dev = device()
+    g = json.load(open(os.path.join(GOLD, "worked_examples.json")))
+    sets = g["oph_example"]["sets"]
+    ids, off = synth.pack_sets([np.asarray(s, dtype=np.uint32) for s in sets])
+    ident = np.arange(16, dtype=np.uint32)
+    E = hoph.HOPH_EMPTY_VALUE
+    with hoph.Plan(16, 4, 4, host_perm=ident) as plan:
+        got = _gpu_sketch(plan, ids, off, dev)
+    want = [[E if v is None else v for v in s] for s in g["oph_example"]["sketches"]]
+    assert got.tolist() == want
+    with hoph.Plan(16, 6, 2, 1, 1, host_perm=ident) as plan:
+        got = _gpu_sketch(plan, ids, off, dev)
+    printed = g["hoph_example"]["sketches_printed"]
+    for row, p in zip(got.tolist(), printed):
+        flat = [E if v is None else v for grp in p for v in grp]
+        assert row == flat
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_synth_ids_match_host_twin(kind):
+    dev = device()
+    n, first, seed = 100003, 12345, 99
+    D = 1 << 20
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    if kind == 0:
+        hoph.hoph_synth_ids(seed, first, n, D, 0, None, 0, out)
+        want = synth.counter_ids(seed, first, n, D)
+    else:
+        cdf = synth.zipf_cdf(D, 1.1)
+        d_cdf = torch.from_numpy(cdf).to(dev)
+        hoph.hoph_synth_ids(seed, first, n, D, 1, d_cdf, len(cdf), out)
+        want = synth.counter_zipf_ids(seed, first, n, cdf)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), want)
