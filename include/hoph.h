@@ -40,6 +40,7 @@ extern "C" {
 #define HOPH_ERR_CUDA (-5)        /* a CUDA runtime call failed              */
 #define HOPH_ERR_NOMEM (-6)       /* host or device allocation failed        */
 #define HOPH_ERR_UNSUPPORTED (-7) /* valid parameters this build cannot run  */
+#define HOPH_ERR_TOO_LARGE (-8)   /* input exceeds a fixed-size scratch area  */
 
 /* ---- enumerations ------------------------------------------------------ */
 /* comparison modes of hoph_query_batch */
@@ -206,6 +207,29 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
                      int64_t n_queries, const uint32_t *d_coll_planes, int64_t n_rows,
                      hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
                      hoph_stats *d_stats, void *stream);
+
+/*
+ * oph_build_sketches without any device allocation.  The paper has no
+ * counterpart: this serves callers that may not allocate device memory
+ * during the call, such as a serving loop whose device memory is owned by
+ * its own pool allocator, or a latency-critical path that cannot take the
+ * device-wide synchronisation a cudaMalloc / cudaFree may cause.
+ * Same arguments, output and error behaviour as oph_build_sketches (and
+ * bit-identical sketches); the plan must already exist.
+ *   - n_sets is limited to 262,144 per call; larger inputs return
+ *     HOPH_ERR_TOO_LARGE before anything is enqueued.
+ *   - The size-sorted work list lives in a fixed ~1 MiB device array inside
+ *     the library, present on every GPU that loads it until the process
+ *     exits.  The first call on each device looks up that array's device
+ *     address (cudaGetSymbolAddress, with the device current); make that
+ *     first call before any stream capture.
+ *   - Every call on a device shares the one array: calls whose work overlaps
+ *     on the GPU (other streams, other host threads) race and corrupt each
+ *     other's work list.  Order such calls on one stream.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+int oph_build_sketches_static(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
+                              int64_t n_sets, uint32_t *d_planes, void *stream);
 
 /*
  * Per-pair, per-group bin counts (Eq. 2-5) of every (query, row) pair with

@@ -394,6 +394,7 @@ const char *hoph_status_string(int status) {
         case HOPH_ERR_CUDA: return "a CUDA runtime call failed";
         case HOPH_ERR_NOMEM: return "allocation failed";
         case HOPH_ERR_UNSUPPORTED: return "parameters not supported by this build";
+        case HOPH_ERR_TOO_LARGE: return "input larger than the fixed scratch of this entry point";
         default: return "unknown status";
     }
 }

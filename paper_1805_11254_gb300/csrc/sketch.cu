@@ -13,6 +13,9 @@
 //    owning the minima of permutations t, t+32, ...; the k permuted values
 //    of an ID are contiguous ([D][k] table) so each gather is coalesced.
 //  * hoph_synth_ids: counter-based synthetic IDs (benchmark inputs).
+#include <algorithm>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace {
@@ -341,3 +344,109 @@ int hoph_synth_ids(uint64_t seed, int64_t first, int64_t n_ids, uint64_t D, uint
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// oph_build_sketches_static: the sketch kernel above with its size-sorted
+// work list held in a fixed device array, for callers that must not allocate
+// device memory while they sketch (a serving loop running on a fixed memory
+// budget owned by its own pool allocator, or a latency-critical path that
+// cannot afford the device-wide synchronisation a cudaMalloc / cudaFree may
+// bring).  oph_build_sketches itself grows plan scratch on demand.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kStaticMaxSets = 1 << 18;  // sets per call (262,144)
+constexpr size_t kStaticWords = 3 * kBuckets + (size_t)kStaticMaxSets;
+
+// Bucket histogram, bucket bases, bucket cursors, then the set order: about
+// 1 MiB.  One copy per GPU that loads the library, kept until the process
+// exits, shared by every call on that GPU.
+static __device__ __align__(256) uint32_t g_static_worklist[kStaticWords];
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+uint32_t *g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_worklist on the current device.  The symbol
+// name is only a host-side handle; the first call on each device looks the
+// address up with cudaGetSymbolAddress (with that device current) and caches
+// it.
+int static_worklist(uint32_t **out) {
+    int dev = 0;
+    HOPH_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return HOPH_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_worklist);
+        if (e != cudaSuccess || !p) return hoph_cuda_fail(e);
+        g_static_addr[dev] = static_cast<uint32_t *>(p);
+    }
+    *out = g_static_addr[dev];
+    return HOPH_OK;
+}
+
+}  // namespace
+
+extern "C" int oph_build_sketches_static(hoph_plan *plan, const uint32_t *d_ids,
+                                         const int64_t *d_offsets, int64_t n_sets,
+                                         uint32_t *d_planes, void *stream) {
+    if (!plan || n_sets < 0 || (n_sets > 0 && (!d_offsets || !d_planes))) return HOPH_ERR_PARAM;
+    if (n_sets > kStaticMaxSets) return HOPH_ERR_TOO_LARGE;
+    if (n_sets == 0) return HOPH_OK;
+    uint32_t *scr = nullptr;
+    const int rc = static_worklist(&scr);
+    if (rc != HOPH_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const hoph_params &P = plan->P;
+    SketchArgs a;
+    a.ids = d_ids;
+    a.off = d_offsets;
+    a.n_sets = n_sets;
+    a.planes = d_planes;
+    a.plane_stride = n_sets * (int64_t)P.k_group;
+    a.k = P.k;
+    a.kg = P.k_group;
+    a.key = plan->d_key;
+    a.key_bits = plan->key_bits;
+    a.D = P.universe_D;
+    a.lo = plan->d_lo;
+    a.ha = plan->hash_a;
+    a.hb = plan->hash_b;
+    a.status = plan->d_status;
+    // the array keeps the previous call's contents: the histogram and the
+    // cursors must start at zero (the bases and the order are overwritten)
+    uint32_t *hist = scr, *base = hist + kBuckets, *cursor = base + kBuckets;
+    int32_t *order = reinterpret_cast<int32_t *>(cursor + kBuckets);
+    HOPH_CUDA_TRY(cudaMemsetAsync(hist, 0, kBuckets * sizeof(uint32_t), s));
+    HOPH_CUDA_TRY(cudaMemsetAsync(cursor, 0, kBuckets * sizeof(uint32_t), s));
+    const int g = plan->num_sms * 4;
+    bucket_hist_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, hist);
+    bucket_base_kernel<<<1, 32, 0, s>>>(hist, base);
+    bucket_scatter_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, base, cursor, order);
+    a.order = order;
+
+    const bool hash = P.perm_kind == HOPH_PERM_HASH61;
+    const size_t smem = (hash ? (P.k + 1) * 8 : 0) + (size_t)kSketchWarps * P.k * 4;
+    int per_sm = 0;
+    if (hash) {
+        HOPH_CUDA_TRY(cudaFuncSetAttribute(oph_sketch_kernel<true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oph_sketch_kernel<true>,
+                                                                    kSketchThreads, smem));
+    } else {
+        HOPH_CUDA_TRY(cudaFuncSetAttribute(oph_sketch_kernel<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, oph_sketch_kernel<false>, kSketchThreads, smem));
+    }
+    if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
+    const int64_t blocks = std::min<int64_t>((n_sets + kSketchWarps - 1) / kSketchWarps,
+                                             (int64_t)grid_for(plan, per_sm));
+    if (hash)
+        oph_sketch_kernel<true><<<(unsigned)blocks, kSketchThreads, smem, s>>>(a);
+    else
+        oph_sketch_kernel<false><<<(unsigned)blocks, kSketchThreads, smem, s>>>(a);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    return HOPH_OK;
+}

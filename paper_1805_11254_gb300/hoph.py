@@ -25,6 +25,7 @@ HOPH_ERR_TIMEOUT = -4
 HOPH_ERR_CUDA = -5
 HOPH_ERR_NOMEM = -6
 HOPH_ERR_UNSUPPORTED = -7
+HOPH_ERR_TOO_LARGE = -8
 
 HOPH_MODE_OPH_FULL = 0
 HOPH_MODE_GOPH = 1
@@ -94,7 +95,7 @@ _EXPORTS = ["hoph_plan_create", "hoph_plan_create_with_perm", "hoph_plan_destroy
             "hoph_plan_get_info", "hoph_plan_set_exec", "oph_build_sketches",
             "minwise_build_sketches", "hoph_query_batch", "hoph_pair_counts", "hoph_synth_ids",
             "hoph_sync_status", "hoph_status_string", "hoph_plan_enable_timing",
-            "hoph_plan_read_timing"]
+            "hoph_plan_read_timing", "oph_build_sketches_static"]
 
 
 def load(path=LIB_PATH):
@@ -120,6 +121,8 @@ def load(path=LIB_PATH):
     lib.hoph_plan_set_exec.restype = i32
     lib.oph_build_sketches.argtypes = [P, P, P, i64, P, P]
     lib.oph_build_sketches.restype = i32
+    lib.oph_build_sketches_static.argtypes = [P, P, P, i64, P, P]
+    lib.oph_build_sketches_static.restype = i32
     lib.minwise_build_sketches.argtypes = [P, P, P, i64, P, P]
     lib.minwise_build_sketches.restype = i32
     lib.hoph_query_batch.argtypes = [P, u32, P, i64, P, i64, P, i64, P, P, P]
@@ -211,6 +214,14 @@ def hoph_plan_set_exec(plan, exec_=None):
 def oph_build_sketches(plan, d_ids, d_offsets, n_sets, d_planes, stream=None):
     return _check(load().oph_build_sketches(plan, _ptr(d_ids), _ptr(d_offsets), int(n_sets),
                                             _ptr(d_planes), _stream(stream)), "oph_build_sketches")
+
+
+def oph_build_sketches_static(plan, d_ids, d_offsets, n_sets, d_planes, stream=None):
+    """oph_build_sketches with its work list in the library's fixed device
+    array (no device allocation; at most 262,144 sets per call)."""
+    return _check(load().oph_build_sketches_static(plan, _ptr(d_ids), _ptr(d_offsets),
+                                                   int(n_sets), _ptr(d_planes), _stream(stream)),
+                  "oph_build_sketches_static")
 
 
 def minwise_build_sketches(plan, d_ids, d_offsets, n_sets, d_sketches, stream=None):
