@@ -111,9 +111,9 @@ typedef struct {
     int64_t accepted[HOPH_MAX_GROUPS]; /* pairs accepted after group g         */
     int64_t rejected[HOPH_MAX_GROUPS]; /* pairs rejected after group g         */
     int64_t sketch_bytes;              /* sketch bytes read from HBM (model)   */
-    int64_t join_hits;                 /* (row value, query) join matches      */
+    int64_t join_hits;                 /* (row value, query) matches counted   */
     int64_t strategy;                  /* 0 dense scan, 1 value join            */
-    int64_t reserved;
+    int64_t rows_counted;              /* join: rows that passed the row filter */
 } hoph_stats;
 
 /* Read-only facts about a plan (for tests and tooling). */
@@ -254,11 +254,13 @@ int hoph_synth_ids(uint64_t seed, int64_t first, int64_t n_ids, uint64_t D, uint
 /*
  * Optional phase timing of hoph_query_batch (for benchmarks; no paper
  * counterpart).  While enabled, every call records CUDA events on its stream
- * around (0) the join-index build, (1) the scan kernel and (2) the sort and
- * statistics kernels.  hoph_plan_read_timing waits for the last event, writes
- * the summed milliseconds of the three phases to ms[0..2], the number of
- * recorded calls to *calls and the number of kernels launched by library
- * calls on this plan to *launches (both nullable), then resets the counters.
+ * around four phases: (0) the join-index build, (1) the streaming pass over
+ * the first plane (join filter or dense scan), (2) the join's counting of
+ * candidate rows, (3) the sort and statistics kernels.
+ * hoph_plan_read_timing waits for the last event, writes the summed
+ * milliseconds of the four phases to ms[0..3], the number of recorded calls
+ * to *calls and the number of kernels launched by library calls on this plan
+ * to *launches (both nullable), then resets the counters.
  */
 int hoph_plan_enable_timing(hoph_plan *plan, int enable);
 int hoph_plan_read_timing(hoph_plan *plan, double *ms, int64_t *calls, int64_t *launches);

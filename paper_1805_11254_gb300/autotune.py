@@ -1,0 +1,71 @@
+"""Autotuner of hoph_query_batch execution knobs.
+
+Knobs (hoph_exec: strategy, consumer warps, pipeline stages, tile rows,
+CTAs per SM) change how the comparison is scheduled, never its result: the
+method's k' and layout are fixed by the plan.  The tuner times each
+candidate setting with CUDA events on the caller's stream, checks that
+every setting returns the same accepted pairs, and leaves the fastest one
+set on the plan.  Results are cached per (plan, mode, batch shape).
+"""
+import numpy as np
+
+from . import hoph
+
+_cache = {}
+
+JOIN_CANDIDATES = [dict(strategy=1, consumer_warps=c, stages=s)
+                   for c, s in ((8, 2), (6, 2), (4, 4), (4, 3), (3, 4), (2, 6), (12, 1))]
+DENSE_CANDIDATES = [dict(strategy=0, consumer_warps=c, stages=s, tile_rows=r)
+                    for c, s, r in ((8, 4, 0), (16, 4, 0), (8, 6, 0), (4, 4, 0), (16, 2, 64))]
+
+
+def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
+               stream=None, reps=3, candidates=None):
+    """Pick the fastest execution setting for this batch shape; returns
+    (best setting, {setting index: ms})."""
+    import torch
+    key = (plan.handle, mode, n_queries, n_rows, plan.k, plan.kg)
+    if key in _cache:
+        best = _cache[key]
+        plan.set_exec(**best)
+        return best, {}
+    if candidates is None:
+        candidates = JOIN_CANDIDATES + DENSE_CANDIDATES if n_queries >= 16 else DENSE_CANDIDATES
+    stream = stream or torch.cuda.current_stream()
+    times = {}
+    ref = None
+    best, best_ms = None, None
+    for i, cand in enumerate(candidates):
+        if cand["strategy"] == 0 and n_queries >= 256 and n_rows >= 1 << 20:
+            continue  # dense at large batches is tens of times slower; skip
+        plan.set_exec(**cand)
+        try:
+            hoph.hoph_query_batch(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out,
+                                  capacity, count, None, stream)
+        except hoph.HophError:
+            continue  # setting not available for this shape
+        stream.synchronize()
+        n = int(count.item())
+        got = out[:min(n, capacity)].cpu().numpy().copy()
+        if ref is None:
+            ref = (n, got)
+        elif n != ref[0] or not np.array_equal(got, ref[1]):
+            raise RuntimeError("execution setting %r changed the result" % cand)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            hoph.hoph_query_batch(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out,
+                                  capacity, count, None, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        times[i] = ms
+        if best_ms is None or ms < best_ms:
+            best, best_ms = cand, ms
+    if best is None:
+        plan.set_exec()
+        return None, times
+    plan.set_exec(**best)
+    _cache[key] = best
+    return best, times

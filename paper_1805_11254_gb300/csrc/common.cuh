@@ -139,7 +139,7 @@ struct hoph_plan {
     hoph_exec exec{};
     // optional event timing of hoph_query_batch phases (bench / tooling)
     bool timing = false;
-    std::vector<cudaEvent_t> events;  // 4 per recorded call
+    std::vector<cudaEvent_t> events;  // kTimingMarks per recorded call
     size_t events_used = 0;
     int64_t launches = 0;  // kernels launched by library calls since last read
     // first-pass decision tables per comparison mode (device copies)
@@ -149,7 +149,12 @@ struct hoph_plan {
     std::vector<uint16_t> h_table[4];
 };
 
-// record timing event `which` (0..3) of the current call when timing is on
+// timing marks of one hoph_query_batch call: before the index, before the
+// filter / dense scan, before the candidate counting, before the sort, end
+constexpr int kTimingMarks = 5;
+
+// record timing event `which` (0..kTimingMarks-1) of the current call
+// when timing is on
 void hoph_timing_mark(hoph_plan *plan, int which, cudaStream_t s);
 
 // grow-only scratch owned by the plan; returns nullptr on failure

@@ -301,7 +301,7 @@ void hoph_timing_mark(hoph_plan *plan, int which, cudaStream_t s) {
         plan->events.push_back(e);
     }
     cudaEventRecord(plan->events[idx], s);
-    if (which == 3) plan->events_used += 4;
+    if (which == kTimingMarks - 1) plan->events_used += kTimingMarks;
 }
 
 extern "C" {
@@ -316,13 +316,14 @@ int hoph_plan_enable_timing(hoph_plan *plan, int enable) {
 
 int hoph_plan_read_timing(hoph_plan *plan, double *ms, int64_t *calls, int64_t *launches) {
     if (!plan || !ms) return HOPH_ERR_PARAM;
-    for (int i = 0; i < 3; ++i) ms[i] = 0.0;
-    const size_t n = plan->events_used / 4;
+    for (int i = 0; i < kTimingMarks - 1; ++i) ms[i] = 0.0;
+    const size_t n = plan->events_used / kTimingMarks;
     if (n) HOPH_CUDA_TRY(cudaEventSynchronize(plan->events[plan->events_used - 1]));
     for (size_t c = 0; c < n; ++c)
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < kTimingMarks - 1; ++i) {
             float t = 0.f;
-            HOPH_CUDA_TRY(cudaEventElapsedTime(&t, plan->events[4 * c + i], plan->events[4 * c + i + 1]));
+            HOPH_CUDA_TRY(cudaEventElapsedTime(&t, plan->events[kTimingMarks * c + i],
+                                               plan->events[kTimingMarks * c + i + 1]));
             ms[i] += t;
         }
     if (calls) *calls = (int64_t)n;

@@ -1,26 +1,36 @@
 // Comparison of query sketches against a device-resident collection:
 // GOPH (Algorithm 1), (a:b)HOPH (Algorithm 2), plain OPH (Eq. 6) and MinWise.
 //
-// One persistent launch streams the first group's plane (or every plane for
-// the full-scan modes) through shared memory: a producer warp issues 3-D
-// TMA tile loads (cp.async.bulk.tensor) into a ring of stages guarded by
-// mbarriers, consumer warps score the tile against the whole query batch.
-// Two scoring strategies give identical results:
-//   dense  - for every (query, row) pair, lanes compare 32 bins at a time and
-//            __popc of __ballot_sync gives matched / both-empty / one-empty
-//            counts;
-//   join   - an exact value join: the batch's first-group query values are
-//            indexed (bitmap + CSR over the group's psi-space), each streamed
-//            row value is looked up once, and per-query match counts build
-//            up in per-warp shared-memory counters.  Pairs without a match are
-//            rejected for every possible denominator (checked on the host
-//            before the join is chosen), so only hit pairs are evaluated.
-// The first-group decision is a table lookup on (matched, effective bins).
-// Pairs that continue are compacted into a per-warp shared-memory list and
-// resolved lane-parallel: each lane gathers only its pair's later groups
-// from HBM and applies the exact integer rule group by group.  Accepted
-// pairs are appended with an atomic cursor and finally sorted by
-// (query, row) by a single-CTA sort, so the output is deterministic.
+// Two strategies give identical results.
+//
+// dense  - one persistent launch streams the scanned plane(s) through shared
+//          memory (a producer warp issues 3-D TMA tile loads into a ring of
+//          mbarrier-guarded stages); for every (query, row) pair, lanes
+//          compare 32 bins at a time and __popc of __ballot_sync gives the
+//          matched / both-empty / one-empty counts.  Cheap for a handful of
+//          queries, ALU-bound for large batches.
+// join   - an exact value join for large batches, in three parts:
+//          (1) an index of the batch's first-group query values: a bitmap and
+//              CSR lists over padded keys (bin << wbits) | value;
+//          (2) a streaming filter: TMA tiles of the first plane, one lane per
+//              row, every row value tested against the bitmap in shared
+//              memory.  A pair's match count is at most the row's number of
+//              bitmap hits and its denominator at least the row's number of
+//              non-empty bins, so a row whose hit count is below the smallest
+//              rejection threshold over the denominators it allows is
+//              rejected against every query; the other rows are compacted
+//              into a candidate list;
+//          (3) a counting kernel over the candidates: per-query match counts
+//              from the CSR lists in per-warp shared-memory counters, then the
+//              exact first-group decision for each query the row met.
+//          It needs "no match => reject" for every possible denominator,
+//          checked on the host when the strategy is chosen.
+// Pairs that continue after the first group are compacted into per-warp
+// shared-memory lists and resolved lane-parallel: each lane gathers only
+// its pair's later groups from HBM and applies the exact integer rule group
+// by group.  Accepted pairs are appended with an atomic cursor and finally
+// sorted by (query, row) by a single-CTA sort, so the output is
+// deterministic.
 #include <string.h>
 
 #include <algorithm>
@@ -30,11 +40,11 @@
 
 namespace {
 
-constexpr int kSurvCap = 32;        // per-warp survivor list (one entry per lane)
-constexpr int kMaxW = 1024;         // scanned bins per row
+constexpr int kSurvCap = 32;  // per-warp survivor list (one entry per lane)
+constexpr int kMaxW = 1024;   // scanned bins per row
 constexpr int kStatWords = 3 * HOPH_MAX_GROUPS + 4;
-constexpr uint32_t kMaxJoinKeys = 1u << 22;
-constexpr uint32_t kSmemBitmapBytes = 96 * 1024;
+constexpr uint64_t kMaxJoinKeys = 1ull << 23;  // padded key space of the join index
+constexpr int kSmemLimit = 227 * 1024;
 
 struct Survivor {
     int64_t row;
@@ -42,7 +52,8 @@ struct Survivor {
     uint16_t m1, k1;
 };
 
-struct ScanArgs {
+// What every comparison kernel needs to score and finish a pair.
+struct PairArgs {
     const uint32_t *coll;
     int64_t cstride;  // elements between collection planes
     const uint32_t *qry;
@@ -51,28 +62,8 @@ struct ScanArgs {
     int32_t n_q;
     int32_t kg, Gs, W, G;
     uint32_t rule;
-    int32_t join;
-    int32_t use_tma;
-    int32_t tile_rows;
-    int32_t stages;
-    int32_t n_cons;      // consumer warps
-    int64_t n_tiles;
-    uint32_t stage_bytes;  // bytes of one tile (the TMA transaction size)
-    uint32_t stage_stride; // stage_bytes rounded up to 128
-    const uint16_t *thr; // rej[W+1] then acc[W+1]
-    DecideParams dp;
-    // join
-    const uint32_t *bitmap;
-    uint32_t bitmap_words;
-    int32_t bitmap_in_smem;
-    const uint32_t *csr_off;
-    const uint16_t *csr_q;
-    const uint64_t *binbase;  // bin lower bounds; key = binbase[w] + value
-    const uint32_t *q_emask;  // [n_q][mask_words]
-    int32_t mask_words;
-    const int32_t *allempty;  // queries whose scanned bins are all empty
-    const uint32_t *n_allempty;
-    // output
+    const uint16_t *thr;  // rej[W+1], acc[W+1], row_min[W+1]
+    DecideParams dp;      // rule for the later groups
     hoph_pair *out;
     int64_t cap;
     unsigned long long *out_count;
@@ -80,34 +71,12 @@ struct ScanArgs {
     int32_t *status;
 };
 
-struct SmemLayout {
-    uint32_t bars, abort_flag, thr, toff, qoff, binbase, bitmap, counters, rowmask, surv, nsurv,
-        stats, stages, total;
-};
+// stats layout: [0..15] entering, [16..31] accepted, [32..47] rejected,
+// [48] later-group sketch bytes, [49] join hits
 
 __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(const ScanArgs &a) {
-    SmemLayout L;
-    uint32_t o = 0;
-    L.bars = o;        o += 16 * 8;                         // full[8], empty[8]
-    L.abort_flag = o;  o += 16;
-    L.thr = o;         o = align_up(o + 2 * (a.W + 1) * 2, 16);
-    L.toff = o;        o = align_up(o + a.W * 4, 16);
-    L.qoff = o;        o = align_up(o + a.W * 8, 16);
-    L.binbase = o;     o = align_up(o + (a.join ? a.W * 4 : 0), 16);
-    L.bitmap = o;      o = align_up(o + (a.join && a.bitmap_in_smem ? a.bitmap_words * 4 : 0), 16);
-    L.counters = o;    o = align_up(o + (a.join ? a.n_cons * ((a.n_q + 1) / 2) * 4 : 0), 16);
-    L.rowmask = o;     o = align_up(o + (a.join ? a.n_cons * a.mask_words * 4 : 0), 16);
-    L.surv = o;        o = align_up(o + a.n_cons * kSurvCap * (uint32_t)sizeof(Survivor), 16);
-    L.nsurv = o;       o = align_up(o + a.n_cons * 4, 16);
-    L.stats = o;       o = align_up(o + kStatWords * 8, 128);
-    L.stages = o;      o += a.stages * a.stage_stride;
-    L.total = o;
-    return L;
-}
-
-__device__ __forceinline__ void emit_pair(const ScanArgs &a, uint32_t q, int64_t row, int groups,
+__device__ __forceinline__ void emit_pair(const PairArgs &a, uint32_t q, int64_t row, int groups,
                                           int matches) {
     const unsigned long long idx = atomicAdd(a.out_count, 1ull);
     if (idx < (unsigned long long)a.cap) {
@@ -120,15 +89,13 @@ __device__ __forceinline__ void emit_pair(const ScanArgs &a, uint32_t q, int64_t
     }
 }
 
-// stats layout: [0..15] entering, [16..31] accepted, [32..47] rejected,
-// [48] sketch bytes, [49] join hits
-__device__ __forceinline__ void stat_add(unsigned long long *s, int idx, unsigned long long v) {
-    if (v) atomicAdd(s + idx, v);
+__host__ __device__ __forceinline__ int table_decide(const uint16_t *thr, int W, int m, int K) {
+    return m < thr[K] ? HOPH_REJECT : (m >= thr[W + 1 + K] ? HOPH_ACCEPT : HOPH_CONTINUE);
 }
 
 // Lane-parallel resolution of the warp's survivor list: lane j finishes
 // entry j by comparing the later groups of its pair one at a time.
-__device__ void resolve_survivors(const ScanArgs &a, Survivor *list, uint32_t *nsurv,
+__device__ void resolve_survivors(const PairArgs &a, Survivor *list, uint32_t *nsurv,
                                   unsigned long long *s_stats) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
@@ -173,7 +140,7 @@ __device__ void resolve_survivors(const ScanArgs &a, Survivor *list, uint32_t *n
     __syncwarp();
 }
 
-// Append one survivor from one lane (the caller guarantees room).
+// Append one survivor from one lane; false if the list is full.
 __device__ __forceinline__ bool push_survivor(Survivor *list, uint32_t *nsurv, uint32_t q,
                                               int64_t row, int m1, int k1) {
     const uint32_t slot = atomicAdd(nsurv, 1u);
@@ -190,38 +157,135 @@ __device__ __forceinline__ bool push_survivor(Survivor *list, uint32_t *nsurv, u
     return true;
 }
 
-__device__ __forceinline__ int table_decide(const uint16_t *thr, int W, int m, int K) {
-    return m < thr[K] ? HOPH_REJECT : (m >= thr[W + 1 + K] ? HOPH_ACCEPT : HOPH_CONTINUE);
+// Fold a CTA's shared counters into the call's global counters.
+__device__ __forceinline__ void flush_stats(const unsigned long long *s_stats,
+                                            unsigned long long *g_stats, int lane) {
+    for (int i = lane; i < kStatWords; i += 32)
+        if (s_stats[i]) atomicAdd(g_stats + i, s_stats[i]);
 }
 
-// ---------------------------------------------------------------------------
-// Dense scoring of one tile: every (query, row) pair, lanes over bins.
-// ---------------------------------------------------------------------------
-__device__ void score_tile_dense(const ScanArgs &a, const uint32_t *tile, int rows_here,
-                                 int64_t row0, const int32_t *s_toff, const int64_t *s_qoff,
-                                 const uint16_t *s_thr, Survivor *list, uint32_t *nsurv,
-                                 unsigned long long *s_stats, int cw, unsigned long long &acc0,
-                                 unsigned long long &cont0) {
+// Producer side of a TMA stage ring: lane 0 of the producer warp issues one
+// 3-D box load per tile of this CTA, then lets every issued copy land before
+// the warp leaves (so no copy targets shared memory of a finished CTA).
+__device__ void produce_tiles(const CUtensorMap *map, unsigned char *stages, uint64_t *full,
+                              uint64_t *empty, volatile int32_t *abort_flag, int nstages,
+                              uint32_t stage_bytes, uint32_t stage_stride, int64_t n_tiles,
+                              int R, int32_t *status) {
+    tma_prefetch_desc(map);
+    int64_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+        const int s = (int)(it % nstages);
+        const uint32_t use = (uint32_t)(it / nstages);
+        if (use > 0 && !mbar_wait_bounded(empty + s, (use - 1) & 1, abort_flag)) {
+            hoph_flag(status, HOPH_ERR_TIMEOUT);
+            *abort_flag = 1;
+            break;
+        }
+        mbar_arrive_expect_tx(full + s, stage_bytes);
+        tma_load_3d(stages + (size_t)s * stage_stride, map, full + s, 0, (int32_t)(tile * R), 0);
+    }
+    const int64_t issued = it;
+    for (int64_t j = (issued > nstages ? issued - nstages : 0); j < issued; ++j) {
+        const int s = (int)(j % nstages);
+        if (!mbar_wait_bounded(full + s, (uint32_t)(j / nstages) & 1, abort_flag)) {
+            const uint64_t t0 = global_ns();
+            while (!mbar_try_wait(full + s, (uint32_t)(j / nstages) & 1) &&
+                   global_ns() - t0 < 1000000000ull) {
+            }
+        }
+    }
+}
+
+// ===========================================================================
+// Dense strategy
+// ===========================================================================
+struct DenseArgs {
+    PairArgs p;
+    int32_t use_tma, tile_rows, stages, n_cons;
+    int64_t n_tiles;
+    uint32_t stage_bytes;   // bytes of one tile (the TMA transaction size)
+    uint32_t stage_stride;  // stage_bytes rounded up to 128
+};
+
+struct DenseSmem {
+    uint32_t bars, abort_flag, thr, toff, qoff, surv, nsurv, stats, stages, total;
+};
+
+__host__ __device__ inline DenseSmem dense_smem(const DenseArgs &a) {
+    DenseSmem L;
+    uint32_t o = 0;
+    L.bars = o;       o += 16 * 8;  // full[8], empty[8]
+    L.abort_flag = o; o += 16;
+    L.thr = o;        o = align_up(o + 3 * (a.p.W + 1) * 2, 16);
+    L.toff = o;       o = align_up(o + a.p.W * 4, 16);
+    L.qoff = o;       o = align_up(o + a.p.W * 8, 16);
+    L.surv = o;       o = align_up(o + a.n_cons * kSurvCap * (uint32_t)sizeof(Survivor), 16);
+    L.nsurv = o;      o = align_up(o + a.n_cons * 4, 16);
+    L.stats = o;      o = align_up(o + kStatWords * 8, 128);
+    L.stages = o;     o += a.stages * a.stage_stride;
+    L.total = o;
+    return L;
+}
+
+constexpr int kQCache = 8;  // query chunks kept in registers (W <= 256)
+
+// Every (query, row) pair of one tile; lanes over bins.  Consecutive pairs of
+// a warp share the query, whose values and empty masks stay in registers.
+__device__ void score_tile_dense(const PairArgs &a, int n_cons, const uint32_t *tile,
+                                 int rows_here, int64_t row0, const int32_t *s_toff,
+                                 const int64_t *s_qoff, const uint16_t *s_thr, Survivor *list,
+                                 uint32_t *nsurv, unsigned long long *s_stats, int cw,
+                                 unsigned long long &acc0) {
     const int lane = threadIdx.x & 31;
     const int nch = (a.W + 31) >> 5;
+    const bool cached = nch <= kQCache;
+    uint32_t qv[kQCache], qem[kQCache];
+    int cur_q = -1;
     const int64_t n_pairs = (int64_t)rows_here * a.n_q;
-    for (int64_t p = cw; p < n_pairs; p += a.n_cons) {
+    for (int64_t p = cw; p < n_pairs; p += n_cons) {
         const int q = (int)(p / rows_here);
         const int rl = (int)(p - (int64_t)q * rows_here);
         const uint32_t *qb = a.qry + (int64_t)q * a.kg;
-        int m = 0, both = 0, one = 0;
-        for (int c = 0; c < nch; ++c) {
-            const int w = (c << 5) + lane;
-            const bool valid = w < a.W;
-            uint32_t rv = 0, qv = 0;
-            if (valid) {
-                rv = tile[s_toff[w] + rl * a.kg];
-                qv = __ldg(qb + s_qoff[w]);
+        if (cached && q != cur_q) {
+            cur_q = q;
+#pragma unroll
+            for (int c = 0; c < kQCache; ++c) {
+                const int w = (c << 5) + lane;
+                const bool valid = c < nch && w < a.W;
+                qv[c] = valid ? __ldg(qb + s_qoff[w]) : 0u;
+                qem[c] = __ballot_sync(0xFFFFFFFFu, valid && qv[c] == HOPH_EMPTY_VALUE);
             }
-            const bool er = rv == HOPH_EMPTY_VALUE, eq = qv == HOPH_EMPTY_VALUE;
-            m += __popc(__ballot_sync(0xFFFFFFFFu, valid && !eq && rv == qv));
-            both += __popc(__ballot_sync(0xFFFFFFFFu, valid && er && eq));
-            one += __popc(__ballot_sync(0xFFFFFFFFu, valid && er != eq));
+        }
+        int m = 0, both = 0, one = 0;
+        if (cached) {
+#pragma unroll
+            for (int c = 0; c < kQCache; ++c) {
+                if (c < nch) {
+                    const int w = (c << 5) + lane;
+                    const bool valid = w < a.W;
+                    const uint32_t rv = valid ? tile[s_toff[w] + rl * a.kg] : 0u;
+                    const uint32_t rem =
+                        __ballot_sync(0xFFFFFFFFu, valid && rv == HOPH_EMPTY_VALUE);
+                    m += __popc(__ballot_sync(0xFFFFFFFFu,
+                                              valid && qv[c] != HOPH_EMPTY_VALUE && rv == qv[c]));
+                    both += __popc(rem & qem[c]);
+                    one += __popc(rem ^ qem[c]);
+                }
+            }
+        } else {
+            for (int c = 0; c < nch; ++c) {
+                const int w = (c << 5) + lane;
+                const bool valid = w < a.W;
+                uint32_t rv = 0, q1 = 0;
+                if (valid) {
+                    rv = tile[s_toff[w] + rl * a.kg];
+                    q1 = __ldg(qb + s_qoff[w]);
+                }
+                const bool er = rv == HOPH_EMPTY_VALUE, eq = q1 == HOPH_EMPTY_VALUE;
+                m += __popc(__ballot_sync(0xFFFFFFFFu, valid && !eq && rv == q1));
+                both += __popc(__ballot_sync(0xFFFFFFFFu, valid && er && eq));
+                one += __popc(__ballot_sync(0xFFFFFFFFu, valid && er != eq));
+            }
         }
         const int K = hoph_effective(a.rule, a.W, both, one);
         const int d = table_decide(s_thr, a.W, m, K);
@@ -229,7 +293,6 @@ __device__ void score_tile_dense(const ScanArgs &a, const uint32_t *tile, int ro
             ++acc0;
             if (lane == 0) emit_pair(a, q, row0 + rl, 1, m);
         } else if (d == HOPH_CONTINUE) {
-            ++cont0;
             if (*nsurv >= (uint32_t)kSurvCap) resolve_survivors(a, list, nsurv, s_stats);
             if (lane == 0) push_survivor(list, nsurv, q, row0 + rl, m, K);
             __syncwarp();
@@ -237,149 +300,17 @@ __device__ void score_tile_dense(const ScanArgs &a, const uint32_t *tile, int ro
     }
 }
 
-// ---------------------------------------------------------------------------
-// Join scoring of one tile: one warp per row.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool bitmap_has(const ScanArgs &a, const uint32_t *s_bitmap,
-                                           uint32_t key) {
-    const uint32_t w = a.bitmap_in_smem ? s_bitmap[key >> 5] : __ldg(a.bitmap + (key >> 5));
-    return (w >> (key & 31)) & 1u;
-}
-
-__device__ void score_tile_join(const ScanArgs &a, const uint32_t *tile, int rows_here,
-                                int64_t row0, const int32_t *s_toff, const uint32_t *s_binbase,
-                                const uint32_t *s_bitmap, const uint16_t *s_thr, uint32_t *cnt,
-                                uint32_t *rowmask, Survivor *list, uint32_t *nsurv,
-                                unsigned long long *s_stats, int cw, unsigned long long &acc0,
-                                unsigned long long &cont0, unsigned long long &hits) {
-    const int lane = threadIdx.x & 31;
-    const int nch = (a.W + 31) >> 5;
-    const int n_allempty = a.join ? (int)*a.n_allempty : 0;
-    // a pair of all-empty scans has M = 0 and K = the rule's effective bins
-    const int d00 = table_decide(s_thr, a.W, 0, hoph_effective(a.rule, a.W, a.W, 0));
-    for (int rl = cw; rl < rows_here; rl += a.n_cons) {
-        const int64_t row = row0 + rl;
-        // pass 1: row empty mask and match counts per query
-        bool all_empty = true;
-        for (int c = 0; c < nch; ++c) {
-            const int w = (c << 5) + lane;
-            const bool valid = w < a.W;
-            const uint32_t v = valid ? tile[s_toff[w] + rl * a.kg] : HOPH_EMPTY_VALUE;
-            const bool e = v == HOPH_EMPTY_VALUE;
-            const uint32_t em = __ballot_sync(0xFFFFFFFFu, valid && e);
-            const uint32_t vm = __ballot_sync(0xFFFFFFFFu, valid);
-            all_empty = all_empty && (em == vm);
-            if (lane == 0) rowmask[c] = em;
-            if (!e) {
-                const uint32_t key = s_binbase[w] + v;
-                if (bitmap_has(a, s_bitmap, key)) {
-                    const uint32_t o1 = __ldg(a.csr_off + key), o2 = __ldg(a.csr_off + key + 1);
-                    for (uint32_t i = o1; i < o2; ++i) {
-                        const uint32_t q = __ldg(a.csr_q + i);
-                        atomicAdd(cnt + (q >> 1), 1u << ((q & 1) * 16));
-                    }
-                    hits += o2 - o1;
-                }
-            }
-        }
-        __syncwarp();
-        // pass 2: each distinct hit query is taken by the first lane that
-        // clears its counter; resumable so a full survivor list can drain
-        int c = 0;
-        uint32_t i = 0, iend = 0;
-        bool done = false;
-        while (true) {
-            while (!done) {
-                if (i == iend) {
-                    // next chunk of this lane with a bitmap hit
-                    bool found = false;
-                    for (; c < nch && !found; ++c) {
-                        const int w = (c << 5) + lane;
-                        if (w >= a.W) continue;
-                        const uint32_t v = tile[s_toff[w] + rl * a.kg];
-                        if (v == HOPH_EMPTY_VALUE) continue;
-                        const uint32_t key = s_binbase[w] + v;
-                        if (!bitmap_has(a, s_bitmap, key)) continue;
-                        i = __ldg(a.csr_off + key);
-                        iend = __ldg(a.csr_off + key + 1);
-                        found = i < iend;
-                    }
-                    if (!found) {
-                        done = true;
-                        break;
-                    }
-                }
-                const uint32_t q = __ldg(a.csr_q + i);
-                const uint32_t sh = (q & 1) * 16;
-                const uint32_t old = atomicAnd(cnt + (q >> 1), ~(0xFFFFu << sh));
-                const int m = (int)((old >> sh) & 0xFFFFu);
-                if (m) {
-                    int both = 0, one = 0;
-                    const uint32_t *qm = a.q_emask + (int64_t)q * a.mask_words;
-                    for (int j = 0; j < a.mask_words; ++j) {
-                        const uint32_t x = __ldg(qm + j), y = rowmask[j];
-                        both += __popc(x & y);
-                        one += __popc(x ^ y);
-                    }
-                    const int K = hoph_effective(a.rule, a.W, both, one);
-                    const int d = table_decide(s_thr, a.W, m, K);
-                    if (d == HOPH_ACCEPT) {
-                        ++acc0;
-                        emit_pair(a, q, row, 1, m);
-                    } else if (d == HOPH_CONTINUE) {
-                        if (!push_survivor(list, nsurv, q, row, m, K)) {
-                            atomicAdd(cnt + (q >> 1), (uint32_t)m << sh);  // retry later
-                            break;
-                        }
-                        ++cont0;
-                    }
-                }
-                ++i;
-            }
-            const bool all_done = __all_sync(0xFFFFFFFFu, done);
-            __syncwarp();
-            if (*nsurv >= (uint32_t)kSurvCap / 2 || !all_done)
-                resolve_survivors(a, list, nsurv, s_stats);
-            if (all_done) break;
-        }
-        // pairs whose scanned bins are empty on both sides (effective bins 0)
-        if (all_empty && n_allempty > 0 && d00 != HOPH_REJECT) {
-            for (int base = 0; base < n_allempty; base += 32) {
-                if (*nsurv + 32 > (uint32_t)kSurvCap) resolve_survivors(a, list, nsurv, s_stats);
-                if (base + lane < n_allempty) {
-                    const uint32_t q = (uint32_t)a.allempty[base + lane];
-                    if (d00 == HOPH_ACCEPT) {
-                        ++acc0;
-                        emit_pair(a, q, row, 1, 0);
-                    } else {
-                        ++cont0;
-                        push_survivor(list, nsurv, q, row, 0, 0);
-                    }
-                }
-                __syncwarp();
-            }
-        }
-        __syncwarp();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// The persistent scan kernel
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * 17) scan_kernel(const __grid_constant__ ScanArgs a,
-                                                       const __grid_constant__ CUtensorMap map) {
+__global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_constant__ DenseArgs a,
+                                                             const __grid_constant__ CUtensorMap map) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const SmemLayout L = smem_layout(a);
+    const DenseSmem L = dense_smem(a);
+    const PairArgs &P = a.p;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint64_t *empty = full + 8;
     volatile int32_t *abort_flag = reinterpret_cast<volatile int32_t *>(smem + L.abort_flag);
     uint16_t *s_thr = reinterpret_cast<uint16_t *>(smem + L.thr);
     int32_t *s_toff = reinterpret_cast<int32_t *>(smem + L.toff);
     int64_t *s_qoff = reinterpret_cast<int64_t *>(smem + L.qoff);
-    uint32_t *s_binbase = reinterpret_cast<uint32_t *>(smem + L.binbase);
-    uint32_t *s_bitmap = reinterpret_cast<uint32_t *>(smem + L.bitmap);
-    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + L.counters);
-    uint32_t *s_rowmask = reinterpret_cast<uint32_t *>(smem + L.rowmask);
     Survivor *s_surv = reinterpret_cast<Survivor *>(smem + L.surv);
     uint32_t *s_nsurv = reinterpret_cast<uint32_t *>(smem + L.nsurv);
     unsigned long long *s_stats = reinterpret_cast<unsigned long long *>(smem + L.stats);
@@ -387,19 +318,12 @@ __global__ void __launch_bounds__(32 * 17) scan_kernel(const __grid_constant__ S
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = a.tile_rows;
-
-    // set-up: tables into shared memory
-    for (int i = tid; i < 2 * (a.W + 1); i += blockDim.x) s_thr[i] = a.thr[i];
-    for (int w = tid; w < a.W; w += blockDim.x) {
-        const int g = w / a.kg, b = w - g * a.kg;
-        s_toff[w] = (g * R) * a.kg + b;
-        s_qoff[w] = (int64_t)g * a.qstride + b;
-        if (a.join) s_binbase[w] = (uint32_t)a.binbase[w];
+    for (int i = tid; i < 3 * (P.W + 1); i += blockDim.x) s_thr[i] = P.thr[i];
+    for (int w = tid; w < P.W; w += blockDim.x) {
+        const int g = w / P.kg, b = w - g * P.kg;
+        s_toff[w] = (g * R) * P.kg + b;
+        s_qoff[w] = (int64_t)g * P.qstride + b;
     }
-    if (a.join && a.bitmap_in_smem)
-        for (uint32_t i = tid; i < a.bitmap_words; i += blockDim.x) s_bitmap[i] = a.bitmap[i];
-    if (a.join)
-        for (int i = tid; i < a.n_cons * ((a.n_q + 1) / 2); i += blockDim.x) s_cnt[i] = 0;
     for (int i = tid; i < a.n_cons; i += blockDim.x) s_nsurv[i] = 0;
     for (int i = tid; i < kStatWords; i += blockDim.x) s_stats[i] = 0;
     if (tid == 0) {
@@ -413,55 +337,26 @@ __global__ void __launch_bounds__(32 * 17) scan_kernel(const __grid_constant__ S
     __syncthreads();
 
     if (warp == a.n_cons) {
-        // ---------------- producer warp ----------------
-        if (a.use_tma && lane == 0) {
-            tma_prefetch_desc(&map);
-            int64_t it = 0;
-            for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
-                const int s = (int)(it % a.stages);
-                const uint32_t use = (uint32_t)(it / a.stages);
-                if (use > 0 && !mbar_wait_bounded(empty + s, (use - 1) & 1, abort_flag)) {
-                    hoph_flag(a.status, HOPH_ERR_TIMEOUT);
-                    *abort_flag = 1;
-                    break;
-                }
-                mbar_arrive_expect_tx(full + s, a.stage_bytes);
-                tma_load_3d(stages + (size_t)s * a.stage_stride, &map, full + s, 0,
-                            (int32_t)(tile * R), 0);
-            }
-            // let every copy this warp issued land before it leaves
-            const int64_t issued = it;
-            for (int64_t j = (issued > a.stages ? issued - a.stages : 0); j < issued; ++j) {
-                const int s = (int)(j % a.stages);
-                if (!mbar_wait_bounded(full + s, (uint32_t)(j / a.stages) & 1, abort_flag)) {
-                    // consumers gave up; give the copy a last bounded chance
-                    const uint64_t t0 = global_ns();
-                    while (!mbar_try_wait(full + s, (uint32_t)(j / a.stages) & 1) &&
-                           global_ns() - t0 < 1000000000ull) {
-                    }
-                }
-            }
-        }
+        if (a.use_tma && lane == 0)
+            produce_tiles(&map, stages, full, empty, abort_flag, a.stages, a.stage_bytes,
+                          a.stage_stride, a.n_tiles, R, P.status);
         return;
     }
 
-    // ---------------- consumer warps ----------------
     const int cw = warp;
     Survivor *list = s_surv + cw * kSurvCap;
     uint32_t *nsurv = s_nsurv + cw;
-    uint32_t *cnt = s_cnt + cw * ((a.n_q + 1) / 2);
-    uint32_t *rowmask = s_rowmask + cw * a.mask_words;
-    unsigned long long acc0 = 0, cont0 = 0, hits = 0;
+    unsigned long long acc0 = 0;
     int64_t it = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
         const int s = a.use_tma ? (int)(it % a.stages) : 0;
         const uint32_t *tp = reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride);
         const int64_t row0 = tile * R;
-        const int rows_here = (int)min((long long)R, (long long)(a.n_rows - row0));
+        const int rows_here = (int)min((long long)R, (long long)(P.n_rows - row0));
         if (a.use_tma) {
             if (!mbar_wait_bounded(full + s, (uint32_t)(it / a.stages) & 1, abort_flag)) {
-                hoph_flag(a.status, HOPH_ERR_TIMEOUT);
+                hoph_flag(P.status, HOPH_ERR_TIMEOUT);
                 *abort_flag = 1;
                 ok = false;
                 break;
@@ -469,19 +364,15 @@ __global__ void __launch_bounds__(32 * 17) scan_kernel(const __grid_constant__ S
         } else {
             // plain cooperative load of the tile ([Gs][R][k'] layout)
             uint32_t *dst = reinterpret_cast<uint32_t *>(stages);
-            const int per_plane = rows_here * a.kg;
-            for (int idx = cw * 32 + lane; idx < a.Gs * per_plane; idx += a.n_cons * 32) {
+            const int per_plane = rows_here * P.kg;
+            for (int idx = cw * 32 + lane; idx < P.Gs * per_plane; idx += a.n_cons * 32) {
                 const int g = idx / per_plane, rem = idx - g * per_plane;
-                dst[g * R * a.kg + rem] = a.coll[(int64_t)g * a.cstride + row0 * a.kg + rem];
+                dst[g * R * P.kg + rem] = P.coll[(int64_t)g * P.cstride + row0 * P.kg + rem];
             }
             named_bar_sync(1, a.n_cons * 32);
         }
-        if (a.join)
-            score_tile_join(a, tp, rows_here, row0, s_toff, s_binbase, s_bitmap, s_thr, cnt,
-                            rowmask, list, nsurv, s_stats, cw, acc0, cont0, hits);
-        else
-            score_tile_dense(a, tp, rows_here, row0, s_toff, s_qoff, s_thr, list, nsurv, s_stats,
-                             cw, acc0, cont0);
+        score_tile_dense(P, a.n_cons, tp, rows_here, row0, s_toff, s_qoff, s_thr, list, nsurv,
+                         s_stats, cw, acc0);
         __syncwarp();
         if (a.use_tma) {
             if (lane == 0) mbar_arrive(empty + s);
@@ -489,34 +380,20 @@ __global__ void __launch_bounds__(32 * 17) scan_kernel(const __grid_constant__ S
             named_bar_sync(1, a.n_cons * 32);
         }
     }
-    if (ok && *nsurv) resolve_survivors(a, list, nsurv, s_stats);
-    // warp totals (dense counts are warp-uniform; join counts are per lane)
-    if (!a.join) {
-        if (lane != 0) acc0 = cont0 = 0;
-    }
-    for (int o = 16; o; o >>= 1) {
-        acc0 += __shfl_xor_sync(0xFFFFFFFFu, acc0, o);
-        cont0 += __shfl_xor_sync(0xFFFFFFFFu, cont0, o);
-        hits += __shfl_xor_sync(0xFFFFFFFFu, hits, o);
-    }
-    if (lane == 0) {
-        stat_add(s_stats, 16, acc0);
-        stat_add(s_stats, 49, hits);
-    }
+    if (ok && *nsurv) resolve_survivors(P, list, nsurv, s_stats);
+    if (lane == 0 && acc0) atomicAdd(s_stats + 16, acc0);
     named_bar_sync(1, a.n_cons * 32);
-    if (cw == 0)
-        for (int i = lane; i < kStatWords; i += 32)
-            if (s_stats[i]) atomicAdd(a.stat + i, s_stats[i]);
+    if (cw == 0) flush_stats(s_stats, P.stat, lane);
 }
 
-// ---------------------------------------------------------------------------
-// Join index over the batch's scanned query bins
-// ---------------------------------------------------------------------------
+// ===========================================================================
+// Join strategy, part 1: index of the batch's scanned query values
+// ===========================================================================
 struct IndexArgs {
     const uint32_t *qry;
     int64_t qstride;
     int32_t n_q, kg, W, mask_words;
-    const uint64_t *binbase;
+    uint32_t wbits;      // key = (w << wbits) | value
     uint32_t *counts;    // [keys + 1]
     uint32_t *bitmap;
     uint32_t *q_emask;   // [n_q][mask_words]
@@ -544,7 +421,7 @@ __global__ void join_count_kernel(const IndexArgs a) {
         all_empty = all_empty && em == vm;
         if (lane == 0) a.q_emask[q * a.mask_words + c] = em;
         if (valid && !e) {
-            const uint32_t key = (uint32_t)(a.binbase[w] + v);
+            const uint32_t key = ((uint32_t)w << a.wbits) | v;
             atomicAdd(a.counts + key, 1u);
             atomicOr(a.bitmap + (key >> 5), 1u << (key & 31));
         }
@@ -560,7 +437,7 @@ __global__ void join_fill_kernel(const IndexArgs a, const uint32_t *csr_off, uin
         const int g = w / a.kg, b = w - g * a.kg;
         const uint32_t v = a.qry[(int64_t)g * a.qstride + q * a.kg + b];
         if (v == HOPH_EMPTY_VALUE) continue;
-        const uint32_t key = (uint32_t)(a.binbase[w] + v);
+        const uint32_t key = ((uint32_t)w << a.wbits) | v;
         const uint32_t pos = csr_off[key] + atomicSub(a.counts + key, 1u) - 1u;
         csr_q[pos] = (uint16_t)q;
     }
@@ -640,9 +517,330 @@ __global__ void __launch_bounds__(kScanBlock) scan_apply_kernel(const uint32_t *
     }
 }
 
-// ---------------------------------------------------------------------------
+// ===========================================================================
+// Join strategy, part 2: streaming row filter (one lane per row)
+// ===========================================================================
+struct FilterArgs {
+    int64_t n_rows;
+    int32_t kg, Gs, W;
+    int32_t tile_rows, n_cons, stages;  // tile_rows = 32 * n_cons
+    int64_t n_tiles;
+    uint32_t stage_bytes, stage_stride;
+    const uint32_t *bitmap;
+    uint32_t bitmap_words;
+    uint32_t wbits;
+    const uint16_t *row_min;  // [W + 1]
+    int32_t keep_empty;       // rows without a non-empty scanned bin are candidates
+    uint32_t *cand;
+    unsigned long long *n_cand;
+    int32_t *status;
+};
+
+struct FilterSmem {
+    uint32_t bars, abort_flag, row_min, choff, bitmap, stages, total;
+};
+
+__host__ __device__ inline FilterSmem filter_smem(const FilterArgs &a) {
+    FilterSmem L;
+    uint32_t o = 0;
+    L.bars = o;       o += 16 * 8;
+    L.abort_flag = o; o += 16;
+    L.row_min = o;    o = align_up(o + (a.W + 1) * 2, 16);
+    L.choff = o;      o = align_up(o + (a.W / 4) * 4, 16);
+    L.bitmap = o;     o = align_up(o + a.bitmap_words * 4, 128);
+    L.stages = o;     o += a.stages * a.stage_stride;
+    L.total = o;
+    return L;
+}
+
+__global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__ FilterArgs a,
+                                                         const __grid_constant__ CUtensorMap map) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const FilterSmem L = filter_smem(a);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
+    uint64_t *empty = full + 8;
+    volatile int32_t *abort_flag = reinterpret_cast<volatile int32_t *>(smem + L.abort_flag);
+    uint16_t *s_rmin = reinterpret_cast<uint16_t *>(smem + L.row_min);
+    int32_t *s_choff = reinterpret_cast<int32_t *>(smem + L.choff);
+    uint32_t *s_bitmap = reinterpret_cast<uint32_t *>(smem + L.bitmap);
+    unsigned char *stages = smem + L.stages;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int R = a.tile_rows;
+    const int nchunk = a.W >> 2;
+    for (int i = tid; i <= a.W; i += blockDim.x) s_rmin[i] = a.row_min[i];
+    for (int j = tid; j < nchunk; j += blockDim.x) {
+        const int w = j << 2, g = w / a.kg, b = w - g * a.kg;
+        s_choff[j] = (g * R) * a.kg + b;  // element offset of chunk j in row 0 of a tile
+    }
+    for (uint32_t i = tid; i < a.bitmap_words; i += blockDim.x) s_bitmap[i] = a.bitmap[i];
+    if (tid == 0) {
+        *abort_flag = 0;
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, a.n_cons);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == a.n_cons) {
+        if (lane == 0)
+            produce_tiles(&map, stages, full, empty, abort_flag, a.stages, a.stage_bytes,
+                          a.stage_stride, a.n_tiles, R, a.status);
+        return;
+    }
+
+    // consumer warp `warp` owns rows warp*32 .. warp*32+31 of every tile; each
+    // lane walks its row's 16-byte chunks starting at chunk (lane mod nchunk)
+    // so the eight lanes of a shared-memory phase touch eight different banks
+    const int rl = (warp << 5) + lane;
+    const int j0 = lane % nchunk;
+    int64_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+        const int s = (int)(it % a.stages);
+        const uint32_t *tp = reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride);
+        const int64_t row = tile * R + rl;
+        if (!mbar_wait_bounded(full + s, (uint32_t)(it / a.stages) & 1, abort_flag)) {
+            hoph_flag(a.status, HOPH_ERR_TIMEOUT);
+            *abort_flag = 1;
+            break;
+        }
+        bool pass = false;
+        if (row < a.n_rows) {
+            int ne = 0, h = 0;
+            const uint32_t *rp = tp + rl * a.kg;
+            int j = j0;
+            for (int step = 0; step < nchunk; ++step) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(rp + s_choff[j]);
+                const uint32_t kb = (uint32_t)(j << 2) << a.wbits;
+                const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (x[c] != HOPH_EMPTY_VALUE) {
+                        const uint32_t key = kb + ((uint32_t)c << a.wbits) + x[c];
+                        ++ne;
+                        h += (s_bitmap[key >> 5] >> (key & 31)) & 1u;
+                    }
+                }
+                if (++j == nchunk) j = 0;
+            }
+            pass = ne == 0 ? (a.keep_empty != 0) : (h >= (int)s_rmin[ne]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + s);
+        const uint32_t pm = __ballot_sync(0xFFFFFFFFu, pass);
+        if (pm) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(a.n_cand, (unsigned long long)__popc(pm));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (pass) a.cand[base + __popc(pm & ((1u << lane) - 1u))] = (uint32_t)row;
+        }
+    }
+}
+
+// ===========================================================================
+// Join strategy, part 3: per-query counts of the candidate rows
+// ===========================================================================
+struct CountArgs {
+    PairArgs p;
+    const uint32_t *cand;
+    const unsigned long long *n_cand;
+    const uint32_t *bitmap;
+    uint32_t wbits;
+    const uint32_t *csr_off;
+    const uint16_t *csr_q;
+    const uint32_t *q_emask;  // [n_q][mask_words]
+    int32_t mask_words;
+    const int32_t *allempty;
+    const uint32_t *n_allempty;
+};
+
+constexpr int kCountThreads = 256;
+constexpr int kCountWarps = kCountThreads / 32;
+
+struct CountSmem {
+    uint32_t thr, woff, counters, rowmask, surv, nsurv, stats, total;
+};
+
+__host__ __device__ inline CountSmem count_smem(const CountArgs &a) {
+    CountSmem L;
+    uint32_t o = 0;
+    L.thr = o;      o = align_up(o + 3 * (a.p.W + 1) * 2, 16);
+    L.woff = o;     o = align_up(o + a.p.W * 8, 16);
+    L.counters = o; o = align_up(o + kCountWarps * ((a.p.n_q + 1) / 2) * 4, 16);
+    L.rowmask = o;  o = align_up(o + kCountWarps * a.mask_words * 4, 16);
+    L.surv = o;     o = align_up(o + kCountWarps * kSurvCap * (uint32_t)sizeof(Survivor), 16);
+    L.nsurv = o;    o = align_up(o + kCountWarps * 4, 16);
+    L.stats = o;    o = align_up(o + kStatWords * 8, 16);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ bool key_in_bitmap(const uint32_t *bm, uint32_t key) {
+    return (__ldg(bm + (key >> 5)) >> (key & 31)) & 1u;
+}
+
+__global__ void __launch_bounds__(kCountThreads) count_kernel(const __grid_constant__ CountArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const CountSmem L = count_smem(a);
+    const PairArgs &P = a.p;
+    uint16_t *s_thr = reinterpret_cast<uint16_t *>(smem + L.thr);
+    int64_t *s_woff = reinterpret_cast<int64_t *>(smem + L.woff);
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + L.counters);
+    uint32_t *s_rowmask = reinterpret_cast<uint32_t *>(smem + L.rowmask);
+    Survivor *s_surv = reinterpret_cast<Survivor *>(smem + L.surv);
+    uint32_t *s_nsurv = reinterpret_cast<uint32_t *>(smem + L.nsurv);
+    unsigned long long *s_stats = reinterpret_cast<unsigned long long *>(smem + L.stats);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cwords = (P.n_q + 1) / 2;
+    for (int i = tid; i < 3 * (P.W + 1); i += blockDim.x) s_thr[i] = P.thr[i];
+    for (int w = tid; w < P.W; w += blockDim.x) {
+        const int g = w / P.kg, b = w - g * P.kg;
+        s_woff[w] = (int64_t)g * P.cstride + b;
+    }
+    for (int i = tid; i < kCountWarps * cwords; i += blockDim.x) s_cnt[i] = 0;
+    for (int i = tid; i < kCountWarps; i += blockDim.x) s_nsurv[i] = 0;
+    for (int i = tid; i < kStatWords; i += blockDim.x) s_stats[i] = 0;
+    __syncthreads();
+
+    uint32_t *cnt = s_cnt + warp * cwords;
+    uint32_t *rowmask = s_rowmask + warp * a.mask_words;
+    Survivor *list = s_surv + warp * kSurvCap;
+    uint32_t *nsurv = s_nsurv + warp;
+    const uint16_t *row_min = s_thr + 2 * (P.W + 1);
+    const int nch = (P.W + 31) >> 5;
+    const int n_allempty = (int)*a.n_allempty;
+    // a pair of all-empty scans has M = 0 and K = the rule's effective bins
+    const int d00 = table_decide(s_thr, P.W, 0, hoph_effective(P.rule, P.W, P.W, 0));
+    const unsigned long long n_cand = *a.n_cand;
+    unsigned long long acc0 = 0, hits = 0;
+
+    for (unsigned long long ci = (unsigned long long)blockIdx.x * kCountWarps + warp; ci < n_cand;
+         ci += (unsigned long long)gridDim.x * kCountWarps) {
+        const int64_t row = a.cand[ci];
+        const uint32_t *rb = P.coll + row * P.kg;
+        int ne = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int w = (c << 5) + lane;
+            const bool valid = w < P.W;
+            const uint32_t v = valid ? __ldg(rb + s_woff[w]) : HOPH_EMPTY_VALUE;
+            const bool fullb = valid && v != HOPH_EMPTY_VALUE;
+            const uint32_t em = __ballot_sync(0xFFFFFFFFu, valid && !fullb);
+            if (lane == 0) rowmask[c] = em;
+            ne += __popc(__ballot_sync(0xFFFFFFFFu, fullb));
+        }
+        if (ne == 0) {
+            // pairs whose scanned bins are empty on both sides
+            if (n_allempty > 0 && d00 != HOPH_REJECT) {
+                for (int base = 0; base < n_allempty; base += 32) {
+                    if (*nsurv + 32 > (uint32_t)kSurvCap) resolve_survivors(P, list, nsurv, s_stats);
+                    if (base + lane < n_allempty) {
+                        const uint32_t q = (uint32_t)a.allempty[base + lane];
+                        if (d00 == HOPH_ACCEPT) {
+                            ++acc0;
+                            emit_pair(P, q, row, 1, 0);
+                        } else {
+                            push_survivor(list, nsurv, q, row, 0, 0);
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            continue;
+        }
+        const int need = row_min[ne];
+        // counting pass: per-query match counts in the warp's counters
+        for (int c = 0; c < nch; ++c) {
+            const int w = (c << 5) + lane;
+            if (w >= P.W) continue;
+            const uint32_t v = __ldg(rb + s_woff[w]);
+            if (v == HOPH_EMPTY_VALUE) continue;
+            const uint32_t key = ((uint32_t)w << a.wbits) | v;
+            if (!key_in_bitmap(a.bitmap, key)) continue;
+            const uint32_t o1 = __ldg(a.csr_off + key), o2 = __ldg(a.csr_off + key + 1);
+            for (uint32_t i = o1; i < o2; ++i) {
+                const uint32_t q = __ldg(a.csr_q + i);
+                atomicAdd(cnt + (q >> 1), 1u << ((q & 1) * 16));
+            }
+            hits += o2 - o1;
+        }
+        __syncwarp();
+        // evaluation: each distinct hit query is taken by the first lane that
+        // clears its counter; resumable so a full survivor list can drain
+        int c = 0;
+        uint32_t i = 0, iend = 0;
+        bool done = false;
+        while (true) {
+            while (!done) {
+                if (i == iend) {
+                    bool found = false;
+                    for (; c < nch && !found; ++c) {
+                        const int w = (c << 5) + lane;
+                        if (w >= P.W) continue;
+                        const uint32_t v = __ldg(rb + s_woff[w]);
+                        if (v == HOPH_EMPTY_VALUE) continue;
+                        const uint32_t key = ((uint32_t)w << a.wbits) | v;
+                        if (!key_in_bitmap(a.bitmap, key)) continue;
+                        i = __ldg(a.csr_off + key);
+                        iend = __ldg(a.csr_off + key + 1);
+                        found = i < iend;
+                    }
+                    if (!found) {
+                        done = true;
+                        break;
+                    }
+                }
+                const uint32_t q = __ldg(a.csr_q + i);
+                const uint32_t sh = (q & 1) * 16;
+                const uint32_t old = atomicAnd(cnt + (q >> 1), ~(0xFFFFu << sh));
+                const int m = (int)((old >> sh) & 0xFFFFu);
+                if (m >= need) {
+                    int both = 0, one = 0;
+                    const uint32_t *qm = a.q_emask + (int64_t)q * a.mask_words;
+                    for (int j = 0; j < a.mask_words; ++j) {
+                        const uint32_t x = __ldg(qm + j), y = rowmask[j];
+                        both += __popc(x & y);
+                        one += __popc(x ^ y);
+                    }
+                    const int K = hoph_effective(P.rule, P.W, both, one);
+                    const int d = table_decide(s_thr, P.W, m, K);
+                    if (d == HOPH_ACCEPT) {
+                        ++acc0;
+                        emit_pair(P, q, row, 1, m);
+                    } else if (d == HOPH_CONTINUE) {
+                        if (!push_survivor(list, nsurv, q, row, m, K)) {
+                            atomicAdd(cnt + (q >> 1), (uint32_t)m << sh);  // retry later
+                            break;
+                        }
+                    }
+                }
+                ++i;
+            }
+            const bool all_done = __all_sync(0xFFFFFFFFu, done);
+            __syncwarp();
+            if (*nsurv >= (uint32_t)kSurvCap / 2 || !all_done)
+                resolve_survivors(P, list, nsurv, s_stats);
+            if (all_done) break;
+        }
+        __syncwarp();
+    }
+    if (*nsurv) resolve_survivors(P, list, nsurv, s_stats);
+    for (int o = 16; o; o >>= 1) {
+        acc0 += __shfl_xor_sync(0xFFFFFFFFu, acc0, o);
+        hits += __shfl_xor_sync(0xFFFFFFFFu, hits, o);
+    }
+    if (lane == 0) {
+        if (acc0) atomicAdd(s_stats + 16, acc0);
+        if (hits) atomicAdd(s_stats + 49, hits);
+    }
+    __syncthreads();
+    if (warp == 0) flush_stats(s_stats, P.stat, lane);
+}
+
+// ===========================================================================
 // Deterministic output order: sort the accepted pairs by (query, row)
-// ---------------------------------------------------------------------------
+// ===========================================================================
 constexpr int kSortThreads = 1024;
 constexpr int kSortSmem = 8192;  // records sorted in shared memory at once
 
@@ -735,8 +933,9 @@ __global__ void __launch_bounds__(kSortThreads) sort_pairs_kernel(
 }
 
 // fold the call's counters into the caller's hoph_stats
-__global__ void stats_fold_kernel(const unsigned long long *st, int64_t pairs, int G, int Gs,
-                                  int64_t first_pass_bytes, int strategy, hoph_stats *out) {
+__global__ void stats_fold_kernel(const unsigned long long *st, const unsigned long long *n_cand,
+                                  int64_t pairs, int G, int Gs, int64_t first_pass_bytes,
+                                  int strategy, hoph_stats *out) {
     if (threadIdx.x != 0 || !out) return;
     out->entering[0] += pairs;
     const int64_t acc0 = (int64_t)st[16], cont = (Gs < G) ? (int64_t)st[1] : 0;
@@ -749,12 +948,13 @@ __global__ void stats_fold_kernel(const unsigned long long *st, int64_t pairs, i
     }
     out->sketch_bytes += first_pass_bytes + (int64_t)st[48];
     out->join_hits += (int64_t)st[49];
+    if (n_cand) out->rows_counted += (int64_t)*n_cand;
     out->strategy = strategy;
 }
 
-// ---------------------------------------------------------------------------
+// ===========================================================================
 // Per-pair counts (no early exit): warp per pair, lanes over bins
-// ---------------------------------------------------------------------------
+// ===========================================================================
 __global__ void pair_counts_kernel(const uint32_t *qry, int64_t qstride, int64_t n_q,
                                    const uint32_t *coll, int64_t cstride, int64_t n_rows, int kg,
                                    int G, uint16_t *out) {
@@ -785,9 +985,9 @@ __global__ void pair_counts_kernel(const uint32_t *qry, int64_t qstride, int64_t
     }
 }
 
-// ---------------------------------------------------------------------------
+// ===========================================================================
 // Host side
-// ---------------------------------------------------------------------------
+// ===========================================================================
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -809,9 +1009,24 @@ EncodeTiledFn get_encode_fn() {
     return fn;
 }
 
-// First-pass decision table for W scanned bins under `dp` after `l` groups.
+// 3-D map over the collection planes: {k', rows, planes}, box {k', R, Gs}
+bool encode_planes_map(CUtensorMap *map, const uint32_t *planes, int kg, int64_t n_rows, int Gs,
+                       int64_t cstride, int R) {
+    EncodeTiledFn fn = get_encode_fn();
+    if (!fn) return false;
+    const cuuint64_t gdim[3] = {(cuuint64_t)kg, (cuuint64_t)n_rows, (cuuint64_t)Gs};
+    const cuuint64_t gstride[2] = {(cuuint64_t)kg * 4, (cuuint64_t)cstride * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kg, (cuuint32_t)R, (cuuint32_t)Gs};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, (void *)planes, gdim, gstride, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// First-pass decision table for W scanned bins under `dp` after `l` groups:
+// rej[K] / acc[K] for K = 0..W, then row_min[n] for n = 0..W.
 bool build_table(const DecideParams &dp, int W, int l, std::vector<uint16_t> &tab) {
-    tab.assign(2 * (W + 1), 0);
+    tab.assign(3 * (W + 1), 0);
     for (int K = 0; K <= W; ++K) {
         int rej = K + 1, acc = K + 1;
         for (int m = 0; m <= K; ++m) {
@@ -830,6 +1045,18 @@ bool build_table(const DecideParams &dp, int W, int l, std::vector<uint16_t> &ta
         tab[K] = (uint16_t)rej;
         tab[W + 1 + K] = (uint16_t)acc;
     }
+    // row_min[n]: a row with n non-empty scanned bins meets every query with a
+    // denominator K >= max(n, 1) (K = W under rule NONE), so a pair below the
+    // smallest rejection threshold over those K is rejected whatever the query
+    for (int n = 0; n <= W; ++n) {
+        int best = W + 1;
+        if (dp.rule == HOPH_EMPTY_NONE) {
+            best = tab[W];
+        } else {
+            for (int K = n > 1 ? n : 1; K <= W; ++K) best = best < tab[K] ? best : tab[K];
+        }
+        tab[2 * (W + 1) + n] = (uint16_t)best;
+    }
     return true;
 }
 
@@ -843,6 +1070,12 @@ struct Bump {
         return p;
     }
 };
+
+int ceil_log2_u64(uint64_t v) {
+    int b = 0;
+    while ((1ull << b) < v) ++b;
+    return b;
+}
 
 }  // namespace
 
@@ -908,60 +1141,61 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
     if (!plan->table_ok[mode]) return HOPH_ERR_UNSUPPORTED;
     const std::vector<uint16_t> &tab = plan->h_table[mode];
 
-    // strategy: the join needs "no match => reject" for every K >= 1, a
-    // small key space and a rule whose K == 0 pairs are the all-empty ones
-    const uint64_t keys = (mode == HOPH_MODE_MINWISE_FULL) ? ~0ull : plan->lo[W];
+    const bool tma_base_ok = (kg % 4 == 0) && kg <= 256 && Gs <= 256 &&
+                             ((uintptr_t)d_coll_planes & 15) == 0 && get_encode_fn() != nullptr;
+
+    // join: needs "no match => reject" for every K >= 1, TMA tiles, a rule
+    // whose K == 0 pairs are the all-empty ones, and a key space whose bitmap
+    // fits in shared memory next to two filter stages
+    uint64_t max_width = 0;
+    for (int w = 0; w < W; ++w) max_width = std::max(max_width, plan->lo[w + 1] - plan->lo[w]);
+    const int wbits = ceil_log2_u64(std::max<uint64_t>(max_width, 2));
+    const uint64_t keys = mode == HOPH_MODE_MINWISE_FULL ? ~0ull : ((uint64_t)W << wbits);
     bool join_ok = mode != HOPH_MODE_MINWISE_FULL && fp.rule != HOPH_EMPTY_EITHER &&
-                   keys < kMaxJoinKeys && n_queries <= 4096;
+                   tma_base_ok && keys <= kMaxJoinKeys && n_queries <= 4096 &&
+                   n_rows < (1ll << 32) && keys / 8 + 2 * 32 * W * 4 + 4096 <= (uint64_t)kSmemLimit;
     for (int K = 1; K <= W && join_ok; ++K) join_ok = tab[K] >= 1;
     int strategy = plan->exec.strategy;
     if (strategy == 1 && !join_ok) return HOPH_ERR_UNSUPPORTED;
     if (strategy < 0) strategy = (join_ok && n_queries >= 16) ? 1 : 0;
 
-    // launch shape
-    const int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 8;
-    int R = plan->exec.tile_rows > 0 ? plan->exec.tile_rows : 0;
-    if (R == 0) {
-        R = (int)std::max<int64_t>(1, std::min<int64_t>(256, 8192 / (W * 4)));
-        if (R >= 8) R &= ~7;
-    }
     const int mask_words = (W + 31) / 32;
-    const bool tma_ok = (kg % 4 == 0) && kg <= 256 && Gs <= 256 &&
-                        ((uintptr_t)d_coll_planes & 15) == 0 && get_encode_fn() != nullptr;
-    const int stages = tma_ok ? (plan->exec.stages > 0 ? plan->exec.stages : 4) : 1;
+    const int64_t qstride = n_queries * (int64_t)kg;
+    const int64_t cstride = n_rows * (int64_t)kg;
 
     // scratch
     Bump bump{nullptr};
     const size_t st_b = kStatWords * 8;
-    size_t need = 0;
+    const size_t cap1 = (size_t)std::max<int64_t>(out_capacity, 1);
     for (int pass = 0; pass < 2; ++pass) {
         bump.off = 0;
         bump.take(st_b);
         if (strategy == 1) {
-            bump.take((keys + 1) * 4);                       // counts
-            bump.take((keys + 1) * 4);                       // csr_off
+            bump.take((keys + 1) * 4);                                  // counts
+            bump.take((keys + 1) * 4);                                  // csr_off
             bump.take(((keys + 1 + kScanChunk - 1) / kScanChunk) * 4);  // block sums
-            bump.take((keys / 32 + 1) * 4);                  // bitmap
-            bump.take((size_t)n_queries * W * 2);            // csr_q
-            bump.take((size_t)n_queries * mask_words * 4);   // q_emask
-            bump.take((size_t)n_queries * 4 + 4);            // allempty + count
+            bump.take((keys / 32 + 1) * 4);                             // bitmap
+            bump.take((size_t)n_queries * W * 2);                       // csr_q
+            bump.take((size_t)n_queries * mask_words * 4);              // q_emask
+            bump.take((size_t)n_queries * 4 + 4);                       // allempty + count
+            bump.take(8);                                               // n_cand
+            bump.take((size_t)n_rows * 4);                              // cand
         }
-        bump.take((size_t)std::max<int64_t>(out_capacity, 1) * 16);  // sort A
-        bump.take((size_t)std::max<int64_t>(out_capacity, 1) * 16);  // sort B
+        bump.take(cap1 * 16);  // sort A
+        bump.take(cap1 * 16);  // sort B
         if (pass == 0) {
-            need = bump.off;
-            unsigned char *base = (unsigned char *)hoph_scratch(plan, need);
+            unsigned char *base = (unsigned char *)hoph_scratch(plan, bump.off);
             if (!base) return HOPH_ERR_NOMEM;
             bump.base = base;
         }
     }
     bump.off = 0;
     unsigned long long *st = (unsigned long long *)bump.take(st_b);
-    const uint16_t *d_thr = plan->d_table[mode];
     uint32_t *counts = nullptr, *csr_off = nullptr, *sums = nullptr, *bitmap = nullptr,
-             *q_emask = nullptr, *n_allempty = nullptr;
+             *q_emask = nullptr, *n_allempty = nullptr, *cand = nullptr;
     uint16_t *csr_q = nullptr;
     int32_t *allempty = nullptr;
+    unsigned long long *n_cand = nullptr;
     if (strategy == 1) {
         counts = (uint32_t *)bump.take((keys + 1) * 4);
         csr_off = (uint32_t *)bump.take((keys + 1) * 4);
@@ -971,16 +1205,38 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         q_emask = (uint32_t *)bump.take((size_t)n_queries * mask_words * 4);
         allempty = (int32_t *)bump.take((size_t)n_queries * 4 + 4);
         n_allempty = (uint32_t *)(allempty + n_queries);
+        n_cand = (unsigned long long *)bump.take(8);
+        cand = (uint32_t *)bump.take((size_t)n_rows * 4);
     }
-    ulonglong2 *sortA = (ulonglong2 *)bump.take((size_t)std::max<int64_t>(out_capacity, 1) * 16);
-    ulonglong2 *sortB = (ulonglong2 *)bump.take((size_t)std::max<int64_t>(out_capacity, 1) * 16);
+    ulonglong2 *sortA = (ulonglong2 *)bump.take(cap1 * 16);
+    ulonglong2 *sortB = (ulonglong2 *)bump.take(cap1 * 16);
+
+    PairArgs pa;
+    pa.coll = d_coll_planes;
+    pa.cstride = cstride;
+    pa.qry = d_query_planes;
+    pa.qstride = qstride;
+    pa.n_rows = n_rows;
+    pa.n_q = (int32_t)n_queries;
+    pa.kg = kg;
+    pa.Gs = Gs;
+    pa.W = W;
+    pa.G = G;
+    pa.rule = fp.rule;
+    pa.thr = plan->d_table[mode];
+    pa.dp = dp;
+    pa.out = d_out;
+    pa.cap = out_capacity;
+    pa.out_count = reinterpret_cast<unsigned long long *>(d_out_count);
+    pa.stat = st;
+    pa.status = plan->d_status;
 
     HOPH_CUDA_TRY(cudaMemsetAsync(st, 0, st_b, s));
-
-    const int64_t qstride = n_queries * (int64_t)kg;
-    const int64_t cstride = n_rows * (int64_t)kg;
     hoph_timing_mark(plan, 0, s);
+    int64_t launches = 0;
+
     if (strategy == 1) {
+        // ---- join: index
         IndexArgs ia;
         ia.qry = d_query_planes;
         ia.qstride = qstride;
@@ -988,7 +1244,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         ia.kg = kg;
         ia.W = W;
         ia.mask_words = mask_words;
-        ia.binbase = plan->d_lo;
+        ia.wbits = (uint32_t)wbits;
         ia.counts = counts;
         ia.bitmap = bitmap;
         ia.q_emask = q_emask;
@@ -997,6 +1253,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         HOPH_CUDA_TRY(cudaMemsetAsync(counts, 0, (keys + 1) * 4, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(bitmap, 0, (keys / 32 + 1) * 4, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(n_allempty, 0, 4, s));
+        HOPH_CUDA_TRY(cudaMemsetAsync(n_cand, 0, 8, s));
         const unsigned qb = (unsigned)((n_queries * 32 + 255) / 256);
         join_count_kernel<<<qb, 256, 0, s>>>(ia);
         const int64_t n_scan = (int64_t)keys + 1;
@@ -1006,90 +1263,142 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         scan_apply_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, n_scan, sums, csr_off);
         join_fill_kernel<<<qb, 256, 0, s>>>(ia, csr_off, csr_q);
         HOPH_CUDA_TRY(cudaGetLastError());
-        plan->launches += 5;
-    }
+        launches += 5;
 
-    ScanArgs a;
-    a.coll = d_coll_planes;
-    a.cstride = cstride;
-    a.qry = d_query_planes;
-    a.qstride = qstride;
-    a.n_rows = n_rows;
-    a.n_q = (int32_t)n_queries;
-    a.kg = kg;
-    a.Gs = Gs;
-    a.W = W;
-    a.G = G;
-    a.rule = fp.rule;
-    a.join = strategy;
-    a.use_tma = tma_ok ? 1 : 0;
-    a.tile_rows = R;
-    a.stages = stages;
-    a.n_cons = n_cons;
-    a.n_tiles = (n_rows + R - 1) / R;
-    a.stage_bytes = (uint32_t)Gs * R * kg * 4;
-    a.stage_stride = align_up(a.stage_bytes, 128);
-    a.thr = d_thr;
-    a.dp = dp;
-    a.bitmap = bitmap;
-    a.bitmap_words = (uint32_t)(strategy == 1 ? keys / 32 + 1 : 0);
-    a.bitmap_in_smem = a.bitmap_words * 4 <= kSmemBitmapBytes;
-    a.csr_off = csr_off;
-    a.csr_q = csr_q;
-    a.binbase = plan->d_lo;
-    a.q_emask = q_emask;
-    a.mask_words = mask_words;
-    a.allempty = allempty;
-    a.n_allempty = n_allempty;
-    a.out = d_out;
-    a.cap = out_capacity;
-    a.out_count = reinterpret_cast<unsigned long long *>(d_out_count);
-    a.stat = st;
-    a.status = plan->d_status;
-
-    CUtensorMap map;
-    memset(&map, 0, sizeof map);
-    if (tma_ok) {
-        const cuuint64_t gdim[3] = {(cuuint64_t)kg, (cuuint64_t)n_rows, (cuuint64_t)Gs};
-        const cuuint64_t gstride[2] = {(cuuint64_t)kg * 4, (cuuint64_t)cstride * 4};
-        const cuuint32_t box[3] = {(cuuint32_t)kg, (cuuint32_t)R, (cuuint32_t)Gs};
-        const cuuint32_t estr[3] = {1, 1, 1};
-        const CUresult r = get_encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
-                                           (void *)d_coll_planes, gdim, gstride, box, estr,
-                                           CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                           CU_TENSOR_MAP_SWIZZLE_NONE,
-                                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            a.use_tma = 0;
-            a.stages = 1;
+        // ---- join: streaming row filter
+        FilterArgs fa;
+        fa.n_rows = n_rows;
+        fa.kg = kg;
+        fa.Gs = Gs;
+        fa.W = W;
+        fa.bitmap = bitmap;
+        fa.bitmap_words = (uint32_t)(keys / 32 + 1);
+        fa.wbits = (uint32_t)wbits;
+        fa.row_min = pa.thr + 2 * (W + 1);
+        const int K0 = hoph_effective(fp.rule, W, W, 0);
+        fa.keep_empty = table_decide(tab.data(), W, 0, K0) != HOPH_REJECT;
+        fa.cand = cand;
+        fa.n_cand = n_cand;
+        fa.status = plan->d_status;
+        // shape: consumer warps (32 rows each) and stages that fit next to
+        // the bitmap, at least two stages
+        const uint32_t fixed = 16 * 8 + 16 + align_up((W + 1) * 2, 16) +
+                               align_up((W / 4) * 4, 16) + align_up(fa.bitmap_words * 4, 128) +
+                               128;
+        int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 8;
+        int stages = plan->exec.stages > 0 ? plan->exec.stages : 3;
+        auto stage_of = [&](int nc) { return align_up((uint32_t)(32 * nc) * W * 4, 128); };
+        while (n_cons > 1 && fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit) {
+            if (stages > 2) --stages; else --n_cons;
         }
+        if (fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit)
+            return HOPH_ERR_UNSUPPORTED;
+        fa.n_cons = n_cons;
+        fa.tile_rows = 32 * n_cons;
+        fa.stages = stages;
+        fa.n_tiles = (n_rows + fa.tile_rows - 1) / fa.tile_rows;
+        fa.stage_bytes = (uint32_t)fa.tile_rows * W * 4;
+        fa.stage_stride = align_up(fa.stage_bytes, 128);
+        CUtensorMap map;
+        memset(&map, 0, sizeof map);
+        if (!encode_planes_map(&map, d_coll_planes, kg, n_rows, Gs, cstride, fa.tile_rows))
+            return HOPH_ERR_UNSUPPORTED;
+        const FilterSmem FL = filter_smem(fa);
+        HOPH_CUDA_TRY(cudaFuncSetAttribute(filter_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)FL.total));
+        const int threads = 32 * (n_cons + 1);
+        int per_sm = 0;
+        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_kernel,
+                                                                    threads, FL.total));
+        if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
+        if (plan->exec.ctas_per_sm > 0) per_sm = std::min(per_sm, plan->exec.ctas_per_sm);
+        const int64_t grid = std::min<int64_t>(fa.n_tiles, (int64_t)plan->num_sms * per_sm);
+        hoph_timing_mark(plan, 1, s);
+        filter_kernel<<<(unsigned)grid, threads, FL.total, s>>>(fa, map);
+        HOPH_CUDA_TRY(cudaGetLastError());
+        hoph_timing_mark(plan, 2, s);
+
+        // ---- join: candidate rows
+        CountArgs ca;
+        ca.p = pa;
+        ca.cand = cand;
+        ca.n_cand = n_cand;
+        ca.bitmap = bitmap;
+        ca.wbits = (uint32_t)wbits;
+        ca.csr_off = csr_off;
+        ca.csr_q = csr_q;
+        ca.q_emask = q_emask;
+        ca.mask_words = mask_words;
+        ca.allempty = allempty;
+        ca.n_allempty = n_allempty;
+        const CountSmem CL = count_smem(ca);
+        if (CL.total > (uint32_t)kSmemLimit) return HOPH_ERR_UNSUPPORTED;
+        HOPH_CUDA_TRY(cudaFuncSetAttribute(count_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)CL.total));
+        int cper = 0;
+        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper, count_kernel,
+                                                                    kCountThreads, CL.total));
+        if (cper < 1) return HOPH_ERR_UNSUPPORTED;
+        count_kernel<<<(unsigned)(plan->num_sms * cper), kCountThreads, CL.total, s>>>(ca);
+        HOPH_CUDA_TRY(cudaGetLastError());
+        hoph_timing_mark(plan, 3, s);
+        launches += 2;
+    } else {
+        // ---- dense
+        DenseArgs da;
+        da.p = pa;
+        const int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 8;
+        int R = plan->exec.tile_rows > 0 ? plan->exec.tile_rows : 0;
+        if (R == 0) {
+            R = (int)std::max<int64_t>(1, std::min<int64_t>(256, 8192 / (W * 4)));
+            if (R >= 8) R &= ~7;
+        }
+        da.n_cons = n_cons;
+        da.tile_rows = R;
+        da.use_tma = tma_base_ok ? 1 : 0;
+        da.stages = tma_base_ok ? (plan->exec.stages > 0 ? plan->exec.stages : 4) : 1;
+        da.n_tiles = (n_rows + R - 1) / R;
+        da.stage_bytes = (uint32_t)Gs * R * kg * 4;
+        da.stage_stride = align_up(da.stage_bytes, 128);
+        CUtensorMap map;
+        memset(&map, 0, sizeof map);
+        if (da.use_tma && !encode_planes_map(&map, d_coll_planes, kg, n_rows, Gs, cstride, R)) {
+            da.use_tma = 0;
+            da.stages = 1;
+        }
+        const DenseSmem DL = dense_smem(da);
+        if (DL.total > (uint32_t)kSmemLimit) return HOPH_ERR_UNSUPPORTED;
+        HOPH_CUDA_TRY(cudaFuncSetAttribute(dense_scan_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)DL.total));
+        const int threads = 32 * (n_cons + 1);
+        int per_sm = 0;
+        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_scan_kernel,
+                                                                    threads, DL.total));
+        if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
+        if (plan->exec.ctas_per_sm > 0) per_sm = std::min(per_sm, plan->exec.ctas_per_sm);
+        const int64_t grid = std::min<int64_t>(da.n_tiles, (int64_t)plan->num_sms * per_sm);
+        hoph_timing_mark(plan, 1, s);
+        dense_scan_kernel<<<(unsigned)grid, threads, DL.total, s>>>(da, map);
+        HOPH_CUDA_TRY(cudaGetLastError());
+        hoph_timing_mark(plan, 2, s);
+        hoph_timing_mark(plan, 3, s);
+        launches += 1;
     }
-    const SmemLayout L = smem_layout(a);
-    if (L.total > 227 * 1024) return HOPH_ERR_UNSUPPORTED;
-    HOPH_CUDA_TRY(
-        cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-    const int threads = 32 * (n_cons + 1);
-    int per_sm = 0;
-    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, threads, L.total));
-    if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
-    if (plan->exec.ctas_per_sm > 0) per_sm = std::min(per_sm, plan->exec.ctas_per_sm);
-    const int64_t grid = std::min<int64_t>(a.n_tiles, (int64_t)plan->num_sms * per_sm);
-    hoph_timing_mark(plan, 1, s);
-    scan_kernel<<<(unsigned)grid, threads, L.total, s>>>(a, map);
-    HOPH_CUDA_TRY(cudaGetLastError());
-    hoph_timing_mark(plan, 2, s);
 
     HOPH_CUDA_TRY(cudaFuncSetAttribute(sort_pairs_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSortSmem * 16));
-    sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(
-        d_out, a.out_count, out_capacity, sortA, sortB, plan->d_status);
+    sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(d_out, pa.out_count, out_capacity,
+                                                              sortA, sortB, plan->d_status);
     const int64_t fp_bytes = n_rows * (int64_t)W * 4 + n_queries * (int64_t)W * 4;
-    stats_fold_kernel<<<1, 32, 0, s>>>(st, n_queries * n_rows, G, Gs, fp_bytes, strategy, d_stats);
+    stats_fold_kernel<<<1, 32, 0, s>>>(st, n_cand, n_queries * n_rows, G, Gs, fp_bytes, strategy,
+                                       d_stats);
     HOPH_CUDA_TRY(cudaGetLastError());
-    hoph_timing_mark(plan, 3, s);
-    plan->launches += 3;
+    hoph_timing_mark(plan, 4, s);
+    plan->launches += launches + 2;
     return HOPH_OK;
 }
 
@@ -1106,6 +1415,7 @@ int hoph_pair_counts(hoph_plan *plan, const uint32_t *d_query_planes, int64_t n_
         d_query_planes, n_queries * kg, n_queries, d_coll_planes, n_rows * kg, n_rows, kg, G,
         d_counts);
     HOPH_CUDA_TRY(cudaGetLastError());
+    plan->launches += 1;
     return HOPH_OK;
 }
 

@@ -66,7 +66,7 @@ class hoph_stats(ctypes.Structure):
                 ("accepted", ctypes.c_int64 * HOPH_MAX_GROUPS),
                 ("rejected", ctypes.c_int64 * HOPH_MAX_GROUPS),
                 ("sketch_bytes", ctypes.c_int64), ("join_hits", ctypes.c_int64),
-                ("strategy", ctypes.c_int64), ("reserved", ctypes.c_int64)]
+                ("strategy", ctypes.c_int64), ("rows_counted", ctypes.c_int64)]
 
 
 STATS_WORDS = ctypes.sizeof(hoph_stats) // 8
@@ -257,8 +257,9 @@ def hoph_plan_enable_timing(plan, enable=True):
 
 
 def hoph_plan_read_timing(plan):
-    """Returns ([index_ms, scan_ms, tail_ms], calls, launches) and resets."""
-    ms = (ctypes.c_double * 3)()
+    """Returns ([index_ms, stream_ms, count_ms, tail_ms], calls, launches)
+    summed over the recorded calls, and resets."""
+    ms = (ctypes.c_double * 4)()
     calls = ctypes.c_int64()
     launches = ctypes.c_int64()
     _check(load().hoph_plan_read_timing(plan, ctypes.addressof(ms), ctypes.addressof(calls),
