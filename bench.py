@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-extras", action="store_true", help="skip sketch/OPH/CPU legs")
     p.add_argument("--profile", action="store_true", help="few launches, for ncu")
+    p.add_argument("--no-graph", action="store_true", help="eager launches instead of a graph")
     return p.parse_args()
 
 
@@ -279,10 +280,10 @@ def run_native(args):
     out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
 
-    def step():
-        hoph.oph_build_sketches(plan.handle, dq_ids, dq_off, nq, q_planes, stream)
+    def step(s=stream):
+        hoph.oph_build_sketches(plan.handle, dq_ids, dq_off, nq, q_planes, s)
         hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_HOPH, q_planes, nq, planes, args.rows,
-                              out, cap, cnt, None, stream)
+                              out, cap, cnt, None, s)
 
     if args.profile:
         for _ in range(max(1, args.warmup)):
@@ -303,9 +304,40 @@ def run_native(args):
     n_acc = int(cnt.item())
     pairs = out[:min(n_acc, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
 
-    # ---- timed region
-    clocks = Clocks(local)
+    # kernels one step launches (library's own count, one eager step)
     hoph.hoph_plan_enable_timing(plan.handle, True)
+    step()
+    _, _, launches_per_step = hoph.hoph_plan_read_timing(plan.handle)
+
+    # ---- the step as one CUDA graph (timing events captured inside it)
+    graph = None
+    if not args.no_graph:
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step(side)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        plan.check()
+        g_pairs = out[:min(int(cnt.item()), cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+        if int(cnt.item()) != n_acc or not np.array_equal(g_pairs, pairs):
+            raise RuntimeError("graph replay changed the result")
+
+    def run_step():
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+
+    # ---- timed region: K steps back to back
+    clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
     barrier()
@@ -313,17 +345,34 @@ def run_native(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        run_step()
     e1.record(stream)
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    phase_ms, calls, launches = hoph.hoph_plan_read_timing(plan.handle)
-    hoph.hoph_plan_enable_timing(plan.handle, False)
     plan.check()
     ms = max_over_ranks(ms)
     pairs_per_step = nq * args.rows
     value = pairs_per_step * world * args.steps / (ms / 1e3)
+
+    # ---- kernel durations: the same K steps again, reading the CUDA events
+    # recorded around each phase (inside the graph when one is used)
+    phase_ms = [0.0, 0.0, 0.0, 0.0]
+    k_time = min(args.steps, 200)
+    if graph is None:
+        hoph.hoph_plan_enable_timing(plan.handle, True)
+        for _ in range(k_time):
+            step()
+        phase_ms, calls, _ = hoph.hoph_plan_read_timing(plan.handle)
+        phase_ms = [p / max(calls, 1) for p in phase_ms]
+    else:
+        for _ in range(k_time):
+            graph.replay()
+            phase_ms = [a + b for a, b in zip(phase_ms, hoph.hoph_plan_peek_timing(plan.handle))]
+        phase_ms = [p / k_time for p in phase_ms]
+    hoph.hoph_plan_enable_timing(plan.handle, False)
+    calls = 1
+    launches = launches_per_step * args.steps
 
     peaks, peak_kind = measured_peaks()
     scan_ms = phase_ms[1] / max(calls, 1)
@@ -346,7 +395,8 @@ def run_native(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": workload_config(args, world), "roofline": roofline,
-            "gpu_launches": int(launches) + args.steps * 1,  # + one sketch kernel per step
+            "gpu_launches": int(launches),
+            "cuda_graph": graph is not None,
             "clocks": clk,
             "autotune": {"best": best, "ms_by_candidate": tune_ms},
             "stats": {"accepted": n_acc, "survivors_entering_group": list(stats.entering[:4]),

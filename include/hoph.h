@@ -132,7 +132,8 @@ typedef struct {
     int32_t consumer_warps;  /* scoring warps per CTA                     */
     int32_t ctas_per_sm;     /* resident CTAs per SM for the scan         */
     int32_t stages;          /* TMA pipeline depth                        */
-    int32_t reserved[3];
+    int32_t lanes_per_row;   /* join filter: lanes sharing one row (1-8)  */
+    int32_t reserved[2];
 } hoph_exec;
 
 typedef struct hoph_plan hoph_plan;
@@ -264,6 +265,12 @@ int hoph_synth_ids(uint64_t seed, int64_t first, int64_t n_ids, uint64_t D, uint
  */
 int hoph_plan_enable_timing(hoph_plan *plan, int enable);
 int hoph_plan_read_timing(hoph_plan *plan, double *ms, int64_t *calls, int64_t *launches);
+
+/* The four phase times of the most recently recorded call, without resetting
+ * anything: for a call captured in a CUDA graph, its events are recorded
+ * again by every replay, so this reads the latest replay (after waiting for
+ * it).  HOPH_ERR_PARAM if no call has been recorded. */
+int hoph_plan_peek_timing(hoph_plan *plan, double *ms);
 
 /* Synchronise `stream`, then return and clear the plan's device status word
  * (HOPH_OK if no device-side error was recorded). */

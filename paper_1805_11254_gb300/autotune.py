@@ -13,8 +13,9 @@ from . import hoph
 
 _cache = {}
 
-JOIN_CANDIDATES = [dict(strategy=1, consumer_warps=c, stages=s)
-                   for c, s in ((8, 2), (6, 2), (4, 4), (4, 3), (3, 4), (2, 6), (12, 1))]
+JOIN_CANDIDATES = [dict(strategy=1, lanes_per_row=l, consumer_warps=c, stages=s)
+                   for l, c, s in ((4, 16, 3), (4, 16, 2), (4, 8, 4), (2, 16, 2), (8, 16, 4),
+                                   (2, 8, 3), (1, 8, 2), (4, 12, 3))]
 DENSE_CANDIDATES = [dict(strategy=0, consumer_warps=c, stages=s, tile_rows=r)
                     for c, s, r in ((8, 4, 0), (16, 4, 0), (8, 6, 0), (4, 4, 0), (16, 2, 64))]
 

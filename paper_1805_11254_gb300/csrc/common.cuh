@@ -157,6 +157,11 @@ constexpr int kTimingMarks = 5;
 // when timing is on
 void hoph_timing_mark(hoph_plan *plan, int which, cudaStream_t s);
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device; the attribute is set only when it grows, so calls made
+// while a stream is being captured issue no attribute change once warm.
+cudaError_t hoph_ensure_smem(const void *func, int bytes);
+
 // grow-only scratch owned by the plan; returns nullptr on failure
 void *hoph_scratch(hoph_plan *plan, size_t bytes);
 

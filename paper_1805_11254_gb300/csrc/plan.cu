@@ -5,7 +5,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -271,6 +274,20 @@ int plan_create(const hoph_params *params, const uint32_t *host_perm, hoph_plan 
 
 }  // namespace
 
+cudaError_t hoph_ensure_smem(const void *func, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> set_to;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    int &cur = set_to[std::make_pair(func, dev)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 void *hoph_scratch(hoph_plan *plan, size_t bytes) {
     if (bytes <= plan->scratch_bytes) return plan->d_scratch;
     size_t want = std::max(bytes, plan->scratch_bytes * 2);
@@ -300,7 +317,14 @@ void hoph_timing_mark(hoph_plan *plan, int which, cudaStream_t s) {
         }
         plan->events.push_back(e);
     }
-    cudaEventRecord(plan->events[idx], s);
+    // while a stream is captured, only an "external" record becomes an event
+    // node of the graph (a plain record would turn into a dependency edge)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cudaGetLastError();
+    if (cap == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(plan->events[idx], s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(plan->events[idx], s);
     if (which == kTimingMarks - 1) plan->events_used += kTimingMarks;
 }
 
@@ -330,6 +354,19 @@ int hoph_plan_read_timing(hoph_plan *plan, double *ms, int64_t *calls, int64_t *
     if (launches) *launches = plan->launches;
     plan->events_used = 0;
     plan->launches = 0;
+    return HOPH_OK;
+}
+
+int hoph_plan_peek_timing(hoph_plan *plan, double *ms) {
+    if (!plan || !ms) return HOPH_ERR_PARAM;
+    if (plan->events_used < (size_t)kTimingMarks) return HOPH_ERR_PARAM;
+    const size_t b = plan->events_used - kTimingMarks;
+    HOPH_CUDA_TRY(cudaEventSynchronize(plan->events[b + kTimingMarks - 1]));
+    for (int i = 0; i < kTimingMarks - 1; ++i) {
+        float t = 0.f;
+        HOPH_CUDA_TRY(cudaEventElapsedTime(&t, plan->events[b + i], plan->events[b + i + 1]));
+        ms[i] = t;
+    }
     return HOPH_OK;
 }
 
@@ -369,7 +406,9 @@ int hoph_plan_set_exec(hoph_plan *plan, const hoph_exec *exec) {
     }
     if (exec->strategy < -1 || exec->strategy > 1 || exec->tile_rows < 0 ||
         exec->tile_rows > 256 || exec->consumer_warps < 0 || exec->consumer_warps > 16 ||
-        exec->ctas_per_sm < 0 || exec->ctas_per_sm > 8 || exec->stages < 0 || exec->stages > 8)
+        exec->ctas_per_sm < 0 || exec->ctas_per_sm > 8 || exec->stages < 0 || exec->stages > 8 ||
+        (exec->lanes_per_row != 0 && exec->lanes_per_row != 1 && exec->lanes_per_row != 2 &&
+         exec->lanes_per_row != 4 && exec->lanes_per_row != 8))
         return HOPH_ERR_PARAM;
     plan->exec = *exec;
     return HOPH_OK;

@@ -523,7 +523,8 @@ __global__ void __launch_bounds__(kScanBlock) scan_apply_kernel(const uint32_t *
 struct FilterArgs {
     int64_t n_rows;
     int32_t kg, Gs, W;
-    int32_t tile_rows, n_cons, stages;  // tile_rows = 32 * n_cons
+    int32_t tile_rows, n_cons, stages;  // tile_rows = n_cons * 32 / lanes_per_row
+    int32_t lanes_per_row;              // 1, 2, 4 or 8; divides W / 4
     int64_t n_tiles;
     uint32_t stage_bytes, stage_stride;
     const uint32_t *bitmap;
@@ -591,11 +592,17 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
         return;
     }
 
-    // consumer warp `warp` owns rows warp*32 .. warp*32+31 of every tile; each
-    // lane walks its row's 16-byte chunks starting at chunk (lane mod nchunk)
-    // so the eight lanes of a shared-memory phase touch eight different banks
-    const int rl = (warp << 5) + lane;
-    const int j0 = lane % nchunk;
+    // consumer warp `warp` owns rows_per_warp = 32 / lpr consecutive rows of
+    // every tile, lpr lanes per row, each lane nsub = nchunk / lpr 16-byte
+    // chunks of its row.  Lane (r, s) starts at chunk (r + s) mod nsub of its
+    // range so the 128-bit loads of a shared-memory phase hit distinct banks.
+    const int lpr = a.lanes_per_row;
+    const int rpw = 32 / lpr;
+    const int r_in = lane / lpr, sub = lane - r_in * lpr;
+    const int rl = warp * rpw + r_in;
+    const int nsub = nchunk / lpr;
+    const int t0 = (r_in + sub) % nsub;
+    const bool one_plane = a.Gs == 1;
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
         const int s = (int)(it % a.stages);
@@ -606,13 +613,16 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
             *abort_flag = 1;
             break;
         }
-        bool pass = false;
+        uint32_t packed = 0;  // (hits << 16) | non-empty bins, this lane's share
         if (row < a.n_rows) {
             int ne = 0, h = 0;
             const uint32_t *rp = tp + rl * a.kg;
-            int j = j0;
-            for (int step = 0; step < nchunk; ++step) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(rp + s_choff[j]);
+            int cc = t0;
+#pragma unroll 4
+            for (int step = 0; step < nsub; ++step) {
+                const int j = sub * nsub + cc;
+                const uint4 v = *reinterpret_cast<const uint4 *>(
+                    rp + (one_plane ? (j << 2) : s_choff[j]));
                 const uint32_t kb = (uint32_t)(j << 2) << a.wbits;
                 const uint32_t x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -623,12 +633,18 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
                         h += (s_bitmap[key >> 5] >> (key & 31)) & 1u;
                     }
                 }
-                if (++j == nchunk) j = 0;
+                if (++cc == nsub) cc = 0;
             }
-            pass = ne == 0 ? (a.keep_empty != 0) : (h >= (int)s_rmin[ne]);
+            packed = ((uint32_t)h << 16) | (uint32_t)ne;
         }
+        for (int o = 1; o < lpr; o <<= 1) packed += __shfl_xor_sync(0xFFFFFFFFu, packed, o);
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + s);
+        bool pass = false;
+        if (sub == 0 && row < a.n_rows) {
+            const int ne = (int)(packed & 0xFFFFu), h = (int)(packed >> 16);
+            pass = ne == 0 ? (a.keep_empty != 0) : (h >= (int)s_rmin[ne]);
+        }
         const uint32_t pm = __ballot_sync(0xFFFFFFFFu, pass);
         if (pm) {
             unsigned long long base = 0;
@@ -681,7 +697,12 @@ __device__ __forceinline__ bool key_in_bitmap(const uint32_t *bm, uint32_t key) 
     return (__ldg(bm + (key >> 5)) >> (key & 31)) & 1u;
 }
 
-__global__ void __launch_bounds__(kCountThreads) count_kernel(const __grid_constant__ CountArgs a) {
+// NCH = 32-bin chunks per row (W <= 32 * NCH).  Each lane keeps its chunks'
+// values and CSR ranges in registers between the counting and evaluation
+// passes, and the next candidate row's values are loaded while the current
+// one is counted.
+template <int NCH>
+__global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_constant__ CountArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const CountSmem L = count_smem(a);
     const PairArgs &P = a.p;
@@ -709,25 +730,44 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(const __grid_const
     Survivor *list = s_surv + warp * kSurvCap;
     uint32_t *nsurv = s_nsurv + warp;
     const uint16_t *row_min = s_thr + 2 * (P.W + 1);
-    const int nch = (P.W + 31) >> 5;
     const int n_allempty = (int)*a.n_allempty;
     // a pair of all-empty scans has M = 0 and K = the rule's effective bins
     const int d00 = table_decide(s_thr, P.W, 0, hoph_effective(P.rule, P.W, P.W, 0));
     const unsigned long long n_cand = *a.n_cand;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kCountWarps;
     unsigned long long acc0 = 0, hits = 0;
 
-    for (unsigned long long ci = (unsigned long long)blockIdx.x * kCountWarps + warp; ci < n_cand;
-         ci += (unsigned long long)gridDim.x * kCountWarps) {
+    int64_t woff[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        const int w = (c << 5) + lane;
+        woff[c] = w < P.W ? s_woff[w] : -1;
+    }
+    auto load_row = [&](unsigned long long ci, uint32_t *v) {
         const int64_t row = a.cand[ci];
         const uint32_t *rb = P.coll + row * P.kg;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) v[c] = woff[c] >= 0 ? __ldg(rb + woff[c]) : HOPH_EMPTY_VALUE;
+        return row;
+    };
+
+    unsigned long long ci = (unsigned long long)blockIdx.x * kCountWarps + warp;
+    uint32_t vn[NCH];
+    int64_t row_n = ci < n_cand ? load_row(ci, vn) : 0;
+    for (; ci < n_cand; ci += stride) {
+        uint32_t v[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) v[c] = vn[c];
+        const int64_t row = row_n;
+        if (ci + stride < n_cand) row_n = load_row(ci + stride, vn);
+
         int ne = 0;
-        for (int c = 0; c < nch; ++c) {
-            const int w = (c << 5) + lane;
-            const bool valid = w < P.W;
-            const uint32_t v = valid ? __ldg(rb + s_woff[w]) : HOPH_EMPTY_VALUE;
-            const bool fullb = valid && v != HOPH_EMPTY_VALUE;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const bool valid = woff[c] >= 0;
+            const bool fullb = valid && v[c] != HOPH_EMPTY_VALUE;
             const uint32_t em = __ballot_sync(0xFFFFFFFFu, valid && !fullb);
-            if (lane == 0) rowmask[c] = em;
+            if (lane == 0 && c < a.mask_words) rowmask[c] = em;
             ne += __popc(__ballot_sync(0xFFFFFFFFu, fullb));
         }
         if (ne == 0) {
@@ -750,46 +790,49 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(const __grid_const
             continue;
         }
         const int need = row_min[ne];
-        // counting pass: per-query match counts in the warp's counters
-        for (int c = 0; c < nch; ++c) {
-            const int w = (c << 5) + lane;
-            if (w >= P.W) continue;
-            const uint32_t v = __ldg(rb + s_woff[w]);
-            if (v == HOPH_EMPTY_VALUE) continue;
-            const uint32_t key = ((uint32_t)w << a.wbits) | v;
-            if (!key_in_bitmap(a.bitmap, key)) continue;
-            const uint32_t o1 = __ldg(a.csr_off + key), o2 = __ldg(a.csr_off + key + 1);
-            for (uint32_t i = o1; i < o2; ++i) {
+        // counting pass: bitmap and CSR ranges of every chunk, then counts
+        uint32_t o1[NCH], o2[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            o1[c] = o2[c] = 0;
+            if (woff[c] >= 0 && v[c] != HOPH_EMPTY_VALUE) {
+                const uint32_t key = ((uint32_t)((c << 5) + lane) << a.wbits) | v[c];
+                if (key_in_bitmap(a.bitmap, key)) {
+                    o1[c] = __ldg(a.csr_off + key);
+                    o2[c] = __ldg(a.csr_off + key + 1);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            for (uint32_t i = o1[c]; i < o2[c]; ++i) {
                 const uint32_t q = __ldg(a.csr_q + i);
                 atomicAdd(cnt + (q >> 1), 1u << ((q & 1) * 16));
             }
-            hits += o2 - o1;
+            hits += o2[c] - o1[c];
         }
         __syncwarp();
         // evaluation: each distinct hit query is taken by the first lane that
         // clears its counter; resumable so a full survivor list can drain
         int c = 0;
-        uint32_t i = 0, iend = 0;
+        uint32_t i = o1[0];
         bool done = false;
         while (true) {
             while (!done) {
-                if (i == iend) {
-                    bool found = false;
-                    for (; c < nch && !found; ++c) {
-                        const int w = (c << 5) + lane;
-                        if (w >= P.W) continue;
-                        const uint32_t v = __ldg(rb + s_woff[w]);
-                        if (v == HOPH_EMPTY_VALUE) continue;
-                        const uint32_t key = ((uint32_t)w << a.wbits) | v;
-                        if (!key_in_bitmap(a.bitmap, key)) continue;
-                        i = __ldg(a.csr_off + key);
-                        iend = __ldg(a.csr_off + key + 1);
-                        found = i < iend;
-                    }
-                    if (!found) {
+                // advance to the next (chunk, list entry) of this lane
+                uint32_t iend = 0;
+#pragma unroll
+                for (int cc = 0; cc < NCH; ++cc)
+                    if (cc == c) iend = o2[cc];
+                if (i >= iend) {
+                    if (++c >= NCH) {
                         done = true;
                         break;
                     }
+#pragma unroll
+                    for (int cc = 0; cc < NCH; ++cc)
+                        if (cc == c) i = o1[cc];
+                    continue;
                 }
                 const uint32_t q = __ldg(a.csr_q + i);
                 const uint32_t sh = (q & 1) * 16;
@@ -836,6 +879,18 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(const __grid_const
     }
     __syncthreads();
     if (warp == 0) flush_stats(s_stats, P.stat, lane);
+}
+
+template <int NCH>
+int launch_count(const CountArgs &ca, uint32_t smem, int num_sms, cudaStream_t s) {
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)count_kernel<NCH>, (int)smem));
+    int per = 0;
+    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, count_kernel<NCH>,
+                                                                kCountThreads, smem));
+    if (per < 1) return HOPH_ERR_UNSUPPORTED;
+    count_kernel<NCH><<<(unsigned)(num_sms * per), kCountThreads, smem, s>>>(ca);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    return HOPH_OK;
 }
 
 // ===========================================================================
@@ -1152,7 +1207,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
     const int wbits = ceil_log2_u64(std::max<uint64_t>(max_width, 2));
     const uint64_t keys = mode == HOPH_MODE_MINWISE_FULL ? ~0ull : ((uint64_t)W << wbits);
     bool join_ok = mode != HOPH_MODE_MINWISE_FULL && fp.rule != HOPH_EMPTY_EITHER &&
-                   tma_base_ok && keys <= kMaxJoinKeys && n_queries <= 4096 &&
+                   tma_base_ok && W <= 256 && keys <= kMaxJoinKeys && n_queries <= 4096 &&
                    n_rows < (1ll << 32) && keys / 8 + 2 * 32 * W * 4 + 4096 <= (uint64_t)kSmemLimit;
     for (int K = 1; K <= W && join_ok; ++K) join_ok = tab[K] >= 1;
     int strategy = plan->exec.strategy;
@@ -1280,21 +1335,24 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         fa.cand = cand;
         fa.n_cand = n_cand;
         fa.status = plan->d_status;
-        // shape: consumer warps (32 rows each) and stages that fit next to
-        // the bitmap, at least two stages
+        // shape: lanes per row, consumer warps and stages that fit next to the
+        // bitmap, at least two stages
+        int lpr = plan->exec.lanes_per_row > 0 ? plan->exec.lanes_per_row : 4;
+        while (lpr > 1 && ((W / 4) % lpr)) lpr >>= 1;
         const uint32_t fixed = 16 * 8 + 16 + align_up((W + 1) * 2, 16) +
                                align_up((W / 4) * 4, 16) + align_up(fa.bitmap_words * 4, 128) +
                                128;
-        int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 8;
+        int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 16;
         int stages = plan->exec.stages > 0 ? plan->exec.stages : 3;
-        auto stage_of = [&](int nc) { return align_up((uint32_t)(32 * nc) * W * 4, 128); };
+        auto stage_of = [&](int nc) { return align_up((uint32_t)(32 / lpr * nc) * W * 4, 128); };
         while (n_cons > 1 && fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit) {
             if (stages > 2) --stages; else --n_cons;
         }
         if (fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit)
             return HOPH_ERR_UNSUPPORTED;
+        fa.lanes_per_row = lpr;
         fa.n_cons = n_cons;
-        fa.tile_rows = 32 * n_cons;
+        fa.tile_rows = 32 / lpr * n_cons;
         fa.stages = stages;
         fa.n_tiles = (n_rows + fa.tile_rows - 1) / fa.tile_rows;
         fa.stage_bytes = (uint32_t)fa.tile_rows * W * 4;
@@ -1304,9 +1362,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         if (!encode_planes_map(&map, d_coll_planes, kg, n_rows, Gs, cstride, fa.tile_rows))
             return HOPH_ERR_UNSUPPORTED;
         const FilterSmem FL = filter_smem(fa);
-        HOPH_CUDA_TRY(cudaFuncSetAttribute(filter_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)FL.total));
+        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)filter_kernel, (int)FL.total));
         const int threads = 32 * (n_cons + 1);
         int per_sm = 0;
         HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_kernel,
@@ -1334,15 +1390,12 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         ca.n_allempty = n_allempty;
         const CountSmem CL = count_smem(ca);
         if (CL.total > (uint32_t)kSmemLimit) return HOPH_ERR_UNSUPPORTED;
-        HOPH_CUDA_TRY(cudaFuncSetAttribute(count_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)CL.total));
-        int cper = 0;
-        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper, count_kernel,
-                                                                    kCountThreads, CL.total));
-        if (cper < 1) return HOPH_ERR_UNSUPPORTED;
-        count_kernel<<<(unsigned)(plan->num_sms * cper), kCountThreads, CL.total, s>>>(ca);
-        HOPH_CUDA_TRY(cudaGetLastError());
+        const int nch = (W + 31) / 32;
+        const int rc = nch <= 1 ? launch_count<1>(ca, CL.total, plan->num_sms, s)
+                     : nch <= 2 ? launch_count<2>(ca, CL.total, plan->num_sms, s)
+                     : nch <= 4 ? launch_count<4>(ca, CL.total, plan->num_sms, s)
+                                : launch_count<8>(ca, CL.total, plan->num_sms, s);
+        if (rc != HOPH_OK) return rc;
         hoph_timing_mark(plan, 3, s);
         launches += 2;
     } else {
@@ -1370,9 +1423,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         }
         const DenseSmem DL = dense_smem(da);
         if (DL.total > (uint32_t)kSmemLimit) return HOPH_ERR_UNSUPPORTED;
-        HOPH_CUDA_TRY(cudaFuncSetAttribute(dense_scan_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)DL.total));
+        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)dense_scan_kernel, (int)DL.total));
         const int threads = 32 * (n_cons + 1);
         int per_sm = 0;
         HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_scan_kernel,
@@ -1388,9 +1439,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         launches += 1;
     }
 
-    HOPH_CUDA_TRY(cudaFuncSetAttribute(sort_pairs_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kSortSmem * 16));
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
     sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(d_out, pa.out_count, out_capacity,
                                                               sortA, sortB, plan->d_status);
     const int64_t fp_bytes = n_rows * (int64_t)W * 4 + n_queries * (int64_t)W * 4;

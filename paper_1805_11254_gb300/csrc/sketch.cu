@@ -23,6 +23,7 @@ namespace {
 constexpr int kSketchThreads = 256;
 constexpr int kSketchWarps = kSketchThreads / 32;
 constexpr int kBuckets = 65;
+constexpr int kBigBucket = 12;  // sets of >= 2048 IDs (bit length >= 12) get a whole CTA
 
 struct SketchArgs {
     const uint32_t *ids;
@@ -37,6 +38,7 @@ struct SketchArgs {
     const uint64_t *lo;    // bin bounds (hash path)
     uint64_t ha, hb;
     const int32_t *order;  // size-sorted set indices, or nullptr for 0..n-1
+    const uint32_t *n_big; // items [0, *n_big) of order are sketched a CTA per set
     int32_t *status;
 };
 
@@ -52,6 +54,75 @@ __device__ __forceinline__ uint32_t hash61(uint64_t x, uint64_t a, uint64_t b) {
     return (uint32_t)(t >> 29);
 }
 
+// One thread's share of the IDs [p, p+n) (thread t of a group of T threads):
+// a scalar head up to a 16-byte boundary, a 128-bit body whose eight table
+// gathers are issued before any of their minima is applied, a scalar tail.
+// Each ID updates the shared sketch `sk` with a read-then-atomicMin.
+template <bool HASH>
+__device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *s_lo,
+                                           uint32_t *sk, const uint32_t *p, int64_t n, int t,
+                                           int T, bool &bad) {
+    const uint32_t mask = a.key_bits >= 32 ? 0xFFFFFFFFu : ((1u << a.key_bits) - 1u);
+    // psi-value of x as (bin << 32) | offset; bin k marks an ID outside V
+    auto locate = [&](uint32_t x) -> uint64_t {
+        if (HASH) {
+            const uint32_t v = hash61(x, a.ha, a.hb);
+            uint32_t l = 0, h = a.k;  // lo[l] <= v < lo[h]
+            while (h - l > 1) {
+                const uint32_t m = (l + h) >> 1;
+                if (s_lo[m] <= v) l = m; else h = m;
+            }
+            return ((uint64_t)l << 32) | (uint32_t)(v - s_lo[l]);
+        } else {
+            if (x >= a.D) return (uint64_t)a.k << 32;
+            const uint32_t key = __ldg(a.key + x);
+            return ((uint64_t)(uint32_t)((uint64_t)key >> a.key_bits) << 32) | (key & mask);
+        }
+    };
+    auto apply = [&](uint64_t bo) {
+        const uint32_t bin = (uint32_t)(bo >> 32), off = (uint32_t)bo;
+        if (bin >= a.k) {
+            bad = true;
+            return;
+        }
+        if (off < sk[bin]) atomicMin(sk + bin, off);
+    };
+    const int64_t head =
+        (int64_t)min((long long)n, (long long)((4 - ((reinterpret_cast<uintptr_t>(p) >> 2) & 3)) & 3));
+    if (t < head) apply(locate(p[t]));
+    const uint4 *p4 = reinterpret_cast<const uint4 *>(p + head);
+    const int64_t nvec = (n - head) >> 2;
+    int64_t i = t;
+    for (; i + T < nvec; i += 2 * (int64_t)T) {
+        const uint4 v0 = ldg_nc_v4(p4 + i);
+        const uint4 v1 = ldg_nc_v4(p4 + i + T);
+        const uint64_t b0 = locate(v0.x), b1 = locate(v0.y), b2 = locate(v0.z), b3 = locate(v0.w);
+        const uint64_t b4 = locate(v1.x), b5 = locate(v1.y), b6 = locate(v1.z), b7 = locate(v1.w);
+        apply(b0); apply(b1); apply(b2); apply(b3);
+        apply(b4); apply(b5); apply(b6); apply(b7);
+    }
+    if (i < nvec) {
+        const uint4 v0 = ldg_nc_v4(p4 + i);
+        const uint64_t b0 = locate(v0.x), b1 = locate(v0.y), b2 = locate(v0.z), b3 = locate(v0.w);
+        apply(b0); apply(b1); apply(b2); apply(b3);
+    }
+    const int64_t tail0 = head + (nvec << 2);
+    for (int64_t j = tail0 + t; j < n; j += T) apply(locate(p[j]));
+}
+
+// group-major store of one finished sketch (bin b -> plane b / k', slot b % k')
+// and reset of the shared copy
+__device__ __forceinline__ void store_sketch(const SketchArgs &a, uint32_t *sk, int64_t set, int t,
+                                             int T) {
+    for (uint32_t b = t; b < a.k; b += T) {
+        const uint32_t g = b / a.kg, j = b - g * a.kg;
+        a.planes[(int64_t)g * a.plane_stride + set * a.kg + j] = sk[b];
+        sk[b] = HOPH_EMPTY_VALUE;
+    }
+}
+
+// Warp per set over work-list items [first, n_sets), first = *n_big (the
+// large sets handled by oph_sketch_big_kernel) or 0.
 template <bool HASH>
 __global__ void __launch_bounds__(kSketchThreads) oph_sketch_kernel(const SketchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -63,65 +134,41 @@ __global__ void __launch_bounds__(kSketchThreads) oph_sketch_kernel(const Sketch
         for (uint32_t i = threadIdx.x; i <= a.k; i += blockDim.x) s_lo[i] = a.lo[i];
     for (uint32_t i = lane; i < a.k; i += 32) sk[i] = HOPH_EMPTY_VALUE;
     __syncthreads();
-
-    const uint32_t mask = a.key_bits >= 32 ? 0xFFFFFFFFu : ((1u << a.key_bits) - 1u);
     bool bad = false;
-    auto take = [&](uint32_t x) {
-        uint32_t bin, off;
-        if (HASH) {
-            const uint32_t v = hash61(x, a.ha, a.hb);
-            uint32_t l = 0, h = a.k;  // lo[l] <= v < lo[h]
-            while (h - l > 1) {
-                const uint32_t m = (l + h) >> 1;
-                if (s_lo[m] <= v) l = m; else h = m;
-            }
-            bin = l;
-            off = (uint32_t)(v - s_lo[l]);
-        } else {
-            if (x >= a.D) {
-                bad = true;
-                return;
-            }
-            const uint32_t key = __ldg(a.key + x);
-            bin = (uint32_t)((uint64_t)key >> a.key_bits);
-            off = key & mask;
-        }
-        if (off < sk[bin]) atomicMin(sk + bin, off);
-    };
-
+    const int64_t first = a.n_big ? (int64_t)*a.n_big : 0;
     const int64_t warps_total = (int64_t)gridDim.x * kSketchWarps;
-    for (int64_t item = (int64_t)blockIdx.x * kSketchWarps + warp; item < a.n_sets;
+    for (int64_t item = first + (int64_t)blockIdx.x * kSketchWarps + warp; item < a.n_sets;
          item += warps_total) {
         const int64_t set = a.order ? a.order[item] : item;
         const int64_t beg = a.off[set], end = a.off[set + 1];
-        const int64_t n = end - beg;
-        const uint32_t *p = a.ids + beg;
-        // scalar head up to a 16-byte boundary, 128-bit body, scalar tail
-        const int64_t head = (int64_t)min((long long)n, (long long)((4 - ((reinterpret_cast<uintptr_t>(p) >> 2) & 3)) & 3));
-        if (lane < head) take(p[lane]);
-        const uint4 *p4 = reinterpret_cast<const uint4 *>(p + head);
-        const int64_t nvec = (n - head) >> 2;
-        int64_t i = lane;
-        for (; i + 32 < nvec; i += 64) {
-            const uint4 v0 = ldg_nc_v4(p4 + i);
-            const uint4 v1 = ldg_nc_v4(p4 + i + 32);
-            take(v0.x); take(v0.y); take(v0.z); take(v0.w);
-            take(v1.x); take(v1.y); take(v1.z); take(v1.w);
-        }
-        if (i < nvec) {
-            const uint4 v0 = ldg_nc_v4(p4 + i);
-            take(v0.x); take(v0.y); take(v0.z); take(v0.w);
-        }
-        const int64_t tail0 = head + (nvec << 2);
-        if (tail0 + lane < n) take(p[tail0 + lane]);
+        sketch_ids<HASH>(a, s_lo, sk, a.ids + beg, end - beg, lane, 32, bad);
         __syncwarp();
-        // group-major store: bin b -> plane b / k', position b % k'
-        for (uint32_t b = lane; b < a.k; b += 32) {
-            const uint32_t g = b / a.kg, j = b - g * a.kg;
-            a.planes[(int64_t)g * a.plane_stride + set * a.kg + j] = sk[b];
-            sk[b] = HOPH_EMPTY_VALUE;
-        }
+        store_sketch(a, sk, set, lane, 32);
         __syncwarp();
+    }
+    if (bad) hoph_flag(a.status, HOPH_ERR_ID_RANGE);
+}
+
+// CTA per set for the large sets at the head of the size-sorted work list
+// (items [0, *n_big)): all warps feed one shared sketch.
+template <bool HASH>
+__global__ void __launch_bounds__(kSketchThreads) oph_sketch_big_kernel(const SketchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *s_lo = reinterpret_cast<uint64_t *>(smem_raw);  // HASH only
+    uint32_t *sk = reinterpret_cast<uint32_t *>(smem_raw + (HASH ? (a.k + 1) * 8 : 0));
+    if (HASH)
+        for (uint32_t i = threadIdx.x; i <= a.k; i += blockDim.x) s_lo[i] = a.lo[i];
+    for (uint32_t i = threadIdx.x; i < a.k; i += blockDim.x) sk[i] = HOPH_EMPTY_VALUE;
+    __syncthreads();
+    bool bad = false;
+    const int64_t n_big = (int64_t)*a.n_big;
+    for (int64_t item = blockIdx.x; item < n_big; item += gridDim.x) {
+        const int64_t set = a.order[item];
+        const int64_t beg = a.off[set], end = a.off[set + 1];
+        sketch_ids<HASH>(a, s_lo, sk, a.ids + beg, end - beg, threadIdx.x, blockDim.x, bad);
+        __syncthreads();
+        store_sketch(a, sk, set, threadIdx.x, blockDim.x);
+        __syncthreads();
     }
     if (bad) hoph_flag(a.status, HOPH_ERR_ID_RANGE);
 }
@@ -142,11 +189,13 @@ __global__ void bucket_hist_kernel(const int64_t *off, int64_t n, uint32_t *hist
         if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-// exclusive prefix over buckets in descending size order (largest first)
-__global__ void bucket_base_kernel(const uint32_t *hist, uint32_t *base) {
+// exclusive prefix over buckets in descending size order (largest first);
+// *n_big = number of sets in the buckets that get a CTA each
+__global__ void bucket_base_kernel(const uint32_t *hist, uint32_t *base, uint32_t *n_big) {
     if (threadIdx.x == 0) {
         uint32_t run = 0;
         for (int b = kBuckets - 1; b >= 0; --b) {
+            if (b == kBigBucket - 1) *n_big = run;
             base[b] = run;
             run += hist[b];
         }
@@ -233,16 +282,8 @@ __global__ void synth_ids_kernel(uint64_t seed, int64_t first, int64_t n, uint64
 
 int grid_for(hoph_plan *pl, int per_sm) { return pl->num_sms * per_sm; }
 
-}  // namespace
-
-extern "C" {
-
-int oph_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
-                       int64_t n_sets, uint32_t *d_planes, void *stream) {
-    if (!plan || n_sets < 0 || (n_sets > 0 && (!d_offsets || !d_planes))) return HOPH_ERR_PARAM;
-    if (n_sets >= (1ll << 31)) return HOPH_ERR_PARAM;
-    if (n_sets == 0) return HOPH_OK;
-    cudaStream_t s = (cudaStream_t)stream;
+SketchArgs sketch_args(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
+                       int64_t n_sets, uint32_t *d_planes) {
     const hoph_params &P = plan->P;
     SketchArgs a;
     a.ids = d_ids;
@@ -259,48 +300,88 @@ int oph_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_
     a.ha = plan->hash_a;
     a.hb = plan->hash_b;
     a.order = nullptr;
+    a.n_big = nullptr;
     a.status = plan->d_status;
+    return a;
+}
 
-    const bool hash = P.perm_kind == HOPH_PERM_HASH61;
-    const size_t smem = (hash ? (P.k + 1) * 8 : 0) + (size_t)kSketchWarps * P.k * 4;
-    int per_sm = 0;
-    if (hash) {
-        HOPH_CUDA_TRY(cudaFuncSetAttribute(oph_sketch_kernel<true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oph_sketch_kernel<true>,
-                                                                    kSketchThreads, smem));
-    } else {
-        HOPH_CUDA_TRY(cudaFuncSetAttribute(oph_sketch_kernel<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+// Size-sorted work list in `wl` (hist, base, cursor: kBuckets words each,
+// then n_big, then the order of n_sets entries); hist and cursor are zeroed.
+int build_work_list(hoph_plan *plan, const int64_t *d_offsets, int64_t n_sets, uint32_t *wl,
+                    SketchArgs &a, cudaStream_t s) {
+    uint32_t *hist = wl, *base = hist + kBuckets, *cursor = base + kBuckets;
+    uint32_t *n_big = cursor + kBuckets;
+    int32_t *order = reinterpret_cast<int32_t *>(n_big + 1);
+    HOPH_CUDA_TRY(cudaMemsetAsync(hist, 0, kBuckets * sizeof(uint32_t), s));
+    HOPH_CUDA_TRY(cudaMemsetAsync(cursor, 0, kBuckets * sizeof(uint32_t), s));
+    const int g = plan->num_sms * 4;
+    bucket_hist_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, hist);
+    bucket_base_kernel<<<1, 32, 0, s>>>(hist, base, n_big);
+    bucket_scatter_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, base, cursor, order);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    plan->launches += 3;
+    a.order = order;
+    a.n_big = n_big;
+    return HOPH_OK;
+}
+
+// The large-set (CTA per set) and warp-per-set kernels over the work list.
+template <bool HASH>
+int launch_sketch_kernels(hoph_plan *plan, const SketchArgs &a, cudaStream_t s) {
+    const uint32_t k = a.k;
+    const size_t lo_b = HASH ? (size_t)(k + 1) * 8 : 0;
+    const size_t smem_w = lo_b + (size_t)kSketchWarps * k * 4;
+    const size_t smem_b = lo_b + (size_t)k * 4;
+    if (a.n_big) {
+        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)oph_sketch_big_kernel<HASH>, (int)smem_b));
+        int per = 0;
         HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, oph_sketch_kernel<false>, kSketchThreads, smem));
+            &per, oph_sketch_big_kernel<HASH>, kSketchThreads, smem_b));
+        if (per < 1) return HOPH_ERR_UNSUPPORTED;
+        const int64_t blocks = std::min<int64_t>(a.n_sets, (int64_t)grid_for(plan, per));
+        oph_sketch_big_kernel<HASH><<<(unsigned)blocks, kSketchThreads, smem_b, s>>>(a);
+        HOPH_CUDA_TRY(cudaGetLastError());
+        plan->launches += 1;
     }
-    if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
-    const int64_t resident = (int64_t)grid_for(plan, per_sm) * kSketchWarps;
-    // size-sorted work list once there are several sets per resident warp
-    if (n_sets > 2 * resident) {
-        const size_t bytes = 3 * kBuckets * sizeof(uint32_t) + (size_t)n_sets * sizeof(int32_t);
-        unsigned char *scr = (unsigned char *)hoph_scratch(plan, bytes);
-        if (!scr) return HOPH_ERR_NOMEM;
-        uint32_t *hist = (uint32_t *)scr, *base = hist + kBuckets, *cursor = base + kBuckets;
-        int32_t *order = (int32_t *)(cursor + kBuckets);
-        HOPH_CUDA_TRY(cudaMemsetAsync(hist, 0, 3 * kBuckets * sizeof(uint32_t), s));
-        const int g = plan->num_sms * 4;
-        bucket_hist_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, hist);
-        bucket_base_kernel<<<1, 32, 0, s>>>(hist, base);
-        bucket_scatter_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, base, cursor, order);
-        a.order = order;
-        plan->launches += 3;
-    }
-    int64_t blocks = std::min<int64_t>((n_sets + kSketchWarps - 1) / kSketchWarps,
-                                       (int64_t)grid_for(plan, per_sm));
-    if (hash)
-        oph_sketch_kernel<true><<<(unsigned)blocks, kSketchThreads, smem, s>>>(a);
-    else
-        oph_sketch_kernel<false><<<(unsigned)blocks, kSketchThreads, smem, s>>>(a);
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)oph_sketch_kernel<HASH>, (int)smem_w));
+    int per = 0;
+    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oph_sketch_kernel<HASH>,
+                                                                kSketchThreads, smem_w));
+    if (per < 1) return HOPH_ERR_UNSUPPORTED;
+    const int64_t blocks = std::min<int64_t>((a.n_sets + kSketchWarps - 1) / kSketchWarps,
+                                             (int64_t)grid_for(plan, per));
+    oph_sketch_kernel<HASH><<<(unsigned)blocks, kSketchThreads, smem_w, s>>>(a);
     HOPH_CUDA_TRY(cudaGetLastError());
     plan->launches += 1;
     return HOPH_OK;
+}
+
+int launch_sketch(hoph_plan *plan, const SketchArgs &a, cudaStream_t s) {
+    return plan->P.perm_kind == HOPH_PERM_HASH61 ? launch_sketch_kernels<true>(plan, a, s)
+                                                 : launch_sketch_kernels<false>(plan, a, s);
+}
+
+constexpr int64_t kWorkListMin = 64;  // below this many sets: identity order, warps only
+
+}  // namespace
+
+extern "C" {
+
+int oph_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
+                       int64_t n_sets, uint32_t *d_planes, void *stream) {
+    if (!plan || n_sets < 0 || (n_sets > 0 && (!d_offsets || !d_planes))) return HOPH_ERR_PARAM;
+    if (n_sets >= (1ll << 31)) return HOPH_ERR_PARAM;
+    if (n_sets == 0) return HOPH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    SketchArgs a = sketch_args(plan, d_ids, d_offsets, n_sets, d_planes);
+    if (n_sets >= kWorkListMin) {
+        const size_t bytes = (3 * kBuckets + 1) * sizeof(uint32_t) + (size_t)n_sets * sizeof(int32_t);
+        uint32_t *wl = (uint32_t *)hoph_scratch(plan, bytes);
+        if (!wl) return HOPH_ERR_NOMEM;
+        const int rc = build_work_list(plan, d_offsets, n_sets, wl, a, s);
+        if (rc != HOPH_OK) return rc;
+    }
+    return launch_sketch(plan, a, s);
 }
 
 int minwise_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
@@ -318,8 +399,7 @@ int minwise_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t
     a.out = d_sketches;
     a.status = plan->d_status;
     const size_t smem = (size_t)8 * a.mk * 4;
-    HOPH_CUDA_TRY(
-        cudaFuncSetAttribute(minwise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)minwise_kernel, (int)smem));
     const int64_t blocks = std::min<int64_t>((n_sets + 7) / 8, (int64_t)plan->num_sms * 8);
     minwise_kernel<<<(unsigned)blocks, 256, smem, (cudaStream_t)stream>>>(a);
     HOPH_CUDA_TRY(cudaGetLastError());
@@ -356,10 +436,10 @@ int hoph_synth_ids(uint64_t seed, int64_t first, int64_t n_ids, uint64_t D, uint
 namespace {
 
 constexpr int64_t kStaticMaxSets = 1 << 18;  // sets per call (262,144)
-constexpr size_t kStaticWords = 3 * kBuckets + (size_t)kStaticMaxSets;
+constexpr size_t kStaticWords = 3 * kBuckets + 1 + (size_t)kStaticMaxSets;
 
-// Bucket histogram, bucket bases, bucket cursors, then the set order: about
-// 1 MiB.  One copy per GPU that loads the library, kept until the process
+// Bucket histogram, bucket bases, bucket cursors, the large-set count, then
+// the set order: about 1 MiB.  One copy per GPU that loads the library, kept until the process
 // exits, shared by every call on that GPU.
 static __device__ __align__(256) uint32_t g_static_worklist[kStaticWords];
 
@@ -398,55 +478,11 @@ extern "C" int oph_build_sketches_static(hoph_plan *plan, const uint32_t *d_ids,
     const int rc = static_worklist(&scr);
     if (rc != HOPH_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    const hoph_params &P = plan->P;
-    SketchArgs a;
-    a.ids = d_ids;
-    a.off = d_offsets;
-    a.n_sets = n_sets;
-    a.planes = d_planes;
-    a.plane_stride = n_sets * (int64_t)P.k_group;
-    a.k = P.k;
-    a.kg = P.k_group;
-    a.key = plan->d_key;
-    a.key_bits = plan->key_bits;
-    a.D = P.universe_D;
-    a.lo = plan->d_lo;
-    a.ha = plan->hash_a;
-    a.hb = plan->hash_b;
-    a.status = plan->d_status;
-    // the array keeps the previous call's contents: the histogram and the
-    // cursors must start at zero (the bases and the order are overwritten)
-    uint32_t *hist = scr, *base = hist + kBuckets, *cursor = base + kBuckets;
-    int32_t *order = reinterpret_cast<int32_t *>(cursor + kBuckets);
-    HOPH_CUDA_TRY(cudaMemsetAsync(hist, 0, kBuckets * sizeof(uint32_t), s));
-    HOPH_CUDA_TRY(cudaMemsetAsync(cursor, 0, kBuckets * sizeof(uint32_t), s));
-    const int g = plan->num_sms * 4;
-    bucket_hist_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, hist);
-    bucket_base_kernel<<<1, 32, 0, s>>>(hist, base);
-    bucket_scatter_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, base, cursor, order);
-    a.order = order;
-
-    const bool hash = P.perm_kind == HOPH_PERM_HASH61;
-    const size_t smem = (hash ? (P.k + 1) * 8 : 0) + (size_t)kSketchWarps * P.k * 4;
-    int per_sm = 0;
-    if (hash) {
-        HOPH_CUDA_TRY(cudaFuncSetAttribute(oph_sketch_kernel<true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oph_sketch_kernel<true>,
-                                                                    kSketchThreads, smem));
-    } else {
-        HOPH_CUDA_TRY(cudaFuncSetAttribute(oph_sketch_kernel<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, oph_sketch_kernel<false>, kSketchThreads, smem));
-    }
-    if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
-    const int64_t blocks = std::min<int64_t>((n_sets + kSketchWarps - 1) / kSketchWarps,
-                                             (int64_t)grid_for(plan, per_sm));
-    if (hash)
-        oph_sketch_kernel<true><<<(unsigned)blocks, kSketchThreads, smem, s>>>(a);
-    else
-        oph_sketch_kernel<false><<<(unsigned)blocks, kSketchThreads, smem, s>>>(a);
-    HOPH_CUDA_TRY(cudaGetLastError());
-    return HOPH_OK;
+    SketchArgs a = sketch_args(plan, d_ids, d_offsets, n_sets, d_planes);
+    // the array keeps the previous call's contents: build_work_list zeroes the
+    // histogram and the cursors (the bases, the count and the order are
+    // overwritten)
+    const int rc2 = build_work_list(plan, d_offsets, n_sets, scr, a, s);
+    if (rc2 != HOPH_OK) return rc2;
+    return launch_sketch(plan, a, s);
 }

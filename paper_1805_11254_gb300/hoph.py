@@ -81,7 +81,8 @@ class hoph_plan_info(ctypes.Structure):
 class hoph_exec(ctypes.Structure):
     _fields_ = [("strategy", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
                 ("consumer_warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("stages", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("stages", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class HophError(RuntimeError):
@@ -95,7 +96,7 @@ _EXPORTS = ["hoph_plan_create", "hoph_plan_create_with_perm", "hoph_plan_destroy
             "hoph_plan_get_info", "hoph_plan_set_exec", "oph_build_sketches",
             "minwise_build_sketches", "hoph_query_batch", "hoph_pair_counts", "hoph_synth_ids",
             "hoph_sync_status", "hoph_status_string", "hoph_plan_enable_timing",
-            "hoph_plan_read_timing", "oph_build_sketches_static"]
+            "hoph_plan_read_timing", "oph_build_sketches_static", "hoph_plan_peek_timing"]
 
 
 def load(path=LIB_PATH):
@@ -137,6 +138,8 @@ def load(path=LIB_PATH):
     lib.hoph_plan_enable_timing.restype = i32
     lib.hoph_plan_read_timing.argtypes = [P, P, P, P]
     lib.hoph_plan_read_timing.restype = i32
+    lib.hoph_plan_peek_timing.argtypes = [P, P]
+    lib.hoph_plan_peek_timing.restype = i32
     lib.hoph_status_string.argtypes = [i32]
     lib.hoph_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -267,6 +270,13 @@ def hoph_plan_read_timing(plan):
     return list(ms), calls.value, launches.value
 
 
+def hoph_plan_peek_timing(plan):
+    """Phase times (ms) of the most recently recorded call, no reset."""
+    ms = (ctypes.c_double * 4)()
+    _check(load().hoph_plan_peek_timing(plan, ctypes.addressof(ms)), "hoph_plan_peek_timing")
+    return list(ms)
+
+
 def hoph_sync_status(plan, stream=None):
     """Synchronise and return (and clear) the plan's device status word."""
     return load().hoph_sync_status(plan, _stream(stream))
@@ -308,9 +318,10 @@ class Plan:
     def __exit__(self, *exc):
         self.close()
 
-    def set_exec(self, strategy=-1, tile_rows=0, consumer_warps=0, ctas_per_sm=0, stages=0):
+    def set_exec(self, strategy=-1, tile_rows=0, consumer_warps=0, ctas_per_sm=0, stages=0,
+                 lanes_per_row=0):
         hoph_plan_set_exec(self.handle, hoph_exec(strategy, tile_rows, consumer_warps,
-                                                  ctas_per_sm, stages))
+                                                  ctas_per_sm, stages, lanes_per_row))
 
     def check(self, stream=None):
         rc = hoph_sync_status(self.handle, stream)

@@ -215,3 +215,20 @@ def test_identical_sets_always_accepted(small):
         pairs, n, _ = plan.query("hoph", d, 300, d, 300)
         got = {(int(p["query"]), int(p["row"])) for p in pairs}
         assert {(i, i) for i in range(300)} <= got
+
+
+@pytest.mark.parametrize("lpr,warps,stages", [(1, 8, 2), (2, 16, 2), (4, 16, 3), (8, 16, 4),
+                                              (4, 3, 5)])
+def test_join_execution_knobs_do_not_change_results(small, lpr, warps, stages):
+    """Lanes per row, consumer warps and pipeline depth of the join filter
+    are scheduling only: the accepted pairs stay the oracle's."""
+    dev = device()
+    D, k, kg = small["D"], 128, 32
+    with hoph.Plan(D, k, kg, 1, 2, seed=1, thr=T, epsilon=EPS) as plan:
+        q, c = _sketch_both(plan, small, dev)
+        z = [plan.info.group_size[g] for g in range(plan.G)]
+        want = _oracle_query("hoph", planes_to_rows(q), planes_to_rows(c), kg, z)
+        plan.set_exec(strategy=1, lanes_per_row=lpr, consumer_warps=warps, stages=stages)
+        pairs, n, st = plan.query("hoph", q, q.shape[1], c, c.shape[1], stats=True)
+        assert pairs_tuples(pairs) == oracle_tuples(want)
+        assert st.strategy == 1 and st.rows_counted < c.shape[1]

@@ -154,3 +154,30 @@ def test_synth_ids_match_host_twin(kind):
         want = synth.counter_zipf_ids(seed, first, n, cdf)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("hash_perm", [False, True])
+def test_large_sets_take_the_cta_path(hash_perm):
+    """With a work list (>= 64 sets), sets of >= 2048 IDs are sketched by a
+    whole CTA; the result must not depend on which path a set took."""
+    dev = device()
+    rng = np.random.default_rng(12)
+    big = [2047, 2048, 2049, 4096, 5000, 30001, 100000]
+    sizes = big + list(rng.integers(0, 300, 90)) + [0, 1, 3]
+    rng.shuffle(sizes)
+    if hash_perm:
+        D, k, kg, ab = 1 << 32, 512, 128, (2, 1)
+        sets = [rng.integers(0, 1 << 32, s, dtype=np.uint64).astype(np.uint32) for s in sizes]
+    else:
+        D, k, kg, ab = 1 << 20, 256, 64, (1, 2)
+        sets = [rng.integers(0, D, s).astype(np.uint32) for s in sizes]
+    ids, off = synth.pack_sets(sets)
+    kind = hoph.HOPH_PERM_HASH61 if hash_perm else hoph.HOPH_PERM_TABLE
+    with hoph.Plan(D, k, kg, *ab, perm_kind=kind, seed=3) as plan:
+        got = _gpu_sketch(plan, ids, off, dev)
+    lo = oc.layout(D, k, kg, *ab)
+    if hash_perm:
+        want = oc.sketch(ids, off, lo, D=D, hash_ab=oc.hash_params(3))
+    else:
+        want = oc.sketch(ids, off, lo, perm=oc.permutation(D, 3))
+    assert np.array_equal(got, want)
