@@ -10,16 +10,19 @@
 //          matched / both-empty / one-empty counts.  Cheap for a handful of
 //          queries, ALU-bound for large batches.
 // join   - an exact value join for large batches, in three parts:
-//          (1) an index of the batch's first-group query values: a bitmap and
-//              CSR lists over padded keys (bin << wbits) | value;
-//          (2) a streaming filter: TMA tiles of the first plane, one lane per
-//              row, every row value tested against the bitmap in shared
+//          (1) an index of the batch's first-group query values over the
+//              keys lo[bin] + value (the value's position in psi-space): CSR
+//              lists of queries per key, and a 2-bit map recording whether an
+//              even- and whether an odd-numbered query has the key;
+//          (2) a streaming filter: TMA tiles of the first plane, a few lanes
+//              per row, every row value looked up in the map in shared
 //              memory.  A pair's match count is at most the row's number of
-//              bitmap hits and its denominator at least the row's number of
-//              non-empty bins, so a row whose hit count is below the smallest
-//              rejection threshold over the denominators it allows is
-//              rejected against every query; the other rows are compacted
-//              into a candidate list;
+//              hits in the map of the query's parity group, and its
+//              denominator at least the row's number of non-empty bins, so a
+//              row whose hits in both groups are below the smallest rejection
+//              threshold over the denominators it allows is rejected against
+//              every query; the other rows are compacted into a candidate
+//              list;
 //          (3) a counting kernel over the candidates: per-query match counts
 //              from the CSR lists in per-warp shared-memory counters, then the
 //              exact first-group decision for each query the row met.
@@ -393,15 +396,15 @@ struct IndexArgs {
     const uint32_t *qry;
     int64_t qstride;
     int32_t n_q, kg, W, mask_words;
-    uint32_t wbits;      // key = (w << wbits) | value
+    const uint64_t *binbase;  // key = lo[w] + value
     uint32_t *counts;    // [keys + 1]
-    uint32_t *bitmap;
+    uint32_t *gmap;      // 2 bits per key: an even / an odd query has it
     uint32_t *q_emask;   // [n_q][mask_words]
     int32_t *allempty;
     uint32_t *n_allempty;
 };
 
-// warp per query: empty masks, all-empty list, key counts and the bitmap
+// warp per query: empty masks, all-empty list, key counts and the group map
 __global__ void join_count_kernel(const IndexArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -421,9 +424,9 @@ __global__ void join_count_kernel(const IndexArgs a) {
         all_empty = all_empty && em == vm;
         if (lane == 0) a.q_emask[q * a.mask_words + c] = em;
         if (valid && !e) {
-            const uint32_t key = ((uint32_t)w << a.wbits) | v;
+            const uint32_t key = (uint32_t)a.binbase[w] + v;
             atomicAdd(a.counts + key, 1u);
-            atomicOr(a.bitmap + (key >> 5), 1u << (key & 31));
+            atomicOr(a.gmap + (key >> 4), 1u << (((key & 15u) << 1) | ((uint32_t)q & 1u)));
         }
     }
     if (lane == 0 && all_empty) a.allempty[atomicAdd(a.n_allempty, 1u)] = (int32_t)q;
@@ -437,7 +440,7 @@ __global__ void join_fill_kernel(const IndexArgs a, const uint32_t *csr_off, uin
         const int g = w / a.kg, b = w - g * a.kg;
         const uint32_t v = a.qry[(int64_t)g * a.qstride + q * a.kg + b];
         if (v == HOPH_EMPTY_VALUE) continue;
-        const uint32_t key = ((uint32_t)w << a.wbits) | v;
+        const uint32_t key = (uint32_t)a.binbase[w] + v;
         const uint32_t pos = csr_off[key] + atomicSub(a.counts + key, 1u) - 1u;
         csr_q[pos] = (uint16_t)q;
     }
@@ -527,9 +530,9 @@ struct FilterArgs {
     int32_t lanes_per_row;              // 1, 2, 4 or 8; divides W / 4
     int64_t n_tiles;
     uint32_t stage_bytes, stage_stride;
-    const uint32_t *bitmap;
-    uint32_t bitmap_words;
-    uint32_t wbits;
+    const uint32_t *gmap;     // 2-bit group map over the keys
+    uint32_t gmap_words;
+    const uint64_t *binbase;  // key = lo[w] + value
     const uint16_t *row_min;  // [W + 1]
     int32_t keep_empty;       // rows without a non-empty scanned bin are candidates
     uint32_t *cand;
@@ -538,7 +541,7 @@ struct FilterArgs {
 };
 
 struct FilterSmem {
-    uint32_t bars, abort_flag, row_min, choff, bitmap, stages, total;
+    uint32_t bars, abort_flag, row_min, choff, binb, gmap, stages, total;
 };
 
 __host__ __device__ inline FilterSmem filter_smem(const FilterArgs &a) {
@@ -548,7 +551,8 @@ __host__ __device__ inline FilterSmem filter_smem(const FilterArgs &a) {
     L.abort_flag = o; o += 16;
     L.row_min = o;    o = align_up(o + (a.W + 1) * 2, 16);
     L.choff = o;      o = align_up(o + (a.W / 4) * 4, 16);
-    L.bitmap = o;     o = align_up(o + a.bitmap_words * 4, 128);
+    L.binb = o;       o = align_up(o + a.W * 4, 16);
+    L.gmap = o;       o = align_up(o + a.gmap_words * 4, 128);
     L.stages = o;     o += a.stages * a.stage_stride;
     L.total = o;
     return L;
@@ -563,7 +567,8 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
     volatile int32_t *abort_flag = reinterpret_cast<volatile int32_t *>(smem + L.abort_flag);
     uint16_t *s_rmin = reinterpret_cast<uint16_t *>(smem + L.row_min);
     int32_t *s_choff = reinterpret_cast<int32_t *>(smem + L.choff);
-    uint32_t *s_bitmap = reinterpret_cast<uint32_t *>(smem + L.bitmap);
+    uint32_t *s_binb = reinterpret_cast<uint32_t *>(smem + L.binb);
+    uint32_t *s_gmap = reinterpret_cast<uint32_t *>(smem + L.gmap);
     unsigned char *stages = smem + L.stages;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -574,7 +579,8 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
         const int w = j << 2, g = w / a.kg, b = w - g * a.kg;
         s_choff[j] = (g * R) * a.kg + b;  // element offset of chunk j in row 0 of a tile
     }
-    for (uint32_t i = tid; i < a.bitmap_words; i += blockDim.x) s_bitmap[i] = a.bitmap[i];
+    for (int w = tid; w < a.W; w += blockDim.x) s_binb[w] = (uint32_t)a.binbase[w];
+    for (uint32_t i = tid; i < a.gmap_words; i += blockDim.x) s_gmap[i] = a.gmap[i];
     if (tid == 0) {
         *abort_flag = 0;
         for (int s = 0; s < a.stages; ++s) {
@@ -613,9 +619,10 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
             *abort_flag = 1;
             break;
         }
-        uint32_t packed = 0;  // (hits << 16) | non-empty bins, this lane's share
+        // this lane's share: non-empty bins | even-group hits << 10 | odd << 20
+        uint32_t packed = 0;
         if (row < a.n_rows) {
-            int ne = 0, h = 0;
+            uint32_t ne = 0, h0 = 0, h1 = 0;
             const uint32_t *rp = tp + rl * a.kg;
             int cc = t0;
 #pragma unroll 4
@@ -623,26 +630,30 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
                 const int j = sub * nsub + cc;
                 const uint4 v = *reinterpret_cast<const uint4 *>(
                     rp + (one_plane ? (j << 2) : s_choff[j]));
-                const uint32_t kb = (uint32_t)(j << 2) << a.wbits;
+                const uint4 bb = *reinterpret_cast<const uint4 *>(s_binb + (j << 2));
                 const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+                const uint32_t base[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     if (x[c] != HOPH_EMPTY_VALUE) {
-                        const uint32_t key = kb + ((uint32_t)c << a.wbits) + x[c];
+                        const uint32_t key = base[c] + x[c];
+                        const uint32_t bits = (s_gmap[key >> 4] >> ((key & 15u) << 1)) & 3u;
                         ++ne;
-                        h += (s_bitmap[key >> 5] >> (key & 31)) & 1u;
+                        h0 += bits & 1u;
+                        h1 += bits >> 1;
                     }
                 }
                 if (++cc == nsub) cc = 0;
             }
-            packed = ((uint32_t)h << 16) | (uint32_t)ne;
+            packed = ne | (h0 << 10) | (h1 << 20);
         }
         for (int o = 1; o < lpr; o <<= 1) packed += __shfl_xor_sync(0xFFFFFFFFu, packed, o);
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + s);
         bool pass = false;
         if (sub == 0 && row < a.n_rows) {
-            const int ne = (int)(packed & 0xFFFFu), h = (int)(packed >> 16);
+            const int ne = (int)(packed & 1023u);
+            const int h = (int)max((packed >> 10) & 1023u, packed >> 20);
             pass = ne == 0 ? (a.keep_empty != 0) : (h >= (int)s_rmin[ne]);
         }
         const uint32_t pm = __ballot_sync(0xFFFFFFFFu, pass);
@@ -662,8 +673,7 @@ struct CountArgs {
     PairArgs p;
     const uint32_t *cand;
     const unsigned long long *n_cand;
-    const uint32_t *bitmap;
-    uint32_t wbits;
+    const uint64_t *binbase;  // key = lo[w] + value
     const uint32_t *csr_off;
     const uint16_t *csr_q;
     const uint32_t *q_emask;  // [n_q][mask_words]
@@ -691,10 +701,6 @@ __host__ __device__ inline CountSmem count_smem(const CountArgs &a) {
     L.stats = o;    o = align_up(o + kStatWords * 8, 16);
     L.total = o;
     return L;
-}
-
-__device__ __forceinline__ bool key_in_bitmap(const uint32_t *bm, uint32_t key) {
-    return (__ldg(bm + (key >> 5)) >> (key & 31)) & 1u;
 }
 
 // NCH = 32-bin chunks per row (W <= 32 * NCH).  Each lane keeps its chunks'
@@ -738,10 +744,12 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
     unsigned long long acc0 = 0, hits = 0;
 
     int64_t woff[NCH];
+    uint32_t kbase[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
         const int w = (c << 5) + lane;
         woff[c] = w < P.W ? s_woff[w] : -1;
+        kbase[c] = w < P.W ? (uint32_t)a.binbase[w] : 0u;
     }
     auto load_row = [&](unsigned long long ci, uint32_t *v) {
         const int64_t row = a.cand[ci];
@@ -790,17 +798,15 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
             continue;
         }
         const int need = row_min[ne];
-        // counting pass: bitmap and CSR ranges of every chunk, then counts
+        // counting pass: CSR ranges of every chunk, then counts
         uint32_t o1[NCH], o2[NCH];
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
             o1[c] = o2[c] = 0;
             if (woff[c] >= 0 && v[c] != HOPH_EMPTY_VALUE) {
-                const uint32_t key = ((uint32_t)((c << 5) + lane) << a.wbits) | v[c];
-                if (key_in_bitmap(a.bitmap, key)) {
-                    o1[c] = __ldg(a.csr_off + key);
-                    o2[c] = __ldg(a.csr_off + key + 1);
-                }
+                const uint32_t key = kbase[c] + v[c];
+                o1[c] = __ldg(a.csr_off + key);
+                o2[c] = __ldg(a.csr_off + key + 1);
             }
         }
 #pragma unroll
@@ -1126,12 +1132,6 @@ struct Bump {
     }
 };
 
-int ceil_log2_u64(uint64_t v) {
-    int b = 0;
-    while ((1ull << b) < v) ++b;
-    return b;
-}
-
 }  // namespace
 
 extern "C" {
@@ -1200,15 +1200,14 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
                              ((uintptr_t)d_coll_planes & 15) == 0 && get_encode_fn() != nullptr;
 
     // join: needs "no match => reject" for every K >= 1, TMA tiles, a rule
-    // whose K == 0 pairs are the all-empty ones, and a key space whose bitmap
-    // fits in shared memory next to two filter stages
-    uint64_t max_width = 0;
-    for (int w = 0; w < W; ++w) max_width = std::max(max_width, plan->lo[w + 1] - plan->lo[w]);
-    const int wbits = ceil_log2_u64(std::max<uint64_t>(max_width, 2));
-    const uint64_t keys = mode == HOPH_MODE_MINWISE_FULL ? ~0ull : ((uint64_t)W << wbits);
+    // whose K == 0 pairs are the all-empty ones, and a key space (the psi-space
+    // of the scanned bins) whose 2-bit group map fits in shared memory next
+    // to two filter stages
+    const uint64_t keys = mode == HOPH_MODE_MINWISE_FULL ? ~0ull : plan->lo[W];
     bool join_ok = mode != HOPH_MODE_MINWISE_FULL && fp.rule != HOPH_EMPTY_EITHER &&
                    tma_base_ok && W <= 256 && keys <= kMaxJoinKeys && n_queries <= 4096 &&
-                   n_rows < (1ll << 32) && keys / 8 + 2 * 32 * W * 4 + 4096 <= (uint64_t)kSmemLimit;
+                   n_rows < (1ll << 32) &&
+                   keys / 4 + 2 * 32 * W * 4 + 8 * W + 4096 <= (uint64_t)kSmemLimit;
     for (int K = 1; K <= W && join_ok; ++K) join_ok = tab[K] >= 1;
     int strategy = plan->exec.strategy;
     if (strategy == 1 && !join_ok) return HOPH_ERR_UNSUPPORTED;
@@ -1229,7 +1228,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
             bump.take((keys + 1) * 4);                                  // counts
             bump.take((keys + 1) * 4);                                  // csr_off
             bump.take(((keys + 1 + kScanChunk - 1) / kScanChunk) * 4);  // block sums
-            bump.take((keys / 32 + 1) * 4);                             // bitmap
+            bump.take((keys / 16 + 1) * 4);                             // group map
             bump.take((size_t)n_queries * W * 2);                       // csr_q
             bump.take((size_t)n_queries * mask_words * 4);              // q_emask
             bump.take((size_t)n_queries * 4 + 4);                       // allempty + count
@@ -1246,7 +1245,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
     }
     bump.off = 0;
     unsigned long long *st = (unsigned long long *)bump.take(st_b);
-    uint32_t *counts = nullptr, *csr_off = nullptr, *sums = nullptr, *bitmap = nullptr,
+    uint32_t *counts = nullptr, *csr_off = nullptr, *sums = nullptr, *gmap = nullptr,
              *q_emask = nullptr, *n_allempty = nullptr, *cand = nullptr;
     uint16_t *csr_q = nullptr;
     int32_t *allempty = nullptr;
@@ -1255,7 +1254,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         counts = (uint32_t *)bump.take((keys + 1) * 4);
         csr_off = (uint32_t *)bump.take((keys + 1) * 4);
         sums = (uint32_t *)bump.take(((keys + 1 + kScanChunk - 1) / kScanChunk) * 4);
-        bitmap = (uint32_t *)bump.take((keys / 32 + 1) * 4);
+        gmap = (uint32_t *)bump.take((keys / 16 + 1) * 4);
         csr_q = (uint16_t *)bump.take((size_t)n_queries * W * 2);
         q_emask = (uint32_t *)bump.take((size_t)n_queries * mask_words * 4);
         allempty = (int32_t *)bump.take((size_t)n_queries * 4 + 4);
@@ -1299,14 +1298,14 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         ia.kg = kg;
         ia.W = W;
         ia.mask_words = mask_words;
-        ia.wbits = (uint32_t)wbits;
+        ia.binbase = plan->d_lo;
         ia.counts = counts;
-        ia.bitmap = bitmap;
+        ia.gmap = gmap;
         ia.q_emask = q_emask;
         ia.allempty = allempty;
         ia.n_allempty = n_allempty;
         HOPH_CUDA_TRY(cudaMemsetAsync(counts, 0, (keys + 1) * 4, s));
-        HOPH_CUDA_TRY(cudaMemsetAsync(bitmap, 0, (keys / 32 + 1) * 4, s));
+        HOPH_CUDA_TRY(cudaMemsetAsync(gmap, 0, (keys / 16 + 1) * 4, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(n_allempty, 0, 4, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(n_cand, 0, 8, s));
         const unsigned qb = (unsigned)((n_queries * 32 + 255) / 256);
@@ -1326,9 +1325,9 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         fa.kg = kg;
         fa.Gs = Gs;
         fa.W = W;
-        fa.bitmap = bitmap;
-        fa.bitmap_words = (uint32_t)(keys / 32 + 1);
-        fa.wbits = (uint32_t)wbits;
+        fa.gmap = gmap;
+        fa.gmap_words = (uint32_t)(keys / 16 + 1);
+        fa.binbase = plan->d_lo;
         fa.row_min = pa.thr + 2 * (W + 1);
         const int K0 = hoph_effective(fp.rule, W, W, 0);
         fa.keep_empty = table_decide(tab.data(), W, 0, K0) != HOPH_REJECT;
@@ -1336,12 +1335,12 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         fa.n_cand = n_cand;
         fa.status = plan->d_status;
         // shape: lanes per row, consumer warps and stages that fit next to the
-        // bitmap, at least two stages
+        // group map, at least two stages
         int lpr = plan->exec.lanes_per_row > 0 ? plan->exec.lanes_per_row : 4;
         while (lpr > 1 && ((W / 4) % lpr)) lpr >>= 1;
         const uint32_t fixed = 16 * 8 + 16 + align_up((W + 1) * 2, 16) +
-                               align_up((W / 4) * 4, 16) + align_up(fa.bitmap_words * 4, 128) +
-                               128;
+                               align_up((W / 4) * 4, 16) + align_up(W * 4, 16) +
+                               align_up(fa.gmap_words * 4, 128) + 128;
         int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 16;
         int stages = plan->exec.stages > 0 ? plan->exec.stages : 3;
         auto stage_of = [&](int nc) { return align_up((uint32_t)(32 / lpr * nc) * W * 4, 128); };
@@ -1380,8 +1379,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         ca.p = pa;
         ca.cand = cand;
         ca.n_cand = n_cand;
-        ca.bitmap = bitmap;
-        ca.wbits = (uint32_t)wbits;
+        ca.binbase = plan->d_lo;
         ca.csr_off = csr_off;
         ca.csr_q = csr_q;
         ca.q_emask = q_emask;
