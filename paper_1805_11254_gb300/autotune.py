@@ -14,10 +14,18 @@ from . import hoph
 _cache = {}
 
 JOIN_CANDIDATES = [dict(strategy=1, lanes_per_row=l, consumer_warps=c, stages=s)
-                   for l, c, s in ((4, 16, 3), (4, 16, 2), (4, 8, 4), (2, 16, 2), (8, 16, 4),
-                                   (2, 8, 3), (1, 8, 2), (4, 12, 3))]
+                   for l, c, s in ((0, 16, 2), (0, 12, 2), (0, 8, 3), (0, 16, 3), (-2, 16, 2),
+                                   (-2, 16, 3), (-2, 16, 4))]
 DENSE_CANDIDATES = [dict(strategy=0, consumer_warps=c, stages=s, tile_rows=r)
                     for c, s, r in ((8, 4, 0), (16, 4, 0), (8, 6, 0), (4, 4, 0), (16, 2, 64))]
+
+
+def _lanes(cand, W):
+    """lanes_per_row 0 = one lane per 32 bins, -2 = one lane per 16 bins."""
+    cand = dict(cand)
+    if cand.get("lanes_per_row", 0) == -2:
+        cand["lanes_per_row"] = max(1, W // 16)
+    return cand
 
 
 def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
@@ -36,7 +44,9 @@ def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity,
     times = {}
     ref = None
     best, best_ms = None, None
+    W = plan.k if mode in (0, "oph_full") else plan.kg
     for i, cand in enumerate(candidates):
+        cand = _lanes(cand, W)
         if cand["strategy"] == 0 and n_queries >= 256 and n_rows >= 1 << 20:
             continue  # dense at large batches is tens of times slower; skip
         plan.set_exec(**cand)

@@ -173,7 +173,7 @@ __device__ __forceinline__ void flush_stats(const unsigned long long *s_stats,
 __device__ void produce_tiles(const CUtensorMap *map, unsigned char *stages, uint64_t *full,
                               uint64_t *empty, volatile int32_t *abort_flag, int nstages,
                               uint32_t stage_bytes, uint32_t stage_stride, int64_t n_tiles,
-                              int R, int32_t *status) {
+                              int R, int32_t *status, bool four_d = false) {
     tma_prefetch_desc(map);
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
@@ -185,7 +185,12 @@ __device__ void produce_tiles(const CUtensorMap *map, unsigned char *stages, uin
             break;
         }
         mbar_arrive_expect_tx(full + s, stage_bytes);
-        tma_load_3d(stages + (size_t)s * stage_stride, map, full + s, 0, (int32_t)(tile * R), 0);
+        if (four_d)
+            tma_load_4d(stages + (size_t)s * stage_stride, map, full + s, 0, 0,
+                        (int32_t)(tile * R), 0);
+        else
+            tma_load_3d(stages + (size_t)s * stage_stride, map, full + s, 0, (int32_t)(tile * R),
+                        0);
     }
     const int64_t issued = it;
     for (int64_t j = (issued > nstages ? issued - nstages : 0); j < issued; ++j) {
@@ -305,7 +310,7 @@ __device__ void score_tile_dense(const PairArgs &a, int n_cons, const uint32_t *
 
 __global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_constant__ DenseArgs a,
                                                              const __grid_constant__ CUtensorMap map) {
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     const DenseSmem L = dense_smem(a);
     const PairArgs &P = a.p;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
@@ -398,7 +403,7 @@ struct IndexArgs {
     int32_t n_q, kg, W, mask_words;
     const uint64_t *binbase;  // key = lo[w] + value
     uint32_t *counts;    // [keys + 1]
-    uint32_t *gmap;      // 2 bits per key: an even / an odd query has it
+    uint32_t *gmap;      // per 16 keys: bit j = an even query has key j, bit 16 + j = an odd one
     uint32_t *q_emask;   // [n_q][mask_words]
     int32_t *allempty;
     uint32_t *n_allempty;
@@ -426,7 +431,7 @@ __global__ void join_count_kernel(const IndexArgs a) {
         if (valid && !e) {
             const uint32_t key = (uint32_t)a.binbase[w] + v;
             atomicAdd(a.counts + key, 1u);
-            atomicOr(a.gmap + (key >> 4), 1u << (((key & 15u) << 1) | ((uint32_t)q & 1u)));
+            atomicOr(a.gmap + (key >> 4), 1u << ((key & 15u) + (((uint32_t)q & 1u) << 4)));
         }
     }
     if (lane == 0 && all_empty) a.allempty[atomicAdd(a.n_allempty, 1u)] = (int32_t)q;
@@ -527,7 +532,7 @@ struct FilterArgs {
     int64_t n_rows;
     int32_t kg, Gs, W;
     int32_t tile_rows, n_cons, stages;  // tile_rows = n_cons * 32 / lanes_per_row
-    int32_t lanes_per_row;              // 1, 2, 4 or 8; divides W / 4
+    int32_t lanes_per_row;              // W / lanes_per_row bins per lane (16 or 32)
     int64_t n_tiles;
     uint32_t stage_bytes, stage_stride;
     const uint32_t *gmap;     // 2-bit group map over the keys
@@ -541,7 +546,7 @@ struct FilterArgs {
 };
 
 struct FilterSmem {
-    uint32_t bars, abort_flag, row_min, choff, binb, gmap, stages, total;
+    uint32_t bars, abort_flag, row_min, gmap, stages, total;
 };
 
 __host__ __device__ inline FilterSmem filter_smem(const FilterArgs &a) {
@@ -550,36 +555,33 @@ __host__ __device__ inline FilterSmem filter_smem(const FilterArgs &a) {
     L.bars = o;       o += 16 * 8;
     L.abort_flag = o; o += 16;
     L.row_min = o;    o = align_up(o + (a.W + 1) * 2, 16);
-    L.choff = o;      o = align_up(o + (a.W / 4) * 4, 16);
-    L.binb = o;       o = align_up(o + a.W * 4, 16);
-    L.gmap = o;       o = align_up(o + a.gmap_words * 4, 128);
+    L.gmap = o;       o = align_up(o + a.gmap_words * 4, 1024);
     L.stages = o;     o += a.stages * a.stage_stride;
     L.total = o;
     return L;
 }
 
+// Tiles arrive through a 4-D TMA box {32 bins, k'/32, rows, planes} with the
+// 128-byte swizzle: in shared memory each 128-byte line (32 bins of one row)
+// holds its 16-byte chunk c at position c ^ (line & 7), so the eight lanes of
+// a shared-memory phase, reading the same chunk of eight consecutive lines,
+// hit eight different banks.  Lane (r, sub) of a warp owns NPER consecutive
+// bins of row r; their psi-space bases stay in registers.
+template <int NPER>
 __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__ FilterArgs a,
                                                          const __grid_constant__ CUtensorMap map) {
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     const FilterSmem L = filter_smem(a);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint64_t *empty = full + 8;
     volatile int32_t *abort_flag = reinterpret_cast<volatile int32_t *>(smem + L.abort_flag);
     uint16_t *s_rmin = reinterpret_cast<uint16_t *>(smem + L.row_min);
-    int32_t *s_choff = reinterpret_cast<int32_t *>(smem + L.choff);
-    uint32_t *s_binb = reinterpret_cast<uint32_t *>(smem + L.binb);
     uint32_t *s_gmap = reinterpret_cast<uint32_t *>(smem + L.gmap);
     unsigned char *stages = smem + L.stages;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = a.tile_rows;
-    const int nchunk = a.W >> 2;
     for (int i = tid; i <= a.W; i += blockDim.x) s_rmin[i] = a.row_min[i];
-    for (int j = tid; j < nchunk; j += blockDim.x) {
-        const int w = j << 2, g = w / a.kg, b = w - g * a.kg;
-        s_choff[j] = (g * R) * a.kg + b;  // element offset of chunk j in row 0 of a tile
-    }
-    for (int w = tid; w < a.W; w += blockDim.x) s_binb[w] = (uint32_t)a.binbase[w];
     for (uint32_t i = tid; i < a.gmap_words; i += blockDim.x) s_gmap[i] = a.gmap[i];
     if (tid == 0) {
         *abort_flag = 0;
@@ -594,66 +596,65 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
     if (warp == a.n_cons) {
         if (lane == 0)
             produce_tiles(&map, stages, full, empty, abort_flag, a.stages, a.stage_bytes,
-                          a.stage_stride, a.n_tiles, R, a.status);
+                          a.stage_stride, a.n_tiles, R, a.status, true);
         return;
     }
 
-    // consumer warp `warp` owns rows_per_warp = 32 / lpr consecutive rows of
-    // every tile, lpr lanes per row, each lane nsub = nchunk / lpr 16-byte
-    // chunks of its row.  Lane (r, s) starts at chunk (r + s) mod nsub of its
-    // range so the 128-bit loads of a shared-memory phase hit distinct banks.
     const int lpr = a.lanes_per_row;
     const int rpw = 32 / lpr;
     const int r_in = lane / lpr, sub = lane - r_in * lpr;
     const int rl = warp * rpw + r_in;
-    const int nsub = nchunk / lpr;
-    const int t0 = (r_in + sub) % nsub;
-    const bool one_plane = a.Gs == 1;
+    const int w0 = sub * NPER;                // first bin of this lane
+    const int g = w0 / a.kg;                  // plane of the lane's bins
+    const int lpr_row = a.kg >> 5;            // 128-byte lines per row and plane
+    // line of (row rl, this lane's bins) within a tile, and the first chunk
+    const int line = (g * R + rl) * lpr_row + ((w0 - g * a.kg) >> 5);
+    const int c0 = (w0 & 31) >> 2;
+    uint32_t kb[NPER];
+#pragma unroll
+    for (int i = 0; i < NPER; ++i) kb[i] = (uint32_t)a.binbase[w0 + i];
+
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
         const int s = (int)(it % a.stages);
-        const uint32_t *tp = reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride);
+        const uint32_t *lp =
+            reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride) + line * 32;
+        // the swizzle XORs the chunk index with bits 7..9 of the line's address
+        const int xr = (int)(smem_u32(lp) >> 7) & 7;
         const int64_t row = tile * R + rl;
         if (!mbar_wait_bounded(full + s, (uint32_t)(it / a.stages) & 1, abort_flag)) {
             hoph_flag(a.status, HOPH_ERR_TIMEOUT);
             *abort_flag = 1;
             break;
         }
-        // this lane's share: non-empty bins | even-group hits << 10 | odd << 20
-        uint32_t packed = 0;
+        // this lane's share: hits = even-group hits | odd-group hits << 16
+        // (one map word gives both bits of a key 16 apart), ne = non-empty bins
+        uint32_t hits = 0, ne = 0;
         if (row < a.n_rows) {
-            uint32_t ne = 0, h0 = 0, h1 = 0;
-            const uint32_t *rp = tp + rl * a.kg;
-            int cc = t0;
-#pragma unroll 4
-            for (int step = 0; step < nsub; ++step) {
-                const int j = sub * nsub + cc;
-                const uint4 v = *reinterpret_cast<const uint4 *>(
-                    rp + (one_plane ? (j << 2) : s_choff[j]));
-                const uint4 bb = *reinterpret_cast<const uint4 *>(s_binb + (j << 2));
-                const uint32_t x[4] = {v.x, v.y, v.z, v.w};
-                const uint32_t base[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (x[c] != HOPH_EMPTY_VALUE) {
-                        const uint32_t key = base[c] + x[c];
-                        const uint32_t bits = (s_gmap[key >> 4] >> ((key & 15u) << 1)) & 3u;
+            for (int c = 0; c < NPER / 4; ++c) {
+                const uint4 v =
+                    *reinterpret_cast<const uint4 *>(lp + (((c0 + c) ^ xr) << 2));
+                const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (x[e] != HOPH_EMPTY_VALUE) {
+                        const uint32_t key = kb[c * 4 + e] + x[e];
+                        hits += (s_gmap[key >> 4] >> (key & 15u)) & 0x10001u;
                         ++ne;
-                        h0 += bits & 1u;
-                        h1 += bits >> 1;
                     }
                 }
-                if (++cc == nsub) cc = 0;
             }
-            packed = ne | (h0 << 10) | (h1 << 20);
         }
-        for (int o = 1; o < lpr; o <<= 1) packed += __shfl_xor_sync(0xFFFFFFFFu, packed, o);
+        for (int o = 1; o < lpr; o <<= 1) {
+            hits += __shfl_xor_sync(0xFFFFFFFFu, hits, o);
+            ne += __shfl_xor_sync(0xFFFFFFFFu, ne, o);
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + s);
         bool pass = false;
         if (sub == 0 && row < a.n_rows) {
-            const int ne = (int)(packed & 1023u);
-            const int h = (int)max((packed >> 10) & 1023u, packed >> 20);
+            const int h = (int)max(hits & 0xFFFFu, hits >> 16);
             pass = ne == 0 ? (a.keep_empty != 0) : (h >= (int)s_rmin[ne]);
         }
         const uint32_t pm = __ballot_sync(0xFFFFFFFFu, pass);
@@ -709,7 +710,7 @@ __host__ __device__ inline CountSmem count_smem(const CountArgs &a) {
 // one is counted.
 template <int NCH>
 __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_constant__ CountArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     const CountSmem L = count_smem(a);
     const PairArgs &P = a.p;
     uint16_t *s_thr = reinterpret_cast<uint16_t *>(smem + L.thr);
@@ -938,7 +939,7 @@ __device__ int64_t lower_bound_key(const ulonglong2 *a, int64_t n, unsigned long
 __global__ void __launch_bounds__(kSortThreads) sort_pairs_kernel(
     hoph_pair *out, const unsigned long long *count, int64_t cap, ulonglong2 *bufA,
     ulonglong2 *bufB, int32_t *status) {
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     ulonglong2 *sv = reinterpret_cast<ulonglong2 *>(smem);
     const unsigned long long total = *count;
     if (total > (unsigned long long)cap && threadIdx.x == 0) hoph_flag(status, HOPH_ERR_CAPACITY);
@@ -1084,6 +1085,37 @@ bool encode_planes_map(CUtensorMap *map, const uint32_t *planes, int kg, int64_t
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 4-D swizzled map for the join filter: {32, k'/32, rows, planes}, box
+// {32, k'/32, R, Gs}, 128-byte swizzle (needs k' % 32 == 0)
+bool encode_swizzled_map(CUtensorMap *map, const uint32_t *planes, int kg, int64_t n_rows, int Gs,
+                         int64_t cstride, int R) {
+    EncodeTiledFn fn = get_encode_fn();
+    if (!fn) return false;
+    const cuuint64_t gdim[4] = {32, (cuuint64_t)(kg / 32), (cuuint64_t)n_rows, (cuuint64_t)Gs};
+    const cuuint64_t gstride[3] = {128, (cuuint64_t)kg * 4, (cuuint64_t)cstride * 4};
+    const cuuint32_t box[4] = {32, (cuuint32_t)(kg / 32), (cuuint32_t)R, (cuuint32_t)Gs};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, (void *)planes, gdim, gstride, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NPER>
+int launch_filter(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem, int num_sms,
+                  int ctas_per_sm, cudaStream_t s) {
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)filter_kernel<NPER>, (int)smem));
+    const int threads = 32 * (fa.n_cons + 1);
+    int per_sm = 0;
+    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_kernel<NPER>,
+                                                                threads, smem));
+    if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+    const int64_t grid = std::min<int64_t>(fa.n_tiles, (int64_t)num_sms * per_sm);
+    filter_kernel<NPER><<<(unsigned)grid, threads, smem, s>>>(fa, map);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    return HOPH_OK;
+}
+
 // First-pass decision table for W scanned bins under `dp` after `l` groups:
 // rej[K] / acc[K] for K = 0..W, then row_min[n] for n = 0..W.
 bool build_table(const DecideParams &dp, int W, int l, std::vector<uint16_t> &tab) {
@@ -1205,7 +1237,8 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
     // to two filter stages
     const uint64_t keys = mode == HOPH_MODE_MINWISE_FULL ? ~0ull : plan->lo[W];
     bool join_ok = mode != HOPH_MODE_MINWISE_FULL && fp.rule != HOPH_EMPTY_EITHER &&
-                   tma_base_ok && W <= 256 && keys <= kMaxJoinKeys && n_queries <= 4096 &&
+                   tma_base_ok && kg % 32 == 0 && W <= 256 && keys <= kMaxJoinKeys &&
+                   n_queries <= 4096 &&
                    n_rows < (1ll << 32) &&
                    keys / 4 + 2 * 32 * W * 4 + 8 * W + 4096 <= (uint64_t)kSmemLimit;
     for (int K = 1; K <= W && join_ok; ++K) join_ok = tab[K] >= 1;
@@ -1334,17 +1367,18 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         fa.cand = cand;
         fa.n_cand = n_cand;
         fa.status = plan->d_status;
-        // shape: lanes per row, consumer warps and stages that fit next to the
-        // group map, at least two stages
-        int lpr = plan->exec.lanes_per_row > 0 ? plan->exec.lanes_per_row : 4;
-        while (lpr > 1 && ((W / 4) % lpr)) lpr >>= 1;
+        // shape: bins per lane (32 or 16), consumer warps and stages that fit
+        // next to the group map, at least two stages
+        int lpr = plan->exec.lanes_per_row > 0 ? plan->exec.lanes_per_row : std::max(1, W / 32);
+        const int nper = W / lpr;
+        if (W % lpr || (nper != 32 && nper != 16) || lpr > 32) return HOPH_ERR_UNSUPPORTED;
         const uint32_t fixed = 16 * 8 + 16 + align_up((W + 1) * 2, 16) +
-                               align_up((W / 4) * 4, 16) + align_up(W * 4, 16) +
-                               align_up(fa.gmap_words * 4, 128) + 128;
+                               align_up(fa.gmap_words * 4, 1024) + 1024;
         int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 16;
-        int stages = plan->exec.stages > 0 ? plan->exec.stages : 3;
-        auto stage_of = [&](int nc) { return align_up((uint32_t)(32 / lpr * nc) * W * 4, 128); };
-        while (n_cons > 1 && fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit) {
+        int stages = plan->exec.stages > 0 ? plan->exec.stages : 2;
+        auto stage_of = [&](int nc) { return align_up((uint32_t)(32 / lpr * nc) * W * 4, 1024); };
+        while (n_cons > 1 && (fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit ||
+                              32 / lpr * n_cons > 256)) {
             if (stages > 2) --stages; else --n_cons;
         }
         if (fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit)
@@ -1355,23 +1389,18 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         fa.stages = stages;
         fa.n_tiles = (n_rows + fa.tile_rows - 1) / fa.tile_rows;
         fa.stage_bytes = (uint32_t)fa.tile_rows * W * 4;
-        fa.stage_stride = align_up(fa.stage_bytes, 128);
+        fa.stage_stride = align_up(fa.stage_bytes, 1024);
         CUtensorMap map;
         memset(&map, 0, sizeof map);
-        if (!encode_planes_map(&map, d_coll_planes, kg, n_rows, Gs, cstride, fa.tile_rows))
+        if (!encode_swizzled_map(&map, d_coll_planes, kg, n_rows, Gs, cstride, fa.tile_rows))
             return HOPH_ERR_UNSUPPORTED;
         const FilterSmem FL = filter_smem(fa);
-        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)filter_kernel, (int)FL.total));
-        const int threads = 32 * (n_cons + 1);
-        int per_sm = 0;
-        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_kernel,
-                                                                    threads, FL.total));
-        if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
-        if (plan->exec.ctas_per_sm > 0) per_sm = std::min(per_sm, plan->exec.ctas_per_sm);
-        const int64_t grid = std::min<int64_t>(fa.n_tiles, (int64_t)plan->num_sms * per_sm);
         hoph_timing_mark(plan, 1, s);
-        filter_kernel<<<(unsigned)grid, threads, FL.total, s>>>(fa, map);
-        HOPH_CUDA_TRY(cudaGetLastError());
+        const int frc = nper == 32 ? launch_filter<32>(fa, map, FL.total, plan->num_sms,
+                                                       plan->exec.ctas_per_sm, s)
+                                   : launch_filter<16>(fa, map, FL.total, plan->num_sms,
+                                                       plan->exec.ctas_per_sm, s);
+        if (frc != HOPH_OK) return frc;
         hoph_timing_mark(plan, 2, s);
 
         // ---- join: candidate rows

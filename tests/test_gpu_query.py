@@ -217,13 +217,14 @@ def test_identical_sets_always_accepted(small):
         assert {(i, i) for i in range(300)} <= got
 
 
-@pytest.mark.parametrize("lpr,warps,stages", [(1, 8, 2), (2, 16, 2), (4, 16, 3), (8, 16, 4),
-                                              (4, 3, 5)])
-def test_join_execution_knobs_do_not_change_results(small, lpr, warps, stages):
+@pytest.mark.parametrize("kg,lpr,warps,stages", [(32, 1, 8, 2), (32, 2, 16, 2), (32, 1, 16, 3),
+                                                 (32, 2, 3, 5), (64, 2, 16, 2), (64, 4, 16, 4),
+                                                 (64, 2, 5, 3)])
+def test_join_execution_knobs_do_not_change_results(small, kg, lpr, warps, stages):
     """Lanes per row, consumer warps and pipeline depth of the join filter
     are scheduling only: the accepted pairs stay the oracle's."""
     dev = device()
-    D, k, kg = small["D"], 128, 32
+    D, k = small["D"], 128
     with hoph.Plan(D, k, kg, 1, 2, seed=1, thr=T, epsilon=EPS) as plan:
         q, c = _sketch_both(plan, small, dev)
         z = [plan.info.group_size[g] for g in range(plan.G)]
