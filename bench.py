@@ -42,7 +42,7 @@ SKETCH_SEED = 21
 # dram read+write bytes per scan-kernel launch from an ncu capture, keyed by
 # the sha256 of the query kernel source it was taken on (null once the
 # source changes)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"e112d6b324568a60": 2577.47e6}  # profiles/filter_kernel_2e6rows.md, x5 rows
 
 
 def parse():
@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip sketch/OPH/CPU legs")
     p.add_argument("--profile", action="store_true", help="few launches, for ncu")
     p.add_argument("--no-graph", action="store_true", help="eager launches instead of a graph")
+    p.add_argument("--no-tune", action="store_true", help="library default execution knobs")
     return p.parse_args()
 
 
@@ -292,8 +293,10 @@ def run_native(args):
         return
 
     from paper_1805_11254_gb300 import autotune
-    best, tune_ms = autotune.tune_query(plan, hoph.HOPH_MODE_HOPH, q_planes, nq, planes, args.rows,
-                                        out, cap, cnt, stream)
+    best, tune_ms = None, {}
+    if not args.no_tune:
+        best, tune_ms = autotune.tune_query(plan, hoph.HOPH_MODE_HOPH, q_planes, nq, planes,
+                                            args.rows, out, cap, cnt, stream)
     for _ in range(args.warmup):
         step()
     plan.check()

@@ -1375,7 +1375,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         const uint32_t fixed = 16 * 8 + 16 + align_up((W + 1) * 2, 16) +
                                align_up(fa.gmap_words * 4, 1024) + 1024;
         int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 16;
-        int stages = plan->exec.stages > 0 ? plan->exec.stages : 2;
+        int stages = plan->exec.stages > 0 ? plan->exec.stages : 3;
         auto stage_of = [&](int nc) { return align_up((uint32_t)(32 / lpr * nc) * W * 4, 1024); };
         while (n_cons > 1 && (fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit ||
                               32 / lpr * n_cons > 256)) {
