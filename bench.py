@@ -39,10 +39,10 @@ T, EPS = (7, 10), 1e-4
 PERM_SEED, COLL_SEED, Q_SEED, PLANT_SEED = 1, 11, 12, 13
 SKETCH_SEED = 21
 
-# dram read+write bytes per scan-kernel launch from an ncu capture, keyed by
-# the sha256 of the query kernel source it was taken on (null once the
+# dram read+write bytes per filter-kernel launch from an ncu capture, keyed by
+# the sha256 of the filter kernel's source it was taken on (null once that
 # source changes)
-NCU_TRAFFIC = {"e112d6b324568a60": 2577.47e6}  # profiles/filter_kernel_2e6rows.md, x5 rows
+NCU_TRAFFIC = {"a887ad91130c470b": 2577.47e6}  # profiles/filter_kernel_2e6rows.md, x5 rows
 
 
 def parse():
@@ -68,9 +68,13 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def src_sha(name):
-    with open(os.path.join(ROOT, "paper_1805_11254_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def filter_src_sha():
+    """sha256[:16] of the join filter's source (FilterArgs through the kernel)."""
+    with open(os.path.join(ROOT, "paper_1805_11254_gb300", "csrc", "query.cu")) as f:
+        text = f.read()
+    a = text.index("struct FilterArgs {")
+    b = text.index("// Join strategy, part 3")
+    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 
 
 def measured_peaks():
@@ -382,7 +386,7 @@ def run_native(args):
     # the streaming pass reads the first plane and the query sketches once
     alg_bytes = int(args.rows * KG * 4 + nq * KG * 4)
     achieved = alg_bytes / (scan_ms / 1e3) / 1e9
-    traffic = NCU_TRAFFIC.get(src_sha("query.cu"))
+    traffic = NCU_TRAFFIC.get(filter_src_sha())
     roofline = {"bound": "hbm", "kernel": "filter_kernel (value join, first-group plane)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,

@@ -272,6 +272,15 @@ int hoph_plan_read_timing(hoph_plan *plan, double *ms, int64_t *calls, int64_t *
  * it).  HOPH_ERR_PARAM if no call has been recorded. */
 int hoph_plan_peek_timing(hoph_plan *plan, double *ms);
 
+/*
+ * Failure-path check of the bounded device waits (no paper counterpart):
+ * launches one warp that runs the pipeline's mbarrier wait on a barrier no
+ * thread ever completes, with a limit of limit_ns (1 ns .. 2 s).  The wait
+ * gives up and records HOPH_ERR_TIMEOUT in the plan's status word, which
+ * hoph_sync_status then returns; the CUDA context stays usable.
+ */
+int hoph_check_bounded_wait(hoph_plan *plan, uint64_t limit_ns, void *stream);
+
 /* Synchronise `stream`, then return and clear the plan's device status word
  * (HOPH_OK if no device-side error was recorded). */
 int hoph_sync_status(hoph_plan *plan, void *stream);

@@ -214,11 +214,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for phase `parity` of an mbarrier, giving up after ~2 s of wall
-// time or when another warp of the CTA raised *abort.  Returns false on
-// give-up (the caller records HOPH_ERR_TIMEOUT and leaves its loop).
+// Wait for phase `parity` of an mbarrier, giving up after `limit_ns` of wall
+// time (2 s by default) or when another warp of the CTA raised *abort.
+// Returns false on give-up (the caller records HOPH_ERR_TIMEOUT and leaves
+// its loop).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                  volatile int32_t *abort_flag) {
+                                                  volatile int32_t *abort_flag,
+                                                  uint64_t limit_ns = 2000000000ull) {
     uint64_t t0 = 0;
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
@@ -226,7 +228,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
             if (*abort_flag) return false;
             const uint64_t now = global_ns();
             if (t0 == 0) t0 = now;
-            else if (now - t0 > 2000000000ull) return false;
+            else if (now - t0 > limit_ns) return false;
         }
     }
 }

@@ -1048,6 +1048,24 @@ __global__ void pair_counts_kernel(const uint32_t *qry, int64_t qstride, int64_t
 }
 
 // ===========================================================================
+// Bounded-wait check: the pipeline's wait routine on an mbarrier that no
+// thread ever arrives on gives up after `limit_ns` and reports
+// HOPH_ERR_TIMEOUT in the status word; nothing faults or hangs.
+// ===========================================================================
+__global__ void bounded_wait_probe_kernel(uint64_t limit_ns, int32_t *status) {
+    __shared__ uint64_t bar;
+    __shared__ int32_t abort_flag;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, &abort_flag, limit_ns))
+        hoph_flag(status, HOPH_ERR_TIMEOUT);
+}
+
+// ===========================================================================
 // Host side
 // ===========================================================================
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -1475,6 +1493,14 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
     HOPH_CUDA_TRY(cudaGetLastError());
     hoph_timing_mark(plan, 4, s);
     plan->launches += launches + 2;
+    return HOPH_OK;
+}
+
+int hoph_check_bounded_wait(hoph_plan *plan, uint64_t limit_ns, void *stream) {
+    if (!plan || limit_ns == 0 || limit_ns > 2000000000ull) return HOPH_ERR_PARAM;
+    bounded_wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(limit_ns, plan->d_status);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    plan->launches += 1;
     return HOPH_OK;
 }
 

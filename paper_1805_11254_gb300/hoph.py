@@ -96,7 +96,8 @@ _EXPORTS = ["hoph_plan_create", "hoph_plan_create_with_perm", "hoph_plan_destroy
             "hoph_plan_get_info", "hoph_plan_set_exec", "oph_build_sketches",
             "minwise_build_sketches", "hoph_query_batch", "hoph_pair_counts", "hoph_synth_ids",
             "hoph_sync_status", "hoph_status_string", "hoph_plan_enable_timing",
-            "hoph_plan_read_timing", "oph_build_sketches_static", "hoph_plan_peek_timing"]
+            "hoph_plan_read_timing", "oph_build_sketches_static", "hoph_plan_peek_timing",
+            "hoph_check_bounded_wait"]
 
 
 def load(path=LIB_PATH):
@@ -138,6 +139,8 @@ def load(path=LIB_PATH):
     lib.hoph_plan_enable_timing.restype = i32
     lib.hoph_plan_read_timing.argtypes = [P, P, P, P]
     lib.hoph_plan_read_timing.restype = i32
+    lib.hoph_check_bounded_wait.argtypes = [P, u64, P]
+    lib.hoph_check_bounded_wait.restype = i32
     lib.hoph_plan_peek_timing.argtypes = [P, P]
     lib.hoph_plan_peek_timing.restype = i32
     lib.hoph_status_string.argtypes = [i32]
@@ -275,6 +278,11 @@ def hoph_plan_peek_timing(plan):
     ms = (ctypes.c_double * 4)()
     _check(load().hoph_plan_peek_timing(plan, ctypes.addressof(ms)), "hoph_plan_peek_timing")
     return list(ms)
+
+
+def hoph_check_bounded_wait(plan, limit_ns, stream=None):
+    return _check(load().hoph_check_bounded_wait(plan, int(limit_ns), _stream(stream)),
+                  "hoph_check_bounded_wait")
 
 
 def hoph_sync_status(plan, stream=None):
