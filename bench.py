@@ -60,6 +60,10 @@ def parse():
     p.add_argument("--profile", action="store_true", help="few launches, for ncu")
     p.add_argument("--no-graph", action="store_true", help="eager launches instead of a graph")
     p.add_argument("--no-tune", action="store_true", help="library default execution knobs")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
+    p.add_argument("--serve-rates", default="2000,20000,100000",
+                   help="Poisson arrival rates (query sets per second)")
+    p.add_argument("--serve-seconds", type=float, default=1.5)
     return p.parse_args()
 
 
@@ -419,6 +423,8 @@ def run_native(args):
         line["oph_full_scan_baseline"] = oph_baseline_leg(args, off, coll_seed, qw, dev, stream,
                                                           value)
         line["cpu_baseline"] = cpu_baseline(qw, off, coll_seed, args.cpu_seconds, args.rows)
+        if not args.no_serve:
+            line["serving"] = serving_leg(args, planes, dev, line["oph_full_scan_baseline"])
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -576,6 +582,50 @@ def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, n_launch
             "hoph_speedup": hoph_value / v,
             "how": "mode OPH_FULL, dense scan of all 256 bins (10.24 GB), one query per launch, "
                    "%d launches" % len(qs)}
+
+
+def serving_leg(args, planes, dev, oph_leg):
+    """Continuous batching against the resident collection: Poisson arrivals
+    of requests of U[1, 256] query sets (lognormal sizes, median 300); each
+    batch (<= 1,024 sets) replays one captured graph.  p50/p99 latency from
+    arrival to results on the host, and throughput, per arrival rate."""
+    from paper_1805_11254_gb300 import serve, synth
+    plan_kw = dict(D=D, k=K, k_group=KG, a=AB[0], b=AB[1], seed=PERM_SEED, thr=T, epsilon=EPS)
+    buckets = (64, 256, 1024)
+    id_cap = 4 << 20
+    ex = serve.GpuExecutor(plan_kw, planes, args.rows, "hoph", buckets, id_cap)
+    ctr = [0]
+
+    def sets_for(rng, n):
+        sizes = synth.lognormal_sizes(n, 300, 1.0, 10, 20000, int(rng.integers(1 << 31)))
+        out = []
+        for sz in sizes:
+            out.append(synth.counter_ids(977, ctr[0], int(sz), D))
+            ctr[0] += int(sz)
+        return out
+
+    results = []
+    try:
+        for i, rate in enumerate(float(x) for x in args.serve_rates.split(",")):
+            reqs = serve.poisson_requests(rate, args.serve_seconds, 100 + i, sets_for)
+            t0 = time.perf_counter()
+            done = serve.serve(ex, serve.Batcher(buckets, id_cap), reqs)
+            wall = time.perf_counter() - t0
+            ok = [r for r in done if r.error is None]
+            n_sets = sum(len(r.sets) for r in ok)
+            summ = serve.latency_summary(ok)
+            summ.update({"rate_query_sets_per_s": rate, "query_sets": n_sets,
+                         "throughput_query_sets_per_s": n_sets / wall,
+                         "pair_comparisons_per_s": n_sets * args.rows / wall,
+                         "rejected": len(done) - len(ok)})
+            results.append(summ)
+    finally:
+        ex.close()
+    return {"rates": results, "collection_rows": args.rows, "batch_slots": list(buckets),
+            "one_request_per_launch_oph_capacity_query_sets_per_s":
+                1e3 / oph_leg["ms_per_query_launch"],
+            "how": "2 streams x 1 plan each, one CUDA graph per (stream, batch size); H2D of a "
+                   "batch's sets and its sketching overlap the query of the other stream"}
 
 
 def main():
