@@ -46,7 +46,9 @@ namespace {
 constexpr int kSurvCap = 32;  // per-warp survivor list (one entry per lane)
 constexpr int kMaxW = 1024;   // scanned bins per row
 constexpr int kStatWords = 3 * HOPH_MAX_GROUPS + 4;
-constexpr uint64_t kMaxJoinKeys = 1ull << 23;  // padded key space of the join index
+constexpr uint64_t kMaxJoinKeys = 1ull << 23;  // key space indexed directly by the CSR
+constexpr uint64_t kDirectMap = 1ull << 19;    // key space indexed directly by the group map
+constexpr uint64_t kHashedMapSlots = 1ull << 18;
 constexpr int kSmemLimit = 227 * 1024;
 
 struct Survivor {
@@ -78,6 +80,45 @@ struct PairArgs {
 // [48] later-group sketch bytes, [49] join hits
 
 __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
+
+// MurmurHash3's 32-bit finalizer (Appleby): spreads keys over a power-of-two
+// table when the key space is too large to index directly.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+constexpr unsigned long long kNoKey = ~0ull;  // empty slot of the key table
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+
+// Open-addressing key table (linear probing, at most half full): slot of
+// `key`, inserted if absent.  Gives up (kNoSlot) after a full sweep.
+__device__ __forceinline__ uint32_t table_insert(unsigned long long *tkey, uint32_t mask,
+                                                 uint32_t key) {
+    uint32_t slot = mix32(key) & mask;
+    for (uint32_t i = 0; i <= mask; ++i) {
+        const unsigned long long prev = atomicCAS(tkey + slot, kNoKey, (unsigned long long)key);
+        if (prev == kNoKey || prev == (unsigned long long)key) return slot;
+        slot = (slot + 1) & mask;
+    }
+    return kNoSlot;
+}
+
+__device__ __forceinline__ uint32_t table_find(const unsigned long long *tkey, uint32_t mask,
+                                               uint32_t key) {
+    uint32_t slot = mix32(key) & mask;
+    for (uint32_t i = 0; i <= mask; ++i) {
+        const unsigned long long k = __ldg(tkey + slot);
+        if (k == (unsigned long long)key) return slot;
+        if (k == kNoKey) return kNoSlot;
+        slot = (slot + 1) & mask;
+    }
+    return kNoSlot;
+}
 
 __device__ __forceinline__ void emit_pair(const PairArgs &a, uint32_t q, int64_t row, int groups,
                                           int matches) {
@@ -402,8 +443,14 @@ struct IndexArgs {
     int64_t qstride;
     int32_t n_q, kg, W, mask_words;
     const uint64_t *binbase;  // key = lo[w] + value
-    uint32_t *counts;    // [keys + 1]
-    uint32_t *gmap;      // per 16 keys: bit j = an even query has key j, bit 16 + j = an odd one
+    uint32_t *counts;    // [slots + 1]: queries per key slot
+    uint32_t *gmap;      // per 16 map slots: bit j = an even query has slot j, bit 16 + j = an odd one
+    int32_t map_hashed;  // map slot = mix32(key) & map_mask, else the key itself
+    uint32_t map_mask;
+    int32_t csr_hashed;  // key slot from the key table, else the key itself
+    unsigned long long *tkey;
+    uint32_t tmask;
+    int32_t *status;
     uint32_t *q_emask;   // [n_q][mask_words]
     int32_t *allempty;
     uint32_t *n_allempty;
@@ -430,8 +477,11 @@ __global__ void join_count_kernel(const IndexArgs a) {
         if (lane == 0) a.q_emask[q * a.mask_words + c] = em;
         if (valid && !e) {
             const uint32_t key = (uint32_t)a.binbase[w] + v;
-            atomicAdd(a.counts + key, 1u);
-            atomicOr(a.gmap + (key >> 4), 1u << ((key & 15u) + (((uint32_t)q & 1u) << 4)));
+            const uint32_t mi = a.map_hashed ? (mix32(key) & a.map_mask) : key;
+            atomicOr(a.gmap + (mi >> 4), 1u << ((mi & 15u) + (((uint32_t)q & 1u) << 4)));
+            const uint32_t slot = a.csr_hashed ? table_insert(a.tkey, a.tmask, key) : key;
+            if (slot == kNoSlot) hoph_flag(a.status, HOPH_ERR_CAPACITY);
+            else atomicAdd(a.counts + slot, 1u);
         }
     }
     if (lane == 0 && all_empty) a.allempty[atomicAdd(a.n_allempty, 1u)] = (int32_t)q;
@@ -446,7 +496,9 @@ __global__ void join_fill_kernel(const IndexArgs a, const uint32_t *csr_off, uin
         const uint32_t v = a.qry[(int64_t)g * a.qstride + q * a.kg + b];
         if (v == HOPH_EMPTY_VALUE) continue;
         const uint32_t key = (uint32_t)a.binbase[w] + v;
-        const uint32_t pos = csr_off[key] + atomicSub(a.counts + key, 1u) - 1u;
+        const uint32_t slot = a.csr_hashed ? table_find(a.tkey, a.tmask, key) : key;
+        if (slot == kNoSlot) continue;
+        const uint32_t pos = csr_off[slot] + atomicSub(a.counts + slot, 1u) - 1u;
         csr_q[pos] = (uint16_t)q;
     }
 }
@@ -535,8 +587,9 @@ struct FilterArgs {
     int32_t lanes_per_row;              // W / lanes_per_row bins per lane (16 or 32)
     int64_t n_tiles;
     uint32_t stage_bytes, stage_stride;
-    const uint32_t *gmap;     // 2-bit group map over the keys
+    const uint32_t *gmap;     // 2-bit group map over the map slots
     uint32_t gmap_words;
+    uint32_t map_mask;        // hashed map: slot = mix32(key) & map_mask
     const uint64_t *binbase;  // key = lo[w] + value
     const uint16_t *row_min;  // [W + 1]
     int32_t keep_empty;       // rows without a non-empty scanned bin are candidates
@@ -567,7 +620,7 @@ __host__ __device__ inline FilterSmem filter_smem(const FilterArgs &a) {
 // a shared-memory phase, reading the same chunk of eight consecutive lines,
 // hit eight different banks.  Lane (r, sub) of a warp owns NPER consecutive
 // bins of row r; their psi-space bases stay in registers.
-template <int NPER>
+template <int NPER, bool HASHED>
 __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__ FilterArgs a,
                                                          const __grid_constant__ CUtensorMap map) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -640,7 +693,8 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
                 for (int e = 0; e < 4; ++e) {
                     if (x[e] != HOPH_EMPTY_VALUE) {
                         const uint32_t key = kb[c * 4 + e] + x[e];
-                        hits += (s_gmap[key >> 4] >> (key & 15u)) & 0x10001u;
+                        const uint32_t mi = HASHED ? (mix32(key) & a.map_mask) : key;
+                        hits += (s_gmap[mi >> 4] >> (mi & 15u)) & 0x10001u;
                         ++ne;
                     }
                 }
@@ -675,6 +729,9 @@ struct CountArgs {
     const uint32_t *cand;
     const unsigned long long *n_cand;
     const uint64_t *binbase;  // key = lo[w] + value
+    int32_t csr_hashed;       // key slots from the key table
+    const unsigned long long *tkey;
+    uint32_t tmask;
     const uint32_t *csr_off;
     const uint16_t *csr_q;
     const uint32_t *q_emask;  // [n_q][mask_words]
@@ -806,8 +863,11 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
             o1[c] = o2[c] = 0;
             if (woff[c] >= 0 && v[c] != HOPH_EMPTY_VALUE) {
                 const uint32_t key = kbase[c] + v[c];
-                o1[c] = __ldg(a.csr_off + key);
-                o2[c] = __ldg(a.csr_off + key + 1);
+                const uint32_t slot = a.csr_hashed ? table_find(a.tkey, a.tmask, key) : key;
+                if (slot != kNoSlot) {
+                    o1[c] = __ldg(a.csr_off + slot);
+                    o2[c] = __ldg(a.csr_off + slot + 1);
+                }
             }
         }
 #pragma unroll
@@ -1118,18 +1178,18 @@ bool encode_swizzled_map(CUtensorMap *map, const uint32_t *planes, int kg, int64
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NPER>
+template <int NPER, bool HASHED>
 int launch_filter(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem, int num_sms,
                   int ctas_per_sm, cudaStream_t s) {
-    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)filter_kernel<NPER>, (int)smem));
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)filter_kernel<NPER, HASHED>, (int)smem));
     const int threads = 32 * (fa.n_cons + 1);
     int per_sm = 0;
-    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_kernel<NPER>,
-                                                                threads, smem));
+    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, filter_kernel<NPER, HASHED>, threads, smem));
     if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
     if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
     const int64_t grid = std::min<int64_t>(fa.n_tiles, (int64_t)num_sms * per_sm);
-    filter_kernel<NPER><<<(unsigned)grid, threads, smem, s>>>(fa, map);
+    filter_kernel<NPER, HASHED><<<(unsigned)grid, threads, smem, s>>>(fa, map);
     HOPH_CUDA_TRY(cudaGetLastError());
     return HOPH_OK;
 }
@@ -1253,12 +1313,23 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
     // whose K == 0 pairs are the all-empty ones, and a key space (the psi-space
     // of the scanned bins) whose 2-bit group map fits in shared memory next
     // to two filter stages
+    // Key space: the psi-space of the scanned bins.  Up to kDirectMap keys the
+    // group map is indexed by key (no false hits); beyond, by a hash into
+    // kHashedMapSlots slots (false hits only loosen the filter).  Up to
+    // kMaxJoinKeys keys the CSR is indexed by key; beyond, through a key table.
     const uint64_t keys = mode == HOPH_MODE_MINWISE_FULL ? ~0ull : plan->lo[W];
+    const bool map_hashed = keys > kDirectMap;
+    const uint64_t map_slots = map_hashed ? kHashedMapSlots : keys;
+    const bool csr_hashed = keys > kMaxJoinKeys;
+    uint64_t csr_slots = keys;
+    if (csr_hashed) {
+        csr_slots = 1024;
+        while (csr_slots < 2ull * (uint64_t)n_queries * W) csr_slots <<= 1;
+    }
     bool join_ok = mode != HOPH_MODE_MINWISE_FULL && fp.rule != HOPH_EMPTY_EITHER &&
-                   tma_base_ok && kg % 32 == 0 && W <= 256 && keys <= kMaxJoinKeys &&
-                   n_queries <= 4096 &&
-                   n_rows < (1ll << 32) &&
-                   keys / 4 + 2 * 32 * W * 4 + 8 * W + 4096 <= (uint64_t)kSmemLimit;
+                   tma_base_ok && kg % 32 == 0 && W <= 256 && n_queries <= 4096 &&
+                   n_rows < (1ll << 32) && csr_slots < (1ull << 31) &&
+                   map_slots / 4 + 2 * 32 * W * 4 + 8 * W + 4096 <= (uint64_t)kSmemLimit;
     for (int K = 1; K <= W && join_ok; ++K) join_ok = tab[K] >= 1;
     int strategy = plan->exec.strategy;
     if (strategy == 1 && !join_ok) return HOPH_ERR_UNSUPPORTED;
@@ -1276,10 +1347,11 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         bump.off = 0;
         bump.take(st_b);
         if (strategy == 1) {
-            bump.take((keys + 1) * 4);                                  // counts
-            bump.take((keys + 1) * 4);                                  // csr_off
-            bump.take(((keys + 1 + kScanChunk - 1) / kScanChunk) * 4);  // block sums
-            bump.take((keys / 16 + 1) * 4);                             // group map
+            bump.take((csr_slots + 1) * 4);                                  // counts
+            bump.take((csr_slots + 1) * 4);                                  // csr_off
+            bump.take(((csr_slots + 1 + kScanChunk - 1) / kScanChunk) * 4);  // block sums
+            bump.take((map_slots / 16 + 1) * 4);                             // group map
+            bump.take(csr_hashed ? csr_slots * 8 : 8);                       // key table
             bump.take((size_t)n_queries * W * 2);                       // csr_q
             bump.take((size_t)n_queries * mask_words * 4);              // q_emask
             bump.take((size_t)n_queries * 4 + 4);                       // allempty + count
@@ -1300,12 +1372,14 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
              *q_emask = nullptr, *n_allempty = nullptr, *cand = nullptr;
     uint16_t *csr_q = nullptr;
     int32_t *allempty = nullptr;
+    unsigned long long *tkey = nullptr;
     unsigned long long *n_cand = nullptr;
     if (strategy == 1) {
-        counts = (uint32_t *)bump.take((keys + 1) * 4);
-        csr_off = (uint32_t *)bump.take((keys + 1) * 4);
-        sums = (uint32_t *)bump.take(((keys + 1 + kScanChunk - 1) / kScanChunk) * 4);
-        gmap = (uint32_t *)bump.take((keys / 16 + 1) * 4);
+        counts = (uint32_t *)bump.take((csr_slots + 1) * 4);
+        csr_off = (uint32_t *)bump.take((csr_slots + 1) * 4);
+        sums = (uint32_t *)bump.take(((csr_slots + 1 + kScanChunk - 1) / kScanChunk) * 4);
+        gmap = (uint32_t *)bump.take((map_slots / 16 + 1) * 4);
+        tkey = (unsigned long long *)bump.take(csr_hashed ? csr_slots * 8 : 8);
         csr_q = (uint16_t *)bump.take((size_t)n_queries * W * 2);
         q_emask = (uint32_t *)bump.take((size_t)n_queries * mask_words * 4);
         allempty = (int32_t *)bump.take((size_t)n_queries * 4 + 4);
@@ -1352,16 +1426,23 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         ia.binbase = plan->d_lo;
         ia.counts = counts;
         ia.gmap = gmap;
+        ia.map_hashed = map_hashed;
+        ia.map_mask = (uint32_t)(map_slots - 1);
+        ia.csr_hashed = csr_hashed;
+        ia.tkey = tkey;
+        ia.tmask = (uint32_t)(csr_slots - 1);
+        ia.status = plan->d_status;
         ia.q_emask = q_emask;
         ia.allempty = allempty;
         ia.n_allempty = n_allempty;
-        HOPH_CUDA_TRY(cudaMemsetAsync(counts, 0, (keys + 1) * 4, s));
-        HOPH_CUDA_TRY(cudaMemsetAsync(gmap, 0, (keys / 16 + 1) * 4, s));
+        HOPH_CUDA_TRY(cudaMemsetAsync(counts, 0, (csr_slots + 1) * 4, s));
+        HOPH_CUDA_TRY(cudaMemsetAsync(gmap, 0, (map_slots / 16 + 1) * 4, s));
+        if (csr_hashed) HOPH_CUDA_TRY(cudaMemsetAsync(tkey, 0xFF, csr_slots * 8, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(n_allempty, 0, 4, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(n_cand, 0, 8, s));
         const unsigned qb = (unsigned)((n_queries * 32 + 255) / 256);
         join_count_kernel<<<qb, 256, 0, s>>>(ia);
-        const int64_t n_scan = (int64_t)keys + 1;
+        const int64_t n_scan = (int64_t)csr_slots + 1;
         const int64_t nb = (n_scan + kScanChunk - 1) / kScanChunk;
         scan_sums_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, n_scan, sums);
         scan_top_kernel<<<1, kScanBlock, 0, s>>>(sums, nb);
@@ -1377,7 +1458,8 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         fa.Gs = Gs;
         fa.W = W;
         fa.gmap = gmap;
-        fa.gmap_words = (uint32_t)(keys / 16 + 1);
+        fa.gmap_words = (uint32_t)(map_slots / 16 + 1);
+        fa.map_mask = (uint32_t)(map_slots - 1);
         fa.binbase = plan->d_lo;
         fa.row_min = pa.thr + 2 * (W + 1);
         const int K0 = hoph_effective(fp.rule, W, W, 0);
@@ -1414,10 +1496,12 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
             return HOPH_ERR_UNSUPPORTED;
         const FilterSmem FL = filter_smem(fa);
         hoph_timing_mark(plan, 1, s);
-        const int frc = nper == 32 ? launch_filter<32>(fa, map, FL.total, plan->num_sms,
-                                                       plan->exec.ctas_per_sm, s)
-                                   : launch_filter<16>(fa, map, FL.total, plan->num_sms,
-                                                       plan->exec.ctas_per_sm, s);
+        const int cps = plan->exec.ctas_per_sm;
+        const int frc =
+            nper == 32 ? (map_hashed ? launch_filter<32, true>(fa, map, FL.total, plan->num_sms, cps, s)
+                                     : launch_filter<32, false>(fa, map, FL.total, plan->num_sms, cps, s))
+                       : (map_hashed ? launch_filter<16, true>(fa, map, FL.total, plan->num_sms, cps, s)
+                                     : launch_filter<16, false>(fa, map, FL.total, plan->num_sms, cps, s));
         if (frc != HOPH_OK) return frc;
         hoph_timing_mark(plan, 2, s);
 
@@ -1427,6 +1511,9 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         ca.cand = cand;
         ca.n_cand = n_cand;
         ca.binbase = plan->d_lo;
+        ca.csr_hashed = csr_hashed;
+        ca.tkey = tkey;
+        ca.tmask = (uint32_t)(csr_slots - 1);
         ca.csr_off = csr_off;
         ca.csr_q = csr_q;
         ca.q_emask = q_emask;

@@ -233,3 +233,52 @@ def test_join_execution_knobs_do_not_change_results(small, kg, lpr, warps, stage
         pairs, n, st = plan.query("hoph", q, q.shape[1], c, c.shape[1], stats=True)
         assert pairs_tuples(pairs) == oracle_tuples(want)
         assert st.strategy == 1 and st.rows_counted < c.shape[1]
+
+
+def _planted_workload(n_rows, size_lo, size_hi, n_q, D, seed):
+    sizes = synth.uniform_sizes(n_rows, size_lo, size_hi, seed)
+    ids, off = synth.distinct_uniform_sets(sizes, D, seed + 1)
+    rng = np.random.default_rng(seed + 2)
+    src = rng.integers(0, n_rows, n_q // 2)
+    planted, _ = synth.plant_near_duplicates([ids[off[r]:off[r + 1]] for r in src], D, 0.5,
+                                             0.98, seed + 3)
+    fresh_ids, fresh_off = synth.distinct_uniform_sets(
+        synth.uniform_sizes(n_q - len(planted), size_lo, size_hi, seed + 4), D, seed + 5)
+    qsets = planted + [fresh_ids[fresh_off[i]:fresh_off[i + 1]] for i in range(len(fresh_off) - 1)]
+    q_ids, q_off = synth.pack_sets(qsets)
+    return ids, off, q_ids, q_off
+
+
+@pytest.mark.parametrize("case", ["hash61_2to1_k512", "oph_full_D2^22"])
+def test_large_key_spaces_use_the_hashed_join(case):
+    """Key spaces too large to index directly: a hashed group map (false hits
+    only loosen the row filter) and, beyond 2^23 keys, an open-addressing key
+    table.  Results stay the oracle's; the join must be the strategy used."""
+    dev = device()
+    if case.startswith("hash61"):
+        D, k, kg, ab, mode = 1 << 32, 512, 128, (2, 1), "hoph"
+        ids, off, q_ids, q_off = _planted_workload(1500, 1000, 3000, 64, D, 41)
+        kw = dict(perm_kind=hoph.HOPH_PERM_HASH61)
+    else:
+        D, k, kg, ab, mode = 1 << 22, 128, 32, (0, 0), "oph_full"
+        ids, off, q_ids, q_off = _planted_workload(3000, 100, 600, 48, D, 43)
+        kw = {}
+    thr = (7, 10)
+    with hoph.Plan(D, k, kg, *ab, seed=7, thr=thr, epsilon=1e-4, **kw) as plan:
+        c = plan.sketch(to_dev(ids, dev), to_dev(off, dev), len(off) - 1)
+        q = plan.sketch(to_dev(q_ids, dev), to_dev(q_off, dev), len(q_off) - 1)
+        plan.check()
+        c_rows, q_rows = planes_to_rows(c), planes_to_rows(q)
+        lo = oc.layout(D, k, kg, *ab)
+        if case.startswith("hash61"):
+            want_c = oc.sketch(ids, off, lo, D=D, hash_ab=oc.hash_params(7))
+        else:
+            want_c = oc.sketch(ids, off, lo, perm=oc.permutation(D, 7))
+        assert np.array_equal(c_rows, want_c)
+        z = np.diff(lo[::kg]).astype(np.uint64)
+        want = oc.query(mode, q_rows, c_rows, kg, thr[0], thr[1], 1e-4, z=z)
+        assert want["count"] > 0
+        plan.set_exec(strategy=1)
+        pairs, n, st = plan.query(mode, q, q.shape[1], c, c.shape[1], stats=True)
+        assert st.strategy == 1
+        assert pairs_tuples(pairs) == oracle_tuples(want)
