@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--serve-rates", default="2000,20000,100000",
                    help="Poisson arrival rates (query sets per second)")
     p.add_argument("--serve-seconds", type=float, default=1.5)
+    p.add_argument("--no-shingle", action="store_true", help="skip the D=2^32 shingle workload")
+    p.add_argument("--shingle-rows", type=int, default=5_000_000)
+    p.add_argument("--shingle-queries", type=int, default=100_000)
     return p.parse_args()
 
 
@@ -425,6 +428,10 @@ def run_native(args):
         line["cpu_baseline"] = cpu_baseline(qw, off, coll_seed, args.cpu_seconds, args.rows)
         if not args.no_serve:
             line["serving"] = serving_leg(args, planes, dev, line["oph_full_scan_baseline"])
+        if not args.no_shingle:
+            del planes
+            torch.cuda.empty_cache()
+            line["shingle"] = shingle_leg(args, dev, stream, peaks)
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -626,6 +633,99 @@ def serving_leg(args, planes, dev, oph_leg):
                 1e3 / oph_leg["ms_per_query_launch"],
             "how": "2 streams x 1 plan each, one CUDA graph per (stream, batch size); H2D of a "
                    "batch's sets and its sketching overlap the query of the other stream"}
+
+
+def shingle_leg(args, dev, stream, peaks, q_batch=1024, n_planted=32):
+    """Large-set shingle regime: IDs uniform over 2^32, psi the 2-universal
+    hash mod 2^61-1, (2:1)HOPH with k = 512, k' = 128 (G = 4), T = 0.7.  The
+    collection (sizes U[1000, 100000]) is generated and sketched inside the
+    kernel; the query sets (same law) are stored in HBM and sketched like any
+    input; queries run in batches of 1,024 through the hashed join."""
+    import torch
+    from paper_1805_11254_gb300 import hoph, synth
+    D4, K4, KG4, AB4 = 1 << 32, 512, 128, (2, 1)
+    seed_c, seed_q = 31, 32
+    out = {"workload": "collection %d sets and %d queries, sizes U[1000, 100000], IDs uniform "
+                       "over 2^32, (2:1)HOPH k=512 k'=128, T=0.7, eps=1e-4"
+                       % (args.shingle_rows, args.shingle_queries)}
+    with hoph.Plan(D4, K4, KG4, *AB4, perm_kind=hoph.HOPH_PERM_HASH61, seed=PERM_SEED, thr=T,
+                   epsilon=EPS) as plan:
+        c_sizes = synth.uniform_sizes(args.shingle_rows, 1000, 100000, seed_c)
+        c_off = synth.offsets_from_sizes(c_sizes)
+        d_coff = to_dev(c_off, dev)
+        planes = torch.empty((plan.G, args.shingle_rows, KG4), dtype=torch.int32, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hoph.hoph_synth_sketch(plan.handle, seed_c, D4, d_coff, args.shingle_rows, planes, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.check()
+        ms = e0.elapsed_time(e1)
+        out["collection_generate_and_sketch"] = {
+            "sets_per_s": args.shingle_rows / (ms / 1e3), "ids_per_s": int(c_off[-1]) / (ms / 1e3),
+            "ms": ms, "ids": int(c_off[-1]), "bound": "alu (generator + 61-bit mulmod + bin search)"}
+        # query sets: a few planted near duplicates of collection rows, the rest fresh
+        rng = np.random.default_rng(seed_q)
+        src = rng.integers(0, args.shingle_rows, n_planted)
+        bases = [synth.counter_ids(seed_c, int(c_off[r]), int(c_sizes[r]), D4) for r in src]
+        planted, _ = synth.plant_near_duplicates(bases, D4, 0.75, 0.98, seed_q + 1)
+        p_ids, p_off = synth.pack_sets(planted)
+        q_sizes = np.concatenate([np.diff(p_off),
+                                  synth.uniform_sizes(args.shingle_queries - n_planted, 1000,
+                                                      100000, seed_q + 2)])
+        q_off = synth.offsets_from_sizes(q_sizes)
+        d_qids = torch.empty(int(q_off[-1]), dtype=torch.int32, device=dev)
+        d_qids[:len(p_ids)].copy_(torch.from_numpy(p_ids.view(np.int32)))
+        hoph.hoph_synth_ids(seed_q + 3, 0, int(q_off[-1]) - len(p_ids), D4, 0, None, 0,
+                            d_qids[len(p_ids):], stream)
+        d_qoff = to_dev(q_off, dev)
+        nq = args.shingle_queries
+        q_planes = torch.empty((plan.G, nq, KG4), dtype=torch.int32, device=dev)
+        for _ in range(2):
+            plan.sketch(d_qids, d_qoff, nq, out=q_planes, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        reps = 3
+        for _ in range(reps):
+            plan.sketch(d_qids, d_qoff, nq, out=q_planes, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.check()
+        ms = e0.elapsed_time(e1) / reps
+        byts = 4 * int(q_off[-1]) + 8 * (nq + 1) + 4 * K4 * nq
+        gbs = byts / (ms / 1e3) / 1e9
+        out["query_sketch"] = {"sets_per_s": nq / (ms / 1e3), "ms": ms, "ids": int(q_off[-1]),
+                               "GB_per_s": gbs, "hbm_frac": gbs / peaks["hbm_gbs"]}
+        del d_qids
+        # batches of 1,024 query sketches against the collection
+        cap = 1 << 16
+        outp = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        st = torch.zeros(hoph.STATS_WORDS, dtype=torch.int64, device=dev)
+        batches = [q_planes[:, b:b + q_batch].contiguous() for b in range(0, nq, q_batch)]
+        sizes_b = [bq.shape[1] for bq in batches]
+        hoph.hoph_query_batch(plan.handle, "hoph", batches[0], sizes_b[0], planes,
+                              args.shingle_rows, outp, cap, cnt, st, stream)
+        torch.cuda.synchronize()
+        plan.check()
+        first = outp[:int(cnt.item())].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+        found = {(int(p["query"]), int(p["row"])) for p in first}
+        stats = hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes())
+        e0.record(stream)
+        for bq, n in zip(batches, sizes_b):
+            hoph.hoph_query_batch(plan.handle, "hoph", bq, n, planes, args.shingle_rows, outp, cap,
+                                  cnt, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.check()
+        ms = e0.elapsed_time(e1)
+        out["hoph_query"] = {
+            "pair_comparisons_per_s": nq * args.shingle_rows / (ms / 1e3),
+            "ms_per_1024_batch": ms / len(batches), "batches": len(batches),
+            "strategy": int(stats.strategy), "candidate_rows_first_batch": int(stats.rows_counted),
+            "planted_found": sum((q, int(r)) in found for q, r in enumerate(src)),
+            "planted": n_planted}
+    return out
 
 
 def main():

@@ -281,6 +281,16 @@ int hoph_plan_peek_timing(hoph_plan *plan, double *ms);
  */
 int hoph_check_bounded_wait(hoph_plan *plan, uint64_t limit_ns, void *stream);
 
+/*
+ * Sketches of synthetic sets whose IDs are generated inside the kernel and
+ * never stored (benchmark inputs of any size; same sketches as
+ * hoph_synth_ids followed by oph_build_sketches): set i holds the kind-0 IDs
+ * (uniform over 0..D-1) of elements d_offsets[i] .. d_offsets[i+1]-1 of the
+ * generator stream `seed`.  Output layout and errors as oph_build_sketches.
+ */
+int hoph_synth_sketch(hoph_plan *plan, uint64_t seed, uint64_t D, const int64_t *d_offsets,
+                      int64_t n_sets, uint32_t *d_planes, void *stream);
+
 /* Synchronise `stream`, then return and clear the plan's device status word
  * (HOPH_OK if no device-side error was recorded). */
 int hoph_sync_status(hoph_plan *plan, void *stream);

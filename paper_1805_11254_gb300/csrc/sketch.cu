@@ -39,8 +39,21 @@ struct SketchArgs {
     uint64_t ha, hb;
     const int32_t *order;  // size-sorted set indices, or nullptr for 0..n-1
     const uint32_t *n_big; // items [0, *n_big) of order are sketched a CTA per set
+    int32_t generate;      // IDs come from the counter generator, not from ids[]
+    uint64_t gen_seed;     // generator stream; set i's IDs are elements off[i]..off[i+1]-1
+    uint64_t gen_D;        // generated IDs are uniform over 0..gen_D-1
     int32_t *status;
 };
+
+// Synthetic ID of element e of stream `seed`: the (e+1)-th SplitMix64 output
+// mapped to [0, D) by a multiply-shift of its top 32 bits (hoph_synth_ids kind 0).
+__device__ __forceinline__ uint32_t synth_id(uint64_t seed, uint64_t e, uint64_t D) {
+    uint64_t z = seed + (e + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (uint32_t)(((z >> 32) * D) >> 32);
+}
 
 // psi(x) = ((a x + b) mod (2^61 - 1)) >> 29 with a Mersenne-prime reduction:
 // a x = hi 2^64 + lo == 8 hi + (lo >> 61) + (lo & p)  (mod p).
@@ -110,6 +123,47 @@ __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *
     for (int64_t j = tail0 + t; j < n; j += T) apply(locate(p[j]));
 }
 
+// As sketch_ids, with the IDs of elements [first, first + n) of the
+// generator stream produced in registers instead of loaded.
+template <bool HASH>
+__device__ __forceinline__ void sketch_generated(const SketchArgs &a, const uint64_t *s_lo,
+                                                 uint32_t *sk, uint64_t first, int64_t n, int t,
+                                                 int T, bool &bad) {
+    const uint32_t mask = a.key_bits >= 32 ? 0xFFFFFFFFu : ((1u << a.key_bits) - 1u);
+    auto locate = [&](uint32_t x) -> uint64_t {
+        if (HASH) {
+            const uint32_t v = hash61(x, a.ha, a.hb);
+            uint32_t l = 0, h = a.k;  // lo[l] <= v < lo[h]
+            while (h - l > 1) {
+                const uint32_t m = (l + h) >> 1;
+                if (s_lo[m] <= v) l = m; else h = m;
+            }
+            return ((uint64_t)l << 32) | (uint32_t)(v - s_lo[l]);
+        } else {
+            if (x >= a.D) return (uint64_t)a.k << 32;
+            const uint32_t key = __ldg(a.key + x);
+            return ((uint64_t)(uint32_t)((uint64_t)key >> a.key_bits) << 32) | (key & mask);
+        }
+    };
+    auto apply = [&](uint64_t bo) {
+        const uint32_t bin = (uint32_t)(bo >> 32), off = (uint32_t)bo;
+        if (bin >= a.k) {
+            bad = true;
+            return;
+        }
+        if (off < sk[bin]) atomicMin(sk + bin, off);
+    };
+    int64_t j = t;
+    for (; j + 3 * (int64_t)T < n; j += 4 * (int64_t)T) {
+        const uint64_t b0 = locate(synth_id(a.gen_seed, first + j, a.gen_D));
+        const uint64_t b1 = locate(synth_id(a.gen_seed, first + j + T, a.gen_D));
+        const uint64_t b2 = locate(synth_id(a.gen_seed, first + j + 2 * T, a.gen_D));
+        const uint64_t b3 = locate(synth_id(a.gen_seed, first + j + 3 * T, a.gen_D));
+        apply(b0); apply(b1); apply(b2); apply(b3);
+    }
+    for (; j < n; j += T) apply(locate(synth_id(a.gen_seed, first + j, a.gen_D)));
+}
+
 // group-major store of one finished sketch (bin b -> plane b / k', slot b % k')
 // and reset of the shared copy
 __device__ __forceinline__ void store_sketch(const SketchArgs &a, uint32_t *sk, int64_t set, int t,
@@ -141,7 +195,10 @@ __global__ void __launch_bounds__(kSketchThreads) oph_sketch_kernel(const Sketch
          item += warps_total) {
         const int64_t set = a.order ? a.order[item] : item;
         const int64_t beg = a.off[set], end = a.off[set + 1];
-        sketch_ids<HASH>(a, s_lo, sk, a.ids + beg, end - beg, lane, 32, bad);
+        if (a.generate)
+            sketch_generated<HASH>(a, s_lo, sk, (uint64_t)beg, end - beg, lane, 32, bad);
+        else
+            sketch_ids<HASH>(a, s_lo, sk, a.ids + beg, end - beg, lane, 32, bad);
         __syncwarp();
         store_sketch(a, sk, set, lane, 32);
         __syncwarp();
@@ -165,7 +222,11 @@ __global__ void __launch_bounds__(kSketchThreads) oph_sketch_big_kernel(const Sk
     for (int64_t item = blockIdx.x; item < n_big; item += gridDim.x) {
         const int64_t set = a.order[item];
         const int64_t beg = a.off[set], end = a.off[set + 1];
-        sketch_ids<HASH>(a, s_lo, sk, a.ids + beg, end - beg, threadIdx.x, blockDim.x, bad);
+        if (a.generate)
+            sketch_generated<HASH>(a, s_lo, sk, (uint64_t)beg, end - beg, threadIdx.x, blockDim.x,
+                                   bad);
+        else
+            sketch_ids<HASH>(a, s_lo, sk, a.ids + beg, end - beg, threadIdx.x, blockDim.x, bad);
         __syncthreads();
         store_sketch(a, sk, set, threadIdx.x, blockDim.x);
         __syncthreads();
@@ -301,6 +362,9 @@ SketchArgs sketch_args(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_
     a.hb = plan->hash_b;
     a.order = nullptr;
     a.n_big = nullptr;
+    a.generate = 0;
+    a.gen_seed = 0;
+    a.gen_D = 0;
     a.status = plan->d_status;
     return a;
 }
@@ -374,6 +438,26 @@ int oph_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_
     if (n_sets == 0) return HOPH_OK;
     cudaStream_t s = (cudaStream_t)stream;
     SketchArgs a = sketch_args(plan, d_ids, d_offsets, n_sets, d_planes);
+    if (n_sets >= kWorkListMin) {
+        const size_t bytes = (3 * kBuckets + 1) * sizeof(uint32_t) + (size_t)n_sets * sizeof(int32_t);
+        uint32_t *wl = (uint32_t *)hoph_scratch(plan, bytes);
+        if (!wl) return HOPH_ERR_NOMEM;
+        const int rc = build_work_list(plan, d_offsets, n_sets, wl, a, s);
+        if (rc != HOPH_OK) return rc;
+    }
+    return launch_sketch(plan, a, s);
+}
+
+int hoph_synth_sketch(hoph_plan *plan, uint64_t seed, uint64_t D, const int64_t *d_offsets,
+                      int64_t n_sets, uint32_t *d_planes, void *stream) {
+    if (!plan || n_sets < 0 || (n_sets > 0 && (!d_offsets || !d_planes))) return HOPH_ERR_PARAM;
+    if (n_sets >= (1ll << 31) || D == 0 || D > (1ull << 32)) return HOPH_ERR_PARAM;
+    if (n_sets == 0) return HOPH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    SketchArgs a = sketch_args(plan, nullptr, d_offsets, n_sets, d_planes);
+    a.generate = 1;
+    a.gen_seed = seed;
+    a.gen_D = D;
     if (n_sets >= kWorkListMin) {
         const size_t bytes = (3 * kBuckets + 1) * sizeof(uint32_t) + (size_t)n_sets * sizeof(int32_t);
         uint32_t *wl = (uint32_t *)hoph_scratch(plan, bytes);

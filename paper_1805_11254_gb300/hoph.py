@@ -97,7 +97,7 @@ _EXPORTS = ["hoph_plan_create", "hoph_plan_create_with_perm", "hoph_plan_destroy
             "minwise_build_sketches", "hoph_query_batch", "hoph_pair_counts", "hoph_synth_ids",
             "hoph_sync_status", "hoph_status_string", "hoph_plan_enable_timing",
             "hoph_plan_read_timing", "oph_build_sketches_static", "hoph_plan_peek_timing",
-            "hoph_check_bounded_wait"]
+            "hoph_check_bounded_wait", "hoph_synth_sketch"]
 
 
 def load(path=LIB_PATH):
@@ -139,6 +139,8 @@ def load(path=LIB_PATH):
     lib.hoph_plan_enable_timing.restype = i32
     lib.hoph_plan_read_timing.argtypes = [P, P, P, P]
     lib.hoph_plan_read_timing.restype = i32
+    lib.hoph_synth_sketch.argtypes = [P, u64, u64, P, i64, P, P]
+    lib.hoph_synth_sketch.restype = i32
     lib.hoph_check_bounded_wait.argtypes = [P, u64, P]
     lib.hoph_check_bounded_wait.restype = i32
     lib.hoph_plan_peek_timing.argtypes = [P, P]
@@ -278,6 +280,11 @@ def hoph_plan_peek_timing(plan):
     ms = (ctypes.c_double * 4)()
     _check(load().hoph_plan_peek_timing(plan, ctypes.addressof(ms)), "hoph_plan_peek_timing")
     return list(ms)
+
+
+def hoph_synth_sketch(plan, seed, D, d_offsets, n_sets, d_planes, stream=None):
+    return _check(load().hoph_synth_sketch(plan, int(seed), int(D), _ptr(d_offsets), int(n_sets),
+                                           _ptr(d_planes), _stream(stream)), "hoph_synth_sketch")
 
 
 def hoph_check_bounded_wait(plan, limit_ns, stream=None):

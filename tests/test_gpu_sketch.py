@@ -181,3 +181,30 @@ def test_large_sets_take_the_cta_path(hash_perm):
     else:
         want = oc.sketch(ids, off, lo, perm=oc.permutation(D, 3))
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("hash_perm", [False, True])
+def test_generated_sets_sketch_like_stored_ones(hash_perm):
+    """hoph_synth_sketch (IDs generated in the kernel) equals the oracle's
+    sketch of the host-regenerated IDs, through both the warp and CTA paths."""
+    dev = device()
+    rng = np.random.default_rng(21)
+    sizes = np.concatenate([rng.integers(0, 3000, 150), [2048, 9000, 40000]]).astype(np.int64)
+    off = synth.offsets_from_sizes(sizes) + 12345  # any element window of the stream
+    if hash_perm:
+        D, k, kg, ab, kind = 1 << 32, 512, 128, (2, 1), hoph.HOPH_PERM_HASH61
+    else:
+        D, k, kg, ab, kind = 1 << 20, 256, 64, (1, 2), hoph.HOPH_PERM_TABLE
+    seed = 77
+    with hoph.Plan(D, k, kg, *ab, perm_kind=kind, seed=5) as plan:
+        planes = torch.empty((plan.G, len(sizes), kg), dtype=torch.int32, device=dev)
+        hoph.hoph_synth_sketch(plan.handle, seed, D, to_dev(off, dev), len(sizes), planes)
+        plan.check()
+        got = planes_to_rows(planes)
+    ids = synth.counter_ids(seed, int(off[0]), int(off[-1] - off[0]), D)
+    lo = oc.layout(D, k, kg, *ab)
+    if hash_perm:
+        want = oc.sketch(ids, off - off[0], lo, D=D, hash_ab=oc.hash_params(5))
+    else:
+        want = oc.sketch(ids, off - off[0], lo, perm=oc.permutation(D, 5))
+    assert np.array_equal(got, want)
