@@ -663,7 +663,7 @@ def shingle_leg(args, dev, stream, peaks, q_batch=1024, n_planted=32):
         ms = e0.elapsed_time(e1)
         out["collection_generate_and_sketch"] = {
             "sets_per_s": args.shingle_rows / (ms / 1e3), "ids_per_s": int(c_off[-1]) / (ms / 1e3),
-            "ms": ms, "ids": int(c_off[-1]), "bound": "alu (generator + 61-bit mulmod + bin search)"}
+            "ms": ms, "ids": int(c_off[-1]), "bound": "alu (generator + 61-bit mulmod + bin arithmetic)"}
         # query sets: a few planted near duplicates of collection rows, the rest fresh
         rng = np.random.default_rng(seed_q)
         src = rng.integers(0, args.shingle_rows, n_planted)

@@ -25,6 +25,17 @@ constexpr int kSketchWarps = kSketchThreads / 32;
 constexpr int kBuckets = 65;
 constexpr int kBigBucket = 12;  // sets of >= 2048 IDs (bit length >= 12) get a whole CTA
 
+// Hash path: psi-space regions of equal-width bins (the whole space for equal
+// bins, one per group for a:b); a value's bin is first + floor(o * nb / z).
+struct RegionTable {
+    int32_t n;
+    uint32_t start[HOPH_MAX_GROUPS];
+    uint64_t size[HOPH_MAX_GROUPS];
+    uint32_t bins[HOPH_MAX_GROUPS];
+    uint32_t first[HOPH_MAX_GROUPS];
+    float ratio[HOPH_MAX_GROUPS];  // bins / size
+};
+
 struct SketchArgs {
     const uint32_t *ids;
     const int64_t *off;
@@ -39,6 +50,7 @@ struct SketchArgs {
     uint64_t ha, hb;
     const int32_t *order;  // size-sorted set indices, or nullptr for 0..n-1
     const uint32_t *n_big; // items [0, *n_big) of order are sketched a CTA per set
+    RegionTable reg;       // hash path: bin regions
     int32_t generate;      // IDs come from the counter generator, not from ids[]
     uint64_t gen_seed;     // generator stream; set i's IDs are elements off[i]..off[i+1]-1
     uint64_t gen_D;        // generated IDs are uniform over 0..gen_D-1
@@ -67,25 +79,38 @@ __device__ __forceinline__ uint32_t hash61(uint64_t x, uint64_t a, uint64_t b) {
     return (uint32_t)(t >> 29);
 }
 
+// Bin and offset of a hashed psi-value v: the region containing v (a few
+// comparisons against the region starts), then floor(o * nb / z) from a
+// float estimate corrected by one exact integer step each way (the float
+// error is far below one bin), then the offset from the bin's lower bound.
+__device__ __forceinline__ uint64_t hash_bin(const RegionTable &t, const uint64_t *s_lo, uint32_t v) {
+    int r = 0;
+    for (int i = 1; i < t.n; ++i) r += v >= t.start[i];
+    const uint32_t o = v - t.start[r];
+    const uint64_t ok = (uint64_t)o * t.bins[r];
+    const uint64_t z = t.size[r];
+    uint32_t q = (uint32_t)((float)o * t.ratio[r]);
+    if (q >= t.bins[r]) q = t.bins[r] - 1;
+    if ((uint64_t)q * z > ok) --q;
+    else if ((uint64_t)(q + 1) * z <= ok) ++q;
+    const uint32_t bin = t.first[r] + q;
+    return ((uint64_t)bin << 32) | (uint32_t)(v - s_lo[bin]);
+}
+
 // One thread's share of the IDs [p, p+n) (thread t of a group of T threads):
 // a scalar head up to a 16-byte boundary, a 128-bit body whose eight table
 // gathers are issued before any of their minima is applied, a scalar tail.
 // Each ID updates the shared sketch `sk` with a read-then-atomicMin.
 template <bool HASH>
 __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *s_lo,
-                                           uint32_t *sk, const uint32_t *p, int64_t n, int t,
-                                           int T, bool &bad) {
+                                           const RegionTable *s_reg, uint32_t *sk,
+                                           const uint32_t *p, int64_t n, int t, int T,
+                                           bool &bad) {
     const uint32_t mask = a.key_bits >= 32 ? 0xFFFFFFFFu : ((1u << a.key_bits) - 1u);
     // psi-value of x as (bin << 32) | offset; bin k marks an ID outside V
     auto locate = [&](uint32_t x) -> uint64_t {
         if (HASH) {
-            const uint32_t v = hash61(x, a.ha, a.hb);
-            uint32_t l = 0, h = a.k;  // lo[l] <= v < lo[h]
-            while (h - l > 1) {
-                const uint32_t m = (l + h) >> 1;
-                if (s_lo[m] <= v) l = m; else h = m;
-            }
-            return ((uint64_t)l << 32) | (uint32_t)(v - s_lo[l]);
+            return hash_bin(*s_reg, s_lo, hash61(x, a.ha, a.hb));
         } else {
             if (x >= a.D) return (uint64_t)a.k << 32;
             const uint32_t key = __ldg(a.key + x);
@@ -127,18 +152,13 @@ __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *
 // generator stream produced in registers instead of loaded.
 template <bool HASH>
 __device__ __forceinline__ void sketch_generated(const SketchArgs &a, const uint64_t *s_lo,
-                                                 uint32_t *sk, uint64_t first, int64_t n, int t,
-                                                 int T, bool &bad) {
+                                                 const RegionTable *s_reg, uint32_t *sk,
+                                                 uint64_t first, int64_t n, int t, int T,
+                                                 bool &bad) {
     const uint32_t mask = a.key_bits >= 32 ? 0xFFFFFFFFu : ((1u << a.key_bits) - 1u);
     auto locate = [&](uint32_t x) -> uint64_t {
         if (HASH) {
-            const uint32_t v = hash61(x, a.ha, a.hb);
-            uint32_t l = 0, h = a.k;  // lo[l] <= v < lo[h]
-            while (h - l > 1) {
-                const uint32_t m = (l + h) >> 1;
-                if (s_lo[m] <= v) l = m; else h = m;
-            }
-            return ((uint64_t)l << 32) | (uint32_t)(v - s_lo[l]);
+            return hash_bin(*s_reg, s_lo, hash61(x, a.ha, a.hb));
         } else {
             if (x >= a.D) return (uint64_t)a.k << 32;
             const uint32_t key = __ldg(a.key + x);
@@ -184,8 +204,11 @@ __global__ void __launch_bounds__(kSketchThreads) oph_sketch_kernel(const Sketch
     uint32_t *s_sk = reinterpret_cast<uint32_t *>(smem_raw + (HASH ? (a.k + 1) * 8 : 0));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *sk = s_sk + (size_t)warp * a.k;
-    if (HASH)
+    __shared__ RegionTable s_reg;
+    if (HASH) {
         for (uint32_t i = threadIdx.x; i <= a.k; i += blockDim.x) s_lo[i] = a.lo[i];
+        if (threadIdx.x == 0) s_reg = a.reg;
+    }
     for (uint32_t i = lane; i < a.k; i += 32) sk[i] = HOPH_EMPTY_VALUE;
     __syncthreads();
     bool bad = false;
@@ -196,9 +219,9 @@ __global__ void __launch_bounds__(kSketchThreads) oph_sketch_kernel(const Sketch
         const int64_t set = a.order ? a.order[item] : item;
         const int64_t beg = a.off[set], end = a.off[set + 1];
         if (a.generate)
-            sketch_generated<HASH>(a, s_lo, sk, (uint64_t)beg, end - beg, lane, 32, bad);
+            sketch_generated<HASH>(a, s_lo, &s_reg, sk, (uint64_t)beg, end - beg, lane, 32, bad);
         else
-            sketch_ids<HASH>(a, s_lo, sk, a.ids + beg, end - beg, lane, 32, bad);
+            sketch_ids<HASH>(a, s_lo, &s_reg, sk, a.ids + beg, end - beg, lane, 32, bad);
         __syncwarp();
         store_sketch(a, sk, set, lane, 32);
         __syncwarp();
@@ -213,8 +236,11 @@ __global__ void __launch_bounds__(kSketchThreads) oph_sketch_big_kernel(const Sk
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *s_lo = reinterpret_cast<uint64_t *>(smem_raw);  // HASH only
     uint32_t *sk = reinterpret_cast<uint32_t *>(smem_raw + (HASH ? (a.k + 1) * 8 : 0));
-    if (HASH)
+    __shared__ RegionTable s_reg;
+    if (HASH) {
         for (uint32_t i = threadIdx.x; i <= a.k; i += blockDim.x) s_lo[i] = a.lo[i];
+        if (threadIdx.x == 0) s_reg = a.reg;
+    }
     for (uint32_t i = threadIdx.x; i < a.k; i += blockDim.x) sk[i] = HOPH_EMPTY_VALUE;
     __syncthreads();
     bool bad = false;
@@ -223,10 +249,11 @@ __global__ void __launch_bounds__(kSketchThreads) oph_sketch_big_kernel(const Sk
         const int64_t set = a.order[item];
         const int64_t beg = a.off[set], end = a.off[set + 1];
         if (a.generate)
-            sketch_generated<HASH>(a, s_lo, sk, (uint64_t)beg, end - beg, threadIdx.x, blockDim.x,
-                                   bad);
+            sketch_generated<HASH>(a, s_lo, &s_reg, sk, (uint64_t)beg, end - beg, threadIdx.x,
+                                   blockDim.x, bad);
         else
-            sketch_ids<HASH>(a, s_lo, sk, a.ids + beg, end - beg, threadIdx.x, blockDim.x, bad);
+            sketch_ids<HASH>(a, s_lo, &s_reg, sk, a.ids + beg, end - beg, threadIdx.x, blockDim.x,
+                             bad);
         __syncthreads();
         store_sketch(a, sk, set, threadIdx.x, blockDim.x);
         __syncthreads();
@@ -365,6 +392,18 @@ SketchArgs sketch_args(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_
     a.generate = 0;
     a.gen_seed = 0;
     a.gen_D = 0;
+    // bin regions of the hash path
+    const bool equal = P.a == 0 && P.b == 0;
+    a.reg.n = equal ? 1 : (int32_t)plan->G;
+    for (int r = 0; r < a.reg.n; ++r) {
+        const uint32_t first = equal ? 0 : (uint32_t)r * P.k_group;
+        const uint32_t nb = equal ? P.k : P.k_group;
+        a.reg.start[r] = (uint32_t)plan->lo[first];
+        a.reg.size[r] = plan->lo[first + nb] - plan->lo[first];
+        a.reg.bins[r] = nb;
+        a.reg.first[r] = first;
+        a.reg.ratio[r] = (float)((double)nb / (double)a.reg.size[r]);
+    }
     a.status = plan->d_status;
     return a;
 }
