@@ -247,7 +247,7 @@ def workload_config(args, world):
 
 def run_native(args):
     import torch
-    from paper_1805_11254_gb300 import build_lib, hoph, synth
+    from paper_1805_11254_gb300 import build_lib, hoph, shard, synth
     rank, world, local = env_rank()
     if world > 1:
         import torch.distributed as dist
@@ -264,11 +264,7 @@ def run_native(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return shard.max_over_ranks(x, device=dev)
 
     # ---- collection (setup, untimed)
     off, coll_seed = collection_host(args.rows, rank)

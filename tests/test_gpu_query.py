@@ -282,3 +282,23 @@ def test_large_key_spaces_use_the_hashed_join(case):
         pairs, n, st = plan.query(mode, q, q.shape[1], c, c.shape[1], stats=True)
         assert st.strategy == 1
         assert pairs_tuples(pairs) == oracle_tuples(want)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_row_shards_merge_to_the_whole_collection(small, world):
+    """Each shard of rows queried alone (as a rank would), rows made global
+    and merged, equals one query of the whole collection."""
+    from paper_1805_11254_gb300 import shard
+    dev = device()
+    with hoph.Plan(small["D"], 128, 32, 1, 1, seed=1, thr=T, epsilon=EPS) as plan:
+        q, c = _sketch_both(plan, small, dev)
+        nq, n = q.shape[1], c.shape[1]
+        whole, _, _ = plan.query(hoph.HOPH_MODE_HOPH, q, nq, c, n)
+        parts = []
+        for r in range(world):
+            r0, r1 = shard.row_range(n, r, world)
+            local = c[:, r0:r1, :].contiguous()
+            run = shard.gpu_local_query(plan, hoph.HOPH_MODE_HOPH, q, nq, local, capacity=4)
+            parts.append(shard.globalize(run(r0, r1), r0))
+        assert len(whole) > 0
+        assert np.array_equal(shard.merge_pairs(parts), whole)
