@@ -57,7 +57,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=100)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-extras", action="store_true", help="skip sketch/OPH/CPU legs")
-    p.add_argument("--profile", action="store_true", help="few launches, for ncu")
+    p.add_argument("--profile", nargs="?", const="query", choices=("query", "sketch"),
+                   help="few launches of the query step (or of the 10^6-set sketch), for ncu")
     p.add_argument("--no-graph", action="store_true", help="eager launches instead of a graph")
     p.add_argument("--no-tune", action="store_true", help="library default execution knobs")
     p.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
@@ -266,6 +267,10 @@ def run_native(args):
     def max_over_ranks(x):
         return shard.max_over_ranks(x, device=dev)
 
+    if args.profile == "sketch":
+        sketch_leg(dev, stream, measured_peaks()[0], steps=2)
+        return
+
     # ---- collection (setup, untimed)
     off, coll_seed = collection_host(args.rows, rank)
     n_ids = int(off[-1])
@@ -417,10 +422,11 @@ def run_native(args):
 
     if rank == 0 and not args.no_extras:
         line["e2e"] = e2e_leg(args, plan, qw, planes, dev, stream)
-        line["quality"] = quality(qw, pairs, off, coll_seed, args)
         line["sketch"] = sketch_leg(dev, stream, peaks)
-        line["oph_full_scan_baseline"] = oph_baseline_leg(args, off, coll_seed, qw, dev, stream,
-                                                          value)
+        line["oph_full_scan_baseline"], oph_pairs = oph_baseline_leg(args, off, coll_seed, qw, dev,
+                                                                     stream, value)
+        line["quality"] = quality(qw, {"hoph": pairs, "oph_full_scan": oph_pairs}, off,
+                                  coll_seed, args)
         line["cpu_baseline"] = cpu_baseline(qw, off, coll_seed, args.cpu_seconds, args.rows)
         if not args.no_serve:
             line["serving"] = serving_leg(args, planes, dev, line["oph_full_scan_baseline"])
@@ -479,14 +485,21 @@ def e2e_leg(args, plan, qw, planes, dev, stream):
             "path": "pinned host sets -> oph_build_sketches -> hoph_query_batch -> host pairs"}
 
 
-def quality(qw, pairs, off, coll_seed, args):
-    """Recall and precision against exact Jaccard >= T: planted pairs (known
-    sources) and every reported pair, exact Jaccard from the CPU oracle."""
+def quality(qw, pairs_by_method, off, coll_seed, args, n_random_rows=2000):
+    """Recall and precision against exact Jaccard >= T, per method, over one
+    ground truth: every planted pair (known source) and every pair any method
+    reported, with exact Jaccard from the CPU oracle.  A random sample of
+    other (query, row) pairs bounds what all methods missed."""
     from oracle import oracle_c as oc
     from paper_1805_11254_gb300 import synth
-    rep = {(int(p["query"]), int(p["row"])) for p in pairs}
+    reps = {m: {(int(p["query"]), int(p["row"])) for p in ps} for m, ps in pairs_by_method.items()}
     planted = {(int(q), int(r)) for q, r in enumerate(qw["src"]) if r >= 0}
-    cand = sorted(rep | planted)
+    rng = np.random.default_rng(Q_SEED + 99)
+    n_rows = len(off) - 1
+    rand_rows = rng.choice(n_rows, size=min(n_random_rows, n_rows), replace=False)
+    nq = len(qw["q_off"]) - 1
+    rand = {(q, int(r)) for q in range(nq) for r in rand_rows}
+    cand = sorted(set().union(*reps.values()) | planted | rand)
     rows = sorted({r for _, r in cand})
     sets = [synth.counter_ids(coll_seed, int(off[r]), int(off[r + 1] - off[r]), D) for r in rows]
     c_ids, c_off = synth.pack_sets(sets)
@@ -495,12 +508,17 @@ def quality(qw, pairs, off, coll_seed, args):
     pb = np.asarray([ridx[r] for _, r in cand], dtype=np.int64)
     inter, uni = oc.jaccard_pairs(qw["q_ids"], qw["q_off"], c_ids, c_off, pa, pb)
     truth = {c for c, i, u in zip(cand, inter, uni) if u and i * T[1] >= T[0] * u}
-    tp = len(rep & truth)
-    return {"reported": len(rep), "truly_similar_among_planted_and_reported": len(truth),
-            "precision": tp / len(rep) if rep else 1.0,
-            "recall": tp / len(truth) if truth else 1.0,
-            "ground_truth": "exact Jaccard (CPU oracle) of planted and reported pairs; random "
-                            "pairs of this workload have Jaccard ~2e-4"}
+    out = {}
+    for m, rep in reps.items():
+        tp = len(rep & truth)
+        out[m] = {"reported": len(rep), "precision": tp / len(rep) if rep else 1.0,
+                  "recall": tp / len(truth) if truth else 1.0}
+    out["truly_similar"] = len(truth)
+    out["random_pairs_checked"] = len(rand)
+    out["truly_similar_among_random"] = len(truth & rand)
+    out["ground_truth"] = ("exact Jaccard (CPU oracle) of planted pairs, of every pair either "
+                           "method reported, and of %d random (query, row) pairs" % len(rand))
+    return out
 
 
 def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
@@ -541,10 +559,12 @@ def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
 
 
 def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, n_launch=8):
-    """Plain OPH over all 256 bins, one query per launch (the dense scan),
-    on a uniform-OPH sketch of the same collection."""
+    """Plain OPH over all 256 bins (Eq. 6) on a uniform-OPH sketch of the same
+    collection: the whole query batch in one call (the library picks the
+    strategy), and one query per launch through the dense scan with its
+    execution knobs tuned for a single query.  Returns (leg, batched pairs)."""
     import torch
-    from paper_1805_11254_gb300 import hoph
+    from paper_1805_11254_gb300 import autotune, hoph
     n_ids = int(off[-1])
     with hoph.Plan(D, K, K, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
         d_off = to_dev(off, dev)
@@ -558,22 +578,44 @@ def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, n_launch
         nq = len(qw["q_off"]) - 1
         q_planes = plan.sketch(dq_ids, dq_off, nq)
         plan.check()
-        plan.set_exec(strategy=0)
         cap = 1 << 16
         out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-        planted = [q for q in range(nq) if qw["src"][q] >= 0][:n_launch]
-        for q in planted[:2]:
-            hoph.hoph_query_batch(plan.handle, 0, q_planes[:, q:q + 1].contiguous(), 1, planes,
-                                  args.rows, out, cap, cnt, None, stream)
-        torch.cuda.synchronize()
-        qs = [q_planes[:, q:q + 1].contiguous() for q in planted]
+        st = torch.zeros(hoph.STATS_WORDS, dtype=torch.int64, device=dev)
+
+        # the whole batch in one call
+        plan.set_exec()
+        hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_OPH_FULL, q_planes, nq, planes,
+                              args.rows, out, cap, cnt, st, stream)
+        plan.check(stream)
+        n_b = int(cnt.item())
+        pairs_b = out[:min(n_b, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1).copy()
+        strategy_b = int(hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes()).strategy)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_OPH_FULL, q_planes, nq, planes,
+                                  args.rows, out, cap, cnt, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1) / reps
+
+        # one query per launch, dense scan tuned for Q = 1
+        planted = [q for q in range(nq) if qw["src"][q] >= 0][:n_launch]
+        qs = [q_planes[:, q:q + 1].contiguous() for q in planted]
+        best, tune_ms = autotune.tune_query(plan, hoph.HOPH_MODE_OPH_FULL, qs[0], 1, planes,
+                                            args.rows, out, cap, cnt, stream,
+                                            candidates=autotune.DENSE_CANDIDATES)
+        for qp in qs[:2]:
+            hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_OPH_FULL, qp, 1, planes, args.rows,
+                                  out, cap, cnt, None, stream)
+        torch.cuda.synchronize()
         e0.record(stream)
         for qp in qs:
-            hoph.hoph_query_batch(plan.handle, 0, qp, 1, planes, args.rows, out, cap, cnt, None,
-                                  stream)
+            hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_OPH_FULL, qp, 1, planes, args.rows,
+                                  out, cap, cnt, None, stream)
         e1.record(stream)
         torch.cuda.synchronize()
         plan.check()
@@ -581,10 +623,17 @@ def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, n_launch
         del planes
         torch.cuda.empty_cache()
     v = args.rows / (ms / 1e3)
-    return {"value": v, "unit": UNIT, "ms_per_query_launch": ms,
-            "hoph_speedup": hoph_value / v,
-            "how": "mode OPH_FULL, dense scan of all 256 bins (10.24 GB), one query per launch, "
-                   "%d launches" % len(qs)}
+    plane_bytes = args.rows * K * 4
+    leg = {"value": v, "unit": UNIT, "ms_per_query_launch": ms,
+           "hbm_GB_per_s": plane_bytes / (ms / 1e3) / 1e9,
+           "hoph_speedup": hoph_value / v,
+           "tuned": best, "tune_ms_by_candidate": tune_ms,
+           "how": "mode OPH_FULL, dense scan of all 256 bins (10.24 GB), one query per launch, "
+                  "%d launches" % len(qs),
+           "batched": {"value": nq * args.rows / (ms_b / 1e3), "unit": UNIT, "ms_per_batch": ms_b,
+                       "queries": nq, "strategy": strategy_b, "accepted": n_b,
+                       "hoph_speedup": hoph_value / (nq * args.rows / (ms_b / 1e3))}}
+    return leg, pairs_b
 
 
 def serving_leg(args, planes, dev, oph_leg):

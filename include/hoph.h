@@ -59,7 +59,8 @@ extern "C" {
 #define HOPH_EMPTY_NONE 2   /* keep all k' bins (Algorithms 1-2 literally)  */
 
 /* HOPH remaining-requirement rule */
-#define HOPH_WEIGHT_SPACE 0 /* groups weighted by their share of V (a:b)   */
+#define HOPH_WEIGHT_SPACE 0   /* groups weighted by their share of V (a:b) */
+#define HOPH_WEIGHT_LITERAL 1 /* Algorithm 2's recursion, r = a / (a + b)  */
 
 #define HOPH_MAX_GROUPS 16
 #define HOPH_EMPTY_VALUE 0xFFFFFFFFu /* the empty-bin marker in a sketch */
@@ -81,7 +82,16 @@ extern "C" {
  *               (0 < T <= 1, thr_den <= 65535).
  *   epsilon     the error tolerance of Definition 1, 0 <= eps.
  *   empty_rule  HOPH_EMPTY_*.
- *   weighting   HOPH_WEIGHT_SPACE.
+ *   weighting   how HOPH turns the groups compared so far into the remaining
+ *               requirement P_r (Algorithm 2).  HOPH_WEIGHT_SPACE: P_r =
+ *               (T Z_all - sum_j z_j M_j / K_j) / Z_rem over the groups' space
+ *               sizes z_j.  HOPH_WEIGHT_LITERAL: Algorithm 2 as printed,
+ *               P <- (P - (M_l / k') r^l) / r^l from P = T with r = a / (a + b)
+ *               (matched bins over k', empty bins ignored); exact only if the
+ *               integers of the scaled recursion fit in 120 bits, else
+ *               hoph_plan_create returns HOPH_ERR_PARAM.  Either way the last
+ *               group ends with the space-weighted estimator of Lemma 3 >= T.
+ *               GOPH / OPH (a = b = 0) ignore it.
  */
 typedef struct {
     uint64_t universe_D;
@@ -129,7 +139,7 @@ typedef struct {
 typedef struct {
     int32_t strategy;        /* -1 auto, 0 dense, 1 value join            */
     int32_t tile_rows;       /* rows per shared-memory tile               */
-    int32_t consumer_warps;  /* scoring warps per CTA                     */
+    int32_t consumer_warps;  /* scoring warps per CTA (dense <= 16, join filter <= 31) */
     int32_t ctas_per_sm;     /* resident CTAs per SM for the scan         */
     int32_t stages;          /* TMA pipeline depth                        */
     int32_t lanes_per_row;   /* join filter: lanes sharing one row (1-8)  */

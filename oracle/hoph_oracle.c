@@ -303,6 +303,8 @@ typedef struct {
     uint32_t td;
     double eps;
     const uint64_t *z; /* group sizes [k/kg] (HOPH) */
+    uint32_t weighting; /* 0 space-weighted, 1 Algorithm 2 as printed */
+    uint32_t a, b;      /* the (a:b) split, r = a/(a+b) */
 } or_query_params;
 
 typedef struct {
@@ -407,9 +409,10 @@ static int compare_pair(query_ctx *c, const uint32_t *s, const uint32_t *t,
         }
         return OR_REJECT;
     }
-    /* HOPH, space-weighted */
+    /* HOPH, space-weighted (or Algorithm 2's printed recursion) */
     {
         i128 Sn = 0, Sd = 1; /* S = Sn/Sd */
+        i128 Pn = tn, Pd = td; /* literal: P = Pn/Pd, from P = T */
         int64_t Zd = 0, Mc = 0, l;
         for (l = 1; l <= n; ++l) {
             int64_t K, Zrem = 0, j;
@@ -429,11 +432,28 @@ static int compare_pair(query_ctx *c, const uint32_t *s, const uint32_t *t,
             *groups = (int)l; *msum = Mc;
             if (l == n)
                 return (Zd > 0 && Sn * td >= (i128)tn * Zd * Sd) ? OR_ACCEPT : OR_REJECT;
-            for (j = l; j < n; ++j) Zrem += (int64_t)p->z[j];
-            /* P_r = (T (Zd + Zrem) - S) / Zrem = num / den */
-            num = (i128)tn * (Zd + Zrem) * Sd - (i128)td * Sn;
-            den = (i128)td * Sd * Zrem;
-            if (Sd > ((i128)1 << 60)) c->err = 3; /* magnitude guard */
+            if (p->weighting == 1) {
+                /* P <- (P - (m/k') r^l) / r^l with r^l = al/cl */
+                i128 al = 1, cl = 1;
+                for (j = 0; j < l; ++j) {
+                    al *= p->a;
+                    cl *= (i128)p->a + p->b;
+                }
+                Pn = Pn * cl * kg - (i128)m * al * Pd;
+                Pd = Pd * al * kg;
+                g = gcd128(Pn < 0 ? -Pn : Pn, Pd);
+                if (g > 1) { Pn /= g; Pd /= g; }
+                if (Pd > ((i128)1 << 60) || Pn > ((i128)1 << 60) || Pn < -((i128)1 << 60))
+                    c->err = 3; /* magnitude guard */
+                num = Pn;
+                den = Pd;
+            } else {
+                for (j = l; j < n; ++j) Zrem += (int64_t)p->z[j];
+                /* P_r = (T (Zd + Zrem) - S) / Zrem = num / den */
+                num = (i128)tn * (Zd + Zrem) * Sd - (i128)td * Sn;
+                den = (i128)td * Sd * Zrem;
+                if (Sd > ((i128)1 << 60)) c->err = 3; /* magnitude guard */
+            }
             ceilm = ceil_div128(num * kg, den);
             if (num * td < (i128)tn * den) { /* P_r < T */
                 if (tail_lower(c, (int64_t)ceilm) <= c->eps) return OR_ACCEPT;

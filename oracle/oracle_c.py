@@ -33,7 +33,8 @@ class QueryParams(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("rule", ctypes.c_uint32),
                 ("k", ctypes.c_uint32), ("kg", ctypes.c_uint32),
                 ("tn", ctypes.c_uint32), ("td", ctypes.c_uint32),
-                ("eps", ctypes.c_double), ("z", ctypes.POINTER(ctypes.c_uint64))]
+                ("eps", ctypes.c_double), ("z", ctypes.POINTER(ctypes.c_uint64)),
+                ("weighting", ctypes.c_uint32), ("a", ctypes.c_uint32), ("b", ctypes.c_uint32)]
 
 
 def load():
@@ -136,10 +137,12 @@ def tails(kg, tn, td):
 
 
 def query(mode, qs, rs, kg, tn, td, eps, rule="both", z=None, per_pair=False,
-          acc_cap=None, threads=None):
+          acc_cap=None, threads=None, weighting="space", ab=(0, 0)):
     """All-pairs comparison.  Returns dict with 'accepted' [n][4] int64
     (q, r, groups, matched) sorted by (q, r), 'count', 'hist' [G+1][3] and,
-    if per_pair, 'dec', 'groups', 'msum' arrays [Q][N]."""
+    if per_pair, 'dec', 'groups', 'msum' arrays [Q][N].  weighting='literal'
+    takes HOPH's remaining requirement from Algorithm 2's recursion with
+    r = a/(a+b), ab = (a, b)."""
     qs = np.ascontiguousarray(qs, dtype=np.uint32)
     rs = np.ascontiguousarray(rs, dtype=np.uint32)
     Q, k = qs.shape
@@ -147,7 +150,8 @@ def query(mode, qs, rs, kg, tn, td, eps, rule="both", z=None, per_pair=False,
     G = k // kg if MODE[mode] in (1, 2) else 1
     zz = np.ascontiguousarray(z if z is not None else np.zeros(max(G, 1)), dtype=np.uint64)
     p = QueryParams(MODE[mode], RULE[rule], k, kg, tn, td, float(eps),
-                    zz.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+                    zz.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                    {"space": 0, "literal": 1}[weighting], ab[0], ab[1])
     dec = grp = ms = None
     if per_pair:
         dec = np.empty((Q, N), dtype=np.int8)
@@ -161,7 +165,7 @@ def query(mode, qs, rs, kg, tn, td, eps, rule="both", z=None, per_pair=False,
     if n < 0:
         raise ValueError("oracle query failed (%d)" % n)
     if n > cap:
-        return query(mode, qs, rs, kg, tn, td, eps, rule, z, per_pair, n, threads)
+        return query(mode, qs, rs, kg, tn, td, eps, rule, z, per_pair, n, threads, weighting, ab)
     out = {"accepted": acc[:n].copy(), "count": int(n), "hist": hist}
     if per_pair:
         out.update(dec=dec, groups=grp, msum=ms)

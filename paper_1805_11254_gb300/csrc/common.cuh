@@ -32,7 +32,8 @@ struct DecideParams {
     int64_t tn, td;     // T = tn / td
     int64_t U, L;       // small-probability limits (valid when !always_stop)
     int32_t always_stop;  // eps >= 1: every tail is <= eps
-    int32_t pad;
+    int32_t literal;      // HOPH_WEIGHT_LITERAL
+    int64_t ra, rc;       // r = ra / rc = a / (a + b) (literal weighting)
     uint64_t zsuf[HOPH_MAX_GROUPS + 1];  // zsuf[g] = sum_{j >= g} z_j
     uint64_t z[HOPH_MAX_GROUPS];
 };
@@ -57,7 +58,8 @@ __host__ __device__ __forceinline__ int32_t hoph_effective(uint32_t rule, int32_
 // i.e. M_ra > U - 1.  All of it is cross-multiplied into integers.
 // HOPH (Algorithm 2, space-weighted): S = sum_{K_j > 0} z_j M_j / K_j is
 // kept as Sn / Lam with Lam = prod K_j; P_r = (T Z_all - S) / Z_rem and the
-// tests read P_r * k' against L and U - 1.
+// tests read P_r * k' against L and U - 1.  With literal weighting P_r
+// follows Algorithm 2's recursion instead (scaled to integers below).
 // After the last group: accept iff the full estimator (Eq. 6 pooled for
 // GOPH, Lemma 3 space-weighted for HOPH) is >= T over a non-empty
 // denominator.
@@ -77,6 +79,29 @@ __host__ __device__ __forceinline__ int hoph_decide(const DecideParams &p, int l
         if (l >= (int)p.G)
             return (Zd > 0 && (__int128)td * Sn >= (__int128)tn * Zd * Lam) ? HOPH_ACCEPT
                                                                             : HOPH_REJECT;
+        if (p.literal) {
+            // P_j = X_j / (td k' a^{s_j}), s_j = j (j + 1) / 2, from X_0 = tn k':
+            // P_j = P_{j-1} (c/a)^j - M_j / k'  <=>  X_j = X_{j-1} c^j - M_j td a^{s_j}
+            __int128 X = (__int128)tn * p.kg, As = 1;
+            for (int j = 1; j <= l; ++j) {
+                __int128 cj = 1, aj = 1;
+                for (int i = 0; i < j; ++i) {
+                    cj *= p.rc;
+                    aj *= p.ra;
+                }
+                As *= aj;
+                X = X * cj - (__int128)M[j - 1] * td * As;
+            }
+            // P_l k' = X / (td a^{s_l})
+            const bool below = X < (__int128)tn * p.kg * As;  // P_l < T
+            if (p.always_stop) return below ? HOPH_ACCEPT : HOPH_REJECT;
+            if (below) {
+                if (X <= (__int128)p.L * td * As) return HOPH_ACCEPT;
+            } else {
+                if (X > (__int128)(p.U - 1) * td * As) return HOPH_REJECT;
+            }
+            return HOPH_CONTINUE;
+        }
         const int64_t Zrem = (int64_t)p.zsuf[l];
         const __int128 num = (__int128)tn * (Zd + Zrem) * Lam - (__int128)td * Sn;
         const __int128 den = (__int128)td * Zrem * Lam;

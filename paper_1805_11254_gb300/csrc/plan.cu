@@ -113,6 +113,20 @@ void small_probability_limits(uint32_t kg, int64_t tn, int64_t td, double eps, i
     *L = l;
 }
 
+// The literal recursion's integers (hoph_decide) stay below 2^120 for every
+// group at which it decides (l < G): |X_j| <= |X_{j-1}| c^j + k' td a^{s_j}.
+bool literal_fits(const DecideParams &dp) {
+    const long double lim = ldexpl(1.0L, 120);
+    long double X = (long double)dp.tn * dp.kg, As = 1.0L;
+    for (uint32_t j = 1; j < dp.G; ++j) {
+        const long double cj = powl((long double)dp.rc, (long double)j);
+        As *= powl((long double)dp.ra, (long double)j);
+        X = X * cj + (long double)dp.kg * dp.td * As;
+        if (X >= lim || (long double)dp.kg * 65536.0L * dp.td * As >= lim) return false;
+    }
+    return true;
+}
+
 int validate(const hoph_params &p) {
     if (p.universe_D == 0 || p.universe_D > (1ull << 32)) return HOPH_ERR_PARAM;
     if (p.k == 0 || p.k_group == 0 || p.k % p.k_group) return HOPH_ERR_PARAM;
@@ -123,7 +137,7 @@ int validate(const hoph_params &p) {
         return HOPH_ERR_PARAM;
     if (!(p.epsilon >= 0.0) || !isfinite(p.epsilon)) return HOPH_ERR_PARAM;
     if (p.empty_rule > HOPH_EMPTY_NONE) return HOPH_ERR_PARAM;
-    if (p.weighting != HOPH_WEIGHT_SPACE) return HOPH_ERR_UNSUPPORTED;
+    if (p.weighting > HOPH_WEIGHT_LITERAL) return HOPH_ERR_PARAM;
     if (p.perm_kind == HOPH_PERM_TABLE) {
         if (p.universe_D > (1ull << 30)) return HOPH_ERR_UNSUPPORTED;
     } else if (p.perm_kind == HOPH_PERM_HASH61) {
@@ -188,6 +202,13 @@ int plan_create(const hoph_params *params, const uint32_t *host_perm, hoph_plan 
     dp.td = p.thr_den;
     small_probability_limits(p.k_group, p.thr_num, p.thr_den, p.epsilon, &dp.U, &dp.L,
                              &dp.always_stop);
+    dp.literal = p.weighting == HOPH_WEIGHT_LITERAL && p.a != 0;
+    dp.ra = p.a;
+    dp.rc = (int64_t)p.a + p.b;
+    if (dp.literal && !literal_fits(dp)) {
+        delete pl;
+        return HOPH_ERR_PARAM;
+    }
     dp.zsuf[pl->G] = 0;
     for (int g = (int)pl->G - 1; g >= 0; --g) {
         dp.z[g] = pl->z[g];
@@ -405,7 +426,7 @@ int hoph_plan_set_exec(hoph_plan *plan, const hoph_exec *exec) {
         return HOPH_OK;
     }
     if (exec->strategy < -1 || exec->strategy > 1 || exec->tile_rows < 0 ||
-        exec->tile_rows > 256 || exec->consumer_warps < 0 || exec->consumer_warps > 16 ||
+        exec->tile_rows > 256 || exec->consumer_warps < 0 || exec->consumer_warps > 31 ||
         exec->ctas_per_sm < 0 || exec->ctas_per_sm > 8 || exec->stages < 0 || exec->stages > 8 ||
         (exec->lanes_per_row != 0 && exec->lanes_per_row != 1 && exec->lanes_per_row != 2 &&
          exec->lanes_per_row != 4 && exec->lanes_per_row != 8))

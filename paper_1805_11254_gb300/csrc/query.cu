@@ -279,17 +279,16 @@ __host__ __device__ inline DenseSmem dense_smem(const DenseArgs &a) {
 constexpr int kQCache = 8;  // query chunks kept in registers (W <= 256)
 
 // Every (query, row) pair of one tile; lanes over bins.  Consecutive pairs of
-// a warp share the query, whose values and empty masks stay in registers.
-__device__ void score_tile_dense(const PairArgs &a, int n_cons, const uint32_t *tile,
-                                 int rows_here, int64_t row0, const int32_t *s_toff,
-                                 const int64_t *s_qoff, const uint16_t *s_thr, Survivor *list,
-                                 uint32_t *nsurv, unsigned long long *s_stats, int cw,
-                                 unsigned long long &acc0) {
+// a warp share the query, whose values and empty masks stay in registers
+// (qv, qem of query cur_q) from one tile to the next.
+__device__ __forceinline__ void score_tile_dense(
+    const PairArgs &a, int n_cons, const uint32_t *tile, int rows_here, int64_t row0,
+    const int32_t *s_toff, const int64_t *s_qoff, const uint16_t *s_thr, Survivor *list,
+    uint32_t *nsurv, unsigned long long *s_stats, int cw, unsigned long long &acc0,
+    uint32_t (&qv)[kQCache], uint32_t (&qem)[kQCache], int &cur_q) {
     const int lane = threadIdx.x & 31;
     const int nch = (a.W + 31) >> 5;
     const bool cached = nch <= kQCache;
-    uint32_t qv[kQCache], qem[kQCache];
-    int cur_q = -1;
     const int64_t n_pairs = (int64_t)rows_here * a.n_q;
     for (int64_t p = cw; p < n_pairs; p += n_cons) {
         const int q = (int)(p / rows_here);
@@ -396,15 +395,17 @@ __global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_consta
     Survivor *list = s_surv + cw * kSurvCap;
     uint32_t *nsurv = s_nsurv + cw;
     unsigned long long acc0 = 0;
-    int64_t it = 0;
+    uint32_t qv[kQCache], qem[kQCache];  // the warp's current query (cached path)
+    int cur_q = -1;
+    int s = 0;        // stage of the current tile
+    uint32_t ph = 0;  // its mbarrier phase
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
-        const int s = a.use_tma ? (int)(it % a.stages) : 0;
+    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         const uint32_t *tp = reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride);
         const int64_t row0 = tile * R;
         const int rows_here = (int)min((long long)R, (long long)(P.n_rows - row0));
         if (a.use_tma) {
-            if (!mbar_wait_bounded(full + s, (uint32_t)(it / a.stages) & 1, abort_flag)) {
+            if (!mbar_wait_bounded(full + s, ph, abort_flag)) {
                 hoph_flag(P.status, HOPH_ERR_TIMEOUT);
                 *abort_flag = 1;
                 ok = false;
@@ -421,10 +422,14 @@ __global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_consta
             named_bar_sync(1, a.n_cons * 32);
         }
         score_tile_dense(P, a.n_cons, tp, rows_here, row0, s_toff, s_qoff, s_thr, list, nsurv,
-                         s_stats, cw, acc0);
+                         s_stats, cw, acc0, qv, qem, cur_q);
         __syncwarp();
         if (a.use_tma) {
             if (lane == 0) mbar_arrive(empty + s);
+            if (++s == a.stages) {
+                s = 0;
+                ph ^= 1u;
+            }
         } else {
             named_bar_sync(1, a.n_cons * 32);
         }
@@ -588,7 +593,7 @@ struct FilterArgs {
     int64_t n_tiles;
     uint32_t stage_bytes, stage_stride;
     const uint32_t *gmap;     // 2-bit group map over the map slots
-    uint32_t gmap_words;
+    uint32_t gmap_words;      // the last word is zero: empty bins look up its slot 0
     uint32_t map_mask;        // hashed map: slot = mix32(key) & map_mask
     const uint64_t *binbase;  // key = lo[w] + value
     const uint16_t *row_min;  // [W + 1]
@@ -619,10 +624,12 @@ __host__ __device__ inline FilterSmem filter_smem(const FilterArgs &a) {
 // holds its 16-byte chunk c at position c ^ (line & 7), so the eight lanes of
 // a shared-memory phase, reading the same chunk of eight consecutive lines,
 // hit eight different banks.  Lane (r, sub) of a warp owns NPER consecutive
-// bins of row r; their psi-space bases stay in registers.
-template <int NPER, bool HASHED>
-__global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__ FilterArgs a,
-                                                         const __grid_constant__ CUtensorMap map) {
+// bins of row r; their psi-space bases stay in registers.  MAXC bounds the
+// consumer warps (16, or 31 for narrow rows: more warps hide the map lookups'
+// latency at fewer registers per thread).
+template <int NPER, bool HASHED, int MAXC>
+__global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_constant__ FilterArgs a,
+                                                                 const __grid_constant__ CUtensorMap map) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const FilterSmem L = filter_smem(a);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
@@ -667,21 +674,23 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
 #pragma unroll
     for (int i = 0; i < NPER; ++i) kb[i] = (uint32_t)a.binbase[w0 + i];
 
-    int64_t it = 0;
-    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
-        const int s = (int)(it % a.stages);
+    const uint32_t zero_slot = (a.gmap_words - 1) * 16;
+    int s = 0;          // stage of the current tile
+    uint32_t ph = 0;    // its mbarrier phase
+    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         const uint32_t *lp =
             reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride) + line * 32;
         // the swizzle XORs the chunk index with bits 7..9 of the line's address
         const int xr = (int)(smem_u32(lp) >> 7) & 7;
         const int64_t row = tile * R + rl;
-        if (!mbar_wait_bounded(full + s, (uint32_t)(it / a.stages) & 1, abort_flag)) {
+        if (!mbar_wait_bounded(full + s, ph, abort_flag)) {
             hoph_flag(a.status, HOPH_ERR_TIMEOUT);
             *abort_flag = 1;
             break;
         }
         // this lane's share: hits = even-group hits | odd-group hits << 16
-        // (one map word gives both bits of a key 16 apart), ne = non-empty bins
+        // (one map word gives both bits of a key 16 apart), ne = non-empty bins;
+        // an empty bin looks up the zero word, so nothing branches
         uint32_t hits = 0, ne = 0;
         if (row < a.n_rows) {
 #pragma unroll
@@ -691,12 +700,12 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
                 const uint32_t x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    if (x[e] != HOPH_EMPTY_VALUE) {
-                        const uint32_t key = kb[c * 4 + e] + x[e];
-                        const uint32_t mi = HASHED ? (mix32(key) & a.map_mask) : key;
-                        hits += (s_gmap[mi >> 4] >> (mi & 15u)) & 0x10001u;
-                        ++ne;
-                    }
+                    const bool full_bin = x[e] != HOPH_EMPTY_VALUE;
+                    const uint32_t key = kb[c * 4 + e] + x[e];
+                    uint32_t mi = HASHED ? (mix32(key) & a.map_mask) : key;
+                    mi = full_bin ? mi : zero_slot;
+                    hits += (s_gmap[mi >> 4] >> (mi & 15u)) & 0x10001u;
+                    ne += full_bin;
                 }
             }
         }
@@ -717,6 +726,10 @@ __global__ void __launch_bounds__(32 * 17) filter_kernel(const __grid_constant__
             if (lane == 0) base = atomicAdd(a.n_cand, (unsigned long long)__popc(pm));
             base = __shfl_sync(0xFFFFFFFFu, base, 0);
             if (pass) a.cand[base + __popc(pm & ((1u << lane) - 1u))] = (uint32_t)row;
+        }
+        if (++s == a.stages) {
+            s = 0;
+            ph ^= 1u;
         }
     }
 }
@@ -1178,20 +1191,27 @@ bool encode_swizzled_map(CUtensorMap *map, const uint32_t *planes, int kg, int64
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NPER, bool HASHED>
-int launch_filter(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem, int num_sms,
-                  int ctas_per_sm, cudaStream_t s) {
-    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)filter_kernel<NPER, HASHED>, (int)smem));
+template <int NPER, bool HASHED, int MAXC>
+int launch_filter_c(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem, int num_sms,
+                    int ctas_per_sm, cudaStream_t s) {
+    auto kern = filter_kernel<NPER, HASHED, MAXC>;
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)kern, (int)smem));
     const int threads = 32 * (fa.n_cons + 1);
     int per_sm = 0;
-    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, filter_kernel<NPER, HASHED>, threads, smem));
+    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
     if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
     const int64_t grid = std::min<int64_t>(fa.n_tiles, (int64_t)num_sms * per_sm);
-    filter_kernel<NPER, HASHED><<<(unsigned)grid, threads, smem, s>>>(fa, map);
+    kern<<<(unsigned)grid, threads, smem, s>>>(fa, map);
     HOPH_CUDA_TRY(cudaGetLastError());
     return HOPH_OK;
+}
+
+template <int NPER, bool HASHED>
+int launch_filter(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem, int num_sms,
+                  int ctas_per_sm, cudaStream_t s) {
+    return fa.n_cons > 16 ? launch_filter_c<NPER, HASHED, 31>(fa, map, smem, num_sms, ctas_per_sm, s)
+                          : launch_filter_c<NPER, HASHED, 16>(fa, map, smem, num_sms, ctas_per_sm, s);
 }
 
 // First-pass decision table for W scanned bins under `dp` after `l` groups:
@@ -1350,7 +1370,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
             bump.take((csr_slots + 1) * 4);                                  // counts
             bump.take((csr_slots + 1) * 4);                                  // csr_off
             bump.take(((csr_slots + 1 + kScanChunk - 1) / kScanChunk) * 4);  // block sums
-            bump.take((map_slots / 16 + 1) * 4);                             // group map
+            bump.take((map_slots / 16 + 2) * 4);                             // group map
             bump.take(csr_hashed ? csr_slots * 8 : 8);                       // key table
             bump.take((size_t)n_queries * W * 2);                       // csr_q
             bump.take((size_t)n_queries * mask_words * 4);              // q_emask
@@ -1378,7 +1398,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         counts = (uint32_t *)bump.take((csr_slots + 1) * 4);
         csr_off = (uint32_t *)bump.take((csr_slots + 1) * 4);
         sums = (uint32_t *)bump.take(((csr_slots + 1 + kScanChunk - 1) / kScanChunk) * 4);
-        gmap = (uint32_t *)bump.take((map_slots / 16 + 1) * 4);
+        gmap = (uint32_t *)bump.take((map_slots / 16 + 2) * 4);
         tkey = (unsigned long long *)bump.take(csr_hashed ? csr_slots * 8 : 8);
         csr_q = (uint16_t *)bump.take((size_t)n_queries * W * 2);
         q_emask = (uint32_t *)bump.take((size_t)n_queries * mask_words * 4);
@@ -1436,7 +1456,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         ia.allempty = allempty;
         ia.n_allempty = n_allempty;
         HOPH_CUDA_TRY(cudaMemsetAsync(counts, 0, (csr_slots + 1) * 4, s));
-        HOPH_CUDA_TRY(cudaMemsetAsync(gmap, 0, (map_slots / 16 + 1) * 4, s));
+        HOPH_CUDA_TRY(cudaMemsetAsync(gmap, 0, (map_slots / 16 + 2) * 4, s));
         if (csr_hashed) HOPH_CUDA_TRY(cudaMemsetAsync(tkey, 0xFF, csr_slots * 8, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(n_allempty, 0, 4, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(n_cand, 0, 8, s));
@@ -1458,7 +1478,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         fa.Gs = Gs;
         fa.W = W;
         fa.gmap = gmap;
-        fa.gmap_words = (uint32_t)(map_slots / 16 + 1);
+        fa.gmap_words = (uint32_t)(map_slots / 16 + 2);  // + a zero word for empty bins
         fa.map_mask = (uint32_t)(map_slots - 1);
         fa.binbase = plan->d_lo;
         fa.row_min = pa.thr + 2 * (W + 1);
@@ -1535,6 +1555,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         DenseArgs da;
         da.p = pa;
         const int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 8;
+        if (n_cons > 16) return HOPH_ERR_UNSUPPORTED;
         int R = plan->exec.tile_rows > 0 ? plan->exec.tile_rows : 0;
         if (R == 0) {
             R = (int)std::max<int64_t>(1, std::min<int64_t>(256, 8192 / (W * 4)));

@@ -40,6 +40,7 @@ HOPH_EMPTY_EITHER = 1
 HOPH_EMPTY_NONE = 2
 RULES = {"both": 0, "either": 1, "none": 2}
 HOPH_WEIGHT_SPACE = 0
+HOPH_WEIGHT_LITERAL = 1
 HOPH_MAX_GROUPS = 16
 HOPH_EMPTY_VALUE = 0xFFFFFFFF
 
@@ -303,9 +304,10 @@ class Plan:
     """A plan plus torch-allocated buffers for sketch / query round trips."""
 
     def __init__(self, D, k, k_group, a=0, b=0, perm_kind=HOPH_PERM_TABLE, minwise_k=0, seed=1,
-                 thr=(7, 10), epsilon=1e-4, empty_rule="both", host_perm=None):
+                 thr=(7, 10), epsilon=1e-4, empty_rule="both", host_perm=None,
+                 weighting=HOPH_WEIGHT_SPACE):
         self.params = make_params(D, k, k_group, a, b, perm_kind, minwise_k, seed, thr, epsilon,
-                                  empty_rule)
+                                  empty_rule, weighting)
         if host_perm is not None:
             self.handle = hoph_plan_create_with_perm(self.params, host_perm)
         else:

@@ -49,7 +49,10 @@ def test_struct_sizes_match_header_layout():
 @pytest.mark.parametrize("kw", [dict(k=100, k_group=32), dict(k=128, k_group=0),
                                 dict(thr=(8, 7)), dict(thr=(0, 7)), dict(a=1, b=0),
                                 dict(epsilon=-1.0), dict(empty_rule=7), dict(k=32 * 17, k_group=32),
-                                dict(D=1 << 33), dict(perm_kind=1)])
+                                dict(D=1 << 33), dict(perm_kind=1), dict(weighting=2),
+                                # Algorithm 2's recursion over 8 groups of a 1:1000 split
+                                # outgrows the 120-bit integers it is decided in
+                                dict(D=1 << 30, k=128, k_group=16, a=1, b=1000, weighting=1)])
 def test_invalid_parameters_rejected_before_any_cuda_call(lib, kw):
     base = dict(D=1 << 16, k=128, k_group=32)
     base.update(kw)

@@ -219,7 +219,7 @@ def test_identical_sets_always_accepted(small):
 
 @pytest.mark.parametrize("kg,lpr,warps,stages", [(32, 1, 8, 2), (32, 2, 16, 2), (32, 1, 16, 3),
                                                  (32, 2, 3, 5), (64, 2, 16, 2), (64, 4, 16, 4),
-                                                 (64, 2, 5, 3)])
+                                                 (64, 2, 5, 3), (64, 4, 31, 2), (64, 4, 20, 2)])
 def test_join_execution_knobs_do_not_change_results(small, kg, lpr, warps, stages):
     """Lanes per row, consumer warps and pipeline depth of the join filter
     are scheduling only: the accepted pairs stay the oracle's."""
@@ -302,3 +302,22 @@ def test_row_shards_merge_to_the_whole_collection(small, world):
             parts.append(shard.globalize(run(r0, r1), r0))
         assert len(whole) > 0
         assert np.array_equal(shard.merge_pairs(parts), whole)
+
+
+@pytest.mark.parametrize("strategy", [0, 1, -1])
+@pytest.mark.parametrize("ab", [(1, 1), (1, 2), (2, 1)])
+def test_literal_weighting_parity(small, ab, strategy):
+    """Algorithm 2's printed recursion (HOPH_WEIGHT_LITERAL) against the
+    oracle's reduced-fraction route; for 1:1 it coincides with the space
+    weighting at l = 1, for 1:2 it rejects near duplicates after group 1."""
+    dev = device()
+    D, k, kg = small["D"], 128, 32
+    with hoph.Plan(D, k, kg, *ab, seed=1, thr=T, epsilon=EPS,
+                   weighting=hoph.HOPH_WEIGHT_LITERAL) as plan:
+        q, c = _sketch_both(plan, small, dev)
+        nq, nr = q.shape[1], c.shape[1]
+        z = [plan.info.group_size[g] for g in range(plan.G)]
+        want = oc.query("hoph", planes_to_rows(q), planes_to_rows(c), kg, T[0], T[1], EPS,
+                        z=np.asarray(z, dtype=np.uint64), weighting="literal", ab=ab)
+        _compare(plan, "hoph", q, c, nq, nr, want, strategy, plan.G)
+

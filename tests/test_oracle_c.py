@@ -113,6 +113,35 @@ def test_query_decisions_equal(rule, eps):
                              if res["dec"][i, j] == hr.ACCEPT)
 
 
+@pytest.mark.parametrize("eps", [0.0, 1e-4, 0.05, 1.0])
+def test_literal_recursion_decisions_equal(eps):
+    """Algorithm 2 as printed (weighting 'literal'): the C oracle's reduced
+    fractions against the Fraction reference, over (a:b) splits whose r is
+    1/2, 1/3, 2/3 and 3/4."""
+    rng = random.Random(int(eps * 1e6) + 7)
+    D, kg, G = 4096, 16, 4
+    k = kg * G
+    perm = hr.permutation_table(D, 5)
+    base = _sets(rng, 10, D, 1, 300, empty_every=9)
+    sets = base + [b[: max(1, len(b) * 4 // 5)] + rng.sample(range(D), 2) for b in base if b]
+    T = Fraction(3, 5)
+    for ab in ((1, 1), (1, 2), (2, 1), (3, 1)):
+        lo, z = hr.layout(D, k, kg, *ab)
+        sk = np.asarray([hr.oph_sketch(S, perm.__getitem__, lo) for S in sets], dtype=np.uint32)
+        res = oc.query("hoph", sk, sk, kg, 3, 5, eps, z=np.asarray(z), per_pair=True,
+                       weighting="literal", ab=ab)
+        seen = set()
+        for i in range(len(sets)):
+            for j in range(len(sets)):
+                s, t = sk[i].tolist(), sk[j].tolist()
+                want = hr.hoph_compare(s, t, kg, z, T, eps, weighting="literal", ab=ab)
+                got = (int(res["dec"][i, j]), int(res["groups"][i, j]), int(res["msum"][i, j]))
+                assert got == want, (ab, i, j)
+                seen.add(want[:2])
+        if eps == 1e-4:  # the cases reach more than the first group
+            assert any(g > 1 for _, g in seen)
+
+
 def test_minwise_decisions_equal():
     rng = random.Random(8)
     D, k = 256, 16
