@@ -42,7 +42,7 @@ SKETCH_SEED = 21
 # dram read+write bytes per filter-kernel launch from an ncu capture, keyed by
 # the sha256 of the filter kernel's source it was taken on (null once that
 # source changes)
-NCU_TRAFFIC = {"a887ad91130c470b": 2577.47e6}  # profiles/filter_kernel_2e6rows.md, x5 rows
+NCU_TRAFFIC = {"d4a43c1c1a1567fa": 2579.19e6}  # profiles/filter_kernel_2e6rows.md, x5 rows
 
 
 def parse():
@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--no-graph", action="store_true", help="eager launches instead of a graph")
     p.add_argument("--no-tune", action="store_true", help="library default execution knobs")
     p.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
+    p.add_argument("--no-sweep", action="store_true",
+                   help="skip the threshold / tolerance sweep on the 5,000-set workload")
     p.add_argument("--serve-rates", default="2000,20000,100000",
                    help="Poisson arrival rates (query sets per second)")
     p.add_argument("--serve-seconds", type=float, default=1.5)
@@ -430,6 +432,8 @@ def run_native(args):
         line["cpu_baseline"] = cpu_baseline(qw, off, coll_seed, args.cpu_seconds, args.rows)
         if not args.no_serve:
             line["serving"] = serving_leg(args, planes, dev, line["oph_full_scan_baseline"])
+        if not args.no_sweep:
+            line["sweeps"] = sweep_leg(dev, stream)
         if not args.no_shingle:
             del planes
             torch.cuda.empty_cache()
@@ -678,6 +682,77 @@ def serving_leg(args, planes, dev, oph_leg):
                 1e3 / oph_leg["ms_per_query_launch"],
             "how": "2 streams x 1 plan each, one CUDA graph per (stream, batch size); H2D of a "
                    "batch's sets and its sketching overlap the query of the other stream"}
+
+
+SWEEP_T = ((1, 2), (3, 5), (7, 10), (4, 5), (9, 10))
+SWEEP_EPS = (1e-3, 1e-4, 1e-5)
+
+
+def sweep_leg(dev, stream, reps=5):
+    """Threshold and tolerance sweeps on the 5,000-set workload (D = 2^16,
+    k = 128, 50 planted queries at J ~ U[0.3, 0.95]): MinWise (128
+    permutations), plain OPH, GOPH (4 x 32) and (1:1)HOPH (k' = 32), each with
+    recall and precision against exact Jaccard of all 250,000 pairs and the
+    query time; T in 0.5..0.9 at eps = 1e-4, then eps in 1e-3..1e-5 at T = 0.7
+    for the early-terminating methods."""
+    import torch
+    from oracle import oracle_c as oc
+    from paper_1805_11254_gb300 import hoph, synth
+    w = synth.small_parity_workload()
+    Dw, k, kg, nq = w["D"], 128, 32, len(w["q_off"]) - 1
+    n = len(w["off"]) - 1
+    pa = np.repeat(np.arange(nq, dtype=np.int64), n)
+    pb = np.tile(np.arange(n, dtype=np.int64), nq)
+    inter, uni = oc.jaccard_pairs(w["q_ids"], w["q_off"], w["ids"], w["off"], pa, pb)
+    inter = inter.reshape(nq, n)
+    uni = uni.reshape(nq, n)
+    d = {key: to_dev(w[key], dev) for key in ("ids", "off", "q_ids", "q_off")}
+    layouts = {"minwise": (0, 0), "oph_full": (0, 0), "goph": (0, 0), "hoph_1_1": (1, 1)}
+    modes = {"minwise": hoph.HOPH_MODE_MINWISE_FULL, "oph_full": hoph.HOPH_MODE_OPH_FULL,
+             "goph": hoph.HOPH_MODE_GOPH, "hoph_1_1": hoph.HOPH_MODE_HOPH}
+    sk = {}
+    for m, ab in layouts.items():  # sketches depend on psi and the layout only
+        with hoph.Plan(Dw, k, kg, *ab, seed=PERM_SEED, minwise_k=k if m == "minwise" else 0) as p:
+            if m == "minwise":
+                sk[m] = (p.minwise(d["q_ids"], d["q_off"], nq), p.minwise(d["ids"], d["off"], n))
+            else:
+                sk[m] = (p.sketch(d["q_ids"], d["q_off"], nq), p.sketch(d["ids"], d["off"], n))
+            p.check()
+    out = []
+    cap = 1 << 16
+    o = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    settings = [(m, t, 1e-4) for t in SWEEP_T for m in layouts] + \
+               [(m, (7, 10), e) for e in SWEEP_EPS for m in ("goph", "hoph_1_1")]
+    for m, t, eps in settings:
+        with hoph.Plan(Dw, k, kg, *layouts[m], seed=PERM_SEED, thr=t, epsilon=eps,
+                       minwise_k=k if m == "minwise" else 0) as p:
+            qs, cs = sk[m]
+            hoph.hoph_query_batch(p.handle, modes[m], qs, nq, cs, n, o, cap, cnt, None, stream)
+            p.check(stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                hoph.hoph_query_batch(p.handle, modes[m], qs, nq, cs, n, o, cap, cnt, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            p.check(stream)
+            ms = e0.elapsed_time(e1) / reps
+            c = int(cnt.item())
+            pairs = o[:min(c, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+        truth = (uni > 0) & (inter * t[1] >= t[0] * uni)
+        got = np.zeros_like(truth)
+        got[pairs["query"].astype(np.int64), pairs["row"]] = True
+        tp = int((got & truth).sum())
+        out.append({"method": m, "T": "%d/%d" % t, "eps": eps, "ms": ms, "reported": int(got.sum()),
+                    "truly_similar": int(truth.sum()),
+                    "recall": tp / int(truth.sum()) if truth.any() else 1.0,
+                    "precision": tp / int(got.sum()) if got.any() else 1.0})
+    return {"workload": "5,000 sets of U[50, 500] distinct IDs over 2^16, 50 planted queries at "
+                        "J ~ U[0.3, 0.95], k = 128 (GOPH 4 x 32, 1:1 HOPH k' = 32, MinWise 128 "
+                        "permutations); ground truth: exact Jaccard of all 250,000 pairs",
+            "points": out}
 
 
 def shingle_leg(args, dev, stream, peaks, q_batch=1024, n_planted=32):
