@@ -57,11 +57,14 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=100)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-extras", action="store_true", help="skip sketch/OPH/CPU legs")
-    p.add_argument("--profile", nargs="?", const="query", choices=("query", "sketch"),
-                   help="few launches of the query step (or of the 10^6-set sketch), for ncu")
+    p.add_argument("--profile", nargs="?", const="query", choices=("query", "sketch", "oph1"),
+                   help="few launches of the query step (or of the 10^6-set sketch, or of the "
+                        "one-query OPH full scan with its tuned knobs), for ncu")
     p.add_argument("--no-graph", action="store_true", help="eager launches instead of a graph")
     p.add_argument("--no-tune", action="store_true", help="library default execution knobs")
     p.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
+    p.add_argument("--no-compact", action="store_true",
+                   help="skip the same step over compact (uint16) sketch planes")
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the threshold / tolerance sweep on the 5,000-set workload")
     p.add_argument("--serve-rates", default="2000,20000,100000",
@@ -275,6 +278,9 @@ def run_native(args):
 
     # ---- collection (setup, untimed)
     off, coll_seed = collection_host(args.rows, rank)
+    if args.profile == "oph1":
+        profile_oph1(args, off, coll_seed, dev, stream)
+        return
     n_ids = int(off[-1])
     plan = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
     d_off = to_dev(off, dev)
@@ -427,11 +433,17 @@ def run_native(args):
         line["sketch"] = sketch_leg(dev, stream, peaks)
         line["oph_full_scan_baseline"], oph_pairs = oph_baseline_leg(args, off, coll_seed, qw, dev,
                                                                      stream, value)
-        line["quality"] = quality(qw, {"hoph": pairs, "oph_full_scan": oph_pairs}, off,
-                                  coll_seed, args)
+        eps_runs = eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream)
+        methods = {"hoph": pairs, "oph_full_scan": oph_pairs}
+        methods.update({"hoph_eps_%g" % e: r["pairs"] for e, r in eps_runs.items()})
+        line["quality"] = quality(qw, methods, off, coll_seed, args)
+        line["equal_recall"] = equal_recall(line["quality"], eps_runs, nq, args.rows)
         line["cpu_baseline"] = cpu_baseline(qw, off, coll_seed, args.cpu_seconds, args.rows)
         if not args.no_serve:
             line["serving"] = serving_leg(args, planes, dev, line["oph_full_scan_baseline"])
+        if not args.no_compact:
+            line["compact"] = compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs, dev,
+                                          stream, peaks)
         if not args.no_sweep:
             line["sweeps"] = sweep_leg(dev, stream)
         if not args.no_shingle:
@@ -487,6 +499,62 @@ def e2e_leg(args, plan, qw, planes, dev, stream):
             "h2d_bytes_per_step": int(h_ids.numel() * 4 + h_off.numel() * 8),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
             "path": "pinned host sets -> oph_build_sketches -> hoph_query_batch -> host pairs"}
+
+
+EQUAL_RECALL_EPS = (1e-4, 1e-5, 1e-6, 1e-8, 0.0)
+
+
+def eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, reps=20):
+    """The same step (sketch the query sets, HOPH query) at smaller error
+    tolerances: the sketches do not depend on eps, only the decisions do.
+    Returns {eps: {"pairs", "ms"}} with eager CUDA-event timing."""
+    import torch
+    from paper_1805_11254_gb300 import hoph
+    out = {}
+    cap = 1 << 20
+    o = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    for eps in EQUAL_RECALL_EPS:
+        with hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=eps) as p:
+            qp = torch.empty((p.G, nq, KG), dtype=torch.int32, device=dev)
+
+            def step():
+                hoph.oph_build_sketches(p.handle, dq_ids, dq_off, nq, qp, stream)
+                hoph.hoph_query_batch(p.handle, hoph.HOPH_MODE_HOPH, qp, nq, planes, args.rows, o,
+                                      cap, cnt, None, stream)
+            for _ in range(3):
+                step()
+            p.check(stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            p.check(stream)
+            n = int(cnt.item())
+            out[eps] = {"pairs": o[:min(n, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+                        .copy(), "ms": e0.elapsed_time(e1) / reps}
+    return out
+
+
+def equal_recall(q, eps_runs, nq, rows):
+    """The largest eps at which HOPH's recall reaches plain OPH's, with the
+    step's eager throughput at each eps."""
+    target = q["oph_full_scan"]["recall"]
+    pts = []
+    for eps, r in eps_runs.items():
+        m = q["hoph_eps_%g" % eps]
+        pts.append({"eps": eps, "recall": m["recall"], "precision": m["precision"],
+                    "ms_per_step_eager": r["ms"], "value": nq * rows / (r["ms"] / 1e3)})
+    ok = [p for p in pts if p["recall"] >= target]
+    best = max(ok, key=lambda p: p["eps"]) if ok else None
+    return {"oph_full_scan_recall": target, "points": pts,
+            "eps_at_equal_recall": best["eps"] if best else None,
+            "value_at_equal_recall": best["value"] if best else None,
+            "unit": UNIT, "how": "same query sets and sketches; eps only changes the decisions; "
+                                 "eager step timing (sketch + query), not the graph replay"}
 
 
 def quality(qw, pairs_by_method, off, coll_seed, args, n_random_rows=2000):
@@ -560,6 +628,34 @@ def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": gbs / peaks["hbm_gbs"], "traffic": None,
                          "algorithmic_bytes_per_launch": bytes_}}
+
+
+# the dense-scan knobs the one-query OPH baseline tunes to (16 consumer warps,
+# 2 stages of 64-row tiles), for its ncu profile
+OPH1_EXEC = dict(strategy=0, consumer_warps=16, stages=2, tile_rows=64)
+
+
+def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
+    """A few one-query OPH full-scan launches (dense scan) for ncu."""
+    import torch
+    from paper_1805_11254_gb300 import hoph
+    n_ids = int(off[-1])
+    qw = query_sets(8, off, coll_seed)
+    with hoph.Plan(D, K, K, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
+        d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+        hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
+        planes = plan.sketch(d_ids, to_dev(off, dev), args.rows)
+        del d_ids
+        q = plan.sketch(to_dev(qw["q_ids"], dev), to_dev(qw["q_off"], dev), 8)
+        plan.check()
+        plan.set_exec(**OPH1_EXEC)
+        cap = 1 << 12
+        out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        for i in range(launches):
+            hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_OPH_FULL, q[:, i:i + 1].contiguous(),
+                                  1, planes, args.rows, out, cap, cnt, None, stream)
+        plan.check()
 
 
 def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, n_launch=8):
@@ -682,6 +778,79 @@ def serving_leg(args, planes, dev, oph_leg):
                 1e3 / oph_leg["ms_per_query_launch"],
             "how": "2 streams x 1 plan each, one CUDA graph per (stream, batch size); H2D of a "
                    "batch's sets and its sketching overlap the query of the other stream"}
+
+
+def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream, peaks,
+                steps=200):
+    """The benchmark step over compact planes: every bin of the (1:2) layout
+    over 2^20 is at most 5,462 values wide, so the stored offsets fit in 16
+    bits (oph_build_sketches16 / hoph_query_batch16) and the streamed plane
+    halves.  Same pairs as the uint32 planes (checked), timed as a graph."""
+    import torch
+    from paper_1805_11254_gb300 import hoph
+    plan = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
+    n_ids = int(off[-1])
+    d_off = to_dev(off, dev)
+    d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+    hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
+    c16 = plan.sketch16(d_ids, d_off, args.rows)
+    plan.check()
+    del d_ids
+    torch.cuda.empty_cache()
+    q16 = torch.empty((plan.G, nq, KG), dtype=torch.int16, device=dev)
+    cap = 1 << 20
+    out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def step(s):
+        hoph.oph_build_sketches16(plan.handle, dq_ids, dq_off, nq, q16, s)
+        hoph.hoph_query_batch16(plan.handle, hoph.HOPH_MODE_HOPH, q16, nq, c16, args.rows, out,
+                                cap, cnt, None, s)
+    for _ in range(3):
+        step(stream)
+    plan.check(stream)
+    n = int(cnt.item())
+    got = out[:min(n, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+    same = bool(n == len(pairs_ref) and np.array_equal(got, pairs_ref))
+    hoph.hoph_plan_enable_timing(plan.handle, True)
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step(side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    phase = [0.0] * 4
+    for _ in range(steps):
+        graph.replay()
+        phase = [a + b for a, b in zip(phase, hoph.hoph_plan_peek_timing(plan.handle))]
+    filt = phase[1] / steps
+    plan.check()
+    plan.close()
+    del c16
+    torch.cuda.empty_cache()
+    alg = int(args.rows * KG * 2 + nq * KG * 2)
+    ach = alg / (filt / 1e3) / 1e9
+    return {"value": nq * args.rows / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "same_pairs_as_uint32_planes": same, "plane_bytes": args.rows * K * 2,
+            "roofline": {"bound": "hbm", "kernel": "filter_kernel (uint16 planes)",
+                         "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": alg,
+                         "kernel_ms_per_launch": filt},
+            "how": "same collection and query sets; sketch values stored as 16-bit bin offsets "
+                   "(empty = 0xFFFF); CUDA graph replays, CUDA events"}
 
 
 SWEEP_T = ((1, 2), (3, 5), (7, 10), (4, 5), (9, 10))

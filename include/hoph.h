@@ -64,6 +64,7 @@ extern "C" {
 
 #define HOPH_MAX_GROUPS 16
 #define HOPH_EMPTY_VALUE 0xFFFFFFFFu /* the empty-bin marker in a sketch */
+#define HOPH_EMPTY_VALUE16 0xFFFFu     /* the same in a compact (uint16) sketch */
 
 /*
  * Method parameters (Sec. 3.1-4.1 and Table 1).
@@ -133,6 +134,7 @@ typedef struct {
     int64_t upper_limit;                /* U = min{j : P(X >= j) <= eps}      */
     int64_t lower_limit;                /* L = max{j : P(X < j) <= eps}       */
     uint64_t group_size[HOPH_MAX_GROUPS]; /* z_g, the values of V in group g  */
+    uint64_t max_bin_width;             /* widest bin (compact planes: <= 65535) */
 } hoph_plan_info;
 
 /* Execution knobs (never change results).  0 = library default. */
@@ -218,6 +220,29 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
                      int64_t n_queries, const uint32_t *d_coll_planes, int64_t n_rows,
                      hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
                      hoph_stats *d_stats, void *stream);
+
+/*
+ * Compact sketches: a bin's stored value is its minimum's offset from the
+ * bin's lower bound (Sec. 3.2 and 4.1 re-index each bin so the stored value
+ * is as small as possible), so when every bin of the plan is at most 65,535
+ * values wide (hoph_plan_info.max_bin_width) the offsets fit in 16 bits,
+ * with HOPH_EMPTY_VALUE16 (0xFFFF) for an empty bin.  Same layout and the
+ * same values as the uint32 planes, half the bytes; decisions and output
+ * identical to oph_build_sketches + hoph_query_batch.
+ *   oph_build_sketches16   as oph_build_sketches, d_planes uint16[G][n_sets][k'].
+ *   hoph_query_batch16     as hoph_query_batch over uint16 planes; modes
+ *                          GOPH, HOPH and OPH_FULL.
+ * Both return HOPH_ERR_UNSUPPORTED for a plan with a bin wider than 65,535
+ * values (and the query for mode MINWISE_FULL, whose values are whole
+ * psi-values).  The value join needs k' to be a multiple of 64 here (32 for
+ * uint32 planes); other shapes use the dense scan.
+ */
+int oph_build_sketches16(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
+                         int64_t n_sets, uint16_t *d_planes, void *stream);
+int hoph_query_batch16(hoph_plan *plan, uint32_t mode, const uint16_t *d_query_planes,
+                       int64_t n_queries, const uint16_t *d_coll_planes, int64_t n_rows,
+                       hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
+                       hoph_stats *d_stats, void *stream);
 
 /*
  * oph_build_sketches without any device allocation.  The paper has no

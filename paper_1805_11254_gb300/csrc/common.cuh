@@ -147,6 +147,7 @@ struct hoph_plan {
     int num_sms = 0;
     uint32_t G = 1;
     std::vector<uint64_t> lo;  // bin lower bounds, k + 1 entries
+    uint64_t max_width = 0;    // widest bin (compact planes need <= 65,535)
     uint64_t z[HOPH_MAX_GROUPS] = {};
     DecideParams dp{};
     // psi on the device

@@ -191,6 +191,7 @@ int plan_create(const hoph_params *params, const uint32_t *host_perm, hoph_plan 
         delete pl;
         return HOPH_ERR_PARAM;
     }
+    pl->max_width = max_width;
 
     // decision parameters shared by GOPH / HOPH
     DecideParams &dp = pl->dp;
@@ -415,6 +416,7 @@ int hoph_plan_get_info(const hoph_plan *plan, hoph_plan_info *out) {
     out->upper_limit = plan->dp.always_stop ? 0 : plan->dp.U;
     out->lower_limit = plan->dp.always_stop ? (int64_t)plan->P.k_group + 1 : plan->dp.L;
     for (uint32_t g = 0; g < plan->G; ++g) out->group_size[g] = plan->z[g];
+    out->max_bin_width = plan->max_width;
     return HOPH_OK;
 }
 

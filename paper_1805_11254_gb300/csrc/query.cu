@@ -58,11 +58,19 @@ struct Survivor {
 };
 
 // What every comparison kernel needs to score and finish a pair.
+// Sketch planes hold uint32 values, or uint16 offsets in the compact form
+// (every bin at most 65,535 values wide, empty marker 0xFFFF); kernels that
+// read them are instantiated for both element types E.
+template <typename E>
+__host__ __device__ constexpr uint32_t empty_of() {
+    return (uint32_t)(E)~(E)0;
+}
+
 struct PairArgs {
-    const uint32_t *coll;
-    int64_t cstride;  // elements between collection planes
-    const uint32_t *qry;
-    int64_t qstride;  // elements between query planes
+    const void *coll;  // E [G][n_rows][k']
+    int64_t cstride;   // elements between collection planes
+    const void *qry;   // E [G][n_q][k']
+    int64_t qstride;   // elements between query planes
     int64_t n_rows;
     int32_t n_q;
     int32_t kg, Gs, W, G;
@@ -139,6 +147,7 @@ __host__ __device__ __forceinline__ int table_decide(const uint16_t *thr, int W,
 
 // Lane-parallel resolution of the warp's survivor list: lane j finishes
 // entry j by comparing the later groups of its pair one at a time.
+template <typename E>
 __device__ void resolve_survivors(const PairArgs &a, Survivor *list, uint32_t *nsurv,
                                   unsigned long long *s_stats) {
     const int lane = threadIdx.x & 31;
@@ -152,12 +161,12 @@ __device__ void resolve_survivors(const PairArgs &a, Survivor *list, uint32_t *n
         int matches = sv.m1;
         for (int l = 2; l <= a.G; ++l) {
             const int g = l - 1;
-            const uint32_t *rp = a.coll + (int64_t)g * a.cstride + sv.row * a.kg;
-            const uint32_t *qp = a.qry + (int64_t)g * a.qstride + (int64_t)sv.q * a.kg;
+            const E *rp = static_cast<const E *>(a.coll) + (int64_t)g * a.cstride + sv.row * a.kg;
+            const E *qp = static_cast<const E *>(a.qry) + (int64_t)g * a.qstride + (int64_t)sv.q * a.kg;
             int32_t m = 0, both = 0, one = 0;
             for (int b = 0; b < a.kg; ++b) {
                 const uint32_t rv = __ldg(rp + b), qv = __ldg(qp + b);
-                const bool er = rv == HOPH_EMPTY_VALUE, eq = qv == HOPH_EMPTY_VALUE;
+                const bool er = rv == empty_of<E>(), eq = qv == empty_of<E>();
                 m += (!eq && rv == qv);
                 both += (er && eq);
                 one += (er != eq);
@@ -166,7 +175,7 @@ __device__ void resolve_survivors(const PairArgs &a, Survivor *list, uint32_t *n
             Ks[g] = hoph_effective(a.rule, a.kg, both, one);
             matches += m;
             atomicAdd(s_stats + g, 1ull);
-            atomicAdd(s_stats + 48, (unsigned long long)a.kg * 8);
+            atomicAdd(s_stats + 48, (unsigned long long)a.kg * 2 * sizeof(E));
             const int d = hoph_decide(a.dp, l, Ms, Ks);
             if (d == HOPH_ACCEPT) {
                 atomicAdd(s_stats + 16 + g, 1ull);
@@ -281,8 +290,9 @@ constexpr int kQCache = 8;  // query chunks kept in registers (W <= 256)
 // Every (query, row) pair of one tile; lanes over bins.  Consecutive pairs of
 // a warp share the query, whose values and empty masks stay in registers
 // (qv, qem of query cur_q) from one tile to the next.
+template <typename E>
 __device__ __forceinline__ void score_tile_dense(
-    const PairArgs &a, int n_cons, const uint32_t *tile, int rows_here, int64_t row0,
+    const PairArgs &a, int n_cons, const E *tile, int rows_here, int64_t row0,
     const int32_t *s_toff, const int64_t *s_qoff, const uint16_t *s_thr, Survivor *list,
     uint32_t *nsurv, unsigned long long *s_stats, int cw, unsigned long long &acc0,
     uint32_t (&qv)[kQCache], uint32_t (&qem)[kQCache], int &cur_q) {
@@ -293,15 +303,15 @@ __device__ __forceinline__ void score_tile_dense(
     for (int64_t p = cw; p < n_pairs; p += n_cons) {
         const int q = (int)(p / rows_here);
         const int rl = (int)(p - (int64_t)q * rows_here);
-        const uint32_t *qb = a.qry + (int64_t)q * a.kg;
+        const E *qb = static_cast<const E *>(a.qry) + (int64_t)q * a.kg;
         if (cached && q != cur_q) {
             cur_q = q;
 #pragma unroll
             for (int c = 0; c < kQCache; ++c) {
                 const int w = (c << 5) + lane;
                 const bool valid = c < nch && w < a.W;
-                qv[c] = valid ? __ldg(qb + s_qoff[w]) : 0u;
-                qem[c] = __ballot_sync(0xFFFFFFFFu, valid && qv[c] == HOPH_EMPTY_VALUE);
+                qv[c] = valid ? (uint32_t)__ldg(qb + s_qoff[w]) : 0u;
+                qem[c] = __ballot_sync(0xFFFFFFFFu, valid && qv[c] == empty_of<E>());
             }
         }
         int m = 0, both = 0, one = 0;
@@ -311,11 +321,11 @@ __device__ __forceinline__ void score_tile_dense(
                 if (c < nch) {
                     const int w = (c << 5) + lane;
                     const bool valid = w < a.W;
-                    const uint32_t rv = valid ? tile[s_toff[w] + rl * a.kg] : 0u;
+                    const uint32_t rv = valid ? (uint32_t)tile[s_toff[w] + rl * a.kg] : 0u;
                     const uint32_t rem =
-                        __ballot_sync(0xFFFFFFFFu, valid && rv == HOPH_EMPTY_VALUE);
+                        __ballot_sync(0xFFFFFFFFu, valid && rv == empty_of<E>());
                     m += __popc(__ballot_sync(0xFFFFFFFFu,
-                                              valid && qv[c] != HOPH_EMPTY_VALUE && rv == qv[c]));
+                                              valid && qv[c] != empty_of<E>() && rv == qv[c]));
                     both += __popc(rem & qem[c]);
                     one += __popc(rem ^ qem[c]);
                 }
@@ -329,7 +339,7 @@ __device__ __forceinline__ void score_tile_dense(
                     rv = tile[s_toff[w] + rl * a.kg];
                     q1 = __ldg(qb + s_qoff[w]);
                 }
-                const bool er = rv == HOPH_EMPTY_VALUE, eq = q1 == HOPH_EMPTY_VALUE;
+                const bool er = rv == empty_of<E>(), eq = q1 == empty_of<E>();
                 m += __popc(__ballot_sync(0xFFFFFFFFu, valid && !eq && rv == q1));
                 both += __popc(__ballot_sync(0xFFFFFFFFu, valid && er && eq));
                 one += __popc(__ballot_sync(0xFFFFFFFFu, valid && er != eq));
@@ -341,13 +351,14 @@ __device__ __forceinline__ void score_tile_dense(
             ++acc0;
             if (lane == 0) emit_pair(a, q, row0 + rl, 1, m);
         } else if (d == HOPH_CONTINUE) {
-            if (*nsurv >= (uint32_t)kSurvCap) resolve_survivors(a, list, nsurv, s_stats);
+            if (*nsurv >= (uint32_t)kSurvCap) resolve_survivors<E>(a, list, nsurv, s_stats);
             if (lane == 0) push_survivor(list, nsurv, q, row0 + rl, m, K);
             __syncwarp();
         }
     }
 }
 
+template <typename E>
 __global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_constant__ DenseArgs a,
                                                              const __grid_constant__ CUtensorMap map) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -401,7 +412,7 @@ __global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_consta
     uint32_t ph = 0;  // its mbarrier phase
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-        const uint32_t *tp = reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride);
+        const E *tp = reinterpret_cast<const E *>(stages + (size_t)s * a.stage_stride);
         const int64_t row0 = tile * R;
         const int rows_here = (int)min((long long)R, (long long)(P.n_rows - row0));
         if (a.use_tma) {
@@ -413,16 +424,17 @@ __global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_consta
             }
         } else {
             // plain cooperative load of the tile ([Gs][R][k'] layout)
-            uint32_t *dst = reinterpret_cast<uint32_t *>(stages);
+            E *dst = reinterpret_cast<E *>(stages);
+            const E *src = static_cast<const E *>(P.coll);
             const int per_plane = rows_here * P.kg;
             for (int idx = cw * 32 + lane; idx < P.Gs * per_plane; idx += a.n_cons * 32) {
                 const int g = idx / per_plane, rem = idx - g * per_plane;
-                dst[g * R * P.kg + rem] = P.coll[(int64_t)g * P.cstride + row0 * P.kg + rem];
+                dst[g * R * P.kg + rem] = src[(int64_t)g * P.cstride + row0 * P.kg + rem];
             }
             named_bar_sync(1, a.n_cons * 32);
         }
-        score_tile_dense(P, a.n_cons, tp, rows_here, row0, s_toff, s_qoff, s_thr, list, nsurv,
-                         s_stats, cw, acc0, qv, qem, cur_q);
+        score_tile_dense<E>(P, a.n_cons, tp, rows_here, row0, s_toff, s_qoff, s_thr, list, nsurv,
+                            s_stats, cw, acc0, qv, qem, cur_q);
         __syncwarp();
         if (a.use_tma) {
             if (lane == 0) mbar_arrive(empty + s);
@@ -434,7 +446,7 @@ __global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_consta
             named_bar_sync(1, a.n_cons * 32);
         }
     }
-    if (ok && *nsurv) resolve_survivors(P, list, nsurv, s_stats);
+    if (ok && *nsurv) resolve_survivors<E>(P, list, nsurv, s_stats);
     if (lane == 0 && acc0) atomicAdd(s_stats + 16, acc0);
     named_bar_sync(1, a.n_cons * 32);
     if (cw == 0) flush_stats(s_stats, P.stat, lane);
@@ -444,7 +456,7 @@ __global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_consta
 // Join strategy, part 1: index of the batch's scanned query values
 // ===========================================================================
 struct IndexArgs {
-    const uint32_t *qry;
+    const void *qry;     // E [G][n_q][k']
     int64_t qstride;
     int32_t n_q, kg, W, mask_words;
     const uint64_t *binbase;  // key = lo[w] + value
@@ -462,6 +474,7 @@ struct IndexArgs {
 };
 
 // warp per query: empty masks, all-empty list, key counts and the group map
+template <typename E>
 __global__ void join_count_kernel(const IndexArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -470,12 +483,12 @@ __global__ void join_count_kernel(const IndexArgs a) {
     for (int c = 0; c < a.mask_words; ++c) {
         const int w = (c << 5) + lane;
         const bool valid = w < a.W;
-        uint32_t v = HOPH_EMPTY_VALUE;
+        uint32_t v = empty_of<E>();
         if (valid) {
             const int g = w / a.kg, b = w - g * a.kg;
-            v = a.qry[(int64_t)g * a.qstride + q * a.kg + b];
+            v = static_cast<const E *>(a.qry)[(int64_t)g * a.qstride + q * a.kg + b];
         }
-        const bool e = v == HOPH_EMPTY_VALUE;
+        const bool e = v == empty_of<E>();
         const uint32_t em = __ballot_sync(0xFFFFFFFFu, valid && e);
         const uint32_t vm = __ballot_sync(0xFFFFFFFFu, valid);
         all_empty = all_empty && em == vm;
@@ -492,14 +505,15 @@ __global__ void join_count_kernel(const IndexArgs a) {
     if (lane == 0 && all_empty) a.allempty[atomicAdd(a.n_allempty, 1u)] = (int32_t)q;
 }
 
+template <typename E>
 __global__ void join_fill_kernel(const IndexArgs a, const uint32_t *csr_off, uint16_t *csr_q) {
     const int lane = threadIdx.x & 31;
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= a.n_q) return;
     for (int w = lane; w < a.W; w += 32) {
         const int g = w / a.kg, b = w - g * a.kg;
-        const uint32_t v = a.qry[(int64_t)g * a.qstride + q * a.kg + b];
-        if (v == HOPH_EMPTY_VALUE) continue;
+        const uint32_t v = static_cast<const E *>(a.qry)[(int64_t)g * a.qstride + q * a.kg + b];
+        if (v == empty_of<E>()) continue;
         const uint32_t key = (uint32_t)a.binbase[w] + v;
         const uint32_t slot = a.csr_hashed ? table_find(a.tkey, a.tmask, key) : key;
         if (slot == kNoSlot) continue;
@@ -627,9 +641,11 @@ __host__ __device__ inline FilterSmem filter_smem(const FilterArgs &a) {
 // bins of row r; their psi-space bases stay in registers.  MAXC bounds the
 // consumer warps (16, or 31 for narrow rows: more warps hide the map lookups'
 // latency at fewer registers per thread).
-template <int NPER, bool HASHED, int MAXC>
+template <int NPER, bool HASHED, int MAXC, typename E>
 __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_constant__ FilterArgs a,
                                                                  const __grid_constant__ CUtensorMap map) {
+    constexpr int VPL = 128 / (int)sizeof(E);  // values per 128-byte line
+    constexpr int VPC = 16 / (int)sizeof(E);   // values per 16-byte chunk
     extern __shared__ __align__(1024) unsigned char smem[];
     const FilterSmem L = filter_smem(a);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
@@ -666,10 +682,10 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
     const int rl = warp * rpw + r_in;
     const int w0 = sub * NPER;                // first bin of this lane
     const int g = w0 / a.kg;                  // plane of the lane's bins
-    const int lpr_row = a.kg >> 5;            // 128-byte lines per row and plane
+    const int lpr_row = a.kg / VPL;           // 128-byte lines per row and plane
     // line of (row rl, this lane's bins) within a tile, and the first chunk
-    const int line = (g * R + rl) * lpr_row + ((w0 - g * a.kg) >> 5);
-    const int c0 = (w0 & 31) >> 2;
+    const int line = (g * R + rl) * lpr_row + (w0 - g * a.kg) / VPL;
+    const int c0 = (w0 % VPL) / VPC;
     uint32_t kb[NPER];
 #pragma unroll
     for (int i = 0; i < NPER; ++i) kb[i] = (uint32_t)a.binbase[w0 + i];
@@ -678,8 +694,7 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
     int s = 0;          // stage of the current tile
     uint32_t ph = 0;    // its mbarrier phase
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-        const uint32_t *lp =
-            reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride) + line * 32;
+        const unsigned char *lp = stages + (size_t)s * a.stage_stride + (size_t)line * 128;
         // the swizzle XORs the chunk index with bits 7..9 of the line's address
         const int xr = (int)(smem_u32(lp) >> 7) & 7;
         const int64_t row = tile * R + rl;
@@ -694,14 +709,26 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
         uint32_t hits = 0, ne = 0;
         if (row < a.n_rows) {
 #pragma unroll
-            for (int c = 0; c < NPER / 4; ++c) {
-                const uint4 v =
-                    *reinterpret_cast<const uint4 *>(lp + (((c0 + c) ^ xr) << 2));
-                const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+            for (int c = 0; c < NPER / VPC; ++c) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(lp + (((c0 + c) ^ xr) << 4));
+                uint32_t x[VPC];
+                if constexpr (VPC == 4) {
+                    x[0] = v.x;
+                    x[1] = v.y;
+                    x[2] = v.z;
+                    x[3] = v.w;
+                } else {
+                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const bool full_bin = x[e] != HOPH_EMPTY_VALUE;
-                    const uint32_t key = kb[c * 4 + e] + x[e];
+                    for (int h = 0; h < 4; ++h) {
+                        x[2 * h] = wv[h] & 0xFFFFu;
+                        x[2 * h + 1] = wv[h] >> 16;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < VPC; ++e) {
+                    const bool full_bin = x[e] != empty_of<E>();
+                    const uint32_t key = kb[c * VPC + e] + x[e];
                     uint32_t mi = HASHED ? (mix32(key) & a.map_mask) : key;
                     mi = full_bin ? mi : zero_slot;
                     hits += (s_gmap[mi >> 4] >> (mi & 15u)) & 0x10001u;
@@ -778,7 +805,7 @@ __host__ __device__ inline CountSmem count_smem(const CountArgs &a) {
 // values and CSR ranges in registers between the counting and evaluation
 // passes, and the next candidate row's values are loaded while the current
 // one is counted.
-template <int NCH>
+template <int NCH, typename E>
 __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_constant__ CountArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const CountSmem L = count_smem(a);
@@ -824,9 +851,10 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
     }
     auto load_row = [&](unsigned long long ci, uint32_t *v) {
         const int64_t row = a.cand[ci];
-        const uint32_t *rb = P.coll + row * P.kg;
+        const E *rb = static_cast<const E *>(P.coll) + row * P.kg;
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) v[c] = woff[c] >= 0 ? __ldg(rb + woff[c]) : HOPH_EMPTY_VALUE;
+        for (int c = 0; c < NCH; ++c)
+            v[c] = woff[c] >= 0 ? (uint32_t)__ldg(rb + woff[c]) : empty_of<E>();
         return row;
     };
 
@@ -844,7 +872,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
             const bool valid = woff[c] >= 0;
-            const bool fullb = valid && v[c] != HOPH_EMPTY_VALUE;
+            const bool fullb = valid && v[c] != empty_of<E>();
             const uint32_t em = __ballot_sync(0xFFFFFFFFu, valid && !fullb);
             if (lane == 0 && c < a.mask_words) rowmask[c] = em;
             ne += __popc(__ballot_sync(0xFFFFFFFFu, fullb));
@@ -853,7 +881,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
             // pairs whose scanned bins are empty on both sides
             if (n_allempty > 0 && d00 != HOPH_REJECT) {
                 for (int base = 0; base < n_allempty; base += 32) {
-                    if (*nsurv + 32 > (uint32_t)kSurvCap) resolve_survivors(P, list, nsurv, s_stats);
+                    if (*nsurv + 32 > (uint32_t)kSurvCap) resolve_survivors<E>(P, list, nsurv, s_stats);
                     if (base + lane < n_allempty) {
                         const uint32_t q = (uint32_t)a.allempty[base + lane];
                         if (d00 == HOPH_ACCEPT) {
@@ -874,7 +902,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
             o1[c] = o2[c] = 0;
-            if (woff[c] >= 0 && v[c] != HOPH_EMPTY_VALUE) {
+            if (woff[c] >= 0 && v[c] != empty_of<E>()) {
                 const uint32_t key = kbase[c] + v[c];
                 const uint32_t slot = a.csr_hashed ? table_find(a.tkey, a.tmask, key) : key;
                 if (slot != kNoSlot) {
@@ -943,12 +971,12 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
             const bool all_done = __all_sync(0xFFFFFFFFu, done);
             __syncwarp();
             if (*nsurv >= (uint32_t)kSurvCap / 2 || !all_done)
-                resolve_survivors(P, list, nsurv, s_stats);
+                resolve_survivors<E>(P, list, nsurv, s_stats);
             if (all_done) break;
         }
         __syncwarp();
     }
-    if (*nsurv) resolve_survivors(P, list, nsurv, s_stats);
+    if (*nsurv) resolve_survivors<E>(P, list, nsurv, s_stats);
     for (int o = 16; o; o >>= 1) {
         acc0 += __shfl_xor_sync(0xFFFFFFFFu, acc0, o);
         hits += __shfl_xor_sync(0xFFFFFFFFu, hits, o);
@@ -961,14 +989,14 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
     if (warp == 0) flush_stats(s_stats, P.stat, lane);
 }
 
-template <int NCH>
+template <int NCH, typename E>
 int launch_count(const CountArgs &ca, uint32_t smem, int num_sms, cudaStream_t s) {
-    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)count_kernel<NCH>, (int)smem));
+    auto kern = count_kernel<NCH, E>;
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)kern, (int)smem));
     int per = 0;
-    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, count_kernel<NCH>,
-                                                                kCountThreads, smem));
+    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kCountThreads, smem));
     if (per < 1) return HOPH_ERR_UNSUPPORTED;
-    count_kernel<NCH><<<(unsigned)(num_sms * per), kCountThreads, smem, s>>>(ca);
+    kern<<<(unsigned)(num_sms * per), kCountThreads, smem, s>>>(ca);
     HOPH_CUDA_TRY(cudaGetLastError());
     return HOPH_OK;
 }
@@ -1162,39 +1190,47 @@ EncodeTiledFn get_encode_fn() {
     return fn;
 }
 
-// 3-D map over the collection planes: {k', rows, planes}, box {k', R, Gs}
-bool encode_planes_map(CUtensorMap *map, const uint32_t *planes, int kg, int64_t n_rows, int Gs,
-                       int64_t cstride, int R) {
+CUtensorMapDataType map_type(int esize) {
+    return esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+}
+
+// 3-D map over the collection planes (elements of esize bytes): {k', rows,
+// planes}, box {k', R, Gs}
+bool encode_planes_map(CUtensorMap *map, const void *planes, int esize, int kg, int64_t n_rows,
+                       int Gs, int64_t cstride, int R) {
     EncodeTiledFn fn = get_encode_fn();
     if (!fn) return false;
     const cuuint64_t gdim[3] = {(cuuint64_t)kg, (cuuint64_t)n_rows, (cuuint64_t)Gs};
-    const cuuint64_t gstride[2] = {(cuuint64_t)kg * 4, (cuuint64_t)cstride * 4};
+    const cuuint64_t gstride[2] = {(cuuint64_t)kg * esize, (cuuint64_t)cstride * esize};
     const cuuint32_t box[3] = {(cuuint32_t)kg, (cuuint32_t)R, (cuuint32_t)Gs};
     const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, (void *)planes, gdim, gstride, box, estr,
+    return fn(map, map_type(esize), 3, (void *)planes, gdim, gstride, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// 4-D swizzled map for the join filter: {32, k'/32, rows, planes}, box
-// {32, k'/32, R, Gs}, 128-byte swizzle (needs k' % 32 == 0)
-bool encode_swizzled_map(CUtensorMap *map, const uint32_t *planes, int kg, int64_t n_rows, int Gs,
-                         int64_t cstride, int R) {
+// 4-D swizzled map for the join filter: {v, k'/v, rows, planes}, box
+// {v, k'/v, R, Gs} with v = 128 / esize values per 128-byte line, 128-byte
+// swizzle (needs k' % v == 0)
+bool encode_swizzled_map(CUtensorMap *map, const void *planes, int esize, int kg, int64_t n_rows,
+                         int Gs, int64_t cstride, int R) {
     EncodeTiledFn fn = get_encode_fn();
     if (!fn) return false;
-    const cuuint64_t gdim[4] = {32, (cuuint64_t)(kg / 32), (cuuint64_t)n_rows, (cuuint64_t)Gs};
-    const cuuint64_t gstride[3] = {128, (cuuint64_t)kg * 4, (cuuint64_t)cstride * 4};
-    const cuuint32_t box[4] = {32, (cuuint32_t)(kg / 32), (cuuint32_t)R, (cuuint32_t)Gs};
+    const int v = 128 / esize;
+    const cuuint64_t gdim[4] = {(cuuint64_t)v, (cuuint64_t)(kg / v), (cuuint64_t)n_rows,
+                                (cuuint64_t)Gs};
+    const cuuint64_t gstride[3] = {128, (cuuint64_t)kg * esize, (cuuint64_t)cstride * esize};
+    const cuuint32_t box[4] = {(cuuint32_t)v, (cuuint32_t)(kg / v), (cuuint32_t)R, (cuuint32_t)Gs};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, (void *)planes, gdim, gstride, box, estr,
+    return fn(map, map_type(esize), 4, (void *)planes, gdim, gstride, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NPER, bool HASHED, int MAXC>
+template <int NPER, bool HASHED, int MAXC, typename E>
 int launch_filter_c(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem, int num_sms,
                     int ctas_per_sm, cudaStream_t s) {
-    auto kern = filter_kernel<NPER, HASHED, MAXC>;
+    auto kern = filter_kernel<NPER, HASHED, MAXC, E>;
     HOPH_CUDA_TRY(hoph_ensure_smem((const void *)kern, (int)smem));
     const int threads = 32 * (fa.n_cons + 1);
     int per_sm = 0;
@@ -1207,11 +1243,12 @@ int launch_filter_c(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem,
     return HOPH_OK;
 }
 
-template <int NPER, bool HASHED>
+template <int NPER, bool HASHED, typename E>
 int launch_filter(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem, int num_sms,
                   int ctas_per_sm, cudaStream_t s) {
-    return fa.n_cons > 16 ? launch_filter_c<NPER, HASHED, 31>(fa, map, smem, num_sms, ctas_per_sm, s)
-                          : launch_filter_c<NPER, HASHED, 16>(fa, map, smem, num_sms, ctas_per_sm, s);
+    return fa.n_cons > 16
+               ? launch_filter_c<NPER, HASHED, 31, E>(fa, map, smem, num_sms, ctas_per_sm, s)
+               : launch_filter_c<NPER, HASHED, 16, E>(fa, map, smem, num_sms, ctas_per_sm, s);
 }
 
 // First-pass decision table for W scanned bins under `dp` after `l` groups:
@@ -1262,20 +1299,23 @@ struct Bump {
     }
 };
 
-}  // namespace
-
-extern "C" {
-
-int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_planes,
-                     int64_t n_queries, const uint32_t *d_coll_planes, int64_t n_rows,
-                     hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
-                     hoph_stats *d_stats, void *stream) {
+// hoph_query_batch / hoph_query_batch16 over planes of element type E
+template <typename E>
+int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, int64_t n_queries,
+                     const E *d_coll_planes, int64_t n_rows, hoph_pair *d_out,
+                     int64_t out_capacity, int64_t *d_out_count, hoph_stats *d_stats,
+                     void *stream) {
+    constexpr int ES = (int)sizeof(E);
     if (!plan || !d_out_count || n_queries < 0 || n_rows < 0 || out_capacity < 0)
         return HOPH_ERR_PARAM;
     if (out_capacity > 0 && !d_out) return HOPH_ERR_PARAM;
     if (n_queries > 65535 || n_rows >= (1ll << 40)) return HOPH_ERR_UNSUPPORTED;
     const hoph_params &P = plan->P;
     cudaStream_t s = (cudaStream_t)stream;
+    // compact planes hold bin offsets: every bin must fit 16 bits with 0xFFFF
+    // left for the empty marker; MinWise values are whole psi-values
+    if (ES == 2 && (mode == HOPH_MODE_MINWISE_FULL || plan->max_width > 0xFFFFu))
+        return HOPH_ERR_UNSUPPORTED;
 
     // mode -> scanned planes and the rule of the first pass
     DecideParams dp = plan->dp;
@@ -1326,7 +1366,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
     if (!plan->table_ok[mode]) return HOPH_ERR_UNSUPPORTED;
     const std::vector<uint16_t> &tab = plan->h_table[mode];
 
-    const bool tma_base_ok = (kg % 4 == 0) && kg <= 256 && Gs <= 256 &&
+    const bool tma_base_ok = ((kg * ES) % 16 == 0) && kg <= 256 && Gs <= 256 &&
                              ((uintptr_t)d_coll_planes & 15) == 0 && get_encode_fn() != nullptr;
 
     // join: needs "no match => reject" for every K >= 1, TMA tiles, a rule
@@ -1347,9 +1387,9 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         while (csr_slots < 2ull * (uint64_t)n_queries * W) csr_slots <<= 1;
     }
     bool join_ok = mode != HOPH_MODE_MINWISE_FULL && fp.rule != HOPH_EMPTY_EITHER &&
-                   tma_base_ok && kg % 32 == 0 && W <= 256 && n_queries <= 4096 &&
+                   tma_base_ok && kg % (128 / ES) == 0 && W <= 256 && n_queries <= 4096 &&
                    n_rows < (1ll << 32) && csr_slots < (1ull << 31) &&
-                   map_slots / 4 + 2 * 32 * W * 4 + 8 * W + 4096 <= (uint64_t)kSmemLimit;
+                   map_slots / 4 + 2 * 32 * W * ES + 8 * W + 4096 <= (uint64_t)kSmemLimit;
     for (int K = 1; K <= W && join_ok; ++K) join_ok = tab[K] >= 1;
     int strategy = plan->exec.strategy;
     if (strategy == 1 && !join_ok) return HOPH_ERR_UNSUPPORTED;
@@ -1461,13 +1501,13 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         HOPH_CUDA_TRY(cudaMemsetAsync(n_allempty, 0, 4, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(n_cand, 0, 8, s));
         const unsigned qb = (unsigned)((n_queries * 32 + 255) / 256);
-        join_count_kernel<<<qb, 256, 0, s>>>(ia);
+        join_count_kernel<E><<<qb, 256, 0, s>>>(ia);
         const int64_t n_scan = (int64_t)csr_slots + 1;
         const int64_t nb = (n_scan + kScanChunk - 1) / kScanChunk;
         scan_sums_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, n_scan, sums);
         scan_top_kernel<<<1, kScanBlock, 0, s>>>(sums, nb);
         scan_apply_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, n_scan, sums, csr_off);
-        join_fill_kernel<<<qb, 256, 0, s>>>(ia, csr_off, csr_q);
+        join_fill_kernel<E><<<qb, 256, 0, s>>>(ia, csr_off, csr_q);
         HOPH_CUDA_TRY(cudaGetLastError());
         launches += 5;
 
@@ -1496,7 +1536,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
                                align_up(fa.gmap_words * 4, 1024) + 1024;
         int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 16;
         int stages = plan->exec.stages > 0 ? plan->exec.stages : 3;
-        auto stage_of = [&](int nc) { return align_up((uint32_t)(32 / lpr * nc) * W * 4, 1024); };
+        auto stage_of = [&](int nc) { return align_up((uint32_t)(32 / lpr * nc) * W * ES, 1024); };
         while (n_cons > 1 && (fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit ||
                               32 / lpr * n_cons > 256)) {
             if (stages > 2) --stages; else --n_cons;
@@ -1508,20 +1548,21 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         fa.tile_rows = 32 / lpr * n_cons;
         fa.stages = stages;
         fa.n_tiles = (n_rows + fa.tile_rows - 1) / fa.tile_rows;
-        fa.stage_bytes = (uint32_t)fa.tile_rows * W * 4;
+        fa.stage_bytes = (uint32_t)fa.tile_rows * W * ES;
         fa.stage_stride = align_up(fa.stage_bytes, 1024);
         CUtensorMap map;
         memset(&map, 0, sizeof map);
-        if (!encode_swizzled_map(&map, d_coll_planes, kg, n_rows, Gs, cstride, fa.tile_rows))
+        if (!encode_swizzled_map(&map, d_coll_planes, ES, kg, n_rows, Gs, cstride, fa.tile_rows))
             return HOPH_ERR_UNSUPPORTED;
         const FilterSmem FL = filter_smem(fa);
         hoph_timing_mark(plan, 1, s);
         const int cps = plan->exec.ctas_per_sm;
+        const int nsm = plan->num_sms;
         const int frc =
-            nper == 32 ? (map_hashed ? launch_filter<32, true>(fa, map, FL.total, plan->num_sms, cps, s)
-                                     : launch_filter<32, false>(fa, map, FL.total, plan->num_sms, cps, s))
-                       : (map_hashed ? launch_filter<16, true>(fa, map, FL.total, plan->num_sms, cps, s)
-                                     : launch_filter<16, false>(fa, map, FL.total, plan->num_sms, cps, s));
+            nper == 32 ? (map_hashed ? launch_filter<32, true, E>(fa, map, FL.total, nsm, cps, s)
+                                     : launch_filter<32, false, E>(fa, map, FL.total, nsm, cps, s))
+                       : (map_hashed ? launch_filter<16, true, E>(fa, map, FL.total, nsm, cps, s)
+                                     : launch_filter<16, false, E>(fa, map, FL.total, nsm, cps, s));
         if (frc != HOPH_OK) return frc;
         hoph_timing_mark(plan, 2, s);
 
@@ -1543,10 +1584,10 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         const CountSmem CL = count_smem(ca);
         if (CL.total > (uint32_t)kSmemLimit) return HOPH_ERR_UNSUPPORTED;
         const int nch = (W + 31) / 32;
-        const int rc = nch <= 1 ? launch_count<1>(ca, CL.total, plan->num_sms, s)
-                     : nch <= 2 ? launch_count<2>(ca, CL.total, plan->num_sms, s)
-                     : nch <= 4 ? launch_count<4>(ca, CL.total, plan->num_sms, s)
-                                : launch_count<8>(ca, CL.total, plan->num_sms, s);
+        const int rc = nch <= 1 ? launch_count<1, E>(ca, CL.total, plan->num_sms, s)
+                     : nch <= 2 ? launch_count<2, E>(ca, CL.total, plan->num_sms, s)
+                     : nch <= 4 ? launch_count<4, E>(ca, CL.total, plan->num_sms, s)
+                                : launch_count<8, E>(ca, CL.total, plan->num_sms, s);
         if (rc != HOPH_OK) return rc;
         hoph_timing_mark(plan, 3, s);
         launches += 2;
@@ -1558,7 +1599,7 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         if (n_cons > 16) return HOPH_ERR_UNSUPPORTED;
         int R = plan->exec.tile_rows > 0 ? plan->exec.tile_rows : 0;
         if (R == 0) {
-            R = (int)std::max<int64_t>(1, std::min<int64_t>(256, 8192 / (W * 4)));
+            R = (int)std::max<int64_t>(1, std::min<int64_t>(256, 8192 / (W * ES)));
             if (R >= 8) R &= ~7;
         }
         da.n_cons = n_cons;
@@ -1566,26 +1607,27 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
         da.use_tma = tma_base_ok ? 1 : 0;
         da.stages = tma_base_ok ? (plan->exec.stages > 0 ? plan->exec.stages : 4) : 1;
         da.n_tiles = (n_rows + R - 1) / R;
-        da.stage_bytes = (uint32_t)Gs * R * kg * 4;
+        da.stage_bytes = (uint32_t)Gs * R * kg * ES;
         da.stage_stride = align_up(da.stage_bytes, 128);
         CUtensorMap map;
         memset(&map, 0, sizeof map);
-        if (da.use_tma && !encode_planes_map(&map, d_coll_planes, kg, n_rows, Gs, cstride, R)) {
+        if (da.use_tma && !encode_planes_map(&map, d_coll_planes, ES, kg, n_rows, Gs, cstride, R)) {
             da.use_tma = 0;
             da.stages = 1;
         }
         const DenseSmem DL = dense_smem(da);
         if (DL.total > (uint32_t)kSmemLimit) return HOPH_ERR_UNSUPPORTED;
-        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)dense_scan_kernel, (int)DL.total));
+        auto dense = dense_scan_kernel<E>;
+        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)dense, (int)DL.total));
         const int threads = 32 * (n_cons + 1);
         int per_sm = 0;
-        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_scan_kernel,
-                                                                    threads, DL.total));
+        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense, threads,
+                                                                    DL.total));
         if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
         if (plan->exec.ctas_per_sm > 0) per_sm = std::min(per_sm, plan->exec.ctas_per_sm);
         const int64_t grid = std::min<int64_t>(da.n_tiles, (int64_t)plan->num_sms * per_sm);
         hoph_timing_mark(plan, 1, s);
-        dense_scan_kernel<<<(unsigned)grid, threads, DL.total, s>>>(da, map);
+        dense<<<(unsigned)grid, threads, DL.total, s>>>(da, map);
         HOPH_CUDA_TRY(cudaGetLastError());
         hoph_timing_mark(plan, 2, s);
         hoph_timing_mark(plan, 3, s);
@@ -1595,13 +1637,33 @@ int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_pla
     HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
     sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(d_out, pa.out_count, out_capacity,
                                                               sortA, sortB, plan->d_status);
-    const int64_t fp_bytes = n_rows * (int64_t)W * 4 + n_queries * (int64_t)W * 4;
+    const int64_t fp_bytes = (n_rows * (int64_t)W + n_queries * (int64_t)W) * ES;
     stats_fold_kernel<<<1, 32, 0, s>>>(st, n_cand, n_queries * n_rows, G, Gs, fp_bytes, strategy,
                                        d_stats);
     HOPH_CUDA_TRY(cudaGetLastError());
     hoph_timing_mark(plan, 4, s);
     plan->launches += launches + 2;
     return HOPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_planes,
+                     int64_t n_queries, const uint32_t *d_coll_planes, int64_t n_rows,
+                     hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
+                     hoph_stats *d_stats, void *stream) {
+    return query_batch_impl<uint32_t>(plan, mode, d_query_planes, n_queries, d_coll_planes, n_rows,
+                                      d_out, out_capacity, d_out_count, d_stats, stream);
+}
+
+int hoph_query_batch16(hoph_plan *plan, uint32_t mode, const uint16_t *d_query_planes,
+                       int64_t n_queries, const uint16_t *d_coll_planes, int64_t n_rows,
+                       hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
+                       hoph_stats *d_stats, void *stream) {
+    return query_batch_impl<uint16_t>(plan, mode, d_query_planes, n_queries, d_coll_planes,
+                                      n_rows, d_out, out_capacity, d_out_count, d_stats, stream);
 }
 
 int hoph_check_bounded_wait(hoph_plan *plan, uint64_t limit_ns, void *stream) {

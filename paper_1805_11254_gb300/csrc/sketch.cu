@@ -40,7 +40,8 @@ struct SketchArgs {
     const uint32_t *ids;
     const int64_t *off;
     int64_t n_sets;
-    uint32_t *planes;
+    void *planes;          // uint32 or (compact) uint16 [G][n_sets][k']
+    int32_t compact;       // uint16 planes
     int64_t plane_stride;  // n_sets * k'
     uint32_t k, kg;
     const uint32_t *key;   // packed psi table (table path)
@@ -190,7 +191,10 @@ __device__ __forceinline__ void store_sketch(const SketchArgs &a, uint32_t *sk, 
                                              int T) {
     for (uint32_t b = t; b < a.k; b += T) {
         const uint32_t g = b / a.kg, j = b - g * a.kg;
-        a.planes[(int64_t)g * a.plane_stride + set * a.kg + j] = sk[b];
+        const int64_t at = (int64_t)g * a.plane_stride + set * a.kg + j;
+        // compact: offsets < 0xFFFF; the empty marker truncates to 0xFFFF
+        if (a.compact) static_cast<uint16_t *>(a.planes)[at] = (uint16_t)sk[b];
+        else static_cast<uint32_t *>(a.planes)[at] = sk[b];
         sk[b] = HOPH_EMPTY_VALUE;
     }
 }
@@ -371,13 +375,14 @@ __global__ void synth_ids_kernel(uint64_t seed, int64_t first, int64_t n, uint64
 int grid_for(hoph_plan *pl, int per_sm) { return pl->num_sms * per_sm; }
 
 SketchArgs sketch_args(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
-                       int64_t n_sets, uint32_t *d_planes) {
+                       int64_t n_sets, void *d_planes) {
     const hoph_params &P = plan->P;
     SketchArgs a;
     a.ids = d_ids;
     a.off = d_offsets;
     a.n_sets = n_sets;
     a.planes = d_planes;
+    a.compact = 0;
     a.plane_stride = n_sets * (int64_t)P.k_group;
     a.k = P.k;
     a.kg = P.k_group;
@@ -466,17 +471,16 @@ int launch_sketch(hoph_plan *plan, const SketchArgs &a, cudaStream_t s) {
 
 constexpr int64_t kWorkListMin = 64;  // below this many sets: identity order, warps only
 
-}  // namespace
-
-extern "C" {
-
-int oph_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
-                       int64_t n_sets, uint32_t *d_planes, void *stream) {
+// oph_build_sketches / oph_build_sketches16
+int build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
+                   int64_t n_sets, void *d_planes, bool compact, void *stream) {
     if (!plan || n_sets < 0 || (n_sets > 0 && (!d_offsets || !d_planes))) return HOPH_ERR_PARAM;
     if (n_sets >= (1ll << 31)) return HOPH_ERR_PARAM;
+    if (compact && plan->max_width > 0xFFFFu) return HOPH_ERR_UNSUPPORTED;
     if (n_sets == 0) return HOPH_OK;
     cudaStream_t s = (cudaStream_t)stream;
     SketchArgs a = sketch_args(plan, d_ids, d_offsets, n_sets, d_planes);
+    a.compact = compact ? 1 : 0;
     if (n_sets >= kWorkListMin) {
         const size_t bytes = (3 * kBuckets + 1) * sizeof(uint32_t) + (size_t)n_sets * sizeof(int32_t);
         uint32_t *wl = (uint32_t *)hoph_scratch(plan, bytes);
@@ -485,6 +489,20 @@ int oph_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_
         if (rc != HOPH_OK) return rc;
     }
     return launch_sketch(plan, a, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int oph_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
+                       int64_t n_sets, uint32_t *d_planes, void *stream) {
+    return build_sketches(plan, d_ids, d_offsets, n_sets, d_planes, false, stream);
+}
+
+int oph_build_sketches16(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offsets,
+                         int64_t n_sets, uint16_t *d_planes, void *stream) {
+    return build_sketches(plan, d_ids, d_offsets, n_sets, d_planes, true, stream);
 }
 
 int hoph_synth_sketch(hoph_plan *plan, uint64_t seed, uint64_t D, const int64_t *d_offsets,

@@ -43,6 +43,7 @@ HOPH_WEIGHT_SPACE = 0
 HOPH_WEIGHT_LITERAL = 1
 HOPH_MAX_GROUPS = 16
 HOPH_EMPTY_VALUE = 0xFFFFFFFF
+HOPH_EMPTY_VALUE16 = 0xFFFF
 
 
 class hoph_params(ctypes.Structure):
@@ -76,7 +77,8 @@ STATS_WORDS = ctypes.sizeof(hoph_stats) // 8
 class hoph_plan_info(ctypes.Structure):
     _fields_ = [("groups", ctypes.c_uint32), ("key_bits", ctypes.c_uint32),
                 ("upper_limit", ctypes.c_int64), ("lower_limit", ctypes.c_int64),
-                ("group_size", ctypes.c_uint64 * HOPH_MAX_GROUPS)]
+                ("group_size", ctypes.c_uint64 * HOPH_MAX_GROUPS),
+                ("max_bin_width", ctypes.c_uint64)]
 
 
 class hoph_exec(ctypes.Structure):
@@ -98,7 +100,8 @@ _EXPORTS = ["hoph_plan_create", "hoph_plan_create_with_perm", "hoph_plan_destroy
             "minwise_build_sketches", "hoph_query_batch", "hoph_pair_counts", "hoph_synth_ids",
             "hoph_sync_status", "hoph_status_string", "hoph_plan_enable_timing",
             "hoph_plan_read_timing", "oph_build_sketches_static", "hoph_plan_peek_timing",
-            "hoph_check_bounded_wait", "hoph_synth_sketch"]
+            "hoph_check_bounded_wait", "hoph_synth_sketch", "oph_build_sketches16",
+            "hoph_query_batch16"]
 
 
 def load(path=LIB_PATH):
@@ -130,6 +133,10 @@ def load(path=LIB_PATH):
     lib.minwise_build_sketches.restype = i32
     lib.hoph_query_batch.argtypes = [P, u32, P, i64, P, i64, P, i64, P, P, P]
     lib.hoph_query_batch.restype = i32
+    lib.oph_build_sketches16.argtypes = [P, P, P, i64, P, P]
+    lib.oph_build_sketches16.restype = i32
+    lib.hoph_query_batch16.argtypes = [P, u32, P, i64, P, i64, P, i64, P, P, P]
+    lib.hoph_query_batch16.restype = i32
     lib.hoph_pair_counts.argtypes = [P, P, i64, P, i64, P, P]
     lib.hoph_pair_counts.restype = i32
     lib.hoph_synth_ids.argtypes = [u64, i64, i64, u64, u32, P, i64, P, P]
@@ -247,6 +254,21 @@ def hoph_query_batch(plan, mode, d_query_planes, n_queries, d_coll_planes, n_row
                                           _ptr(d_stats), _stream(stream)), "hoph_query_batch")
 
 
+def oph_build_sketches16(plan, d_ids, d_offsets, n_sets, d_planes, stream=None):
+    """Compact (uint16) sketches; d_planes int16/uint16 [G][n_sets][k']."""
+    return _check(load().oph_build_sketches16(plan, _ptr(d_ids), _ptr(d_offsets), int(n_sets),
+                                              _ptr(d_planes), _stream(stream)),
+                  "oph_build_sketches16")
+
+
+def hoph_query_batch16(plan, mode, d_query_planes, n_queries, d_coll_planes, n_rows, d_out,
+                       out_capacity, d_out_count, d_stats=None, stream=None):
+    return _check(load().hoph_query_batch16(plan, MODES.get(mode, mode), _ptr(d_query_planes),
+                                            int(n_queries), _ptr(d_coll_planes), int(n_rows),
+                                            _ptr(d_out), int(out_capacity), _ptr(d_out_count),
+                                            _ptr(d_stats), _stream(stream)), "hoph_query_batch16")
+
+
 def hoph_pair_counts(plan, d_query_planes, n_queries, d_coll_planes, n_rows, d_counts,
                      stream=None):
     return _check(load().hoph_pair_counts(plan, _ptr(d_query_planes), int(n_queries),
@@ -354,6 +376,14 @@ class Plan:
         oph_build_sketches(self.handle, d_ids, d_offsets, n_sets, out, stream)
         return out
 
+    def sketch16(self, d_ids, d_offsets, n_sets, out=None, stream=None):
+        """Compact sketches, int16 tensor [G][n_sets][k'] (0xFFFF = empty)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.G, n_sets, self.kg), dtype=torch.int16, device=d_offsets.device)
+        oph_build_sketches16(self.handle, d_ids, d_offsets, n_sets, out, stream)
+        return out
+
     def minwise(self, d_ids, d_offsets, n_sets, out=None, stream=None):
         import torch
         if out is None:
@@ -369,8 +399,9 @@ class Plan:
         out = torch.empty((max(capacity, 1), 2), dtype=torch.int64, device=dev)
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
         st = torch.zeros(STATS_WORDS, dtype=torch.int64, device=dev) if stats else None
-        hoph_query_batch(self.handle, mode, q_planes, n_queries, c_planes, n_rows, out, capacity,
-                         cnt, st, stream)
+        call = hoph_query_batch16 if c_planes.element_size() == 2 else hoph_query_batch
+        call(self.handle, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, cnt, st,
+             stream)
         if check:
             rc = hoph_sync_status(self.handle, stream)
             if rc not in (HOPH_OK, HOPH_ERR_CAPACITY):

@@ -321,3 +321,36 @@ def test_literal_weighting_parity(small, ab, strategy):
                         z=np.asarray(z, dtype=np.uint64), weighting="literal", ab=ab)
         _compare(plan, "hoph", q, c, nq, nr, want, strategy, plan.G)
 
+
+
+@pytest.mark.parametrize("strategy", [0, 1, -1])
+@pytest.mark.parametrize("mode,ab,kg", [("goph", (0, 0), 32), ("hoph", (1, 2), 64),
+                                        ("oph_full", (0, 0), 64), ("hoph", (1, 1), 32)])
+def test_compact_planes_give_the_same_pairs(small, mode, ab, kg, strategy):
+    """hoph_query_batch16 over uint16 planes: the oracle's pairs and
+    per-group decision counts, through the dense scan and the value join
+    (the join needs k' % 64 == 0 here; otherwise forcing it is UNSUPPORTED)."""
+    dev = device()
+    D, k = small["D"], 128
+    with hoph.Plan(D, k, kg, *ab, seed=1, thr=T, epsilon=EPS) as plan:
+        q, c = _sketch_both(plan, small, dev)
+        z = [plan.info.group_size[g] for g in range(plan.G)]
+        want = _oracle_query(mode, planes_to_rows(q), planes_to_rows(c), kg, z)
+        q16 = plan.sketch16(to_dev(small["q_ids"], dev), to_dev(small["q_off"], dev), q.shape[1])
+        c16 = plan.sketch16(to_dev(small["ids"], dev), to_dev(small["off"], dev), c.shape[1])
+        plan.check()
+        G = plan.G if mode in ("goph", "hoph") else 1
+        plan.set_exec(strategy=strategy)
+        try:
+            pairs, n, st = plan.query(mode, q16, q.shape[1], c16, c.shape[1], capacity=1 << 16,
+                                      stats=True)
+        except hoph.HophError as e:
+            assert strategy == 1 and e.code == hoph.HOPH_ERR_UNSUPPORTED
+            return
+        assert n == want["count"]
+        assert pairs_tuples(pairs) == oracle_tuples(want)
+        hist = want["hist"]
+        for g in range(G):
+            assert st.accepted[g] == hist[g + 1][1] and st.rejected[g] == hist[g + 1][2]
+        if strategy >= 0:
+            assert st.strategy == strategy

@@ -208,3 +208,31 @@ def test_generated_sets_sketch_like_stored_ones(hash_perm):
     else:
         want = oc.sketch(ids, off - off[0], lo, perm=oc.permutation(D, 5))
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("ab,kg", [((0, 0), 32), ((1, 2), 64)])
+def test_compact_sketches_are_the_offsets_in_16_bits(small, ab, kg):
+    """oph_build_sketches16: the oracle's values, empty bins as 0xFFFF."""
+    dev = device()
+    D, k = small["D"], 128
+    with hoph.Plan(D, k, kg, *ab, seed=1) as plan:
+        assert plan.info.max_bin_width <= 0xFFFF
+        d_ids, d_off = to_dev(small["ids"], dev), to_dev(small["off"], dev)
+        got = plan.sketch16(d_ids, d_off, len(small["off"]) - 1)
+        plan.check()
+    want = oc.sketch(small["ids"], small["off"], oc.layout(D, k, kg, *ab),
+                     perm=oc.permutation(D, 1))
+    want16 = np.where(want == hoph.HOPH_EMPTY_VALUE, hoph.HOPH_EMPTY_VALUE16, want)
+    rows = got.cpu().numpy().view(np.uint16).transpose(1, 0, 2).reshape(len(want), -1)
+    assert np.array_equal(rows, want16.astype(np.uint16))
+
+
+def test_compact_sketches_need_bins_of_at_most_65535_values():
+    dev = device()
+    with hoph.Plan(1 << 20, 8, 8, seed=1) as plan:  # bins of 131,072 values
+        assert plan.info.max_bin_width == 1 << 17
+        out = torch.empty((1, 1, 8), dtype=torch.int16, device=dev)
+        off = to_dev(np.zeros(2, dtype=np.int64), dev)
+        with pytest.raises(hoph.HophError) as e:
+            hoph.oph_build_sketches16(plan.handle, off, off, 1, out)
+        assert e.value.code == hoph.HOPH_ERR_UNSUPPORTED
