@@ -42,7 +42,7 @@ SKETCH_SEED = 21
 # dram read+write bytes per filter-kernel launch from an ncu capture, keyed by
 # the sha256 of the filter kernel's source it was taken on (null once that
 # source changes)
-NCU_TRAFFIC = {"d4a43c1c1a1567fa": 2579.19e6}  # profiles/filter_kernel_2e6rows.md, x5 rows
+NCU_TRAFFIC = {"5e10f542db8a3057": 2576.60e6}  # profiles/filter_kernel_2e6rows.md, x5 rows
 
 
 def parse():
@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
     p.add_argument("--no-compact", action="store_true",
                    help="skip the same step over compact (uint16) sketch planes")
+    p.add_argument("--no-self-join", action="store_true",
+                   help="skip the all-pairs self-join of a 10^6-row collection")
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the threshold / tolerance sweep on the 5,000-set workload")
     p.add_argument("--serve-rates", default="2000,20000,100000",
@@ -431,13 +433,16 @@ def run_native(args):
     if rank == 0 and not args.no_extras:
         line["e2e"] = e2e_leg(args, plan, qw, planes, dev, stream)
         line["sketch"] = sketch_leg(dev, stream, peaks)
-        line["oph_full_scan_baseline"], oph_pairs = oph_baseline_leg(args, off, coll_seed, qw, dev,
-                                                                     stream, value)
-        eps_runs = eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream)
-        methods = {"hoph": pairs, "oph_full_scan": oph_pairs}
+        rq = recall_queries(off, coll_seed)
+        line["oph_full_scan_baseline"], oph_pairs, oph_rq_pairs = oph_baseline_leg(
+            args, off, coll_seed, qw, dev, stream, value, rq)
+        line["quality"] = quality(qw, {"hoph": pairs, "oph_full_scan": oph_pairs}, off,
+                                  coll_seed, args)
+        eps_runs = eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq)
+        methods = {"oph_full_scan": oph_rq_pairs}
         methods.update({"hoph_eps_%g" % e: r["pairs"] for e, r in eps_runs.items()})
-        line["quality"] = quality(qw, methods, off, coll_seed, args)
-        line["equal_recall"] = equal_recall(line["quality"], eps_runs, nq, args.rows)
+        study = quality(rq, methods, off, coll_seed, args, n_random_rows=500)
+        line["equal_recall"] = equal_recall(study, eps_runs, nq, args.rows, len(rq["q_off"]) - 1)
         line["cpu_baseline"] = cpu_baseline(qw, off, coll_seed, args.cpu_seconds, args.rows)
         if not args.no_serve:
             line["serving"] = serving_leg(args, planes, dev, line["oph_full_scan_baseline"])
@@ -446,6 +451,8 @@ def run_native(args):
                                           stream, peaks)
         if not args.no_sweep:
             line["sweeps"] = sweep_leg(dev, stream)
+        if not args.no_self_join:
+            line["self_join"] = self_join_leg(off, coll_seed, dev, stream)
         if not args.no_shingle:
             del planes
             torch.cuda.empty_cache()
@@ -502,14 +509,27 @@ def e2e_leg(args, plan, qw, planes, dev, stream):
 
 
 EQUAL_RECALL_EPS = (1e-4, 1e-5, 1e-6, 1e-8, 0.0)
+RECALL_QUERIES = 4096
 
 
-def eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, reps=20):
+def recall_queries(off, coll_seed):
+    """A larger query set for comparing recalls: 4,096 query sets, half of
+    them planted near duplicates (J ~ U[0.6, 0.95]) of collection rows."""
+    from paper_1805_11254_gb300 import synth
+    return synth.query_batch(RECALL_QUERIES, 0.5, D, coll_seed, off, 0.6, 0.95, Q_SEED + 50,
+                             PLANT_SEED + 50)
+
+
+def eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq, reps=20):
     """The same step (sketch the query sets, HOPH query) at smaller error
     tolerances: the sketches do not depend on eps, only the decisions do.
-    Returns {eps: {"pairs", "ms"}} with eager CUDA-event timing."""
+    Returns {eps: {"pairs", "ms"}}: the pairs of the recall query set `rq`
+    (one call of 4,096 queries) and the eager CUDA-event time of the
+    benchmark's 1,024-query step."""
     import torch
     from paper_1805_11254_gb300 import hoph
+    rq_ids, rq_off = to_dev(rq["q_ids"], dev), to_dev(rq["q_off"], dev)
+    n_rq = len(rq["q_off"]) - 1
     out = {}
     cap = 1 << 20
     o = torch.empty((cap, 2), dtype=torch.int64, device=dev)
@@ -533,15 +553,20 @@ def eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, reps=20):
             e1.record(stream)
             torch.cuda.synchronize()
             p.check(stream)
+            ms = e0.elapsed_time(e1) / reps
+            rqp = p.sketch(rq_ids, rq_off, n_rq, stream=stream)
+            hoph.hoph_query_batch(p.handle, hoph.HOPH_MODE_HOPH, rqp, n_rq, planes, args.rows, o,
+                                  cap, cnt, None, stream)
+            p.check(stream)
             n = int(cnt.item())
             out[eps] = {"pairs": o[:min(n, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
-                        .copy(), "ms": e0.elapsed_time(e1) / reps}
+                        .copy(), "ms": ms}
     return out
 
 
-def equal_recall(q, eps_runs, nq, rows):
-    """The largest eps at which HOPH's recall reaches plain OPH's, with the
-    step's eager throughput at each eps."""
+def equal_recall(q, eps_runs, nq, rows, n_rq):
+    """The largest eps at which HOPH's recall on the recall query set reaches
+    plain OPH's, with the benchmark step's eager throughput at each eps."""
     target = q["oph_full_scan"]["recall"]
     pts = []
     for eps, r in eps_runs.items():
@@ -553,8 +578,10 @@ def equal_recall(q, eps_runs, nq, rows):
     return {"oph_full_scan_recall": target, "points": pts,
             "eps_at_equal_recall": best["eps"] if best else None,
             "value_at_equal_recall": best["value"] if best else None,
-            "unit": UNIT, "how": "same query sets and sketches; eps only changes the decisions; "
-                                 "eager step timing (sketch + query), not the graph replay"}
+            "unit": UNIT, "recall_queries": n_rq, "truly_similar": q["truly_similar"],
+            "how": "recall of %d query sets (half planted) against exact Jaccard; eps only "
+                   "changes the decisions; throughput = eager step timing (sketch + query) of "
+                   "the 1,024-query step, not the graph replay" % n_rq}
 
 
 def quality(qw, pairs_by_method, off, coll_seed, args, n_random_rows=2000):
@@ -658,11 +685,12 @@ def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
         plan.check()
 
 
-def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, n_launch=8):
+def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, rq, n_launch=8):
     """Plain OPH over all 256 bins (Eq. 6) on a uniform-OPH sketch of the same
     collection: the whole query batch in one call (the library picks the
     strategy), and one query per launch through the dense scan with its
-    execution knobs tuned for a single query.  Returns (leg, batched pairs)."""
+    execution knobs tuned for a single query.  Returns (leg, batched pairs,
+    pairs of the recall query set rq)."""
     import torch
     from paper_1805_11254_gb300 import autotune, hoph
     n_ids = int(off[-1])
@@ -691,6 +719,14 @@ def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, n_launch
         n_b = int(cnt.item())
         pairs_b = out[:min(n_b, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1).copy()
         strategy_b = int(hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes()).strategy)
+        n_rq = len(rq["q_off"]) - 1
+        rqp = plan.sketch(to_dev(rq["q_ids"], dev), to_dev(rq["q_off"], dev), n_rq)
+        hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_OPH_FULL, rqp, n_rq, planes, args.rows,
+                              out, cap, cnt, None, stream)
+        plan.check(stream)
+        n_r = int(cnt.item())
+        pairs_rq = out[:min(n_r, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1).copy()
+        del rqp
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         reps = 5
@@ -733,7 +769,7 @@ def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, n_launch
            "batched": {"value": nq * args.rows / (ms_b / 1e3), "unit": UNIT, "ms_per_batch": ms_b,
                        "queries": nq, "strategy": strategy_b, "accepted": n_b,
                        "hoph_speedup": hoph_value / (nq * args.rows / (ms_b / 1e3))}}
-    return leg, pairs_b
+    return leg, pairs_b, pairs_rq
 
 
 def serving_leg(args, planes, dev, oph_leg):
@@ -806,6 +842,10 @@ def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream
         hoph.oph_build_sketches16(plan.handle, dq_ids, dq_off, nq, q16, s)
         hoph.hoph_query_batch16(plan.handle, hoph.HOPH_MODE_HOPH, q16, nq, c16, args.rows, out,
                                 cap, cnt, None, s)
+    from paper_1805_11254_gb300 import autotune
+    hoph.oph_build_sketches16(plan.handle, dq_ids, dq_off, nq, q16, stream)
+    best, tune_ms = autotune.tune_query(plan, hoph.HOPH_MODE_HOPH, q16, nq, c16, args.rows, out,
+                                        cap, cnt, stream)
     for _ in range(3):
         step(stream)
     plan.check(stream)
@@ -845,12 +885,73 @@ def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream
     ach = alg / (filt / 1e3) / 1e9
     return {"value": nq * args.rows / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "same_pairs_as_uint32_planes": same, "plane_bytes": args.rows * K * 2,
+            "autotune": {"best": best, "ms_by_candidate": tune_ms},
             "roofline": {"bound": "hbm", "kernel": "filter_kernel (uint16 planes)",
                          "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": alg,
                          "kernel_ms_per_launch": filt},
             "how": "same collection and query sets; sketch values stored as 16-bit bin offsets "
                    "(empty = 0xFFFF); CUDA graph replays, CUDA events"}
+
+
+def self_join_leg(off, coll_seed, dev, stream, n_base=1_000_000, n_planted=1000, batch=1024,
+                  reps=3):
+    """All near-duplicate pairs inside one collection (hoph_self_join): the
+    first 10^6 rows of the query workload's collection plus 1,000 planted
+    near duplicates of random rows among them (J ~ U[0.6, 0.95]), (1:2)HOPH,
+    blocks of 1,024 rows as queries.  Reports pairs compared per second and
+    how many planted pairs with exact Jaccard >= T were found."""
+    import torch
+    from oracle import oracle_c as oc
+    from paper_1805_11254_gb300 import hoph, synth
+    rng = np.random.default_rng(PLANT_SEED + 7)
+    src = np.sort(rng.choice(n_base, n_planted, replace=False))
+    bases = [synth.counter_ids(coll_seed, int(off[r]), int(off[r + 1] - off[r]), D) for r in src]
+    planted, _ = synth.plant_near_duplicates(bases, D, 0.6, 0.95, PLANT_SEED + 8)
+    p_ids, p_off = synth.pack_sets(planted)
+    b_ids, b_off = synth.pack_sets([np.unique(b) for b in bases])
+    inter, uni = oc.jaccard_pairs(b_ids, b_off, p_ids, p_off, np.arange(n_planted),
+                                  np.arange(n_planted))
+    truly = inter * T[1] >= T[0] * uni
+    n = n_base + n_planted
+    with hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
+        n_ids = int(off[n_base])
+        d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+        hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
+        base_planes = plan.sketch(d_ids, to_dev(off[:n_base + 1], dev), n_base)
+        del d_ids
+        pl_planes = plan.sketch(to_dev(p_ids, dev), to_dev(p_off, dev), n_planted)
+        planes = torch.cat([base_planes, pl_planes], dim=1).contiguous()
+        del base_planes, pl_planes
+        plan.check()
+        cap = 1 << 20
+        out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        hoph.hoph_self_join(plan.handle, hoph.HOPH_MODE_HOPH, planes, n, batch, out, cap, cnt,
+                            None, stream)
+        plan.check(stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            hoph.hoph_self_join(plan.handle, hoph.HOPH_MODE_HOPH, planes, n, batch, out, cap,
+                                cnt, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.check(stream)
+        ms = e0.elapsed_time(e1) / reps
+        m = int(cnt.item())
+        pairs = out[:min(m, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+        del planes
+        torch.cuda.empty_cache()
+    found = {(int(p["query"]), int(p["row"])) for p in pairs}
+    want = {(int(src[i]), n_base + i) for i in range(n_planted) if truly[i]}
+    compared = n * (n - 1) // 2
+    return {"rows": n, "pairs_compared": compared, "ms": ms,
+            "value": compared / (ms / 1e3), "unit": UNIT, "accepted": m,
+            "planted_truly_similar": len(want), "planted_found": len(want & found),
+            "how": "hoph_self_join, blocks of %d rows as queries against the rows from the "
+                   "block on; (1:2)HOPH k=256 k'=64, T=0.7, eps=1e-4" % batch}
 
 
 SWEEP_T = ((1, 2), (3, 5), (7, 10), (4, 5), (9, 10))

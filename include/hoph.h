@@ -245,6 +245,26 @@ int hoph_query_batch16(hoph_plan *plan, uint32_t mode, const uint16_t *d_query_p
                        hoph_stats *d_stats, void *stream);
 
 /*
+ * All near-duplicate pairs inside one collection (Sec. 3.1 states the task
+ * over a single dataset: every pair of its items): every pair of rows
+ * (i, j), i < j, that the rule of `mode` accepts, as hoph_pair {query = i,
+ * row = j, groups, matches}, sorted by (i, j).
+ *   d_planes    uint32[G][n_rows][k'] sketches (as for hoph_query_batch).
+ *   batch       rows taken as queries per block (1..4096): block b compares
+ *               rows b*batch .. b*batch+batch-1 with rows b*batch .. n_rows-1,
+ *               so about n_rows^2 / 2 pairs are compared in all.
+ *   d_out, out_capacity, d_out_count, d_stats   as for hoph_query_batch (the
+ *               statistics count every pair a block compares, including
+ *               those with i >= j inside the block, which are never output).
+ * Modes GOPH, HOPH and OPH_FULL (not MinWise).  The plan owns a buffer for
+ * one block's query planes (G * batch * k' * 4 bytes; growing it
+ * synchronises the device).  n_rows < 2^32.
+ */
+int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int64_t n_rows,
+                   int64_t batch, hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
+                   hoph_stats *d_stats, void *stream);
+
+/*
  * oph_build_sketches without any device allocation.  The paper has no
  * counterpart: this serves callers that may not allocate device memory
  * during the call, such as a serving loop whose device memory is owned by

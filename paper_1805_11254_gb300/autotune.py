@@ -32,9 +32,11 @@ def _lanes(cand, W):
 def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
                stream=None, reps=3, candidates=None):
     """Pick the fastest execution setting for this batch shape; returns
-    (best setting, {setting index: ms})."""
+    (best setting, {setting index: ms}).  Compact (16-bit) planes go through
+    hoph_query_batch16."""
     import torch
-    key = (plan.handle, mode, n_queries, n_rows, plan.k, plan.kg)
+    call = hoph.hoph_query_batch16 if c_planes.element_size() == 2 else hoph.hoph_query_batch
+    key = (plan.handle, mode, n_queries, n_rows, plan.k, plan.kg, c_planes.element_size())
     if key in _cache:
         best = _cache[key]
         plan.set_exec(**best)
@@ -52,8 +54,8 @@ def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity,
             continue  # dense at large batches is tens of times slower; skip
         plan.set_exec(**cand)
         try:
-            hoph.hoph_query_batch(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out,
-                                  capacity, count, None, stream)
+            call(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
+                 None, stream)
         except hoph.HophError:
             continue  # setting not available for this shape
         stream.synchronize()
@@ -67,8 +69,8 @@ def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity,
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            hoph.hoph_query_batch(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out,
-                                  capacity, count, None, stream)
+            call(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
+                 None, stream)
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / reps

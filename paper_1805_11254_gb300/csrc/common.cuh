@@ -154,6 +154,7 @@ struct hoph_plan {
     uint32_t *d_key = nullptr;   // packed (bin << key_bits) | offset, D entries
     uint32_t key_bits = 0;
     uint64_t *d_lo = nullptr;    // k + 1 bounds (hash path)
+    uint64_t *d_kb = nullptr;    // k + 1 guarded join-key bases lo[w] + w + 1
     uint64_t hash_a = 0, hash_b = 0;
     uint32_t *d_minwise = nullptr;  // [D][minwise_k], psi_t(x) at x * mk + t
     // status word
@@ -162,6 +163,8 @@ struct hoph_plan {
     // scratch
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    void *d_aux = nullptr;      // hoph_self_join: one block's query planes
+    size_t aux_bytes = 0;
     hoph_exec exec{};
     // optional event timing of hoph_query_batch phases (bench / tooling)
     bool timing = false;

@@ -161,9 +161,11 @@ void plan_free(hoph_plan *pl) {
     for (int m = 0; m < 4; ++m) cudaFree(pl->d_table[m]);
     cudaFree(pl->d_key);
     cudaFree(pl->d_lo);
+    cudaFree(pl->d_kb);
     cudaFree(pl->d_minwise);
     cudaFree(pl->d_status);
     cudaFree(pl->d_scratch);
+    cudaFree(pl->d_aux);
     if (pl->h_status) cudaFreeHost(pl->h_status);
     delete pl;
 }
@@ -285,6 +287,12 @@ int plan_create(const hoph_params *params, const uint32_t *host_perm, hoph_plan 
     if (e == cudaSuccess)
         e = cudaMemcpy(pl->d_lo, pl->lo.data(), (p.k + 1) * sizeof(uint64_t),
                        cudaMemcpyHostToDevice);
+    // join keys with a guard key below every bin: kb[w] = lo[w] + w + 1
+    std::vector<uint64_t> kb(p.k + 1);
+    for (uint32_t w = 0; w <= p.k; ++w) kb[w] = pl->lo[w] + w + 1;
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_kb, (p.k + 1) * sizeof(uint64_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pl->d_kb, kb.data(), (p.k + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         plan_free(pl);
         return hoph_cuda_fail(e);

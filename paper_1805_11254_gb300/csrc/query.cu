@@ -79,6 +79,7 @@ struct PairArgs {
     DecideParams dp;      // rule for the later groups
     hoph_pair *out;
     int64_t cap;
+    int64_t self_off;  // >= 0: self-join block, keep row > query, both shifted by it
     unsigned long long *out_count;
     unsigned long long *stat;  // kStatWords counters
     int32_t *status;
@@ -130,6 +131,11 @@ __device__ __forceinline__ uint32_t table_find(const unsigned long long *tkey, u
 
 __device__ __forceinline__ void emit_pair(const PairArgs &a, uint32_t q, int64_t row, int groups,
                                           int matches) {
+    if (a.self_off >= 0) {  // one unordered pair per (i, j), i < j
+        if (row <= (int64_t)q) return;
+        q += (uint32_t)a.self_off;
+        row += a.self_off;
+    }
     const unsigned long long idx = atomicAdd(a.out_count, 1ull);
     if (idx < (unsigned long long)a.cap) {
         hoph_pair p;
@@ -285,50 +291,54 @@ __host__ __device__ inline DenseSmem dense_smem(const DenseArgs &a) {
     return L;
 }
 
-constexpr int kQCache = 8;  // query chunks kept in registers (W <= 256)
 
-// Every (query, row) pair of one tile; lanes over bins.  Consecutive pairs of
-// a warp share the query, whose values and empty masks stay in registers
-// (qv, qem of query cur_q) from one tile to the next.
-template <typename E>
+// Every (query, row) pair of one tile; lanes over bins.  NCH > 0: the W
+// scanned bins fit in NCH 32-bin chunks, and consecutive pairs of a warp
+// share the query, whose values and empty masks stay in registers (qv, qem
+// of query cur_q) from one tile to the next; NCH = 0: any W, nothing cached.
+template <typename E, int NCH>
 __device__ __forceinline__ void score_tile_dense(
     const PairArgs &a, int n_cons, const E *tile, int rows_here, int64_t row0,
     const int32_t *s_toff, const int64_t *s_qoff, const uint16_t *s_thr, Survivor *list,
     uint32_t *nsurv, unsigned long long *s_stats, int cw, unsigned long long &acc0,
-    uint32_t (&qv)[kQCache], uint32_t (&qem)[kQCache], int &cur_q) {
+    uint32_t (&qv)[NCH > 0 ? NCH : 1], uint32_t (&qem)[NCH > 0 ? NCH : 1], int &cur_q,
+    const int32_t (&toff)[NCH > 0 ? NCH : 1]) {
     const int lane = threadIdx.x & 31;
     const int nch = (a.W + 31) >> 5;
-    const bool cached = nch <= kQCache;
-    const int64_t n_pairs = (int64_t)rows_here * a.n_q;
-    for (int64_t p = cw; p < n_pairs; p += n_cons) {
-        const int q = (int)(p / rows_here);
-        const int rl = (int)(p - (int64_t)q * rows_here);
-        const E *qb = static_cast<const E *>(a.qry) + (int64_t)q * a.kg;
-        if (cached && q != cur_q) {
-            cur_q = q;
-#pragma unroll
-            for (int c = 0; c < kQCache; ++c) {
-                const int w = (c << 5) + lane;
-                const bool valid = c < nch && w < a.W;
-                qv[c] = valid ? (uint32_t)__ldg(qb + s_qoff[w]) : 0u;
-                qem[c] = __ballot_sync(0xFFFFFFFFu, valid && qv[c] == empty_of<E>());
-            }
+    constexpr bool cached = NCH > 0;
+    // the warp's pairs p = cw, cw + n_cons, ... of the tile in query-major
+    // order, as (q, rl) = (p / rows_here, p % rows_here) advanced by steps
+    int q = cw / rows_here, rl = cw - q * rows_here;
+    for (; q < a.n_q; rl += n_cons) {
+        while (rl >= rows_here) {
+            rl -= rows_here;
+            ++q;
         }
+        if (q >= a.n_q) break;
+        const E *qb = static_cast<const E *>(a.qry) + (int64_t)q * a.kg;
         int m = 0, both = 0, one = 0;
-        if (cached) {
+        if constexpr (cached) {
+            if (q != cur_q) {
+                cur_q = q;
 #pragma unroll
-            for (int c = 0; c < kQCache; ++c) {
-                if (c < nch) {
+                for (int c = 0; c < NCH; ++c) {
                     const int w = (c << 5) + lane;
                     const bool valid = w < a.W;
-                    const uint32_t rv = valid ? (uint32_t)tile[s_toff[w] + rl * a.kg] : 0u;
-                    const uint32_t rem =
-                        __ballot_sync(0xFFFFFFFFu, valid && rv == empty_of<E>());
-                    m += __popc(__ballot_sync(0xFFFFFFFFu,
-                                              valid && qv[c] != empty_of<E>() && rv == qv[c]));
-                    both += __popc(rem & qem[c]);
-                    one += __popc(rem ^ qem[c]);
+                    qv[c] = valid ? (uint32_t)__ldg(qb + s_qoff[w]) : 0u;
+                    qem[c] = __ballot_sync(0xFFFFFFFFu, valid && qv[c] == empty_of<E>());
                 }
+            }
+            const E *tr = tile + rl * a.kg;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const int w = (c << 5) + lane;
+                const bool valid = w < a.W;
+                const uint32_t rv = valid ? (uint32_t)tr[toff[c]] : 0u;
+                const uint32_t rem = __ballot_sync(0xFFFFFFFFu, valid && rv == empty_of<E>());
+                m += __popc(__ballot_sync(0xFFFFFFFFu,
+                                          valid && qv[c] != empty_of<E>() && rv == qv[c]));
+                both += __popc(rem & qem[c]);
+                one += __popc(rem ^ qem[c]);
             }
         } else {
             for (int c = 0; c < nch; ++c) {
@@ -358,9 +368,12 @@ __device__ __forceinline__ void score_tile_dense(
     }
 }
 
-template <typename E>
-__global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_constant__ DenseArgs a,
-                                                             const __grid_constant__ CUtensorMap map) {
+// 17 warps (16 consumers + the producer) x 112 registers fit one SM's
+// register file; the 8-chunk query cache needs about that many.
+template <typename E, int NCH>
+__global__ void __maxnreg__(112) dense_scan_kernel(const __grid_constant__ DenseArgs a,
+                                                   const __grid_constant__ CUtensorMap map) {
+    constexpr int NQ = NCH > 0 ? NCH : 1;
     extern __shared__ __align__(1024) unsigned char smem[];
     const DenseSmem L = dense_smem(a);
     const PairArgs &P = a.p;
@@ -406,8 +419,14 @@ __global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_consta
     Survivor *list = s_surv + cw * kSurvCap;
     uint32_t *nsurv = s_nsurv + cw;
     unsigned long long acc0 = 0;
-    uint32_t qv[kQCache], qem[kQCache];  // the warp's current query (cached path)
+    uint32_t qv[NQ], qem[NQ];  // the warp's current query (cached path)
     int cur_q = -1;
+    int32_t toff[NQ];  // tile offsets of this lane's bins (cached path)
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+        const int w = (c << 5) + lane;
+        toff[c] = w < P.W ? s_toff[w] : 0;
+    }
     int s = 0;        // stage of the current tile
     uint32_t ph = 0;  // its mbarrier phase
     bool ok = true;
@@ -433,8 +452,8 @@ __global__ void __launch_bounds__(32 * 17) dense_scan_kernel(const __grid_consta
             }
             named_bar_sync(1, a.n_cons * 32);
         }
-        score_tile_dense<E>(P, a.n_cons, tp, rows_here, row0, s_toff, s_qoff, s_thr, list, nsurv,
-                            s_stats, cw, acc0, qv, qem, cur_q);
+        score_tile_dense<E, NCH>(P, a.n_cons, tp, rows_here, row0, s_toff, s_qoff, s_thr, list, nsurv,
+                            s_stats, cw, acc0, qv, qem, cur_q, toff);
         __syncwarp();
         if (a.use_tma) {
             if (lane == 0) mbar_arrive(empty + s);
@@ -461,7 +480,7 @@ struct IndexArgs {
     int32_t n_q, kg, W, mask_words;
     const uint64_t *binbase;  // key = lo[w] + value
     uint32_t *counts;    // [slots + 1]: queries per key slot
-    uint32_t *gmap;      // per 16 map slots: bit j = an even query has slot j, bit 16 + j = an odd one
+    uint32_t *gmap;      // per 16 map slots: an even / an odd query has slot j (bits j, 16 + j; swapped in odd words)
     int32_t map_hashed;  // map slot = mix32(key) & map_mask, else the key itself
     uint32_t map_mask;
     int32_t csr_hashed;  // key slot from the key table, else the key itself
@@ -496,7 +515,11 @@ __global__ void join_count_kernel(const IndexArgs a) {
         if (valid && !e) {
             const uint32_t key = (uint32_t)a.binbase[w] + v;
             const uint32_t mi = a.map_hashed ? (mix32(key) & a.map_mask) : key;
-            atomicOr(a.gmap + (mi >> 4), 1u << ((mi & 15u) + (((uint32_t)q & 1u) << 4)));
+            // slot j of word mi >> 4: even-query bit at j and odd-query bit at
+            // 16 + j, the halves swapped in odd words, so a right rotation of
+            // the word by (mi & 31) brings the even bit to 0 and the odd to 16
+            const uint32_t word = mi >> 4;
+            atomicOr(a.gmap + word, 1u << ((mi & 15u) + ((((uint32_t)q ^ word) & 1u) << 4)));
             const uint32_t slot = a.csr_hashed ? table_insert(a.tkey, a.tmask, key) : key;
             if (slot == kNoSlot) hoph_flag(a.status, HOPH_ERR_CAPACITY);
             else atomicAdd(a.counts + slot, 1u);
@@ -730,8 +753,11 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
                     const bool full_bin = x[e] != empty_of<E>();
                     const uint32_t key = kb[c * VPC + e] + x[e];
                     uint32_t mi = HASHED ? (mix32(key) & a.map_mask) : key;
-                    mi = full_bin ? mi : zero_slot;
-                    hits += (s_gmap[mi >> 4] >> (mi & 15u)) & 0x10001u;
+                    // direct map, uint32 values: the empty marker lands on the
+                    // bin's guard key (base - 1), which no query sets
+                    if (HASHED || sizeof(E) != 4) mi = full_bin ? mi : zero_slot;
+                    const uint32_t w = s_gmap[mi >> 4];
+                    hits += __funnelshift_r(w, w, mi) & 0x10001u;
                     ne += full_bin;
                 }
             }
@@ -1299,12 +1325,17 @@ struct Bump {
     }
 };
 
-// hoph_query_batch / hoph_query_batch16 over planes of element type E
+// hoph_query_batch / hoph_query_batch16 over planes of element type E, and
+// one block of hoph_self_join: collection planes cstride elements apart
+// (n_rows * k' when negative); self_off >= 0 keeps only row > query and
+// shifts both by self_off; `first` zeroes the output count, `last` sorts the
+// output.
 template <typename E>
 int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, int64_t n_queries,
                      const E *d_coll_planes, int64_t n_rows, hoph_pair *d_out,
                      int64_t out_capacity, int64_t *d_out_count, hoph_stats *d_stats,
-                     void *stream) {
+                     void *stream, int64_t cstride_in = -1, int64_t self_off = -1,
+                     bool first = true, bool last = true) {
     constexpr int ES = (int)sizeof(E);
     if (!plan || !d_out_count || n_queries < 0 || n_rows < 0 || out_capacity < 0)
         return HOPH_ERR_PARAM;
@@ -1347,7 +1378,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     const int W = Gs * kg;
     if (W > kMaxW) return HOPH_ERR_UNSUPPORTED;
 
-    HOPH_CUDA_TRY(cudaMemsetAsync(d_out_count, 0, sizeof(int64_t), s));
+    if (first) HOPH_CUDA_TRY(cudaMemsetAsync(d_out_count, 0, sizeof(int64_t), s));
     if (n_queries == 0 || n_rows == 0) return HOPH_OK;
     if (!d_query_planes || !d_coll_planes) return HOPH_ERR_PARAM;
 
@@ -1377,8 +1408,12 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     // group map is indexed by key (no false hits); beyond, by a hash into
     // kHashedMapSlots slots (false hits only loosen the filter).  Up to
     // kMaxJoinKeys keys the CSR is indexed by key; beyond, through a key table.
-    const uint64_t keys = mode == HOPH_MODE_MINWISE_FULL ? ~0ull : plan->lo[W];
-    const bool map_hashed = keys > kDirectMap;
+    // A small key space takes the guarded keys lo[w] + w + 1 + value (a key
+    // below every bin that no value reaches; the empty marker wraps onto it).
+    const uint64_t plain_keys = mode == HOPH_MODE_MINWISE_FULL ? ~0ull : plan->lo[W];
+    const bool map_hashed = plain_keys > kDirectMap - W - 1;
+    const uint64_t keys = map_hashed ? plain_keys : plain_keys + W + 1;
+    const uint64_t *binbase = map_hashed ? plan->d_lo : plan->d_kb;
     const uint64_t map_slots = map_hashed ? kHashedMapSlots : keys;
     const bool csr_hashed = keys > kMaxJoinKeys;
     uint64_t csr_slots = keys;
@@ -1397,7 +1432,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
 
     const int mask_words = (W + 31) / 32;
     const int64_t qstride = n_queries * (int64_t)kg;
-    const int64_t cstride = n_rows * (int64_t)kg;
+    const int64_t cstride = cstride_in >= 0 ? cstride_in : n_rows * (int64_t)kg;
 
     // scratch
     Bump bump{nullptr};
@@ -1466,6 +1501,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     pa.dp = dp;
     pa.out = d_out;
     pa.cap = out_capacity;
+    pa.self_off = self_off;
     pa.out_count = reinterpret_cast<unsigned long long *>(d_out_count);
     pa.stat = st;
     pa.status = plan->d_status;
@@ -1483,7 +1519,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ia.kg = kg;
         ia.W = W;
         ia.mask_words = mask_words;
-        ia.binbase = plan->d_lo;
+        ia.binbase = binbase;
         ia.counts = counts;
         ia.gmap = gmap;
         ia.map_hashed = map_hashed;
@@ -1520,7 +1556,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         fa.gmap = gmap;
         fa.gmap_words = (uint32_t)(map_slots / 16 + 2);  // + a zero word for empty bins
         fa.map_mask = (uint32_t)(map_slots - 1);
-        fa.binbase = plan->d_lo;
+        fa.binbase = binbase;
         fa.row_min = pa.thr + 2 * (W + 1);
         const int K0 = hoph_effective(fp.rule, W, W, 0);
         fa.keep_empty = table_decide(tab.data(), W, 0, K0) != HOPH_REJECT;
@@ -1571,7 +1607,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ca.p = pa;
         ca.cand = cand;
         ca.n_cand = n_cand;
-        ca.binbase = plan->d_lo;
+        ca.binbase = binbase;
         ca.csr_hashed = csr_hashed;
         ca.tkey = tkey;
         ca.tmask = (uint32_t)(csr_slots - 1);
@@ -1617,7 +1653,12 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         }
         const DenseSmem DL = dense_smem(da);
         if (DL.total > (uint32_t)kSmemLimit) return HOPH_ERR_UNSUPPORTED;
-        auto dense = dense_scan_kernel<E>;
+        const int nch = (W + 31) / 32;
+        auto dense = nch <= 1   ? dense_scan_kernel<E, 1>
+                     : nch <= 2 ? dense_scan_kernel<E, 2>
+                     : nch <= 4 ? dense_scan_kernel<E, 4>
+                     : nch <= 8 ? dense_scan_kernel<E, 8>
+                                : dense_scan_kernel<E, 0>;
         HOPH_CUDA_TRY(hoph_ensure_smem((const void *)dense, (int)DL.total));
         const int threads = 32 * (n_cons + 1);
         int per_sm = 0;
@@ -1634,15 +1675,17 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         launches += 1;
     }
 
-    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
-    sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(d_out, pa.out_count, out_capacity,
-                                                              sortA, sortB, plan->d_status);
+    if (last) {
+        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
+        sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(d_out, pa.out_count, out_capacity,
+                                                                  sortA, sortB, plan->d_status);
+    }
     const int64_t fp_bytes = (n_rows * (int64_t)W + n_queries * (int64_t)W) * ES;
     stats_fold_kernel<<<1, 32, 0, s>>>(st, n_cand, n_queries * n_rows, G, Gs, fp_bytes, strategy,
                                        d_stats);
     HOPH_CUDA_TRY(cudaGetLastError());
     hoph_timing_mark(plan, 4, s);
-    plan->launches += launches + 2;
+    plan->launches += launches + (last ? 2 : 1);
     return HOPH_OK;
 }
 
@@ -1664,6 +1707,48 @@ int hoph_query_batch16(hoph_plan *plan, uint32_t mode, const uint16_t *d_query_p
                        hoph_stats *d_stats, void *stream) {
     return query_batch_impl<uint16_t>(plan, mode, d_query_planes, n_queries, d_coll_planes,
                                       n_rows, d_out, out_capacity, d_out_count, d_stats, stream);
+}
+
+int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int64_t n_rows,
+                   int64_t batch, hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
+                   hoph_stats *d_stats, void *stream) {
+    if (!plan || !d_out_count || n_rows < 0 || batch < 1 || batch > 4096 || out_capacity < 0)
+        return HOPH_ERR_PARAM;
+    if (out_capacity > 0 && !d_out) return HOPH_ERR_PARAM;
+    if (mode == HOPH_MODE_MINWISE_FULL) return HOPH_ERR_UNSUPPORTED;
+    if (n_rows >= (1ll << 32)) return HOPH_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    HOPH_CUDA_TRY(cudaMemsetAsync(d_out_count, 0, sizeof(int64_t), s));
+    if (n_rows < 2) return HOPH_OK;
+    if (!d_planes) return HOPH_ERR_PARAM;
+    const int64_t kg = plan->P.k_group, G = plan->G;
+    // the block's query planes, gathered contiguous ([G][nb][k'])
+    const size_t qbytes = (size_t)G * std::min(batch, n_rows) * kg * sizeof(uint32_t);
+    if (qbytes > plan->aux_bytes) {
+        if (plan->d_aux) {
+            HOPH_CUDA_TRY(cudaDeviceSynchronize());
+            HOPH_CUDA_TRY(cudaFree(plan->d_aux));
+            plan->d_aux = nullptr;
+            plan->aux_bytes = 0;
+        }
+        HOPH_CUDA_TRY(cudaMalloc(&plan->d_aux, qbytes));
+        plan->aux_bytes = qbytes;
+    }
+    uint32_t *q = static_cast<uint32_t *>(plan->d_aux);
+    const int64_t cstride = n_rows * kg;
+    for (int64_t q0 = 0; q0 < n_rows - 1; q0 += batch) {
+        const int64_t nb = std::min(batch, n_rows - 1 - q0);
+        HOPH_CUDA_TRY(cudaMemcpy2DAsync(q, (size_t)nb * kg * 4, d_planes + q0 * kg,
+                                        (size_t)cstride * 4, (size_t)nb * kg * 4, (size_t)G,
+                                        cudaMemcpyDeviceToDevice, s));
+        // rows q0 .. n_rows-1 against queries q0 .. q0+nb-1
+        const bool last = q0 + batch >= n_rows - 1;
+        const int rc = query_batch_impl<uint32_t>(plan, mode, q, nb, d_planes + q0 * kg,
+                                                  n_rows - q0, d_out, out_capacity, d_out_count,
+                                                  d_stats, stream, cstride, q0, false, last);
+        if (rc != HOPH_OK) return rc;
+    }
+    return HOPH_OK;
 }
 
 int hoph_check_bounded_wait(hoph_plan *plan, uint64_t limit_ns, void *stream) {

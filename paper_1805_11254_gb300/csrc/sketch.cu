@@ -1,9 +1,10 @@
 // Sketch construction on the GPU.
 //
-//  * oph_build_sketches: OPH / HOPH sketches (Sec. 3.2, Sec. 4.1).  One warp
-//    owns one set.  Sets are visited in descending size order (a counting
-//    sort by size bucket builds the work list) and striped across all
-//    resident warps of one persistent launch.  IDs are read with 128-bit
+//  * oph_build_sketches: OPH / HOPH sketches (Sec. 3.2, Sec. 4.1).  Sets are
+//    visited in descending size order (a counting sort by size bucket builds
+//    the work list); in one persistent launch the sets of >= 2048 IDs get a
+//    whole CTA each and the others one warp each, striped across all
+//    resident warps.  IDs are read with 128-bit
 //    loads; each ID is mapped through the packed psi table (psi value ->
 //    bin and offset) that stays resident in L2, and the per-bin minimum is
 //    kept in the warp's shared-memory sketch with a read-then-atomicMin.
@@ -24,6 +25,7 @@ constexpr int kSketchThreads = 256;
 constexpr int kSketchWarps = kSketchThreads / 32;
 constexpr int kBuckets = 65;
 constexpr int kBigBucket = 12;  // sets of >= 2048 IDs (bit length >= 12) get a whole CTA
+constexpr int64_t kSplitPhases = 16384;  // from this many sets: one launch per phase
 
 // Hash path: psi-space regions of equal-width bins (the whole space for equal
 // bins, one per group for a:b); a value's bin is first + floor(o * nb / z).
@@ -52,6 +54,7 @@ struct SketchArgs {
     const int32_t *order;  // size-sorted set indices, or nullptr for 0..n-1
     const uint32_t *n_big; // items [0, *n_big) of order are sketched a CTA per set
     RegionTable reg;       // hash path: bin regions
+    int32_t phases;        // oph_sketch_kernel: bit 0 large sets, bit 1 the rest
     int32_t generate;      // IDs come from the counter generator, not from ids[]
     uint64_t gen_seed;     // generator stream; set i's IDs are elements off[i]..off[i+1]-1
     uint64_t gen_D;        // generated IDs are uniform over 0..gen_D-1
@@ -199,26 +202,47 @@ __device__ __forceinline__ void store_sketch(const SketchArgs &a, uint32_t *sk, 
     }
 }
 
-// Warp per set over work-list items [first, n_sets), first = *n_big (the
-// large sets handled by oph_sketch_big_kernel) or 0.
+// The work list in two phases (both in one launch for small batches, one
+// launch each for large ones; a.phases says which).  Phase 1: the large sets
+// at its head (items [0, *n_big)), a CTA per set, all warps feeding one
+// shared sketch.  Phase 2: warp per set over the rest, strided so that the
+// CTAs that took a large set get the smallest of the remaining sets.
+// Without a work list (a.n_big null) only phase 2 runs, in input order.
 template <bool HASH>
-__global__ void __launch_bounds__(kSketchThreads) oph_sketch_kernel(const SketchArgs a) {
+__global__ void __launch_bounds__(kSketchThreads, 6) oph_sketch_kernel(const SketchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *s_lo = reinterpret_cast<uint64_t *>(smem_raw);  // HASH only
     uint32_t *s_sk = reinterpret_cast<uint32_t *>(smem_raw + (HASH ? (a.k + 1) * 8 : 0));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *sk = s_sk + (size_t)warp * a.k;
     __shared__ RegionTable s_reg;
     if (HASH) {
         for (uint32_t i = threadIdx.x; i <= a.k; i += blockDim.x) s_lo[i] = a.lo[i];
         if (threadIdx.x == 0) s_reg = a.reg;
     }
-    for (uint32_t i = lane; i < a.k; i += 32) sk[i] = HOPH_EMPTY_VALUE;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kSketchWarps * a.k; i += blockDim.x)
+        s_sk[i] = HOPH_EMPTY_VALUE;
     __syncthreads();
     bool bad = false;
-    const int64_t first = a.n_big ? (int64_t)*a.n_big : 0;
+    const int64_t n_big = a.n_big ? (int64_t)*a.n_big : 0;
+    // phase 1 (warp 0's sketch region serves the CTA; store_sketch resets it)
+    for (int64_t item = (a.phases & 1) ? blockIdx.x : n_big; item < n_big; item += gridDim.x) {
+        const int64_t set = a.order[item];
+        const int64_t beg = a.off[set], end = a.off[set + 1];
+        if (a.generate)
+            sketch_generated<HASH>(a, s_lo, &s_reg, s_sk, (uint64_t)beg, end - beg, threadIdx.x,
+                                   blockDim.x, bad);
+        else
+            sketch_ids<HASH>(a, s_lo, &s_reg, s_sk, a.ids + beg, end - beg, threadIdx.x,
+                             blockDim.x, bad);
+        __syncthreads();
+        store_sketch(a, s_sk, set, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    // phase 2
+    uint32_t *sk = s_sk + (size_t)warp * a.k;
     const int64_t warps_total = (int64_t)gridDim.x * kSketchWarps;
-    for (int64_t item = first + (int64_t)blockIdx.x * kSketchWarps + warp; item < a.n_sets;
+    const int64_t slot = (int64_t)(gridDim.x - 1 - blockIdx.x) * kSketchWarps + warp;
+    for (int64_t item = (a.phases & 2) ? n_big + slot : a.n_sets; item < a.n_sets;
          item += warps_total) {
         const int64_t set = a.order ? a.order[item] : item;
         const int64_t beg = a.off[set], end = a.off[set + 1];
@@ -229,38 +253,6 @@ __global__ void __launch_bounds__(kSketchThreads) oph_sketch_kernel(const Sketch
         __syncwarp();
         store_sketch(a, sk, set, lane, 32);
         __syncwarp();
-    }
-    if (bad) hoph_flag(a.status, HOPH_ERR_ID_RANGE);
-}
-
-// CTA per set for the large sets at the head of the size-sorted work list
-// (items [0, *n_big)): all warps feed one shared sketch.
-template <bool HASH>
-__global__ void __launch_bounds__(kSketchThreads) oph_sketch_big_kernel(const SketchArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *s_lo = reinterpret_cast<uint64_t *>(smem_raw);  // HASH only
-    uint32_t *sk = reinterpret_cast<uint32_t *>(smem_raw + (HASH ? (a.k + 1) * 8 : 0));
-    __shared__ RegionTable s_reg;
-    if (HASH) {
-        for (uint32_t i = threadIdx.x; i <= a.k; i += blockDim.x) s_lo[i] = a.lo[i];
-        if (threadIdx.x == 0) s_reg = a.reg;
-    }
-    for (uint32_t i = threadIdx.x; i < a.k; i += blockDim.x) sk[i] = HOPH_EMPTY_VALUE;
-    __syncthreads();
-    bool bad = false;
-    const int64_t n_big = (int64_t)*a.n_big;
-    for (int64_t item = blockIdx.x; item < n_big; item += gridDim.x) {
-        const int64_t set = a.order[item];
-        const int64_t beg = a.off[set], end = a.off[set + 1];
-        if (a.generate)
-            sketch_generated<HASH>(a, s_lo, &s_reg, sk, (uint64_t)beg, end - beg, threadIdx.x,
-                                   blockDim.x, bad);
-        else
-            sketch_ids<HASH>(a, s_lo, &s_reg, sk, a.ids + beg, end - beg, threadIdx.x, blockDim.x,
-                             bad);
-        __syncthreads();
-        store_sketch(a, sk, set, threadIdx.x, blockDim.x);
-        __syncthreads();
     }
     if (bad) hoph_flag(a.status, HOPH_ERR_ID_RANGE);
 }
@@ -383,6 +375,7 @@ SketchArgs sketch_args(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_
     a.n_sets = n_sets;
     a.planes = d_planes;
     a.compact = 0;
+    a.phases = 3;
     a.plane_stride = n_sets * (int64_t)P.k_group;
     a.k = P.k;
     a.kg = P.k_group;
@@ -433,34 +426,30 @@ int build_work_list(hoph_plan *plan, const int64_t *d_offsets, int64_t n_sets, u
     return HOPH_OK;
 }
 
-// The large-set (CTA per set) and warp-per-set kernels over the work list.
+// The sketch kernel over the work list (or the input order).
 template <bool HASH>
 int launch_sketch_kernels(hoph_plan *plan, const SketchArgs &a, cudaStream_t s) {
     const uint32_t k = a.k;
     const size_t lo_b = HASH ? (size_t)(k + 1) * 8 : 0;
-    const size_t smem_w = lo_b + (size_t)kSketchWarps * k * 4;
-    const size_t smem_b = lo_b + (size_t)k * 4;
-    if (a.n_big) {
-        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)oph_sketch_big_kernel<HASH>, (int)smem_b));
-        int per = 0;
-        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per, oph_sketch_big_kernel<HASH>, kSketchThreads, smem_b));
-        if (per < 1) return HOPH_ERR_UNSUPPORTED;
-        const int64_t blocks = std::min<int64_t>(a.n_sets, (int64_t)grid_for(plan, per));
-        oph_sketch_big_kernel<HASH><<<(unsigned)blocks, kSketchThreads, smem_b, s>>>(a);
-        HOPH_CUDA_TRY(cudaGetLastError());
-        plan->launches += 1;
-    }
-    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)oph_sketch_kernel<HASH>, (int)smem_w));
+    const size_t smem = lo_b + (size_t)kSketchWarps * k * 4;
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)oph_sketch_kernel<HASH>, (int)smem));
     int per = 0;
     HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oph_sketch_kernel<HASH>,
-                                                                kSketchThreads, smem_w));
+                                                                kSketchThreads, smem));
     if (per < 1) return HOPH_ERR_UNSUPPORTED;
     const int64_t blocks = std::min<int64_t>((a.n_sets + kSketchWarps - 1) / kSketchWarps,
                                              (int64_t)grid_for(plan, per));
-    oph_sketch_kernel<HASH><<<(unsigned)blocks, kSketchThreads, smem_w, s>>>(a);
-    HOPH_CUDA_TRY(cudaGetLastError());
-    plan->launches += 1;
+    // a large batch keeps the phases apart: one launch of the large sets
+    // with the whole GPU, then one of the rest
+    const bool split = a.n_big && a.n_sets >= kSplitPhases;
+    const int phases[2] = {split ? 1 : 3, 2};
+    for (int i = 0; i < (split ? 2 : 1); ++i) {
+        SketchArgs b = a;
+        b.phases = phases[i];
+        oph_sketch_kernel<HASH><<<(unsigned)blocks, kSketchThreads, smem, s>>>(b);
+        HOPH_CUDA_TRY(cudaGetLastError());
+        plan->launches += 1;
+    }
     return HOPH_OK;
 }
 

@@ -101,7 +101,7 @@ _EXPORTS = ["hoph_plan_create", "hoph_plan_create_with_perm", "hoph_plan_destroy
             "hoph_sync_status", "hoph_status_string", "hoph_plan_enable_timing",
             "hoph_plan_read_timing", "oph_build_sketches_static", "hoph_plan_peek_timing",
             "hoph_check_bounded_wait", "hoph_synth_sketch", "oph_build_sketches16",
-            "hoph_query_batch16"]
+            "hoph_query_batch16", "hoph_self_join"]
 
 
 def load(path=LIB_PATH):
@@ -133,6 +133,8 @@ def load(path=LIB_PATH):
     lib.minwise_build_sketches.restype = i32
     lib.hoph_query_batch.argtypes = [P, u32, P, i64, P, i64, P, i64, P, P, P]
     lib.hoph_query_batch.restype = i32
+    lib.hoph_self_join.argtypes = [P, u32, P, i64, i64, P, i64, P, P, P]
+    lib.hoph_self_join.restype = i32
     lib.oph_build_sketches16.argtypes = [P, P, P, i64, P, P]
     lib.oph_build_sketches16.restype = i32
     lib.hoph_query_batch16.argtypes = [P, u32, P, i64, P, i64, P, i64, P, P, P]
@@ -252,6 +254,14 @@ def hoph_query_batch(plan, mode, d_query_planes, n_queries, d_coll_planes, n_row
                                           int(n_queries), _ptr(d_coll_planes), int(n_rows),
                                           _ptr(d_out), int(out_capacity), _ptr(d_out_count),
                                           _ptr(d_stats), _stream(stream)), "hoph_query_batch")
+
+
+def hoph_self_join(plan, mode, d_planes, n_rows, batch, d_out, out_capacity, d_out_count,
+                   d_stats=None, stream=None):
+    return _check(load().hoph_self_join(plan, MODES.get(mode, mode), _ptr(d_planes), int(n_rows),
+                                        int(batch), _ptr(d_out), int(out_capacity),
+                                        _ptr(d_out_count), _ptr(d_stats), _stream(stream)),
+                  "hoph_self_join")
 
 
 def oph_build_sketches16(plan, d_ids, d_offsets, n_sets, d_planes, stream=None):

@@ -354,3 +354,35 @@ def test_compact_planes_give_the_same_pairs(small, mode, ab, kg, strategy):
             assert st.accepted[g] == hist[g + 1][1] and st.rejected[g] == hist[g + 1][2]
         if strategy >= 0:
             assert st.strategy == strategy
+
+
+@pytest.mark.parametrize("batch", [777, 4096])
+@pytest.mark.parametrize("mode,ab,kg", [("hoph", (1, 2), 64), ("goph", (0, 0), 32),
+                                        ("oph_full", (0, 0), 64)])
+def test_self_join_is_the_upper_triangle_of_the_all_pairs_query(small, mode, ab, kg, batch):
+    """hoph_self_join over the 5,000 sets plus the 50 planted near duplicates
+    appended as rows: exactly the oracle's accepted pairs (i, j) with i < j
+    of the all-pairs comparison, in (i, j) order; ragged last block."""
+    dev = device()
+    D, k = small["D"], 128
+    ids = np.concatenate([small["ids"], small["q_ids"]])
+    off = np.concatenate([small["off"], small["off"][-1] + small["q_off"][1:]])
+    n = len(off) - 1
+    with hoph.Plan(D, k, kg, *ab, seed=1, thr=T, epsilon=EPS) as plan:
+        c = plan.sketch(to_dev(ids, dev), to_dev(off, dev), n)
+        plan.check()
+        rows = planes_to_rows(c)
+        z = [plan.info.group_size[g] for g in range(plan.G)]
+        want = _oracle_query(mode, rows, rows, kg, z)["accepted"]
+        want = want[want[:, 0] < want[:, 1]]
+        cap = 1 << 14
+        out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        hoph.hoph_self_join(plan.handle, mode, c, n, batch, out, cap, cnt)
+        plan.check()
+        m = int(cnt.item())
+        got = out[:m].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+    assert len(want) > 5  # the planted pairs at J >= T
+    assert m == len(want)
+    assert [(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"])) for p in got] \
+        == [tuple(int(x) for x in w) for w in want]
