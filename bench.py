@@ -657,15 +657,12 @@ def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
                          "algorithmic_bytes_per_launch": bytes_}}
 
 
-# the dense-scan knobs the one-query OPH baseline tunes to (16 consumer warps,
-# 2 stages of 64-row tiles), for its ncu profile
-OPH1_EXEC = dict(strategy=0, consumer_warps=16, stages=2, tile_rows=64)
-
-
 def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
-    """A few one-query OPH full-scan launches (dense scan) for ncu."""
+    """One-query OPH full-scan launches (dense scan) for ncu: the knobs are
+    tuned first as in the baseline leg, then the profiled launches run inside
+    the NVTX range "oph1"."""
     import torch
-    from paper_1805_11254_gb300 import hoph
+    from paper_1805_11254_gb300 import autotune, hoph
     n_ids = int(off[-1])
     qw = query_sets(8, off, coll_seed)
     with hoph.Plan(D, K, K, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
@@ -675,13 +672,20 @@ def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
         del d_ids
         q = plan.sketch(to_dev(qw["q_ids"], dev), to_dev(qw["q_off"], dev), 8)
         plan.check()
-        plan.set_exec(**OPH1_EXEC)
         cap = 1 << 12
         out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-        for i in range(launches):
-            hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_OPH_FULL, q[:, i:i + 1].contiguous(),
-                                  1, planes, args.rows, out, cap, cnt, None, stream)
+        qs = [q[:, i:i + 1].contiguous() for i in range(launches)]
+        best, _ = autotune.tune_query(plan, hoph.HOPH_MODE_OPH_FULL, qs[0], 1, planes, args.rows,
+                                      out, cap, cnt, stream, candidates=autotune.DENSE_CANDIDATES)
+        print(json.dumps({"tuned": best}), flush=True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("oph1")
+        for qp in qs:
+            hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_OPH_FULL, qp, 1, planes, args.rows,
+                                  out, cap, cnt, None, stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         plan.check()
 
 

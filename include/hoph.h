@@ -141,7 +141,7 @@ typedef struct {
 typedef struct {
     int32_t strategy;        /* -1 auto, 0 dense, 1 value join            */
     int32_t tile_rows;       /* rows per shared-memory tile               */
-    int32_t consumer_warps;  /* scoring warps per CTA (dense <= 16, join filter <= 31) */
+    int32_t consumer_warps;  /* scoring warps per CTA (dense <= 15, join filter <= 31) */
     int32_t ctas_per_sm;     /* resident CTAs per SM for the scan         */
     int32_t stages;          /* TMA pipeline depth                        */
     int32_t lanes_per_row;   /* join filter: lanes sharing one row (1-8)  */

@@ -17,8 +17,8 @@ JOIN_CANDIDATES = [dict(strategy=1, lanes_per_row=l, consumer_warps=c, stages=s)
                    for l, c, s in ((0, 16, 2), (0, 12, 2), (0, 8, 3), (0, 16, 3), (-2, 16, 2),
                                    (-2, 16, 3), (-2, 16, 4), (-2, 31, 2), (-2, 24, 2))]
 DENSE_CANDIDATES = [dict(strategy=0, consumer_warps=c, stages=s, tile_rows=r)
-                    for c, s, r in ((8, 4, 0), (16, 4, 0), (8, 6, 0), (4, 4, 0), (16, 2, 64),
-                                    (8, 4, 32), (16, 3, 32), (8, 2, 64))]
+                    for c, s, r in ((8, 4, 0), (15, 4, 0), (8, 6, 0), (4, 4, 0), (15, 2, 64),
+                                    (8, 4, 32), (15, 3, 32), (8, 2, 64), (4, 8, 16), (6, 4, 32))]
 
 
 def _lanes(cand, W):

@@ -191,6 +191,10 @@ void hoph_timing_mark(hoph_plan *plan, int which, cudaStream_t s);
 // while a stream is being captured issue no attribute change once warm.
 cudaError_t hoph_ensure_smem(const void *func, int bytes);
 
+// cudaOccupancyMaxActiveBlocksPerMultiprocessor, remembered per (kernel,
+// device, block size, dynamic shared memory): host time off the launch path
+cudaError_t hoph_occupancy(int *blocks, const void *func, int threads, size_t smem);
+
 // grow-only scratch owned by the plan; returns nullptr on failure
 void *hoph_scratch(hoph_plan *plan, size_t bytes);
 

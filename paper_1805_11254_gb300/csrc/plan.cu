@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -316,6 +317,28 @@ cudaError_t hoph_ensure_smem(const void *func, int bytes) {
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) cur = bytes;
     return e;
+}
+
+cudaError_t hoph_occupancy(int *blocks, const void *func, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int, size_t>, int> known;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const auto key = std::make_tuple(func, dev, threads, smem);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = known.find(key);
+        if (it != known.end()) {
+            *blocks = it->second;
+            return cudaSuccess;
+        }
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, func, threads, smem);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    known[key] = *blocks;
+    return cudaSuccess;
 }
 
 void *hoph_scratch(hoph_plan *plan, size_t bytes) {

@@ -11,9 +11,10 @@
 //          queries, ALU-bound for large batches.
 // join   - an exact value join for large batches, in three parts:
 //          (1) an index of the batch's first-group query values over the
-//              keys lo[bin] + value (the value's position in psi-space): CSR
-//              lists of queries per key, and a 2-bit map recording whether an
-//              even- and whether an odd-numbered query has the key;
+//              keys lo[bin] + value (the value's position in psi-space): a
+//              linked list of the queries of every key (one kernel, no
+//              scan), and a 2-bit map recording whether an even- and whether
+//              an odd-numbered query has the key;
 //          (2) a streaming filter: TMA tiles of the first plane, a few lanes
 //              per row, every row value looked up in the map in shared
 //              memory.  A pair's match count is at most the row's number of
@@ -24,7 +25,7 @@
 //              every query; the other rows are compacted into a candidate
 //              list;
 //          (3) a counting kernel over the candidates: per-query match counts
-//              from the CSR lists in per-warp shared-memory counters, then the
+//              from the key lists in per-warp shared-memory counters, then the
 //              exact first-group decision for each query the row met.
 //          It needs "no match => reject" for every possible denominator,
 //          checked on the host when the strategy is chosen.
@@ -46,7 +47,7 @@ namespace {
 constexpr int kSurvCap = 32;  // per-warp survivor list (one entry per lane)
 constexpr int kMaxW = 1024;   // scanned bins per row
 constexpr int kStatWords = 3 * HOPH_MAX_GROUPS + 4;
-constexpr uint64_t kMaxJoinKeys = 1ull << 23;  // key space indexed directly by the CSR
+constexpr uint64_t kMaxJoinKeys = 1ull << 23;  // key space indexing the list heads directly
 constexpr uint64_t kDirectMap = 1ull << 19;    // key space indexed directly by the group map
 constexpr uint64_t kHashedMapSlots = 1ull << 18;
 constexpr int kSmemLimit = 227 * 1024;
@@ -103,6 +104,7 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
 
 constexpr unsigned long long kNoKey = ~0ull;  // empty slot of the key table
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+constexpr uint32_t kNil = 0xFFFFFFFFu;  // end of a key's query list
 
 // Open-addressing key table (linear probing, at most half full): slot of
 // `key`, inserted if absent.  Gives up (kNoSlot) after a full sweep.
@@ -368,8 +370,9 @@ __device__ __forceinline__ void score_tile_dense(
     }
 }
 
-// 17 warps (16 consumers + the producer) x 112 registers fit one SM's
-// register file; the 8-chunk query cache needs about that many.
+// Up to 16 warps (15 consumers + the producer, four per SM sub-partition) x
+// 112 registers fit the register file; the 8-chunk query cache needs about
+// that many.
 template <typename E, int NCH>
 __global__ void __maxnreg__(112) dense_scan_kernel(const __grid_constant__ DenseArgs a,
                                                    const __grid_constant__ CUtensorMap map) {
@@ -479,7 +482,9 @@ struct IndexArgs {
     int64_t qstride;
     int32_t n_q, kg, W, mask_words;
     const uint64_t *binbase;  // key = lo[w] + value
-    uint32_t *counts;    // [slots + 1]: queries per key slot
+    uint32_t *head;      // [slots]: first entry of the key's list, kNil if none
+    uint32_t *next;      // [n_q << wshift]: entry (q << wshift) | w -> next entry
+    int32_t wshift;      // bits of a scanned-bin index
     uint32_t *gmap;      // per 16 map slots: an even / an odd query has slot j (bits j, 16 + j; swapped in odd words)
     int32_t map_hashed;  // map slot = mix32(key) & map_mask, else the key itself
     uint32_t map_mask;
@@ -492,7 +497,9 @@ struct IndexArgs {
     uint32_t *n_allempty;
 };
 
-// warp per query: empty masks, all-empty list, key counts and the group map
+// warp per query: empty masks, all-empty list, the group map, and the
+// queries of every key as a linked list (entry (q << wshift) | w pushed on
+// the key's list)
 template <typename E>
 __global__ void join_count_kernel(const IndexArgs a) {
     const int lane = threadIdx.x & 31;
@@ -521,102 +528,15 @@ __global__ void join_count_kernel(const IndexArgs a) {
             const uint32_t word = mi >> 4;
             atomicOr(a.gmap + word, 1u << ((mi & 15u) + ((((uint32_t)q ^ word) & 1u) << 4)));
             const uint32_t slot = a.csr_hashed ? table_insert(a.tkey, a.tmask, key) : key;
-            if (slot == kNoSlot) hoph_flag(a.status, HOPH_ERR_CAPACITY);
-            else atomicAdd(a.counts + slot, 1u);
+            if (slot == kNoSlot) {
+                hoph_flag(a.status, HOPH_ERR_CAPACITY);
+            } else {
+                const uint32_t e = ((uint32_t)q << a.wshift) | (uint32_t)w;
+                a.next[e] = atomicExch(a.head + slot, e);
+            }
         }
     }
     if (lane == 0 && all_empty) a.allempty[atomicAdd(a.n_allempty, 1u)] = (int32_t)q;
-}
-
-template <typename E>
-__global__ void join_fill_kernel(const IndexArgs a, const uint32_t *csr_off, uint16_t *csr_q) {
-    const int lane = threadIdx.x & 31;
-    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (q >= a.n_q) return;
-    for (int w = lane; w < a.W; w += 32) {
-        const int g = w / a.kg, b = w - g * a.kg;
-        const uint32_t v = static_cast<const E *>(a.qry)[(int64_t)g * a.qstride + q * a.kg + b];
-        if (v == empty_of<E>()) continue;
-        const uint32_t key = (uint32_t)a.binbase[w] + v;
-        const uint32_t slot = a.csr_hashed ? table_find(a.tkey, a.tmask, key) : key;
-        if (slot == kNoSlot) continue;
-        const uint32_t pos = csr_off[slot] + atomicSub(a.counts + slot, 1u) - 1u;
-        csr_q[pos] = (uint16_t)q;
-    }
-}
-
-// exclusive scan of n uint32 values in three launches: block sums, scan of
-// the sums, scan inside each block plus its offset
-constexpr int kScanBlock = 1024;
-constexpr int kScanPer = 8;  // items per thread
-constexpr int kScanChunk = kScanBlock * kScanPer;
-
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *tmp, uint32_t *total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) tmp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t s = lane < (int)(blockDim.x >> 5) ? tmp[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
-            if (lane >= o) s += y;
-        }
-        tmp[lane] = s;
-    }
-    __syncthreads();
-    const uint32_t excl = x - v + (warp ? tmp[warp - 1] : 0);
-    if (total) *total = tmp[(blockDim.x >> 5) - 1];
-    __syncthreads();
-    return excl;
-}
-
-__global__ void __launch_bounds__(kScanBlock) scan_sums_kernel(const uint32_t *in, int64_t n,
-                                                               uint32_t *sums) {
-    __shared__ uint32_t tmp[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
-    uint32_t s = 0;
-    for (int j = 0; j < kScanPer; ++j) {
-        const int64_t i = base + (int64_t)threadIdx.x * kScanPer + j;
-        if (i < n) s += in[i];
-    }
-    uint32_t tot;
-    block_exclusive_scan(s, tmp, &tot);
-    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(kScanBlock) scan_top_kernel(uint32_t *sums, int64_t nb) {
-    __shared__ uint32_t tmp[32];
-    uint32_t carry = 0;
-    for (int64_t base = 0; base < nb; base += kScanBlock) {
-        const int64_t i = base + threadIdx.x;
-        const uint32_t v = i < nb ? sums[i] : 0;
-        uint32_t tot;
-        const uint32_t e = block_exclusive_scan(v, tmp, &tot);
-        if (i < nb) sums[i] = e + carry;
-        carry += tot;
-    }
-}
-
-__global__ void __launch_bounds__(kScanBlock) scan_apply_kernel(const uint32_t *in, int64_t n,
-                                                                const uint32_t *sums,
-                                                                uint32_t *out) {
-    __shared__ uint32_t tmp[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
-    uint32_t v[kScanPer], s = 0;
-    for (int j = 0; j < kScanPer; ++j) {
-        v[j] = base + j < n ? in[base + j] : 0;
-        s += v[j];
-    }
-    uint32_t run = block_exclusive_scan(s, tmp, nullptr) + sums[blockIdx.x];
-    for (int j = 0; j < kScanPer; ++j) {
-        if (base + j < n) out[base + j] = run;
-        run += v[j];
-    }
 }
 
 // ===========================================================================
@@ -798,8 +718,9 @@ struct CountArgs {
     int32_t csr_hashed;       // key slots from the key table
     const unsigned long long *tkey;
     uint32_t tmask;
-    const uint32_t *csr_off;
-    const uint16_t *csr_q;
+    const uint32_t *head;     // key slot -> first entry of its query list
+    const uint32_t *next;     // entry -> next entry
+    int32_t wshift;           // query of an entry = entry >> wshift
     const uint32_t *q_emask;  // [n_q][mask_words]
     int32_t mask_words;
     const int32_t *allempty;
@@ -828,7 +749,7 @@ __host__ __device__ inline CountSmem count_smem(const CountArgs &a) {
 }
 
 // NCH = 32-bin chunks per row (W <= 32 * NCH).  Each lane keeps its chunks'
-// values and CSR ranges in registers between the counting and evaluation
+// values and list heads in registers between the counting and evaluation
 // passes, and the next candidate row's values are loaded while the current
 // one is counted.
 template <int NCH, typename E>
@@ -923,52 +844,45 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
             continue;
         }
         const int need = row_min[ne];
-        // counting pass: CSR ranges of every chunk, then counts
-        uint32_t o1[NCH], o2[NCH];
+        // counting pass: the query list of every chunk's key, then counts
+        uint32_t f[NCH];
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
-            o1[c] = o2[c] = 0;
+            f[c] = kNil;
             if (woff[c] >= 0 && v[c] != empty_of<E>()) {
                 const uint32_t key = kbase[c] + v[c];
                 const uint32_t slot = a.csr_hashed ? table_find(a.tkey, a.tmask, key) : key;
-                if (slot != kNoSlot) {
-                    o1[c] = __ldg(a.csr_off + slot);
-                    o2[c] = __ldg(a.csr_off + slot + 1);
-                }
+                if (slot != kNoSlot) f[c] = __ldg(a.head + slot);
             }
         }
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
-            for (uint32_t i = o1[c]; i < o2[c]; ++i) {
-                const uint32_t q = __ldg(a.csr_q + i);
+            for (uint32_t e = f[c]; e != kNil; e = __ldg(a.next + e)) {
+                const uint32_t q = e >> a.wshift;
                 atomicAdd(cnt + (q >> 1), 1u << ((q & 1) * 16));
+                ++hits;
             }
-            hits += o2[c] - o1[c];
         }
         __syncwarp();
         // evaluation: each distinct hit query is taken by the first lane that
         // clears its counter; resumable so a full survivor list can drain
         int c = 0;
-        uint32_t i = o1[0];
+        uint32_t i = f[0];
         bool done = false;
         while (true) {
             while (!done) {
                 // advance to the next (chunk, list entry) of this lane
-                uint32_t iend = 0;
-#pragma unroll
-                for (int cc = 0; cc < NCH; ++cc)
-                    if (cc == c) iend = o2[cc];
-                if (i >= iend) {
+                if (i == kNil) {
                     if (++c >= NCH) {
                         done = true;
                         break;
                     }
 #pragma unroll
                     for (int cc = 0; cc < NCH; ++cc)
-                        if (cc == c) i = o1[cc];
+                        if (cc == c) i = f[cc];
                     continue;
                 }
-                const uint32_t q = __ldg(a.csr_q + i);
+                const uint32_t q = i >> a.wshift;
                 const uint32_t sh = (q & 1) * 16;
                 const uint32_t old = atomicAnd(cnt + (q >> 1), ~(0xFFFFu << sh));
                 const int m = (int)((old >> sh) & 0xFFFFu);
@@ -992,7 +906,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
                         }
                     }
                 }
-                ++i;
+                i = __ldg(a.next + i);
             }
             const bool all_done = __all_sync(0xFFFFFFFFu, done);
             __syncwarp();
@@ -1020,7 +934,7 @@ int launch_count(const CountArgs &ca, uint32_t smem, int num_sms, cudaStream_t s
     auto kern = count_kernel<NCH, E>;
     HOPH_CUDA_TRY(hoph_ensure_smem((const void *)kern, (int)smem));
     int per = 0;
-    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kCountThreads, smem));
+    HOPH_CUDA_TRY(hoph_occupancy(&per, (const void *)kern, kCountThreads, smem));
     if (per < 1) return HOPH_ERR_UNSUPPORTED;
     kern<<<(unsigned)(num_sms * per), kCountThreads, smem, s>>>(ca);
     HOPH_CUDA_TRY(cudaGetLastError());
@@ -1260,7 +1174,7 @@ int launch_filter_c(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem,
     HOPH_CUDA_TRY(hoph_ensure_smem((const void *)kern, (int)smem));
     const int threads = 32 * (fa.n_cons + 1);
     int per_sm = 0;
-    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    HOPH_CUDA_TRY(hoph_occupancy(&per_sm, (const void *)kern, threads, smem));
     if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
     if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
     const int64_t grid = std::min<int64_t>(fa.n_tiles, (int64_t)num_sms * per_sm);
@@ -1407,7 +1321,8 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     // Key space: the psi-space of the scanned bins.  Up to kDirectMap keys the
     // group map is indexed by key (no false hits); beyond, by a hash into
     // kHashedMapSlots slots (false hits only loosen the filter).  Up to
-    // kMaxJoinKeys keys the CSR is indexed by key; beyond, through a key table.
+    // kMaxJoinKeys keys the list heads are indexed by key; beyond, through a
+    // key table.
     // A small key space takes the guarded keys lo[w] + w + 1 + value (a key
     // below every bin that no value reaches; the empty marker wraps onto it).
     const uint64_t plain_keys = mode == HOPH_MODE_MINWISE_FULL ? ~0ull : plan->lo[W];
@@ -1431,6 +1346,8 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     if (strategy < 0) strategy = (join_ok && n_queries >= 16) ? 1 : 0;
 
     const int mask_words = (W + 31) / 32;
+    int wshift = 0;  // bits of a scanned-bin index (join index entries)
+    while ((1 << wshift) < W) ++wshift;
     const int64_t qstride = n_queries * (int64_t)kg;
     const int64_t cstride = cstride_in >= 0 ? cstride_in : n_rows * (int64_t)kg;
 
@@ -1442,12 +1359,10 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         bump.off = 0;
         bump.take(st_b);
         if (strategy == 1) {
-            bump.take((csr_slots + 1) * 4);                                  // counts
-            bump.take((csr_slots + 1) * 4);                                  // csr_off
-            bump.take(((csr_slots + 1 + kScanChunk - 1) / kScanChunk) * 4);  // block sums
-            bump.take((map_slots / 16 + 2) * 4);                             // group map
-            bump.take(csr_hashed ? csr_slots * 8 : 8);                       // key table
-            bump.take((size_t)n_queries * W * 2);                       // csr_q
+            bump.take(csr_slots * 4);                                   // list heads
+            bump.take(((size_t)n_queries << wshift) * 4);               // list links
+            bump.take((map_slots / 16 + 2) * 4);                        // group map
+            bump.take(csr_hashed ? csr_slots * 8 : 8);                  // key table
             bump.take((size_t)n_queries * mask_words * 4);              // q_emask
             bump.take((size_t)n_queries * 4 + 4);                       // allempty + count
             bump.take(8);                                               // n_cand
@@ -1463,19 +1378,16 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     }
     bump.off = 0;
     unsigned long long *st = (unsigned long long *)bump.take(st_b);
-    uint32_t *counts = nullptr, *csr_off = nullptr, *sums = nullptr, *gmap = nullptr,
-             *q_emask = nullptr, *n_allempty = nullptr, *cand = nullptr;
-    uint16_t *csr_q = nullptr;
+    uint32_t *head = nullptr, *next = nullptr, *gmap = nullptr, *q_emask = nullptr,
+             *n_allempty = nullptr, *cand = nullptr;
     int32_t *allempty = nullptr;
     unsigned long long *tkey = nullptr;
     unsigned long long *n_cand = nullptr;
     if (strategy == 1) {
-        counts = (uint32_t *)bump.take((csr_slots + 1) * 4);
-        csr_off = (uint32_t *)bump.take((csr_slots + 1) * 4);
-        sums = (uint32_t *)bump.take(((csr_slots + 1 + kScanChunk - 1) / kScanChunk) * 4);
+        head = (uint32_t *)bump.take(csr_slots * 4);
+        next = (uint32_t *)bump.take(((size_t)n_queries << wshift) * 4);
         gmap = (uint32_t *)bump.take((map_slots / 16 + 2) * 4);
         tkey = (unsigned long long *)bump.take(csr_hashed ? csr_slots * 8 : 8);
-        csr_q = (uint16_t *)bump.take((size_t)n_queries * W * 2);
         q_emask = (uint32_t *)bump.take((size_t)n_queries * mask_words * 4);
         allempty = (int32_t *)bump.take((size_t)n_queries * 4 + 4);
         n_allempty = (uint32_t *)(allempty + n_queries);
@@ -1520,7 +1432,9 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ia.W = W;
         ia.mask_words = mask_words;
         ia.binbase = binbase;
-        ia.counts = counts;
+        ia.head = head;
+        ia.next = next;
+        ia.wshift = wshift;
         ia.gmap = gmap;
         ia.map_hashed = map_hashed;
         ia.map_mask = (uint32_t)(map_slots - 1);
@@ -1531,21 +1445,15 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ia.q_emask = q_emask;
         ia.allempty = allempty;
         ia.n_allempty = n_allempty;
-        HOPH_CUDA_TRY(cudaMemsetAsync(counts, 0, (csr_slots + 1) * 4, s));
+        HOPH_CUDA_TRY(cudaMemsetAsync(head, 0xFF, csr_slots * 4, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(gmap, 0, (map_slots / 16 + 2) * 4, s));
         if (csr_hashed) HOPH_CUDA_TRY(cudaMemsetAsync(tkey, 0xFF, csr_slots * 8, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(n_allempty, 0, 4, s));
         HOPH_CUDA_TRY(cudaMemsetAsync(n_cand, 0, 8, s));
         const unsigned qb = (unsigned)((n_queries * 32 + 255) / 256);
         join_count_kernel<E><<<qb, 256, 0, s>>>(ia);
-        const int64_t n_scan = (int64_t)csr_slots + 1;
-        const int64_t nb = (n_scan + kScanChunk - 1) / kScanChunk;
-        scan_sums_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, n_scan, sums);
-        scan_top_kernel<<<1, kScanBlock, 0, s>>>(sums, nb);
-        scan_apply_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, n_scan, sums, csr_off);
-        join_fill_kernel<E><<<qb, 256, 0, s>>>(ia, csr_off, csr_q);
         HOPH_CUDA_TRY(cudaGetLastError());
-        launches += 5;
+        launches += 1;
 
         // ---- join: streaming row filter
         FilterArgs fa;
@@ -1611,8 +1519,9 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ca.csr_hashed = csr_hashed;
         ca.tkey = tkey;
         ca.tmask = (uint32_t)(csr_slots - 1);
-        ca.csr_off = csr_off;
-        ca.csr_q = csr_q;
+        ca.head = head;
+        ca.next = next;
+        ca.wshift = wshift;
         ca.q_emask = q_emask;
         ca.mask_words = mask_words;
         ca.allempty = allempty;
@@ -1632,7 +1541,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         DenseArgs da;
         da.p = pa;
         const int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 8;
-        if (n_cons > 16) return HOPH_ERR_UNSUPPORTED;
+        if (n_cons > 15) return HOPH_ERR_UNSUPPORTED;
         int R = plan->exec.tile_rows > 0 ? plan->exec.tile_rows : 0;
         if (R == 0) {
             R = (int)std::max<int64_t>(1, std::min<int64_t>(256, 8192 / (W * ES)));
@@ -1662,8 +1571,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         HOPH_CUDA_TRY(hoph_ensure_smem((const void *)dense, (int)DL.total));
         const int threads = 32 * (n_cons + 1);
         int per_sm = 0;
-        HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense, threads,
-                                                                    DL.total));
+        HOPH_CUDA_TRY(hoph_occupancy(&per_sm, (const void *)dense, threads, DL.total));
         if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
         if (plan->exec.ctas_per_sm > 0) per_sm = std::min(per_sm, plan->exec.ctas_per_sm);
         const int64_t grid = std::min<int64_t>(da.n_tiles, (int64_t)plan->num_sms * per_sm);

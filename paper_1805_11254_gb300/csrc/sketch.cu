@@ -16,6 +16,7 @@
 //  * hoph_synth_ids: counter-based synthetic IDs (benchmark inputs).
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -25,6 +26,7 @@ constexpr int kSketchThreads = 256;
 constexpr int kSketchWarps = kSketchThreads / 32;
 constexpr int kBuckets = 65;
 constexpr int kBigBucket = 12;  // sets of >= 2048 IDs (bit length >= 12) get a whole CTA
+constexpr int kResidentCtas = 6;  // sketch CTAs per SM (40 registers x 256 threads)
 constexpr int64_t kSplitPhases = 16384;  // from this many sets: one launch per phase
 
 // Hash path: psi-space regions of equal-width bins (the whole space for equal
@@ -45,7 +47,7 @@ struct SketchArgs {
     void *planes;          // uint32 or (compact) uint16 [G][n_sets][k']
     int32_t compact;       // uint16 planes
     int64_t plane_stride;  // n_sets * k'
-    uint32_t k, kg;
+    uint32_t k, kg, G;
     const uint32_t *key;   // packed psi table (table path)
     uint32_t key_bits;
     uint64_t D;
@@ -54,7 +56,6 @@ struct SketchArgs {
     const int32_t *order;  // size-sorted set indices, or nullptr for 0..n-1
     const uint32_t *n_big; // items [0, *n_big) of order are sketched a CTA per set
     RegionTable reg;       // hash path: bin regions
-    int32_t phases;        // oph_sketch_kernel: bit 0 large sets, bit 1 the rest
     int32_t generate;      // IDs come from the counter generator, not from ids[]
     uint64_t gen_seed;     // generator stream; set i's IDs are elements off[i]..off[i+1]-1
     uint64_t gen_D;        // generated IDs are uniform over 0..gen_D-1
@@ -190,25 +191,27 @@ __device__ __forceinline__ void sketch_generated(const SketchArgs &a, const uint
 
 // group-major store of one finished sketch (bin b -> plane b / k', slot b % k')
 // and reset of the shared copy
+// (compact planes: offsets < 0xFFFF; the empty marker truncates to 0xFFFF)
+template <bool COMPACT>
 __device__ __forceinline__ void store_sketch(const SketchArgs &a, uint32_t *sk, int64_t set, int t,
                                              int T) {
-    for (uint32_t b = t; b < a.k; b += T) {
-        const uint32_t g = b / a.kg, j = b - g * a.kg;
-        const int64_t at = (int64_t)g * a.plane_stride + set * a.kg + j;
-        // compact: offsets < 0xFFFF; the empty marker truncates to 0xFFFF
-        if (a.compact) static_cast<uint16_t *>(a.planes)[at] = (uint16_t)sk[b];
-        else static_cast<uint32_t *>(a.planes)[at] = sk[b];
-        sk[b] = HOPH_EMPTY_VALUE;
+    using E = typename std::conditional<COMPACT, uint16_t, uint32_t>::type;
+    E *dst = static_cast<E *>(a.planes) + set * a.kg;
+    for (uint32_t g = 0; g < a.G; ++g, dst += a.plane_stride, sk += a.kg) {
+        for (uint32_t j = t; j < a.kg; j += T) {
+            dst[j] = (E)sk[j];
+            sk[j] = HOPH_EMPTY_VALUE;
+        }
     }
 }
 
-// The work list in two phases (both in one launch for small batches, one
-// launch each for large ones; a.phases says which).  Phase 1: the large sets
-// at its head (items [0, *n_big)), a CTA per set, all warps feeding one
-// shared sketch.  Phase 2: warp per set over the rest, strided so that the
-// CTAs that took a large set get the smallest of the remaining sets.
-// Without a work list (a.n_big null) only phase 2 runs, in input order.
-template <bool HASH>
+// The work list in two phases.  Phase 1 (PHASES & 1): the large sets at its
+// head (items [0, *n_big)), a CTA per set, all warps feeding one shared
+// sketch.  Phase 2 (PHASES & 2): warp per set over the rest; when both run in
+// one launch (small batches), strided so that the CTAs that took a large set
+// get the smallest of the remaining sets.  Without a work list (a.n_big null)
+// only phase 2 runs, in input order.
+template <bool HASH, int PHASES, bool COMPACT>
 __global__ void __launch_bounds__(kSketchThreads, 6) oph_sketch_kernel(const SketchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *s_lo = reinterpret_cast<uint64_t *>(smem_raw);  // HASH only
@@ -219,13 +222,13 @@ __global__ void __launch_bounds__(kSketchThreads, 6) oph_sketch_kernel(const Ske
         for (uint32_t i = threadIdx.x; i <= a.k; i += blockDim.x) s_lo[i] = a.lo[i];
         if (threadIdx.x == 0) s_reg = a.reg;
     }
-    for (uint32_t i = threadIdx.x; i < (uint32_t)kSketchWarps * a.k; i += blockDim.x)
-        s_sk[i] = HOPH_EMPTY_VALUE;
+    const uint32_t regions = (PHASES & 2) ? kSketchWarps : 1;
+    for (uint32_t i = threadIdx.x; i < regions * a.k; i += blockDim.x) s_sk[i] = HOPH_EMPTY_VALUE;
     __syncthreads();
     bool bad = false;
     const int64_t n_big = a.n_big ? (int64_t)*a.n_big : 0;
     // phase 1 (warp 0's sketch region serves the CTA; store_sketch resets it)
-    for (int64_t item = (a.phases & 1) ? blockIdx.x : n_big; item < n_big; item += gridDim.x) {
+    for (int64_t item = (PHASES & 1) ? blockIdx.x : n_big; item < n_big; item += gridDim.x) {
         const int64_t set = a.order[item];
         const int64_t beg = a.off[set], end = a.off[set + 1];
         if (a.generate)
@@ -235,15 +238,18 @@ __global__ void __launch_bounds__(kSketchThreads, 6) oph_sketch_kernel(const Ske
             sketch_ids<HASH>(a, s_lo, &s_reg, s_sk, a.ids + beg, end - beg, threadIdx.x,
                              blockDim.x, bad);
         __syncthreads();
-        store_sketch(a, s_sk, set, threadIdx.x, blockDim.x);
+        store_sketch<COMPACT>(a, s_sk, set, threadIdx.x, blockDim.x);
         __syncthreads();
     }
     // phase 2
+    if (!(PHASES & 2)) {
+        if (bad) hoph_flag(a.status, HOPH_ERR_ID_RANGE);
+        return;
+    }
     uint32_t *sk = s_sk + (size_t)warp * a.k;
     const int64_t warps_total = (int64_t)gridDim.x * kSketchWarps;
-    const int64_t slot = (int64_t)(gridDim.x - 1 - blockIdx.x) * kSketchWarps + warp;
-    for (int64_t item = (a.phases & 2) ? n_big + slot : a.n_sets; item < a.n_sets;
-         item += warps_total) {
+    const int64_t cta = PHASES == 3 ? (int64_t)(gridDim.x - 1 - blockIdx.x) : blockIdx.x;
+    for (int64_t item = n_big + cta * kSketchWarps + warp; item < a.n_sets; item += warps_total) {
         const int64_t set = a.order ? a.order[item] : item;
         const int64_t beg = a.off[set], end = a.off[set + 1];
         if (a.generate)
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(kSketchThreads, 6) oph_sketch_kernel(const Ske
         else
             sketch_ids<HASH>(a, s_lo, &s_reg, sk, a.ids + beg, end - beg, lane, 32, bad);
         __syncwarp();
-        store_sketch(a, sk, set, lane, 32);
+        store_sketch<COMPACT>(a, sk, set, lane, 32);
         __syncwarp();
     }
     if (bad) hoph_flag(a.status, HOPH_ERR_ID_RANGE);
@@ -274,12 +280,20 @@ __global__ void bucket_hist_kernel(const int64_t *off, int64_t n, uint32_t *hist
 }
 
 // exclusive prefix over buckets in descending size order (largest first);
-// *n_big = number of sets in the buckets that get a CTA each
-__global__ void bucket_base_kernel(const uint32_t *hist, uint32_t *base, uint32_t *n_big) {
+// *n_big = number of sets that get a CTA each: those of at least 2,048 IDs
+// and, when warps > 0 (a batch sketched in one launch), also more than four
+// times the batch's IDs per resident warp
+__global__ void bucket_base_kernel(const uint32_t *hist, uint32_t *base, uint32_t *n_big,
+                                   const int64_t *off, int64_t n, int64_t warps) {
     if (threadIdx.x == 0) {
+        int big = kBigBucket;
+        if (warps > 0) {
+            const uint64_t per_warp = (uint64_t)(off[n] - off[0]) / (uint64_t)warps;
+            big = max(big, size_bucket((int64_t)(4 * per_warp)) + 1);
+        }
         uint32_t run = 0;
         for (int b = kBuckets - 1; b >= 0; --b) {
-            if (b == kBigBucket - 1) *n_big = run;
+            if (b == big - 1) *n_big = run;
             base[b] = run;
             run += hist[b];
         }
@@ -375,10 +389,10 @@ SketchArgs sketch_args(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_
     a.n_sets = n_sets;
     a.planes = d_planes;
     a.compact = 0;
-    a.phases = 3;
     a.plane_stride = n_sets * (int64_t)P.k_group;
     a.k = P.k;
     a.kg = P.k_group;
+    a.G = P.k / P.k_group;
     a.key = plan->d_key;
     a.key_bits = plan->key_bits;
     a.D = P.universe_D;
@@ -417,7 +431,9 @@ int build_work_list(hoph_plan *plan, const int64_t *d_offsets, int64_t n_sets, u
     HOPH_CUDA_TRY(cudaMemsetAsync(cursor, 0, kBuckets * sizeof(uint32_t), s));
     const int g = plan->num_sms * 4;
     bucket_hist_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, hist);
-    bucket_base_kernel<<<1, 32, 0, s>>>(hist, base, n_big);
+    const int64_t warps =
+        n_sets >= kSplitPhases ? 0 : (int64_t)plan->num_sms * kResidentCtas * kSketchWarps;
+    bucket_base_kernel<<<1, 32, 0, s>>>(hist, base, n_big, d_offsets, n_sets, warps);
     bucket_scatter_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, base, cursor, order);
     HOPH_CUDA_TRY(cudaGetLastError());
     plan->launches += 3;
@@ -426,36 +442,43 @@ int build_work_list(hoph_plan *plan, const int64_t *d_offsets, int64_t n_sets, u
     return HOPH_OK;
 }
 
-// The sketch kernel over the work list (or the input order).
-template <bool HASH>
-int launch_sketch_kernels(hoph_plan *plan, const SketchArgs &a, cudaStream_t s) {
+template <bool HASH, int PHASES, bool COMPACT>
+int launch_phases(hoph_plan *plan, const SketchArgs &a, cudaStream_t s) {
     const uint32_t k = a.k;
     const size_t lo_b = HASH ? (size_t)(k + 1) * 8 : 0;
-    const size_t smem = lo_b + (size_t)kSketchWarps * k * 4;
-    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)oph_sketch_kernel<HASH>, (int)smem));
+    const size_t smem = lo_b + (size_t)((PHASES & 2) ? kSketchWarps : 1) * k * 4;
+    auto kern = oph_sketch_kernel<HASH, PHASES, COMPACT>;
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)kern, (int)smem));
     int per = 0;
-    HOPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oph_sketch_kernel<HASH>,
-                                                                kSketchThreads, smem));
+    HOPH_CUDA_TRY(hoph_occupancy(&per, (const void *)kern, kSketchThreads, smem));
     if (per < 1) return HOPH_ERR_UNSUPPORTED;
-    const int64_t blocks = std::min<int64_t>((a.n_sets + kSketchWarps - 1) / kSketchWarps,
-                                             (int64_t)grid_for(plan, per));
-    // a large batch keeps the phases apart: one launch of the large sets
-    // with the whole GPU, then one of the rest
-    const bool split = a.n_big && a.n_sets >= kSplitPhases;
-    const int phases[2] = {split ? 1 : 3, 2};
-    for (int i = 0; i < (split ? 2 : 1); ++i) {
-        SketchArgs b = a;
-        b.phases = phases[i];
-        oph_sketch_kernel<HASH><<<(unsigned)blocks, kSketchThreads, smem, s>>>(b);
-        HOPH_CUDA_TRY(cudaGetLastError());
-        plan->launches += 1;
-    }
+    const int64_t want = PHASES == 1 ? a.n_sets : (a.n_sets + kSketchWarps - 1) / kSketchWarps;
+    const int64_t blocks = std::min<int64_t>(want, (int64_t)grid_for(plan, per));
+    kern<<<(unsigned)blocks, kSketchThreads, smem, s>>>(a);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    plan->launches += 1;
     return HOPH_OK;
 }
 
+// The sketch kernel(s) over the work list (or the input order): one launch
+// for a small batch; a large one sketches its large sets (a CTA each) with
+// the whole GPU first, then the rest.
+template <bool HASH, bool COMPACT>
+int launch_sketch_kernels(hoph_plan *plan, const SketchArgs &a, cudaStream_t s) {
+    if (a.n_big && a.n_sets >= kSplitPhases) {
+        const int rc = launch_phases<HASH, 1, COMPACT>(plan, a, s);
+        return rc != HOPH_OK ? rc : launch_phases<HASH, 2, COMPACT>(plan, a, s);
+    }
+    return launch_phases<HASH, 3, COMPACT>(plan, a, s);
+}
+
 int launch_sketch(hoph_plan *plan, const SketchArgs &a, cudaStream_t s) {
-    return plan->P.perm_kind == HOPH_PERM_HASH61 ? launch_sketch_kernels<true>(plan, a, s)
-                                                 : launch_sketch_kernels<false>(plan, a, s);
+    const bool hash = plan->P.perm_kind == HOPH_PERM_HASH61;
+    if (a.compact)
+        return hash ? launch_sketch_kernels<true, true>(plan, a, s)
+                    : launch_sketch_kernels<false, true>(plan, a, s);
+    return hash ? launch_sketch_kernels<true, false>(plan, a, s)
+                : launch_sketch_kernels<false, false>(plan, a, s);
 }
 
 constexpr int64_t kWorkListMin = 64;  // below this many sets: identity order, warps only
