@@ -28,6 +28,7 @@ constexpr int kBuckets = 65;
 constexpr int kBigBucket = 12;  // sets of >= 2048 IDs (bit length >= 12) get a whole CTA
 constexpr int kResidentCtas = 6;  // sketch CTAs per SM (40 registers x 256 threads)
 constexpr int64_t kSplitPhases = 16384;  // from this many sets: one launch per phase
+constexpr int64_t kSmallList = 4096;     // up to this many sets: the work list in one CTA
 
 // Hash path: psi-space regions of equal-width bins (the whole space for equal
 // bins, one per group for a:b); a value's bin is first + floor(o * nb / z).
@@ -300,6 +301,32 @@ __global__ void bucket_base_kernel(const uint32_t *hist, uint32_t *base, uint32_
     }
 }
 
+// The three steps above in one CTA, for a batch of at most kSmallList sets
+// (a query batch): histogram, prefix and large-set count, scatter.
+__global__ void __launch_bounds__(1024) bucket_small_kernel(const int64_t *off, int64_t n,
+                                                            uint32_t *n_big, int32_t *order,
+                                                            int64_t warps) {
+    __shared__ uint32_t h[kBuckets], cur[kBuckets];
+    for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        atomicAdd(&h[size_bucket(off[i + 1] - off[i])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t per_warp = (uint64_t)(off[n] - off[0]) / (uint64_t)warps;
+        const int big = max(kBigBucket, size_bucket((int64_t)(4 * per_warp)) + 1);
+        uint32_t run = 0;
+        for (int b = kBuckets - 1; b >= 0; --b) {
+            if (b == big - 1) *n_big = run;
+            cur[b] = run;
+            run += h[b];
+        }
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        order[atomicAdd(&cur[size_bucket(off[i + 1] - off[i])], 1u)] = (int32_t)i;
+}
+
 __global__ void bucket_scatter_kernel(const int64_t *off, int64_t n, const uint32_t *base,
                                       uint32_t *cursor, int32_t *order) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -427,6 +454,16 @@ int build_work_list(hoph_plan *plan, const int64_t *d_offsets, int64_t n_sets, u
     uint32_t *hist = wl, *base = hist + kBuckets, *cursor = base + kBuckets;
     uint32_t *n_big = cursor + kBuckets;
     int32_t *order = reinterpret_cast<int32_t *>(n_big + 1);
+    a.order = order;
+    a.n_big = n_big;
+    if (n_sets <= kSmallList) {
+        bucket_small_kernel<<<1, 1024, 0, s>>>(
+            d_offsets, n_sets, n_big, order,
+            (int64_t)plan->num_sms * kResidentCtas * kSketchWarps);
+        HOPH_CUDA_TRY(cudaGetLastError());
+        plan->launches += 1;
+        return HOPH_OK;
+    }
     HOPH_CUDA_TRY(cudaMemsetAsync(hist, 0, kBuckets * sizeof(uint32_t), s));
     HOPH_CUDA_TRY(cudaMemsetAsync(cursor, 0, kBuckets * sizeof(uint32_t), s));
     const int g = plan->num_sms * 4;
