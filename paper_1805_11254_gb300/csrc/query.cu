@@ -497,6 +497,24 @@ struct IndexArgs {
     uint32_t *n_allempty;
 };
 
+// A join batch's state reset in one launch: list heads to kNil, the group
+// map and the call's counters to zero (out_count: null when the output
+// accumulates over several calls).
+__global__ void join_init_kernel(uint32_t *head, int64_t n_head, uint32_t *gmap, int64_t n_gmap,
+                                 unsigned long long *st, int n_st, uint32_t *n_allempty,
+                                 unsigned long long *n_cand, int64_t *out_count) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = t; i < n_head; i += T) head[i] = kNil;
+    for (int64_t i = t; i < n_gmap; i += T) gmap[i] = 0u;
+    if (t < n_st) st[t] = 0ull;
+    if (t == 0) {
+        *n_allempty = 0u;
+        *n_cand = 0ull;
+        if (out_count) *out_count = 0;
+    }
+}
+
 // warp per query: empty masks, all-empty list, the group map, and the
 // queries of every key as a linked list (entry (q << wshift) | w pushed on
 // the key's list)
@@ -1292,8 +1310,10 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     const int W = Gs * kg;
     if (W > kMaxW) return HOPH_ERR_UNSUPPORTED;
 
-    if (first) HOPH_CUDA_TRY(cudaMemsetAsync(d_out_count, 0, sizeof(int64_t), s));
-    if (n_queries == 0 || n_rows == 0) return HOPH_OK;
+    if (n_queries == 0 || n_rows == 0) {
+        if (first) HOPH_CUDA_TRY(cudaMemsetAsync(d_out_count, 0, sizeof(int64_t), s));
+        return HOPH_OK;
+    }
     if (!d_query_planes || !d_coll_planes) return HOPH_ERR_PARAM;
 
     if (plan->table_W[mode] != W) {
@@ -1418,7 +1438,10 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     pa.stat = st;
     pa.status = plan->d_status;
 
-    HOPH_CUDA_TRY(cudaMemsetAsync(st, 0, st_b, s));
+    if (strategy != 1) {  // the join resets its state in join_init_kernel
+        if (first) HOPH_CUDA_TRY(cudaMemsetAsync(d_out_count, 0, sizeof(int64_t), s));
+        HOPH_CUDA_TRY(cudaMemsetAsync(st, 0, st_b, s));
+    }
     hoph_timing_mark(plan, 0, s);
     int64_t launches = 0;
 
@@ -1445,15 +1468,14 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ia.q_emask = q_emask;
         ia.allempty = allempty;
         ia.n_allempty = n_allempty;
-        HOPH_CUDA_TRY(cudaMemsetAsync(head, 0xFF, csr_slots * 4, s));
-        HOPH_CUDA_TRY(cudaMemsetAsync(gmap, 0, (map_slots / 16 + 2) * 4, s));
+        join_init_kernel<<<(unsigned)plan->num_sms * 4, 256, 0, s>>>(
+            head, (int64_t)csr_slots, gmap, (int64_t)(map_slots / 16 + 2), st, kStatWords,
+            n_allempty, n_cand, first ? d_out_count : nullptr);
         if (csr_hashed) HOPH_CUDA_TRY(cudaMemsetAsync(tkey, 0xFF, csr_slots * 8, s));
-        HOPH_CUDA_TRY(cudaMemsetAsync(n_allempty, 0, 4, s));
-        HOPH_CUDA_TRY(cudaMemsetAsync(n_cand, 0, 8, s));
         const unsigned qb = (unsigned)((n_queries * 32 + 255) / 256);
         join_count_kernel<E><<<qb, 256, 0, s>>>(ia);
         HOPH_CUDA_TRY(cudaGetLastError());
-        launches += 1;
+        launches += 2;
 
         // ---- join: streaming row filter
         FilterArgs fa;

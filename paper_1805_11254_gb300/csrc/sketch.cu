@@ -7,7 +7,7 @@
 //    resident warps.  IDs are read with 128-bit
 //    loads; each ID is mapped through the packed psi table (psi value ->
 //    bin and offset) that stays resident in L2, and the per-bin minimum is
-//    kept in the warp's shared-memory sketch with a read-then-atomicMin.
+//    kept in the warp's shared-memory sketch with a shared atomicMin.
 //    The finished sketch is written group-major ([G][n][k']) with coalesced
 //    stores.
 //  * minwise_build_sketches: MinWise (Sec. 1), one warp per set, lane t
@@ -106,7 +106,9 @@ __device__ __forceinline__ uint64_t hash_bin(const RegionTable &t, const uint64_
 // One thread's share of the IDs [p, p+n) (thread t of a group of T threads):
 // a scalar head up to a 16-byte boundary, a 128-bit body whose eight table
 // gathers are issued before any of their minima is applied, a scalar tail.
-// Each ID updates the shared sketch `sk` with a read-then-atomicMin.
+// Each ID updates the shared sketch `sk` with an atomicMin (no read first: one
+// shared-memory operation per ID instead of a read and, when it improves, an
+// atomic).
 template <bool HASH>
 __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *s_lo,
                                            const RegionTable *s_reg, uint32_t *sk,
@@ -129,7 +131,7 @@ __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *
             bad = true;
             return;
         }
-        if (off < sk[bin]) atomicMin(sk + bin, off);
+        atomicMin(sk + bin, off);
     };
     const int64_t head =
         (int64_t)min((long long)n, (long long)((4 - ((reinterpret_cast<uintptr_t>(p) >> 2) & 3)) & 3));
@@ -177,7 +179,7 @@ __device__ __forceinline__ void sketch_generated(const SketchArgs &a, const uint
             bad = true;
             return;
         }
-        if (off < sk[bin]) atomicMin(sk + bin, off);
+        atomicMin(sk + bin, off);
     };
     int64_t j = t;
     for (; j + 3 * (int64_t)T < n; j += 4 * (int64_t)T) {

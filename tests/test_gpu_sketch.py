@@ -236,3 +236,20 @@ def test_compact_sketches_need_bins_of_at_most_65535_values():
         with pytest.raises(hoph.HophError) as e:
             hoph.oph_build_sketches16(plan.handle, off, off, 1, out)
         assert e.value.code == hoph.HOPH_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("n", [64, 4096, 4097, 16383, 16384])
+def test_work_list_shapes_at_their_boundaries(n):
+    """The work list in one CTA (<= 4,096 sets) or three kernels, one launch
+    or two (>= 16,384 sets): the same sketches as the oracle either way."""
+    dev = device()
+    D, k, kg = 1 << 16, 128, 32
+    rng = np.random.default_rng(n)
+    sizes = rng.integers(0, 600, n)
+    sizes[rng.integers(0, n, 3)] = [2048, 3000, 5000]
+    off = synth.offsets_from_sizes(sizes)
+    ids = synth.counter_ids(5, 0, int(off[-1]), D)
+    with hoph.Plan(D, k, kg, 1, 1, seed=4) as plan:
+        got = _gpu_sketch(plan, ids, off, dev)
+    want = oc.sketch(ids, off, oc.layout(D, k, kg, 1, 1), perm=oc.permutation(D, 4))
+    assert np.array_equal(got, want)
