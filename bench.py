@@ -633,11 +633,15 @@ def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
     d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
     hoph.hoph_synth_ids(SKETCH_SEED, 0, n_ids, D, 1, d_cdf, len(cdf), d_ids)
     d_off = to_dev(off, dev)
+    from paper_1805_11254_gb300 import autotune
     with hoph.Plan(D, K, K, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
         out = torch.empty((1, n_sets, K), dtype=torch.int32, device=dev)
         for _ in range(3):
             plan.sketch(d_ids, d_off, n_sets, out=out, stream=stream)
         plan.check()
+        best, tune_ms = autotune.tune_sketch(plan, d_ids, d_off, n_sets, out, stream)
+        for _ in range(2):
+            plan.sketch(d_ids, d_off, n_sets, out=out, stream=stream)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -650,6 +654,7 @@ def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
     bytes_ = 4 * n_ids + 8 * (n_sets + 1) + 4 * K * n_sets
     gbs = bytes_ / (ms / 1e3) / 1e9
     return {"sets_per_s": n_sets / (ms / 1e3), "ms_per_launch": ms,
+            "autotune": {"sketch_cta_bits": best, "ms_by_bits": tune_ms},
             "workload": "1,000,000 sets, lognormal(300, 1.0) [10, 20000], Zipf(1.1) IDs over 2^20,"
                         " k = 256 OPH",
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -658,7 +663,7 @@ def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
 
 
 def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
-    """One-query OPH full-scan launches (dense scan) for ncu: the knobs are
+    """One-query OPH full-scan launches for ncu: the strategy and knobs are
     tuned first as in the baseline leg, then the profiled launches run inside
     the NVTX range "oph1"."""
     import torch
@@ -677,7 +682,8 @@ def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
         qs = [q[:, i:i + 1].contiguous() for i in range(launches)]
         best, _ = autotune.tune_query(plan, hoph.HOPH_MODE_OPH_FULL, qs[0], 1, planes, args.rows,
-                                      out, cap, cnt, stream, candidates=autotune.DENSE_CANDIDATES)
+                                      out, cap, cnt, stream,
+                                      candidates=autotune.JOIN_CANDIDATES + autotune.DENSE_CANDIDATES)
         print(json.dumps({"tuned": best}), flush=True)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("oph1")
@@ -692,8 +698,8 @@ def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
 def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, rq, n_launch=8):
     """Plain OPH over all 256 bins (Eq. 6) on a uniform-OPH sketch of the same
     collection: the whole query batch in one call (the library picks the
-    strategy), and one query per launch through the dense scan with its
-    execution knobs tuned for a single query.  Returns (leg, batched pairs,
+    strategy), and one query per launch with the strategy (dense scan or
+    value join) and knobs tuned for a single query.  Returns (leg, batched pairs,
     pairs of the recall query set rq)."""
     import torch
     from paper_1805_11254_gb300 import autotune, hoph
@@ -742,12 +748,12 @@ def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, rq, n_la
         torch.cuda.synchronize()
         ms_b = e0.elapsed_time(e1) / reps
 
-        # one query per launch, dense scan tuned for Q = 1
+        # one query per launch, the strategy and knobs tuned for Q = 1
         planted = [q for q in range(nq) if qw["src"][q] >= 0][:n_launch]
         qs = [q_planes[:, q:q + 1].contiguous() for q in planted]
         best, tune_ms = autotune.tune_query(plan, hoph.HOPH_MODE_OPH_FULL, qs[0], 1, planes,
                                             args.rows, out, cap, cnt, stream,
-                                            candidates=autotune.DENSE_CANDIDATES)
+                                            candidates=autotune.JOIN_CANDIDATES + autotune.DENSE_CANDIDATES)
         for qp in qs[:2]:
             hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_OPH_FULL, qp, 1, planes, args.rows,
                                   out, cap, cnt, None, stream)
@@ -768,8 +774,8 @@ def oph_baseline_leg(args, off, coll_seed, qw, dev, stream, hoph_value, rq, n_la
            "hbm_GB_per_s": plane_bytes / (ms / 1e3) / 1e9,
            "hoph_speedup": hoph_value / v,
            "tuned": best, "tune_ms_by_candidate": tune_ms,
-           "how": "mode OPH_FULL, dense scan of all 256 bins (10.24 GB), one query per launch, "
-                  "%d launches" % len(qs),
+           "how": "mode OPH_FULL over all 256 bins (10.24 GB of planes per launch), one query "
+                  "per launch, %d launches, strategy and knobs tuned for one query" % len(qs),
            "batched": {"value": nq * args.rows / (ms_b / 1e3), "unit": UNIT, "ms_per_batch": ms_b,
                        "queries": nq, "strategy": strategy_b, "accepted": n_b,
                        "hoph_speedup": hoph_value / (nq * args.rows / (ms_b / 1e3))}}

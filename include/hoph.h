@@ -145,7 +145,10 @@ typedef struct {
     int32_t ctas_per_sm;     /* resident CTAs per SM for the scan         */
     int32_t stages;          /* TMA pipeline depth                        */
     int32_t lanes_per_row;   /* join filter: lanes sharing one row (1-8)  */
-    int32_t reserved[2];
+    int32_t sketch_cta_bits; /* sketch: sets whose size has at least this
+                              * many bits get a whole CTA, the rest a warp;
+                              * 0 = library choice, 64 = warps only      */
+    int32_t reserved;
 } hoph_exec;
 
 typedef struct hoph_plan hoph_plan;

@@ -13,6 +13,8 @@ from . import hoph
 
 _cache = {}
 
+QUERY_DEFAULTS = dict(strategy=-1, tile_rows=0, consumer_warps=0, ctas_per_sm=0, stages=0,
+                      lanes_per_row=0)
 JOIN_CANDIDATES = [dict(strategy=1, lanes_per_row=l, consumer_warps=c, stages=s)
                    for l, c, s in ((0, 16, 2), (0, 12, 2), (0, 8, 3), (0, 16, 3), (-2, 16, 2),
                                    (-2, 16, 3), (-2, 16, 4), (-2, 31, 2), (-2, 24, 2))]
@@ -39,7 +41,7 @@ def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity,
     key = (plan.handle, mode, n_queries, n_rows, plan.k, plan.kg, c_planes.element_size())
     if key in _cache:
         best = _cache[key]
-        plan.set_exec(**best)
+        plan.update_exec(**{**QUERY_DEFAULTS, **best})
         return best, {}
     if candidates is None:
         candidates = JOIN_CANDIDATES + DENSE_CANDIDATES if n_queries >= 16 else DENSE_CANDIDATES
@@ -52,7 +54,7 @@ def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity,
         cand = _lanes(cand, W)
         if cand["strategy"] == 0 and n_queries >= 256 and n_rows >= 1 << 20:
             continue  # dense at large batches is tens of times slower; skip
-        plan.set_exec(**cand)
+        plan.update_exec(**{**QUERY_DEFAULTS, **cand})
         try:
             call(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
                  None, stream)
@@ -78,8 +80,49 @@ def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity,
         if best_ms is None or ms < best_ms:
             best, best_ms = cand, ms
     if best is None:
-        plan.set_exec()
+        plan.update_exec(**QUERY_DEFAULTS)
         return None, times
-    plan.set_exec(**best)
+    plan.update_exec(**{**QUERY_DEFAULTS, **best})
+    _cache[key] = best
+    return best, times
+
+
+SKETCH_CANDIDATES = (0, 10, 11, 12, 13, 14, 64)
+
+
+def tune_sketch(plan, d_ids, d_offsets, n_sets, out, stream=None, reps=3,
+                candidates=SKETCH_CANDIDATES):
+    """Pick the size (bits of a set's ID count) from which a set gets a whole
+    CTA instead of one warp, for this batch; 0 is the library's own choice,
+    64 warps only.  Every setting must give the same sketches.  Returns
+    (best bits, {bits: ms})."""
+    import torch
+    key = ("sketch", plan.handle, n_sets, out.element_size())
+    if key in _cache:
+        plan.update_exec(sketch_cta_bits=_cache[key])
+        return _cache[key], {}
+    stream = stream or torch.cuda.current_stream()
+    call = hoph.oph_build_sketches16 if out.element_size() == 2 else hoph.oph_build_sketches
+    times, ref, best, best_ms = {}, None, None, None
+    for bits in candidates:
+        plan.update_exec(sketch_cta_bits=bits)
+        call(plan.handle, d_ids, d_offsets, n_sets, out, stream)
+        stream.synchronize()
+        got = out.cpu()
+        if ref is None:
+            ref = got
+        elif not torch.equal(got, ref):
+            raise RuntimeError("sketch_cta_bits=%d changed the sketches" % bits)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call(plan.handle, d_ids, d_offsets, n_sets, out, stream)
+        e1.record(stream)
+        e1.synchronize()
+        times[bits] = e0.elapsed_time(e1) / reps
+        if best_ms is None or times[bits] < best_ms:
+            best, best_ms = bits, times[bits]
+    plan.update_exec(sketch_cta_bits=best)
     _cache[key] = best
     return best, times

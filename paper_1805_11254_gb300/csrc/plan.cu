@@ -462,7 +462,8 @@ int hoph_plan_set_exec(hoph_plan *plan, const hoph_exec *exec) {
         exec->tile_rows > 256 || exec->consumer_warps < 0 || exec->consumer_warps > 31 ||
         exec->ctas_per_sm < 0 || exec->ctas_per_sm > 8 || exec->stages < 0 || exec->stages > 8 ||
         (exec->lanes_per_row != 0 && exec->lanes_per_row != 1 && exec->lanes_per_row != 2 &&
-         exec->lanes_per_row != 4 && exec->lanes_per_row != 8))
+         exec->lanes_per_row != 4 && exec->lanes_per_row != 8) ||
+        exec->sketch_cta_bits < 0 || exec->sketch_cta_bits > 64)
         return HOPH_ERR_PARAM;
     plan->exec = *exec;
     return HOPH_OK;

@@ -282,18 +282,26 @@ __global__ void bucket_hist_kernel(const int64_t *off, int64_t n, uint32_t *hist
         if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
+// The size bucket from which a set gets a whole CTA: `bits` when given (an
+// execution knob), else sets of at least 2,048 IDs and, when warps > 0 (a
+// batch sketched in one launch), also more than four times the batch's IDs
+// per resident warp.
+__device__ __forceinline__ int cta_bucket(const int64_t *off, int64_t n, int64_t warps, int bits) {
+    if (bits > 0) return bits;
+    int big = kBigBucket;
+    if (warps > 0) {
+        const uint64_t per_warp = (uint64_t)(off[n] - off[0]) / (uint64_t)warps;
+        big = max(big, size_bucket((int64_t)(4 * per_warp)) + 1);
+    }
+    return big;
+}
+
 // exclusive prefix over buckets in descending size order (largest first);
-// *n_big = number of sets that get a CTA each: those of at least 2,048 IDs
-// and, when warps > 0 (a batch sketched in one launch), also more than four
-// times the batch's IDs per resident warp
+// *n_big = number of sets from the CTA bucket up
 __global__ void bucket_base_kernel(const uint32_t *hist, uint32_t *base, uint32_t *n_big,
-                                   const int64_t *off, int64_t n, int64_t warps) {
+                                   const int64_t *off, int64_t n, int64_t warps, int bits) {
     if (threadIdx.x == 0) {
-        int big = kBigBucket;
-        if (warps > 0) {
-            const uint64_t per_warp = (uint64_t)(off[n] - off[0]) / (uint64_t)warps;
-            big = max(big, size_bucket((int64_t)(4 * per_warp)) + 1);
-        }
+        const int big = cta_bucket(off, n, warps, bits);
         uint32_t run = 0;
         for (int b = kBuckets - 1; b >= 0; --b) {
             if (b == big - 1) *n_big = run;
@@ -307,7 +315,7 @@ __global__ void bucket_base_kernel(const uint32_t *hist, uint32_t *base, uint32_
 // (a query batch): histogram, prefix and large-set count, scatter.
 __global__ void __launch_bounds__(1024) bucket_small_kernel(const int64_t *off, int64_t n,
                                                             uint32_t *n_big, int32_t *order,
-                                                            int64_t warps) {
+                                                            int64_t warps, int bits) {
     __shared__ uint32_t h[kBuckets], cur[kBuckets];
     for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) h[i] = 0;
     __syncthreads();
@@ -315,8 +323,7 @@ __global__ void __launch_bounds__(1024) bucket_small_kernel(const int64_t *off, 
         atomicAdd(&h[size_bucket(off[i + 1] - off[i])], 1u);
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint64_t per_warp = (uint64_t)(off[n] - off[0]) / (uint64_t)warps;
-        const int big = max(kBigBucket, size_bucket((int64_t)(4 * per_warp)) + 1);
+        const int big = cta_bucket(off, n, warps, bits);
         uint32_t run = 0;
         for (int b = kBuckets - 1; b >= 0; --b) {
             if (b == big - 1) *n_big = run;
@@ -461,7 +468,7 @@ int build_work_list(hoph_plan *plan, const int64_t *d_offsets, int64_t n_sets, u
     if (n_sets <= kSmallList) {
         bucket_small_kernel<<<1, 1024, 0, s>>>(
             d_offsets, n_sets, n_big, order,
-            (int64_t)plan->num_sms * kResidentCtas * kSketchWarps);
+            (int64_t)plan->num_sms * kResidentCtas * kSketchWarps, plan->exec.sketch_cta_bits);
         HOPH_CUDA_TRY(cudaGetLastError());
         plan->launches += 1;
         return HOPH_OK;
@@ -472,7 +479,8 @@ int build_work_list(hoph_plan *plan, const int64_t *d_offsets, int64_t n_sets, u
     bucket_hist_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, hist);
     const int64_t warps =
         n_sets >= kSplitPhases ? 0 : (int64_t)plan->num_sms * kResidentCtas * kSketchWarps;
-    bucket_base_kernel<<<1, 32, 0, s>>>(hist, base, n_big, d_offsets, n_sets, warps);
+    bucket_base_kernel<<<1, 32, 0, s>>>(hist, base, n_big, d_offsets, n_sets, warps,
+                                        plan->exec.sketch_cta_bits);
     bucket_scatter_kernel<<<g, 256, 0, s>>>(d_offsets, n_sets, base, cursor, order);
     HOPH_CUDA_TRY(cudaGetLastError());
     plan->launches += 3;

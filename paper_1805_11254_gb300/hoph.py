@@ -85,7 +85,7 @@ class hoph_exec(ctypes.Structure):
     _fields_ = [("strategy", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
                 ("consumer_warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("sketch_cta_bits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class HophError(RuntimeError):
@@ -345,6 +345,7 @@ class Plan:
         else:
             self.handle = hoph_plan_create(self.params)
         self.info = hoph_plan_get_info(self.handle)
+        self.exec_kwargs = dict(strategy=-1)
         self.G = self.info.groups
         self.k = k
         self.kg = k_group
@@ -368,9 +369,19 @@ class Plan:
         self.close()
 
     def set_exec(self, strategy=-1, tile_rows=0, consumer_warps=0, ctas_per_sm=0, stages=0,
-                 lanes_per_row=0):
+                 lanes_per_row=0, sketch_cta_bits=0):
+        """Replace all execution knobs (kept in self.exec_kwargs)."""
         hoph_plan_set_exec(self.handle, hoph_exec(strategy, tile_rows, consumer_warps,
-                                                  ctas_per_sm, stages, lanes_per_row))
+                                                  ctas_per_sm, stages, lanes_per_row,
+                                                  sketch_cta_bits))
+        self.exec_kwargs = dict(strategy=strategy, tile_rows=tile_rows,
+                                consumer_warps=consumer_warps, ctas_per_sm=ctas_per_sm,
+                                stages=stages, lanes_per_row=lanes_per_row,
+                                sketch_cta_bits=sketch_cta_bits)
+
+    def update_exec(self, **knobs):
+        """Change some execution knobs, keeping the others."""
+        self.set_exec(**{**self.exec_kwargs, **knobs})
 
     def check(self, stream=None):
         rc = hoph_sync_status(self.handle, stream)

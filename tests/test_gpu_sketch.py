@@ -156,10 +156,13 @@ def test_synth_ids_match_host_twin(kind):
     assert np.array_equal(out.cpu().numpy().view(np.uint32), want)
 
 
+@pytest.mark.parametrize("bits", [0, 10, 13, 64])
 @pytest.mark.parametrize("hash_perm", [False, True])
-def test_large_sets_take_the_cta_path(hash_perm):
-    """With a work list (>= 64 sets), sets of >= 2048 IDs are sketched by a
-    whole CTA; the result must not depend on which path a set took."""
+def test_large_sets_take_the_cta_path(hash_perm, bits):
+    """With a work list (>= 64 sets), the large sets are sketched by a whole
+    CTA (from 2,048 IDs by default, from 2^(bits-1) IDs with the
+    sketch_cta_bits knob, never with 64); the result must not depend on which
+    path a set took."""
     dev = device()
     rng = np.random.default_rng(12)
     big = [2047, 2048, 2049, 4096, 5000, 30001, 100000]
@@ -174,6 +177,7 @@ def test_large_sets_take_the_cta_path(hash_perm):
     ids, off = synth.pack_sets(sets)
     kind = hoph.HOPH_PERM_HASH61 if hash_perm else hoph.HOPH_PERM_TABLE
     with hoph.Plan(D, k, kg, *ab, perm_kind=kind, seed=3) as plan:
+        plan.update_exec(sketch_cta_bits=bits)  # which sets get a CTA: never the result
         got = _gpu_sketch(plan, ids, off, dev)
     lo = oc.layout(D, k, kg, *ab)
     if hash_perm:
