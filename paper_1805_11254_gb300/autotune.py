@@ -54,8 +54,8 @@ def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity,
         cand = _lanes(cand, W)
         if cand["strategy"] == 0 and n_queries >= 256 and n_rows >= 1 << 20:
             continue  # dense at large batches is tens of times slower; skip
-        plan.update_exec(**{**QUERY_DEFAULTS, **cand})
         try:
+            plan.update_exec(**{**QUERY_DEFAULTS, **cand})
             call(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
                  None, stream)
         except hoph.HophError:

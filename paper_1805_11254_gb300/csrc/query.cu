@@ -995,11 +995,47 @@ __device__ int64_t lower_bound_key(const ulonglong2 *a, int64_t n, unsigned long
     return l;
 }
 
+// The call's counters folded into the caller's hoph_stats (one thread).
+struct StatsFold {
+    const unsigned long long *st;
+    const unsigned long long *n_cand;  // null for the dense scan
+    int64_t pairs, first_pass_bytes;
+    int32_t G, Gs, strategy;
+    hoph_stats *out;                   // null: no statistics wanted
+};
+
+__device__ void stats_fold(const StatsFold &f) {
+    if (!f.out) return;
+    const unsigned long long *st = f.st;
+    const int64_t pairs = f.pairs;
+    const int G = f.G, Gs = f.Gs;
+    hoph_stats *out = f.out;
+    out->entering[0] += pairs;
+    const int64_t acc0 = (int64_t)st[16], cont = (Gs < G) ? (int64_t)st[1] : 0;
+    out->accepted[0] += acc0;
+    out->rejected[0] += pairs - acc0 - cont;
+    for (int g = 1; g < G && Gs < G; ++g) {
+        out->entering[g] += (int64_t)st[g];
+        out->accepted[g] += (int64_t)st[16 + g];
+        out->rejected[g] += (int64_t)st[32 + g];
+    }
+    out->sketch_bytes += f.first_pass_bytes + (int64_t)st[48];
+    out->join_hits += (int64_t)st[49];
+    if (f.n_cand) out->rows_counted += (int64_t)*f.n_cand;
+    out->strategy = f.strategy;
+}
+
+__global__ void stats_fold_kernel(const StatsFold f) {
+    if (threadIdx.x == 0) stats_fold(f);
+}
+
+// Sort the accepted pairs by (query, row); thread 0 also folds the statistics.
 __global__ void __launch_bounds__(kSortThreads) sort_pairs_kernel(
     hoph_pair *out, const unsigned long long *count, int64_t cap, ulonglong2 *bufA,
-    ulonglong2 *bufB, int32_t *status) {
+    ulonglong2 *bufB, int32_t *status, const StatsFold f) {
     extern __shared__ __align__(1024) unsigned char smem[];
     ulonglong2 *sv = reinterpret_cast<ulonglong2 *>(smem);
+    if (threadIdx.x == 0) stats_fold(f);
     const unsigned long long total = *count;
     if (total > (unsigned long long)cap && threadIdx.x == 0) hoph_flag(status, HOPH_ERR_CAPACITY);
     const int64_t n = (int64_t)min(total, (unsigned long long)cap);
@@ -1053,25 +1089,6 @@ __global__ void __launch_bounds__(kSortThreads) sort_pairs_kernel(
     }
 }
 
-// fold the call's counters into the caller's hoph_stats
-__global__ void stats_fold_kernel(const unsigned long long *st, const unsigned long long *n_cand,
-                                  int64_t pairs, int G, int Gs, int64_t first_pass_bytes,
-                                  int strategy, hoph_stats *out) {
-    if (threadIdx.x != 0 || !out) return;
-    out->entering[0] += pairs;
-    const int64_t acc0 = (int64_t)st[16], cont = (Gs < G) ? (int64_t)st[1] : 0;
-    out->accepted[0] += acc0;
-    out->rejected[0] += pairs - acc0 - cont;
-    for (int g = 1; g < G && Gs < G; ++g) {
-        out->entering[g] += (int64_t)st[g];
-        out->accepted[g] += (int64_t)st[16 + g];
-        out->rejected[g] += (int64_t)st[32 + g];
-    }
-    out->sketch_bytes += first_pass_bytes + (int64_t)st[48];
-    out->join_hits += (int64_t)st[49];
-    if (n_cand) out->rows_counted += (int64_t)*n_cand;
-    out->strategy = strategy;
-}
 
 // ===========================================================================
 // Per-pair counts (no early exit): warp per pair, lanes over bins
@@ -1605,17 +1622,25 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         launches += 1;
     }
 
+    StatsFold sf;
+    sf.st = st;
+    sf.n_cand = n_cand;
+    sf.pairs = n_queries * n_rows;
+    sf.first_pass_bytes = (n_rows * (int64_t)W + n_queries * (int64_t)W) * ES;
+    sf.G = G;
+    sf.Gs = Gs;
+    sf.strategy = strategy;
+    sf.out = d_stats;
     if (last) {
         HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
-        sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(d_out, pa.out_count, out_capacity,
-                                                                  sortA, sortB, plan->d_status);
+        sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(
+            d_out, pa.out_count, out_capacity, sortA, sortB, plan->d_status, sf);
+    } else {
+        stats_fold_kernel<<<1, 32, 0, s>>>(sf);
     }
-    const int64_t fp_bytes = (n_rows * (int64_t)W + n_queries * (int64_t)W) * ES;
-    stats_fold_kernel<<<1, 32, 0, s>>>(st, n_cand, n_queries * n_rows, G, Gs, fp_bytes, strategy,
-                                       d_stats);
     HOPH_CUDA_TRY(cudaGetLastError());
     hoph_timing_mark(plan, 4, s);
-    plan->launches += launches + (last ? 2 : 1);
+    plan->launches += launches + 1;
     return HOPH_OK;
 }
 
