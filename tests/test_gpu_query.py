@@ -386,3 +386,29 @@ def test_self_join_is_the_upper_triangle_of_the_all_pairs_query(small, mode, ab,
     assert m == len(want)
     assert [(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"])) for p in got] \
         == [tuple(int(x) for x in w) for w in want]
+
+
+def test_compact_planes_with_a_hashed_join():
+    """Compact planes over a key space that needs the hashed group map and
+    the key table (D = 256 x 65,535, k = 256 bins of 65,535 values, the
+    widest a 16-bit offset allows; all four groups of 64 bins scanned as
+    plain OPH): the oracle's pairs through the join."""
+    dev = device()
+    D, k, kg = 256 * 65535, 256, 64
+    ids, off, q_ids, q_off = _planted_workload(2000, 200, 900, 40, D, 47)
+    thr = (7, 10)
+    with hoph.Plan(D, k, kg, seed=9, thr=thr, epsilon=1e-4) as plan:
+        assert plan.info.max_bin_width == 0xFFFF
+        c = plan.sketch(to_dev(ids, dev), to_dev(off, dev), len(off) - 1)
+        q = plan.sketch(to_dev(q_ids, dev), to_dev(q_off, dev), len(q_off) - 1)
+        c16 = plan.sketch16(to_dev(ids, dev), to_dev(off, dev), len(off) - 1)
+        q16 = plan.sketch16(to_dev(q_ids, dev), to_dev(q_off, dev), len(q_off) - 1)
+        plan.check()
+        z = np.diff(oc.layout(D, k, kg)[::kg]).astype(np.uint64)
+        want = oc.query("oph_full", planes_to_rows(q), planes_to_rows(c), kg, thr[0], thr[1],
+                        1e-4, z=z)
+        assert want["count"] > 0
+        plan.set_exec(strategy=1)
+        pairs, n, st = plan.query("oph_full", q16, q16.shape[1], c16, c16.shape[1], stats=True)
+        assert st.strategy == 1
+        assert pairs_tuples(pairs) == oracle_tuples(want)
