@@ -1173,6 +1173,9 @@ def shingle_leg(args, dev, stream, peaks, q_batch=1024, n_planted=32):
         st = torch.zeros(hoph.STATS_WORDS, dtype=torch.int64, device=dev)
         batches = [q_planes[:, b:b + q_batch].contiguous() for b in range(0, nq, q_batch)]
         sizes_b = [bq.shape[1] for bq in batches]
+        from paper_1805_11254_gb300 import autotune
+        best, tune_ms = autotune.tune_query(plan, hoph.HOPH_MODE_HOPH, batches[0], sizes_b[0],
+                                            planes, args.shingle_rows, outp, cap, cnt, stream)
         hoph.hoph_query_batch(plan.handle, "hoph", batches[0], sizes_b[0], planes,
                               args.shingle_rows, outp, cap, cnt, st, stream)
         torch.cuda.synchronize()
@@ -1188,9 +1191,12 @@ def shingle_leg(args, dev, stream, peaks, q_batch=1024, n_planted=32):
         torch.cuda.synchronize()
         plan.check()
         ms = e0.elapsed_time(e1)
+        plane_gb = args.shingle_rows * KG4 * 4 / 1e9
         out["hoph_query"] = {
             "pair_comparisons_per_s": nq * args.shingle_rows / (ms / 1e3),
             "ms_per_1024_batch": ms / len(batches), "batches": len(batches),
+            "first_plane_GB_per_s": plane_gb / (ms / len(batches) / 1e3),
+            "autotune": {"best": best, "ms_by_candidate": tune_ms},
             "strategy": int(stats.strategy), "candidate_rows_first_batch": int(stats.rows_counted),
             "planted_found": sum((q, int(r)) in found for q, r in enumerate(src)),
             "planted": n_planted}

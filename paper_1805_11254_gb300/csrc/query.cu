@@ -102,6 +102,13 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
     return h;
 }
 
+// Slot of a key in the hashed group map of 2^(32 - shift) slots: the top bits
+// of the key times 2^32 / golden ratio (Knuth's multiplicative hashing; two
+// instructions per lookup in the filter).
+__host__ __device__ __forceinline__ uint32_t map_slot(uint32_t key, uint32_t shift) {
+    return (key * 0x9E3779B1u) >> shift;
+}
+
 constexpr unsigned long long kNoKey = ~0ull;  // empty slot of the key table
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 constexpr uint32_t kNil = 0xFFFFFFFFu;  // end of a key's query list
@@ -486,8 +493,8 @@ struct IndexArgs {
     uint32_t *next;      // [n_q << wshift]: entry (q << wshift) | w -> next entry
     int32_t wshift;      // bits of a scanned-bin index
     uint32_t *gmap;      // per 16 map slots: an even / an odd query has slot j (bits j, 16 + j; swapped in odd words)
-    int32_t map_hashed;  // map slot = mix32(key) & map_mask, else the key itself
-    uint32_t map_mask;
+    int32_t map_hashed;  // map slot = map_slot(key, map_shift), else the key itself
+    uint32_t map_shift;
     int32_t csr_hashed;  // key slot from the key table, else the key itself
     unsigned long long *tkey;
     uint32_t tmask;
@@ -539,7 +546,7 @@ __global__ void join_count_kernel(const IndexArgs a) {
         if (lane == 0) a.q_emask[q * a.mask_words + c] = em;
         if (valid && !e) {
             const uint32_t key = (uint32_t)a.binbase[w] + v;
-            const uint32_t mi = a.map_hashed ? (mix32(key) & a.map_mask) : key;
+            const uint32_t mi = a.map_hashed ? map_slot(key, a.map_shift) : key;
             // slot j of word mi >> 4: even-query bit at j and odd-query bit at
             // 16 + j, the halves swapped in odd words, so a right rotation of
             // the word by (mi & 31) brings the even bit to 0 and the odd to 16
@@ -569,7 +576,7 @@ struct FilterArgs {
     uint32_t stage_bytes, stage_stride;
     const uint32_t *gmap;     // 2-bit group map over the map slots
     uint32_t gmap_words;      // the last word is zero: empty bins look up its slot 0
-    uint32_t map_mask;        // hashed map: slot = mix32(key) & map_mask
+    uint32_t map_shift;       // hashed map: slot = map_slot(key, map_shift)
     const uint64_t *binbase;  // key = lo[w] + value
     const uint16_t *row_min;  // [W + 1]
     int32_t keep_empty;       // rows without a non-empty scanned bin are candidates
@@ -690,7 +697,7 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
                 for (int e = 0; e < VPC; ++e) {
                     const bool full_bin = x[e] != empty_of<E>();
                     const uint32_t key = kb[c * VPC + e] + x[e];
-                    uint32_t mi = HASHED ? (mix32(key) & a.map_mask) : key;
+                    uint32_t mi = HASHED ? map_slot(key, a.map_shift) : key;
                     // direct map, uint32 values: the empty marker lands on the
                     // bin's guard key (base - 1), which no query sets
                     if (HASHED || sizeof(E) != 4) mi = full_bin ? mi : zero_slot;
@@ -1367,6 +1374,8 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     const uint64_t keys = map_hashed ? plain_keys : plain_keys + W + 1;
     const uint64_t *binbase = map_hashed ? plan->d_lo : plan->d_kb;
     const uint64_t map_slots = map_hashed ? kHashedMapSlots : keys;
+    uint32_t map_shift = 32;  // hashed map: 32 - log2(kHashedMapSlots)
+    while ((1ull << (32 - map_shift)) < kHashedMapSlots) --map_shift;
     const bool csr_hashed = keys > kMaxJoinKeys;
     uint64_t csr_slots = keys;
     if (csr_hashed) {
@@ -1477,7 +1486,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ia.wshift = wshift;
         ia.gmap = gmap;
         ia.map_hashed = map_hashed;
-        ia.map_mask = (uint32_t)(map_slots - 1);
+        ia.map_shift = map_shift;
         ia.csr_hashed = csr_hashed;
         ia.tkey = tkey;
         ia.tmask = (uint32_t)(csr_slots - 1);
@@ -1502,7 +1511,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         fa.W = W;
         fa.gmap = gmap;
         fa.gmap_words = (uint32_t)(map_slots / 16 + 2);  // + a zero word for empty bins
-        fa.map_mask = (uint32_t)(map_slots - 1);
+        fa.map_shift = map_shift;
         fa.binbase = binbase;
         fa.row_min = pa.thr + 2 * (W + 1);
         const int K0 = hoph_effective(fp.rule, W, W, 0);
