@@ -495,7 +495,7 @@ struct IndexArgs {
     uint32_t *gmap;      // per 16 map slots: an even / an odd query has slot j (bits j, 16 + j; swapped in odd words)
     int32_t map_hashed;  // map slot = map_slot(key, map_shift), else the key itself
     uint32_t map_shift;
-    int32_t csr_hashed;  // key slot from the key table, else the key itself
+    int32_t keys_hashed;  // key slot from the key table, else the key itself
     unsigned long long *tkey;
     uint32_t tmask;
     int32_t *status;
@@ -552,7 +552,7 @@ __global__ void join_count_kernel(const IndexArgs a) {
             // the word by (mi & 31) brings the even bit to 0 and the odd to 16
             const uint32_t word = mi >> 4;
             atomicOr(a.gmap + word, 1u << ((mi & 15u) + ((((uint32_t)q ^ word) & 1u) << 4)));
-            const uint32_t slot = a.csr_hashed ? table_insert(a.tkey, a.tmask, key) : key;
+            const uint32_t slot = a.keys_hashed ? table_insert(a.tkey, a.tmask, key) : key;
             if (slot == kNoSlot) {
                 hoph_flag(a.status, HOPH_ERR_CAPACITY);
             } else {
@@ -740,7 +740,7 @@ struct CountArgs {
     const uint32_t *cand;
     const unsigned long long *n_cand;
     const uint64_t *binbase;  // key = lo[w] + value
-    int32_t csr_hashed;       // key slots from the key table
+    int32_t keys_hashed;       // key slots from the key table
     const unsigned long long *tkey;
     uint32_t tmask;
     const uint32_t *head;     // key slot -> first entry of its query list
@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
             f[c] = kNil;
             if (woff[c] >= 0 && v[c] != empty_of<E>()) {
                 const uint32_t key = kbase[c] + v[c];
-                const uint32_t slot = a.csr_hashed ? table_find(a.tkey, a.tmask, key) : key;
+                const uint32_t slot = a.keys_hashed ? table_find(a.tkey, a.tmask, key) : key;
                 if (slot != kNoSlot) f[c] = __ldg(a.head + slot);
             }
         }
@@ -1376,15 +1376,15 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     const uint64_t map_slots = map_hashed ? kHashedMapSlots : keys;
     uint32_t map_shift = 32;  // hashed map: 32 - log2(kHashedMapSlots)
     while ((1ull << (32 - map_shift)) < kHashedMapSlots) --map_shift;
-    const bool csr_hashed = keys > kMaxJoinKeys;
-    uint64_t csr_slots = keys;
-    if (csr_hashed) {
-        csr_slots = 1024;
-        while (csr_slots < 2ull * (uint64_t)n_queries * W) csr_slots <<= 1;
+    const bool keys_hashed = keys > kMaxJoinKeys;
+    uint64_t head_slots = keys;
+    if (keys_hashed) {
+        head_slots = 1024;
+        while (head_slots < 2ull * (uint64_t)n_queries * W) head_slots <<= 1;
     }
     bool join_ok = mode != HOPH_MODE_MINWISE_FULL && fp.rule != HOPH_EMPTY_EITHER &&
                    tma_base_ok && kg % (128 / ES) == 0 && W <= 256 && n_queries <= 4096 &&
-                   n_rows < (1ll << 32) && csr_slots < (1ull << 31) &&
+                   n_rows < (1ll << 32) && head_slots < (1ull << 31) &&
                    map_slots / 4 + 2 * 32 * W * ES + 8 * W + 4096 <= (uint64_t)kSmemLimit;
     for (int K = 1; K <= W && join_ok; ++K) join_ok = tab[K] >= 1;
     int strategy = plan->exec.strategy;
@@ -1405,10 +1405,10 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         bump.off = 0;
         bump.take(st_b);
         if (strategy == 1) {
-            bump.take(csr_slots * 4);                                   // list heads
+            bump.take(head_slots * 4);                                   // list heads
             bump.take(((size_t)n_queries << wshift) * 4);               // list links
             bump.take((map_slots / 16 + 2) * 4);                        // group map
-            bump.take(csr_hashed ? csr_slots * 8 : 8);                  // key table
+            bump.take(keys_hashed ? head_slots * 8 : 8);                  // key table
             bump.take((size_t)n_queries * mask_words * 4);              // q_emask
             bump.take((size_t)n_queries * 4 + 4);                       // allempty + count
             bump.take(8);                                               // n_cand
@@ -1430,10 +1430,10 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     unsigned long long *tkey = nullptr;
     unsigned long long *n_cand = nullptr;
     if (strategy == 1) {
-        head = (uint32_t *)bump.take(csr_slots * 4);
+        head = (uint32_t *)bump.take(head_slots * 4);
         next = (uint32_t *)bump.take(((size_t)n_queries << wshift) * 4);
         gmap = (uint32_t *)bump.take((map_slots / 16 + 2) * 4);
-        tkey = (unsigned long long *)bump.take(csr_hashed ? csr_slots * 8 : 8);
+        tkey = (unsigned long long *)bump.take(keys_hashed ? head_slots * 8 : 8);
         q_emask = (uint32_t *)bump.take((size_t)n_queries * mask_words * 4);
         allempty = (int32_t *)bump.take((size_t)n_queries * 4 + 4);
         n_allempty = (uint32_t *)(allempty + n_queries);
@@ -1487,17 +1487,17 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ia.gmap = gmap;
         ia.map_hashed = map_hashed;
         ia.map_shift = map_shift;
-        ia.csr_hashed = csr_hashed;
+        ia.keys_hashed = keys_hashed;
         ia.tkey = tkey;
-        ia.tmask = (uint32_t)(csr_slots - 1);
+        ia.tmask = (uint32_t)(head_slots - 1);
         ia.status = plan->d_status;
         ia.q_emask = q_emask;
         ia.allempty = allempty;
         ia.n_allempty = n_allempty;
         join_init_kernel<<<(unsigned)plan->num_sms * 4, 256, 0, s>>>(
-            head, (int64_t)csr_slots, gmap, (int64_t)(map_slots / 16 + 2), st, kStatWords,
+            head, (int64_t)head_slots, gmap, (int64_t)(map_slots / 16 + 2), st, kStatWords,
             n_allempty, n_cand, first ? d_out_count : nullptr);
-        if (csr_hashed) HOPH_CUDA_TRY(cudaMemsetAsync(tkey, 0xFF, csr_slots * 8, s));
+        if (keys_hashed) HOPH_CUDA_TRY(cudaMemsetAsync(tkey, 0xFF, head_slots * 8, s));
         const unsigned qb = (unsigned)((n_queries * 32 + 255) / 256);
         join_count_kernel<E><<<qb, 256, 0, s>>>(ia);
         HOPH_CUDA_TRY(cudaGetLastError());
@@ -1564,9 +1564,9 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ca.cand = cand;
         ca.n_cand = n_cand;
         ca.binbase = binbase;
-        ca.csr_hashed = csr_hashed;
+        ca.keys_hashed = keys_hashed;
         ca.tkey = tkey;
-        ca.tmask = (uint32_t)(csr_slots - 1);
+        ca.tmask = (uint32_t)(head_slots - 1);
         ca.head = head;
         ca.next = next;
         ca.wshift = wshift;
