@@ -581,10 +581,84 @@ def e2e_leg(args, plan, qw, planes, dev, stream):
     for _ in range(args.e2e_steps):
         once()
     dt = (time.perf_counter() - t0) / args.e2e_steps
-    return {"value": nq * args.rows / dt, "unit": UNIT,
-            "h2d_bytes_per_step": int(h_ids.numel() * 4 + h_off.numel() * 8),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
+    h2d = int(h_ids.numel() * 4 + h_off.numel() * 8)
+    serial = {"value": nq * args.rows / dt, "ms_per_step": dt * 1e3, "d2h_bytes_per_step": d2h}
+    pipe = e2e_in_flight(args, plan, h_ids, h_off, planes, dev)
+    best = pipe if pipe["value"] > serial["value"] else serial
+    return {"value": best["value"], "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": int(best["d2h_bytes_per_step"]),
+            "ms_per_step": best["ms_per_step"],
+            "schedule": best.get("schedule", "one batch at a time"),
+            "serial": serial, "in_flight": pipe,
             "path": "pinned host sets -> oph_build_sketches -> hoph_query_batch -> host pairs"}
+
+
+def e2e_in_flight(args, plan, h_ids, h_off, planes, dev, n_lanes=3, window=4096):
+    """The end-to-end step with several batches in flight: each lane (its own
+    plan and stream) copies a batch's sets in, sketches and queries them and
+    copies the count and the first `window` pairs back; a lane's results are
+    read (the rest of its pairs copied if there are more) before it takes the
+    next batch.  Host wall time over K steps."""
+    import torch
+    from paper_1805_11254_gb300 import hoph
+    nq = args.queries
+    lanes = []
+    for _ in range(n_lanes):
+        p = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
+        p.set_exec(**plan.exec_kwargs)
+        lanes.append(dict(
+            plan=p, s=torch.cuda.Stream(device=dev), d_ids=torch.empty_like(h_ids, device=dev),
+            d_off=torch.empty_like(h_off, device=dev),
+            q=torch.empty((p.G, nq, KG), dtype=torch.int32, device=dev),
+            out=torch.empty((1 << 20, 2), dtype=torch.int64, device=dev),
+            cnt=torch.zeros(1, dtype=torch.int64, device=dev),
+            h_cnt=torch.zeros(1, dtype=torch.int64).pin_memory(),
+            h_out=torch.empty((1 << 20, 2), dtype=torch.int64).pin_memory(),
+            ev=torch.cuda.Event(), busy=False, extra=0))
+
+    def issue(ln):
+        s = ln["s"]
+        with torch.cuda.stream(s):
+            ln["d_ids"].copy_(h_ids, non_blocking=True)
+            ln["d_off"].copy_(h_off, non_blocking=True)
+            hoph.oph_build_sketches(ln["plan"].handle, ln["d_ids"], ln["d_off"], nq, ln["q"], s)
+            hoph.hoph_query_batch(ln["plan"].handle, hoph.HOPH_MODE_HOPH, ln["q"], nq, planes,
+                                  args.rows, ln["out"], 1 << 20, ln["cnt"], None, s)
+            ln["h_cnt"].copy_(ln["cnt"], non_blocking=True)
+            ln["h_out"][:window].copy_(ln["out"][:window], non_blocking=True)
+            ln["ev"].record(s)
+        ln["busy"] = True
+
+    def finish(ln):
+        ln["ev"].synchronize()
+        n = min(int(ln["h_cnt"][0]), 1 << 20)
+        if n > window:  # the rest of the pairs
+            ln["h_out"][window:n].copy_(ln["out"][window:n])
+            ln["extra"] += 16 * (n - window)
+        ln["busy"] = False
+
+    def run(k):
+        for i in range(k):
+            ln = lanes[i % n_lanes]
+            if ln["busy"]:
+                finish(ln)
+            issue(ln)
+        for ln in lanes:
+            if ln["busy"]:
+                finish(ln)
+    run(3 * n_lanes)
+    for ln in lanes:
+        ln["extra"] = 0
+    t0 = time.perf_counter()
+    run(args.e2e_steps)
+    dt = (time.perf_counter() - t0) / args.e2e_steps
+    extra = sum(ln["extra"] for ln in lanes) / args.e2e_steps
+    for ln in lanes:
+        ln["plan"].check()
+        ln["plan"].close()
+    return {"value": nq * args.rows / dt, "ms_per_step": dt * 1e3,
+            "d2h_bytes_per_step": 8 + 16 * window + extra,
+            "schedule": "%d batches in flight (one plan and stream each)" % n_lanes}
 
 
 EQUAL_RECALL_EPS = (1e-4, 1e-5, 1e-6, 1e-8, 0.0)
