@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import subprocess
 import sys
 import time
@@ -198,9 +199,31 @@ def cpu_baseline(qw, off, coll_seed, target_s, n_rows):
     t, nq = cpu_oracle_pass(qw, off, coll_seed, probe, threads, lo, perm, z)
     rows = int(min(n_rows, max(probe, probe * target_s / max(t, 1e-6))))
     t, nq = cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z)
+    t1, _ = cpu_oracle_pass(qw, off, coll_seed, probe, 1, lo, perm, z)  # one core, small sample
     return {"value": nq * rows / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "cpu_model": cpu_model(), "value_one_core": nq * probe / t1,
             "sample": "oracle sketches of the %d query sets + (1:2)HOPH comparison against "
-                      "collection rows 0..%d (%d pairs, %.1f s)" % (nq, rows - 1, nq * rows, t)}
+                      "collection rows 0..%d (%d pairs, %.1f s); one core: rows 0..%d"
+                      % (nq, rows - 1, nq * rows, t, probe - 1)}
+
+
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo or lscpu), for the record."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args):
