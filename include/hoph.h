@@ -256,12 +256,12 @@ int hoph_query_batch16(hoph_plan *plan, uint32_t mode, const uint16_t *d_query_p
  *   batch       rows taken as queries per block (1..4096): block b compares
  *               rows b*batch .. b*batch+batch-1 with rows b*batch .. n_rows-1,
  *               so about n_rows^2 / 2 pairs are compared in all.
- *   d_out, out_capacity, d_out_count, d_stats   as for hoph_query_batch (the
- *               statistics count every pair a block compares, including
- *               those with i >= j inside the block, which are never output).
- * Modes GOPH, HOPH and OPH_FULL (not MinWise).  The plan owns a buffer for
- * one block's query planes (G * batch * k' * 4 bytes; growing it
- * synchronises the device).  n_rows < 2^32.
+ *   d_out, out_capacity, d_out_count, d_stats   as for hoph_query_batch; the
+ *               statistics cover exactly the pairs i < j (entering[0] sums to
+ *               n_rows (n_rows - 1) / 2): a block skips the pairs i >= j
+ *               among its own rows before counting or deciding them.
+ * Modes GOPH, HOPH and OPH_FULL (not MinWise).  A block reads its query
+ * planes in place (no copy).  n_rows < 2^32.
  */
 int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int64_t n_rows,
                    int64_t batch, hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,

@@ -163,8 +163,6 @@ struct hoph_plan {
     // scratch
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
-    void *d_aux = nullptr;      // hoph_self_join: one block's query planes
-    size_t aux_bytes = 0;
     hoph_exec exec{};
     // optional event timing of hoph_query_batch phases (bench / tooling)
     bool timing = false;

@@ -166,7 +166,6 @@ void plan_free(hoph_plan *pl) {
     cudaFree(pl->d_minwise);
     cudaFree(pl->d_status);
     cudaFree(pl->d_scratch);
-    cudaFree(pl->d_aux);
     if (pl->h_status) cudaFreeHost(pl->h_status);
     delete pl;
 }

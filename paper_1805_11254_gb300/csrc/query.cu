@@ -140,7 +140,7 @@ __device__ __forceinline__ uint32_t table_find(const unsigned long long *tkey, u
 
 __device__ __forceinline__ void emit_pair(const PairArgs &a, uint32_t q, int64_t row, int groups,
                                           int matches) {
-    if (a.self_off >= 0) {  // one unordered pair per (i, j), i < j
+    if (a.self_off >= 0) {  // one unordered pair per (i, j), i < j (checked again here)
         if (row <= (int64_t)q) return;
         q += (uint32_t)a.self_off;
         row += a.self_off;
@@ -324,6 +324,7 @@ __device__ __forceinline__ void score_tile_dense(
             ++q;
         }
         if (q >= a.n_q) break;
+        if (a.self_off >= 0 && row0 + rl <= (int64_t)q) continue;  // pair i >= j of a self-join
         const E *qb = static_cast<const E *>(a.qry) + (int64_t)q * a.kg;
         int m = 0, both = 0, one = 0;
         if constexpr (cached) {
@@ -574,7 +575,8 @@ struct FilterArgs {
     int32_t lanes_per_row;              // W / lanes_per_row bins per lane (16 or 32)
     int64_t n_tiles;
     uint32_t stage_bytes, stage_stride;
-    const uint32_t *gmap;     // 2-bit group map over the map slots
+    const uint32_t *gmap;     // 2-bit group map over the map slots (16-byte aligned,
+                              // zero-padded to a multiple of 4 words)
     uint32_t gmap_words;      // the last word is zero: empty bins look up its slot 0
     uint32_t map_shift;       // hashed map: slot = map_slot(key, map_shift)
     const uint64_t *binbase;  // key = lo[w] + value
@@ -620,13 +622,12 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
     uint64_t *empty = full + 8;
     volatile int32_t *abort_flag = reinterpret_cast<volatile int32_t *>(smem + L.abort_flag);
     uint16_t *s_rmin = reinterpret_cast<uint16_t *>(smem + L.row_min);
-    uint32_t *s_gmap = reinterpret_cast<uint32_t *>(smem + L.gmap);
+    const uint32_t *s_gmap = reinterpret_cast<const uint32_t *>(smem + L.gmap);
     unsigned char *stages = smem + L.stages;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = a.tile_rows;
     for (int i = tid; i <= a.W; i += blockDim.x) s_rmin[i] = a.row_min[i];
-    for (uint32_t i = tid; i < a.gmap_words; i += blockDim.x) s_gmap[i] = a.gmap[i];
     if (tid == 0) {
         *abort_flag = 0;
         for (int s = 0; s < a.stages; ++s) {
@@ -642,6 +643,17 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
             produce_tiles(&map, stages, full, empty, abort_flag, a.stages, a.stage_bytes,
                           a.stage_stride, a.n_tiles, R, a.status, true);
         return;
+    }
+    {
+        // the consumers copy the group map (16-byte pieces; the map is padded
+        // to a multiple of four words) while the first tiles are in flight
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.gmap);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem + L.gmap);
+        const uint32_t n4 = (a.gmap_words + 3) / 4;
+        const uint32_t nt = (uint32_t)a.n_cons * 32;
+#pragma unroll 4
+        for (uint32_t i = tid; i < n4; i += nt) dst[i] = __ldg(src + i);
+        named_bar_sync(1, nt);
     }
 
     const int lpr = a.lanes_per_row;
@@ -854,8 +866,9 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
             if (n_allempty > 0 && d00 != HOPH_REJECT) {
                 for (int base = 0; base < n_allempty; base += 32) {
                     if (*nsurv + 32 > (uint32_t)kSurvCap) resolve_survivors<E>(P, list, nsurv, s_stats);
-                    if (base + lane < n_allempty) {
-                        const uint32_t q = (uint32_t)a.allempty[base + lane];
+                    const uint32_t q =
+                        base + lane < n_allempty ? (uint32_t)a.allempty[base + lane] : 0u;
+                    if (base + lane < n_allempty && (P.self_off < 0 || row > (int64_t)q)) {
                         if (d00 == HOPH_ACCEPT) {
                             ++acc0;
                             emit_pair(P, q, row, 1, 0);
@@ -869,6 +882,8 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
             continue;
         }
         const int need = row_min[ne];
+        // a self-join block pairs a row only with the queries before it
+        const uint32_t qlim = P.self_off >= 0 ? (uint32_t)min(row, (int64_t)P.n_q) : (uint32_t)P.n_q;
         // counting pass: the query list of every chunk's key, then counts
         uint32_t f[NCH];
 #pragma unroll
@@ -884,8 +899,10 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
         for (int c = 0; c < NCH; ++c) {
             for (uint32_t e = f[c]; e != kNil; e = __ldg(a.next + e)) {
                 const uint32_t q = e >> a.wshift;
-                atomicAdd(cnt + (q >> 1), 1u << ((q & 1) * 16));
-                ++hits;
+                if (q < qlim) {
+                    atomicAdd(cnt + (q >> 1), 1u << ((q & 1) * 16));
+                    ++hits;
+                }
             }
         }
         __syncwarp();
@@ -907,6 +924,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_co
                         if (cc == c) i = f[cc];
                     continue;
                 }
+                // (a query at or past qlim was not counted: m = 0 below)
                 const uint32_t q = i >> a.wshift;
                 const uint32_t sh = (q & 1) * 16;
                 const uint32_t old = atomicAnd(cnt + (q >> 1), ~(0xFFFFu << sh));
@@ -1283,15 +1301,15 @@ struct Bump {
 
 // hoph_query_batch / hoph_query_batch16 over planes of element type E, and
 // one block of hoph_self_join: collection planes cstride elements apart
-// (n_rows * k' when negative); self_off >= 0 keeps only row > query and
-// shifts both by self_off; `first` zeroes the output count, `last` sorts the
-// output.
+// (n_rows * k' when negative), query planes qstride_in apart (n_queries * k'
+// when negative); self_off >= 0 keeps only row > query and shifts both by
+// self_off; `first` zeroes the output count, `last` sorts the output.
 template <typename E>
 int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, int64_t n_queries,
                      const E *d_coll_planes, int64_t n_rows, hoph_pair *d_out,
                      int64_t out_capacity, int64_t *d_out_count, hoph_stats *d_stats,
-                     void *stream, int64_t cstride_in = -1, int64_t self_off = -1,
-                     bool first = true, bool last = true) {
+                     void *stream, int64_t cstride_in = -1, int64_t qstride_in = -1,
+                     int64_t self_off = -1, bool first = true, bool last = true) {
     constexpr int ES = (int)sizeof(E);
     if (!plan || !d_out_count || n_queries < 0 || n_rows < 0 || out_capacity < 0)
         return HOPH_ERR_PARAM;
@@ -1392,9 +1410,11 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     if (strategy < 0) strategy = (join_ok && n_queries >= 16) ? 1 : 0;
 
     const int mask_words = (W + 31) / 32;
+    // group map words (+ the zero word), padded for the filter's bulk copy
+    const uint64_t gmap_alloc = (map_slots / 16 + 2 + 3) & ~3ull;
     int wshift = 0;  // bits of a scanned-bin index (join index entries)
     while ((1 << wshift) < W) ++wshift;
-    const int64_t qstride = n_queries * (int64_t)kg;
+    const int64_t qstride = qstride_in >= 0 ? qstride_in : n_queries * (int64_t)kg;
     const int64_t cstride = cstride_in >= 0 ? cstride_in : n_rows * (int64_t)kg;
 
     // scratch
@@ -1407,7 +1427,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         if (strategy == 1) {
             bump.take(head_slots * 4);                                   // list heads
             bump.take(((size_t)n_queries << wshift) * 4);               // list links
-            bump.take((map_slots / 16 + 2) * 4);                        // group map
+            bump.take(gmap_alloc * 4);                                  // group map
             bump.take(keys_hashed ? head_slots * 8 : 8);                  // key table
             bump.take((size_t)n_queries * mask_words * 4);              // q_emask
             bump.take((size_t)n_queries * 4 + 4);                       // allempty + count
@@ -1432,7 +1452,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     if (strategy == 1) {
         head = (uint32_t *)bump.take(head_slots * 4);
         next = (uint32_t *)bump.take(((size_t)n_queries << wshift) * 4);
-        gmap = (uint32_t *)bump.take((map_slots / 16 + 2) * 4);
+        gmap = (uint32_t *)bump.take(gmap_alloc * 4);
         tkey = (unsigned long long *)bump.take(keys_hashed ? head_slots * 8 : 8);
         q_emask = (uint32_t *)bump.take((size_t)n_queries * mask_words * 4);
         allempty = (int32_t *)bump.take((size_t)n_queries * 4 + 4);
@@ -1495,7 +1515,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ia.allempty = allempty;
         ia.n_allempty = n_allempty;
         join_init_kernel<<<(unsigned)plan->num_sms * 4, 256, 0, s>>>(
-            head, (int64_t)head_slots, gmap, (int64_t)(map_slots / 16 + 2), st, kStatWords,
+            head, (int64_t)head_slots, gmap, (int64_t)gmap_alloc, st, kStatWords,
             n_allempty, n_cand, first ? d_out_count : nullptr);
         if (keys_hashed) HOPH_CUDA_TRY(cudaMemsetAsync(tkey, 0xFF, head_slots * 8, s));
         const unsigned qb = (unsigned)((n_queries * 32 + 255) / 256);
@@ -1634,7 +1654,8 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     StatsFold sf;
     sf.st = st;
     sf.n_cand = n_cand;
-    sf.pairs = n_queries * n_rows;
+    // a self-join block compares its queries only with the rows after each
+    sf.pairs = n_queries * n_rows - (self_off >= 0 ? n_queries * (n_queries + 1) / 2 : 0);
     sf.first_pass_bytes = (n_rows * (int64_t)W + n_queries * (int64_t)W) * ES;
     sf.G = G;
     sf.Gs = Gs;
@@ -1644,8 +1665,10 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
         sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(
             d_out, pa.out_count, out_capacity, sortA, sortB, plan->d_status, sf);
-    } else {
+    } else if (d_stats) {
         stats_fold_kernel<<<1, 32, 0, s>>>(sf);
+    } else {
+        --launches;  // nothing to fold
     }
     HOPH_CUDA_TRY(cudaGetLastError());
     hoph_timing_mark(plan, 4, s);
@@ -1685,31 +1708,16 @@ int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int
     HOPH_CUDA_TRY(cudaMemsetAsync(d_out_count, 0, sizeof(int64_t), s));
     if (n_rows < 2) return HOPH_OK;
     if (!d_planes) return HOPH_ERR_PARAM;
-    const int64_t kg = plan->P.k_group, G = plan->G;
-    // the block's query planes, gathered contiguous ([G][nb][k'])
-    const size_t qbytes = (size_t)G * std::min(batch, n_rows) * kg * sizeof(uint32_t);
-    if (qbytes > plan->aux_bytes) {
-        if (plan->d_aux) {
-            HOPH_CUDA_TRY(cudaDeviceSynchronize());
-            HOPH_CUDA_TRY(cudaFree(plan->d_aux));
-            plan->d_aux = nullptr;
-            plan->aux_bytes = 0;
-        }
-        HOPH_CUDA_TRY(cudaMalloc(&plan->d_aux, qbytes));
-        plan->aux_bytes = qbytes;
-    }
-    uint32_t *q = static_cast<uint32_t *>(plan->d_aux);
+    const int64_t kg = plan->P.k_group;
     const int64_t cstride = n_rows * kg;
     for (int64_t q0 = 0; q0 < n_rows - 1; q0 += batch) {
         const int64_t nb = std::min(batch, n_rows - 1 - q0);
-        HOPH_CUDA_TRY(cudaMemcpy2DAsync(q, (size_t)nb * kg * 4, d_planes + q0 * kg,
-                                        (size_t)cstride * 4, (size_t)nb * kg * 4, (size_t)G,
-                                        cudaMemcpyDeviceToDevice, s));
-        // rows q0 .. n_rows-1 against queries q0 .. q0+nb-1
+        // rows q0 .. n_rows-1 against queries q0 .. q0+nb-1, both read in place
         const bool last = q0 + batch >= n_rows - 1;
-        const int rc = query_batch_impl<uint32_t>(plan, mode, q, nb, d_planes + q0 * kg,
-                                                  n_rows - q0, d_out, out_capacity, d_out_count,
-                                                  d_stats, stream, cstride, q0, false, last);
+        const uint32_t *blk = d_planes + q0 * kg;
+        const int rc = query_batch_impl<uint32_t>(plan, mode, blk, nb, blk, n_rows - q0, d_out,
+                                                  out_capacity, d_out_count, d_stats, stream,
+                                                  cstride, cstride, q0, false, last);
         if (rc != HOPH_OK) return rc;
     }
     return HOPH_OK;

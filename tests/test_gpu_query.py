@@ -362,7 +362,9 @@ def test_compact_planes_give_the_same_pairs(small, mode, ab, kg, strategy):
 def test_self_join_is_the_upper_triangle_of_the_all_pairs_query(small, mode, ab, kg, batch):
     """hoph_self_join over the 5,000 sets plus the 50 planted near duplicates
     appended as rows: exactly the oracle's accepted pairs (i, j) with i < j
-    of the all-pairs comparison, in (i, j) order; ragged last block."""
+    of the all-pairs comparison, in (i, j) order; ragged last block.  The
+    statistics cover exactly the n (n - 1) / 2 pairs i < j, each decided in
+    the group where the oracle decides it."""
     dev = device()
     D, k = small["D"], 128
     ids = np.concatenate([small["ids"], small["q_ids"]])
@@ -373,19 +375,31 @@ def test_self_join_is_the_upper_triangle_of_the_all_pairs_query(small, mode, ab,
         plan.check()
         rows = planes_to_rows(c)
         z = [plan.info.group_size[g] for g in range(plan.G)]
-        want = _oracle_query(mode, rows, rows, kg, z)["accepted"]
+        full = oc.query(mode, rows, rows, kg, T[0], T[1], EPS, z=np.asarray(z, dtype=np.uint64),
+                        per_pair=True)
+        want = full["accepted"]
         want = want[want[:, 0] < want[:, 1]]
+        iu = np.triu_indices(n, 1)
+        dec, grp = full["dec"][iu], full["groups"][iu]
+        del full
         cap = 1 << 14
         out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-        hoph.hoph_self_join(plan.handle, mode, c, n, batch, out, cap, cnt)
+        st = torch.zeros(hoph.STATS_WORDS, dtype=torch.int64, device=dev)
+        hoph.hoph_self_join(plan.handle, mode, c, n, batch, out, cap, cnt, st)
         plan.check()
         m = int(cnt.item())
         got = out[:m].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+        stats = hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes())
+        G = plan.G if mode != "oph_full" else 1
     assert len(want) > 5  # the planted pairs at J >= T
     assert m == len(want)
     assert [(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"])) for p in got] \
         == [tuple(int(x) for x in w) for w in want]
+    assert stats.entering[0] == n * (n - 1) // 2
+    for g in range(G):
+        assert stats.accepted[g] == np.count_nonzero((grp == g + 1) & (dec == 1)), ("acc", g)
+        assert stats.rejected[g] == np.count_nonzero((grp == g + 1) & (dec == 2)), ("rej", g)
 
 
 def test_compact_planes_with_a_hashed_join():
