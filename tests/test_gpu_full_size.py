@@ -1,0 +1,201 @@
+"""Parity at the benchmark's full sizes, in the launch configurations the
+benchmark times, on outputs the oracle can compute one by one:
+
+* the batched (1:2)HOPH query of 1,024 query sets against 10^7 resident
+  k = 256 sketches (value join, 16 consumer warps): sampled rows against
+  every query;
+* the 10^6-set sketch with Zipf IDs, with the default and the tuned
+  size from which a set gets a whole CTA: sampled sets, all the largest ones;
+* the self-join of 10^6 rows plus 1,000 planted near duplicates: every
+  reported pair, every planted pair and a random sample of pairs.
+
+The collection's IDs come from the counter generator on the device; the
+oracle regenerates the sampled sets on the host (synth's twin of the
+generator) and sketches and decides them itself.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import device, planes_to_rows, to_dev, torch
+from oracle import oracle_c as oc
+from paper_1805_11254_gb300 import hoph, synth
+
+pytestmark = pytest.mark.gpu
+
+D = 1 << 20
+K, KG, AB = 256, 64, (1, 2)
+T = (7, 10)
+EPS = 1e-4
+PERM_SEED, COLL_SEED, Q_SEED, PLANT_SEED, SKETCH_SEED = 1, 11, 12, 13, 21
+
+
+def _row_ids(coll_seed, off, r):
+    return synth.counter_ids(coll_seed, int(off[r]), int(off[r + 1] - off[r]), D)
+
+
+def _oracle_rows(coll_seed, off, rows, lo, perm):
+    ids, offs = synth.pack_sets([_row_ids(coll_seed, off, int(r)) for r in rows])
+    return oc.sketch(ids, offs, lo, perm)
+
+
+def _device_rows(planes, rows, dev):
+    idx = torch.from_numpy(np.asarray(rows, dtype=np.int64)).to(dev)
+    return planes_to_rows(planes.index_select(1, idx))
+
+
+def test_full_size_query_matches_the_oracle_on_sampled_rows():
+    """1,024 query sets (10% planted at J 0.6-0.95) against 10^7 rows: the
+    sketches of 4,096 random rows, of every row the GPU reported and of
+    every planted source row equal the oracle's, the accepted pairs among
+    those rows (each against all 1,024 queries) are exactly the oracle's,
+    and the statistics count all 1.024 x 10^10 pairs."""
+    dev = device()
+    n, nq = 10_000_000, 1024
+    off = synth.offsets_from_sizes(synth.counter_collection_sizes(n, COLL_SEED))
+    qw = synth.query_batch(nq, 0.1, D, COLL_SEED, off, 0.6, 0.95, Q_SEED, PLANT_SEED)
+    lo = oc.layout(D, K, KG, *AB)
+    perm = oc.permutation(D, PERM_SEED)
+    with hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
+        n_ids = int(off[-1])
+        d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+        hoph.hoph_synth_ids(COLL_SEED, 0, n_ids, D, 0, None, 0, d_ids)
+        planes = plan.sketch(d_ids, to_dev(off, dev), n)
+        del d_ids
+        torch.cuda.empty_cache()
+        q = plan.sketch(to_dev(qw["q_ids"], dev), to_dev(qw["q_off"], dev), nq)
+        plan.check()
+        plan.set_exec(strategy=1, lanes_per_row=0, consumer_warps=16, stages=3)
+        pairs, m, st = plan.query(hoph.HOPH_MODE_HOPH, q, nq, planes, n, stats=True)
+        G = plan.G
+        rng = np.random.default_rng(5)
+        src = qw["src"][qw["src"] >= 0]
+        sample = np.unique(np.concatenate([rng.choice(n, 4096, replace=False),
+                                           pairs["row"].astype(np.int64), src]))
+        got_rows = _device_rows(planes, sample, dev)
+        got_q = planes_to_rows(q)
+        del planes
+        torch.cuda.empty_cache()
+    want_rows = _oracle_rows(COLL_SEED, off, sample, lo, perm)
+    want_q = oc.sketch(qw["q_ids"], qw["q_off"], lo, perm)
+    assert np.array_equal(got_q, want_q)
+    assert np.array_equal(got_rows, want_rows)
+    z = np.diff(lo[::KG]).astype(np.uint64)
+    want = oc.query("hoph", want_q, want_rows, KG, T[0], T[1], EPS, z=z)["accepted"]
+    want_set = {(int(a), int(sample[b]), int(g), int(mm)) for a, b, g, mm in want}
+    got_set = {(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"]))
+               for p in pairs}
+    assert m == len(pairs) and m > 0
+    assert got_set == want_set  # every reported row is in the sample
+    assert sum(1 for p in want_set if p[1] in set(src.tolist())) > 0
+    assert st.entering[0] == nq * n
+    assert sum(st.accepted[g] for g in range(G)) == m
+    assert sum(st.accepted[g] + st.rejected[g] for g in range(G)) == nq * n
+
+
+@pytest.mark.parametrize("bits", [0, 13, 14])
+def test_full_size_sketch_matches_the_oracle_on_sampled_sets(bits):
+    """10^6 sets, lognormal sizes (median 300, sigma 1, [10, 20000]), Zipf(1.1)
+    IDs over 2^20, k = 256: 2,000 random sets and the 256 largest (which a
+    whole CTA sketches) equal the oracle's sketches, with the default and
+    the tuned CTA-size knob."""
+    dev = device()
+    n = 1_000_000
+    sizes = synth.lognormal_sizes(n, 300, 1.0, 10, 20000, SKETCH_SEED)
+    off = synth.offsets_from_sizes(sizes)
+    cdf = synth.zipf_cdf(D, 1.1)
+    lo = oc.layout(D, K, K)
+    perm = oc.permutation(D, PERM_SEED)
+    with hoph.Plan(D, K, K, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
+        n_ids = int(off[-1])
+        d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+        hoph.hoph_synth_ids(SKETCH_SEED, 0, n_ids, D, 1, torch.from_numpy(cdf).to(dev),
+                            len(cdf), d_ids)
+        plan.update_exec(sketch_cta_bits=bits)
+        sk = plan.sketch(d_ids, to_dev(off, dev), n)
+        plan.check()
+        rng = np.random.default_rng(6)
+        sample = np.unique(np.concatenate([rng.choice(n, 2000, replace=False),
+                                           np.argsort(sizes, kind="stable")[-256:]]))
+        got = _device_rows(sk, sample, dev)
+    ids, offs = synth.pack_sets([synth.counter_zipf_ids(SKETCH_SEED, int(off[r]),
+                                                        int(off[r + 1] - off[r]), cdf)
+                                 for r in sample])
+    assert np.array_equal(got, oc.sketch(ids, offs, lo, perm))
+
+
+def test_full_size_self_join_on_reported_planted_and_random_pairs():
+    """hoph_self_join over the first 10^6 rows of the query workload's
+    collection plus 1,000 planted near duplicates (J 0.6-0.95) of random rows
+    among them, blocks of 1,536 rows: every reported pair is one the oracle
+    accepts, with its groups and matches; every planted pair the oracle
+    accepts is reported; so is every accepted pair of 4,000 random pairs;
+    and the statistics cover exactly the n (n - 1) / 2 pairs."""
+    dev = device()
+    n_base, n_pl = 1_000_000, 1000
+    off_all = synth.offsets_from_sizes(synth.counter_collection_sizes(10_000_000, COLL_SEED))
+    off = off_all[:n_base + 1]
+    rng = np.random.default_rng(PLANT_SEED + 7)
+    src = np.sort(rng.choice(n_base, n_pl, replace=False))
+    bases = [_row_ids(COLL_SEED, off, r) for r in src]
+    planted, _ = synth.plant_near_duplicates(bases, D, 0.6, 0.95, PLANT_SEED + 8)
+    p_ids, p_off = synth.pack_sets(planted)
+    n = n_base + n_pl
+    lo = oc.layout(D, K, KG, *AB)
+    perm = oc.permutation(D, PERM_SEED)
+    z = np.diff(lo[::KG]).astype(np.uint64)
+    with hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
+        n_ids = int(off[n_base])
+        d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+        hoph.hoph_synth_ids(COLL_SEED, 0, n_ids, D, 0, None, 0, d_ids)
+        base = plan.sketch(d_ids, to_dev(off, dev), n_base)
+        del d_ids
+        pl = plan.sketch(to_dev(p_ids, dev), to_dev(p_off, dev), n_pl)
+        planes = torch.cat([base, pl], dim=1).contiguous()
+        del base, pl
+        plan.check()
+        cap = 1 << 20
+        out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        st = torch.zeros(hoph.STATS_WORDS, dtype=torch.int64, device=dev)
+        hoph.hoph_self_join(plan.handle, hoph.HOPH_MODE_HOPH, planes, n, 1536, out, cap, cnt, st)
+        plan.check()
+        m = int(cnt.item())
+        got = out[:m].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+        stats = hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes())
+        G = plan.G
+        del planes
+        torch.cuda.empty_cache()
+
+    def ids_of(r):
+        return _row_ids(COLL_SEED, off, r) if r < n_base else planted[r - n_base]
+
+    def decide(pairs_ij):
+        """oracle (accepted, groups, matches) of each pair (i, j)."""
+        rows = sorted({r for p in pairs_ij for r in p})
+        pos = {r: i for i, r in enumerate(rows)}
+        ids, offs = synth.pack_sets([ids_of(r) for r in rows])
+        sk = oc.sketch(ids, offs, lo, perm)
+        res = []
+        for i, j in pairs_ij:
+            w = oc.query("hoph", sk[pos[i]][None], sk[pos[j]][None], KG, T[0], T[1], EPS, z=z,
+                         threads=1)
+            a = w["accepted"]
+            res.append((True, int(a[0][2]), int(a[0][3])) if len(a) else (False, 0, 0))
+        return res
+
+    assert m > n_pl // 2
+    got_pairs = [(int(p["query"]), int(p["row"])) for p in got]
+    assert all(i < j for i, j in got_pairs) and got_pairs == sorted(got_pairs)
+    for p, (acc, g, mm) in zip(got, decide(got_pairs)):
+        assert acc and (g, mm) == (int(p["groups"]), int(p["matches"]))
+    reported = set(got_pairs)
+    planted_pairs = [(int(src[i]), n_base + i) for i in range(n_pl)]
+    for pr, (acc, _, _) in zip(planted_pairs, decide(planted_pairs)):
+        assert acc == (pr in reported)
+    rng = np.random.default_rng(8)
+    a, b = rng.integers(0, n, 4000), rng.integers(0, n, 4000)
+    rand = [(int(min(x, y)), int(max(x, y))) for x, y in zip(a, b) if x != y]
+    for pr, (acc, _, _) in zip(rand, decide(rand)):
+        assert acc == (pr in reported)
+    assert stats.entering[0] == n * (n - 1) // 2
+    assert sum(stats.accepted[g] for g in range(G)) == m
