@@ -2,8 +2,10 @@
 benchmark times, on outputs the oracle can compute one by one:
 
 * the batched (1:2)HOPH query of 1,024 query sets against 10^7 resident
-  k = 256 sketches (value join, 16 consumer warps): sampled rows against
-  every query;
+  k = 256 sketches (value join, 16 consumer warps; and over compact 16-bit
+  planes): sampled rows against every query;
+* the shingle regime (D = 2^32, hashed psi, (2:1)HOPH, k = 512) against
+  5*10^6 sketches generated inside the kernel;
 * the 10^6-set sketch with Zipf IDs, with the default and the tuned
   size from which a set gets a whole CTA: sampled sets, all the largest ones;
 * the self-join of 10^6 rows plus 1,000 planted near duplicates: every
@@ -48,7 +50,8 @@ def test_full_size_query_matches_the_oracle_on_sampled_rows():
     sketches of 4,096 random rows, of every row the GPU reported and of
     every planted source row equal the oracle's, the accepted pairs among
     those rows (each against all 1,024 queries) are exactly the oracle's,
-    and the statistics count all 1.024 x 10^10 pairs."""
+    and the statistics count all 1.024 x 10^10 pairs.  The same over compact
+    16-bit planes (the offsets in 16 bits, the same pairs)."""
     dev = device()
     n, nq = 10_000_000, 1024
     off = synth.offsets_from_sizes(synth.counter_collection_sizes(n, COLL_SEED))
@@ -59,21 +62,32 @@ def test_full_size_query_matches_the_oracle_on_sampled_rows():
         n_ids = int(off[-1])
         d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
         hoph.hoph_synth_ids(COLL_SEED, 0, n_ids, D, 0, None, 0, d_ids)
-        planes = plan.sketch(d_ids, to_dev(off, dev), n)
+        d_off = to_dev(off, dev)
+        planes = plan.sketch(d_ids, d_off, n)
+        planes16 = plan.sketch16(d_ids, d_off, n)
         del d_ids
         torch.cuda.empty_cache()
-        q = plan.sketch(to_dev(qw["q_ids"], dev), to_dev(qw["q_off"], dev), nq)
+        d_qids, d_qoff = to_dev(qw["q_ids"], dev), to_dev(qw["q_off"], dev)
+        q = plan.sketch(d_qids, d_qoff, nq)
+        q16 = plan.sketch16(d_qids, d_qoff, nq)
         plan.check()
         plan.set_exec(strategy=1, lanes_per_row=0, consumer_warps=16, stages=3)
         pairs, m, st = plan.query(hoph.HOPH_MODE_HOPH, q, nq, planes, n, stats=True)
+        # compact 16-bit planes in the shape the benchmark tunes for them
+        plan.set_exec(strategy=1, lanes_per_row=4, consumer_warps=31, stages=2)
+        pairs16, m16, _ = plan.query(hoph.HOPH_MODE_HOPH, q16, nq, planes16, n)
         G = plan.G
         rng = np.random.default_rng(5)
         src = qw["src"][qw["src"] >= 0]
         sample = np.unique(np.concatenate([rng.choice(n, 4096, replace=False),
-                                           pairs["row"].astype(np.int64), src]))
+                                           pairs["row"].astype(np.int64),
+                                           pairs16["row"].astype(np.int64), src]))
         got_rows = _device_rows(planes, sample, dev)
+        idx = torch.from_numpy(sample).to(dev)
+        got_rows16 = planes16.index_select(1, idx).cpu().numpy().view(np.uint16) \
+            .transpose(1, 0, 2).reshape(len(sample), -1)
         got_q = planes_to_rows(q)
-        del planes
+        del planes, planes16
         torch.cuda.empty_cache()
     want_rows = _oracle_rows(COLL_SEED, off, sample, lo, perm)
     want_q = oc.sketch(qw["q_ids"], qw["q_off"], lo, perm)
@@ -86,6 +100,11 @@ def test_full_size_query_matches_the_oracle_on_sampled_rows():
                for p in pairs}
     assert m == len(pairs) and m > 0
     assert got_set == want_set  # every reported row is in the sample
+    # compact planes: the offsets in 16 bits (empty 0xFFFF), the same pairs
+    want16 = np.where(want_rows == hoph.HOPH_EMPTY_VALUE, hoph.HOPH_EMPTY_VALUE16, want_rows)
+    assert np.array_equal(got_rows16, want16.astype(np.uint16))
+    assert m16 == m and {(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"]))
+                         for p in pairs16} == want_set
     assert sum(1 for p in want_set if p[1] in set(src.tolist())) > 0
     assert st.entering[0] == nq * n
     assert sum(st.accepted[g] for g in range(G)) == m
@@ -199,3 +218,60 @@ def test_full_size_self_join_on_reported_planted_and_random_pairs():
         assert acc == (pr in reported)
     assert stats.entering[0] == n * (n - 1) // 2
     assert sum(stats.accepted[g] for g in range(G)) == m
+
+
+def test_full_size_shingle_regime_on_sampled_rows():
+    """IDs uniform over 2^32, psi the 2-universal hash mod 2^61-1, (2:1)HOPH
+    with k = 512, k' = 128: the 5*10^6-set collection (sizes U[1000,
+    100000]) generated and sketched inside the kernel, and one batch of
+    1,024 query sets (32 planted near duplicates at J 0.75-0.98) through the
+    hashed join in the benchmark's tuned shape.  512 random rows, every
+    reported row and every planted source row: sketches equal the oracle's
+    and, against all 1,024 queries, so do the accepted pairs."""
+    dev = device()
+    D4, K4, KG4, AB4 = 1 << 32, 512, 128, (2, 1)
+    seed_c, seed_q, n, nq, n_pl = 31, 32, 5_000_000, 1024, 32
+    c_sizes = synth.uniform_sizes(n, 1000, 100000, seed_c)
+    c_off = synth.offsets_from_sizes(c_sizes)
+    rng = np.random.default_rng(seed_q)
+    src = rng.integers(0, n, n_pl)
+    bases = [synth.counter_ids(seed_c, int(c_off[r]), int(c_sizes[r]), D4) for r in src]
+    planted, _ = synth.plant_near_duplicates(bases, D4, 0.75, 0.98, seed_q + 1)
+    p_ids, p_off = synth.pack_sets(planted)
+    q_sizes = np.concatenate([np.diff(p_off),
+                              synth.uniform_sizes(nq - n_pl, 1000, 100000, seed_q + 2)])
+    q_off = synth.offsets_from_sizes(q_sizes)
+    q_ids = np.concatenate([p_ids, synth.counter_ids(seed_q + 3, 0, int(q_off[-1]) - len(p_ids),
+                                                     D4)])
+    with hoph.Plan(D4, K4, KG4, *AB4, perm_kind=hoph.HOPH_PERM_HASH61, seed=PERM_SEED, thr=T,
+                   epsilon=EPS) as plan:
+        planes = torch.empty((plan.G, n, KG4), dtype=torch.int32, device=dev)
+        hoph.hoph_synth_sketch(plan.handle, seed_c, D4, to_dev(c_off, dev), n, planes)
+        q = plan.sketch(to_dev(q_ids, dev), to_dev(q_off, dev), nq)
+        plan.check()
+        plan.set_exec(strategy=1, lanes_per_row=0, consumer_warps=16, stages=3)
+        pairs, m, st = plan.query(hoph.HOPH_MODE_HOPH, q, nq, planes, n, stats=True)
+        sample = np.unique(np.concatenate([np.random.default_rng(7).choice(n, 512, replace=False),
+                                           pairs["row"].astype(np.int64), src]))
+        got_rows = _device_rows(planes, sample, dev)
+        got_q = planes_to_rows(q)
+        G = plan.G
+        del planes
+        torch.cuda.empty_cache()
+    lo = oc.layout(D4, K4, KG4, *AB4)
+    hab = oc.hash_params(PERM_SEED)
+    ids, offs = synth.pack_sets([synth.counter_ids(seed_c, int(c_off[r]), int(c_sizes[r]), D4)
+                                 for r in sample])
+    want_rows = oc.sketch(ids, offs, lo, D=D4, hash_ab=hab)
+    want_q = oc.sketch(q_ids, q_off, lo, D=D4, hash_ab=hab)
+    assert np.array_equal(got_q, want_q)
+    assert np.array_equal(got_rows, want_rows)
+    z = np.diff(lo[::KG4]).astype(np.uint64)
+    want = oc.query("hoph", want_q, want_rows, KG4, T[0], T[1], EPS, z=z)["accepted"]
+    want_set = {(int(a), int(sample[b]), int(g), int(mm)) for a, b, g, mm in want}
+    got_set = {(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"]))
+               for p in pairs}
+    assert m == len(pairs) and m >= n_pl // 2
+    assert got_set == want_set
+    assert st.entering[0] == nq * n
+    assert sum(st.accepted[g] for g in range(G)) == m
