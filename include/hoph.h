@@ -148,7 +148,9 @@ typedef struct {
     int32_t sketch_cta_bits; /* sketch: sets whose size has at least this
                               * many bits get a whole CTA, the rest a warp;
                               * 0 = library choice, 64 = warps only      */
-    int32_t reserved;
+    int32_t join_lanes;      /* hoph_self_join: blocks in flight at once,
+                              * each on a stream and scratch of the plan's
+                              * own (1-4; 0 = library choice, 3)         */
 } hoph_exec;
 
 typedef struct hoph_plan hoph_plan;
@@ -261,7 +263,12 @@ int hoph_query_batch16(hoph_plan *plan, uint32_t mode, const uint16_t *d_query_p
  *               n_rows (n_rows - 1) / 2): a block skips the pairs i >= j
  *               among its own rows before counting or deciding them.
  * Modes GOPH, HOPH and OPH_FULL (not MinWise).  A block reads its query
- * planes in place (no copy).  n_rows < 2^32.
+ * planes in place (no copy).  Up to exec.join_lanes blocks (default 3) are
+ * in flight at once, each on a stream and a scratch buffer the plan owns,
+ * forked from `stream` and joined back to it before the final sort, so the
+ * call stays ordered on `stream` (and can be captured into a graph).  The
+ * first call with more than one lane creates those streams: make it outside
+ * a stream capture.  n_rows < 2^32.
  */
 int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int64_t n_rows,
                    int64_t batch, hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,

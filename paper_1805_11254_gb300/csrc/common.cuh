@@ -160,9 +160,16 @@ struct hoph_plan {
     // status word
     int32_t *d_status = nullptr;
     int32_t *h_status = nullptr;  // pinned mirror
-    // scratch
+    // scratch (lane 0; lanes 1.. serve the other blocks a self-join keeps in
+    // flight, each on a stream of the plan's own)
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    static constexpr int kMaxLanes = 4;
+    void *lane_scratch[kMaxLanes] = {};
+    size_t lane_scratch_bytes[kMaxLanes] = {};
+    cudaStream_t lane_stream[kMaxLanes] = {};
+    cudaEvent_t lane_event[kMaxLanes] = {};
+    cudaEvent_t fork_event = nullptr;
     hoph_exec exec{};
     // optional event timing of hoph_query_batch phases (bench / tooling)
     bool timing = false;
@@ -193,8 +200,9 @@ cudaError_t hoph_ensure_smem(const void *func, int bytes);
 // device, block size, dynamic shared memory): host time off the launch path
 cudaError_t hoph_occupancy(int *blocks, const void *func, int threads, size_t smem);
 
-// grow-only scratch owned by the plan; returns nullptr on failure
-void *hoph_scratch(hoph_plan *plan, size_t bytes);
+// grow-only scratch owned by the plan (one per lane, lane 0 for every call
+// but a self-join's other blocks in flight); returns nullptr on failure
+void *hoph_scratch(hoph_plan *plan, size_t bytes, int lane = 0);
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -166,6 +166,12 @@ void plan_free(hoph_plan *pl) {
     cudaFree(pl->d_minwise);
     cudaFree(pl->d_status);
     cudaFree(pl->d_scratch);
+    for (int i = 0; i < hoph_plan::kMaxLanes; ++i) {
+        cudaFree(pl->lane_scratch[i]);
+        if (pl->lane_stream[i]) cudaStreamDestroy(pl->lane_stream[i]);
+        if (pl->lane_event[i]) cudaEventDestroy(pl->lane_event[i]);
+    }
+    if (pl->fork_event) cudaEventDestroy(pl->fork_event);
     if (pl->h_status) cudaFreeHost(pl->h_status);
     delete pl;
 }
@@ -340,22 +346,24 @@ cudaError_t hoph_occupancy(int *blocks, const void *func, int threads, size_t sm
     return cudaSuccess;
 }
 
-void *hoph_scratch(hoph_plan *plan, size_t bytes) {
-    if (bytes <= plan->scratch_bytes) return plan->d_scratch;
-    size_t want = std::max(bytes, plan->scratch_bytes * 2);
+void *hoph_scratch(hoph_plan *plan, size_t bytes, int lane) {
+    void *&buf = lane > 0 ? plan->lane_scratch[lane] : plan->d_scratch;
+    size_t &have = lane > 0 ? plan->lane_scratch_bytes[lane] : plan->scratch_bytes;
+    if (bytes <= have) return buf;
+    size_t want = std::max(bytes, have * 2);
     want = (want + 255) & ~(size_t)255;
-    if (plan->d_scratch) {
+    if (buf) {
         cudaDeviceSynchronize();  // a previous launch may still read the old buffer
-        cudaFree(plan->d_scratch);
-        plan->d_scratch = nullptr;
-        plan->scratch_bytes = 0;
+        cudaFree(buf);
+        buf = nullptr;
+        have = 0;
     }
-    if (cudaMalloc(&plan->d_scratch, want) != cudaSuccess) {
+    if (cudaMalloc(&buf, want) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
-    plan->scratch_bytes = want;
-    return plan->d_scratch;
+    have = want;
+    return buf;
 }
 
 void hoph_timing_mark(hoph_plan *plan, int which, cudaStream_t s) {
@@ -462,7 +470,8 @@ int hoph_plan_set_exec(hoph_plan *plan, const hoph_exec *exec) {
         exec->ctas_per_sm < 0 || exec->ctas_per_sm > 8 || exec->stages < 0 || exec->stages > 8 ||
         (exec->lanes_per_row != 0 && exec->lanes_per_row != 1 && exec->lanes_per_row != 2 &&
          exec->lanes_per_row != 4 && exec->lanes_per_row != 8) ||
-        exec->sketch_cta_bits < 0 || exec->sketch_cta_bits > 64)
+        exec->sketch_cta_bits < 0 || exec->sketch_cta_bits > 64 || exec->join_lanes < 0 ||
+        exec->join_lanes > hoph_plan::kMaxLanes)
         return HOPH_ERR_PARAM;
     plan->exec = *exec;
     return HOPH_OK;

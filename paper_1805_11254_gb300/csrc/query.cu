@@ -1035,18 +1035,22 @@ __device__ void stats_fold(const StatsFold &f) {
     const int64_t pairs = f.pairs;
     const int G = f.G, Gs = f.Gs;
     hoph_stats *out = f.out;
-    out->entering[0] += pairs;
+    // atomic: a self-join's blocks in flight fold into the same statistics
+    auto add = [](int64_t *dst, int64_t v) {
+        if (v) atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)v);
+    };
+    add(&out->entering[0], pairs);
     const int64_t acc0 = (int64_t)st[16], cont = (Gs < G) ? (int64_t)st[1] : 0;
-    out->accepted[0] += acc0;
-    out->rejected[0] += pairs - acc0 - cont;
+    add(&out->accepted[0], acc0);
+    add(&out->rejected[0], pairs - acc0 - cont);
     for (int g = 1; g < G && Gs < G; ++g) {
-        out->entering[g] += (int64_t)st[g];
-        out->accepted[g] += (int64_t)st[16 + g];
-        out->rejected[g] += (int64_t)st[32 + g];
+        add(&out->entering[g], (int64_t)st[g]);
+        add(&out->accepted[g], (int64_t)st[16 + g]);
+        add(&out->rejected[g], (int64_t)st[32 + g]);
     }
-    out->sketch_bytes += f.first_pass_bytes + (int64_t)st[48];
-    out->join_hits += (int64_t)st[49];
-    if (f.n_cand) out->rows_counted += (int64_t)*f.n_cand;
+    add(&out->sketch_bytes, f.first_pass_bytes + (int64_t)st[48]);
+    add(&out->join_hits, (int64_t)st[49]);
+    if (f.n_cand) add(&out->rows_counted, (int64_t)*f.n_cand);
     out->strategy = f.strategy;
 }
 
@@ -1303,13 +1307,15 @@ struct Bump {
 // one block of hoph_self_join: collection planes cstride elements apart
 // (n_rows * k' when negative), query planes qstride_in apart (n_queries * k'
 // when negative); self_off >= 0 keeps only row > query and shifts both by
-// self_off; `first` zeroes the output count, `last` sorts the output.
+// self_off; `first` zeroes the output count, `last` sorts the output; `lane`
+// picks the plan's scratch (a self-join's blocks in flight use one each).
 template <typename E>
 int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, int64_t n_queries,
                      const E *d_coll_planes, int64_t n_rows, hoph_pair *d_out,
                      int64_t out_capacity, int64_t *d_out_count, hoph_stats *d_stats,
                      void *stream, int64_t cstride_in = -1, int64_t qstride_in = -1,
-                     int64_t self_off = -1, bool first = true, bool last = true) {
+                     int64_t self_off = -1, bool first = true, bool last = true,
+                     int lane = 0) {
     constexpr int ES = (int)sizeof(E);
     if (!plan || !d_out_count || n_queries < 0 || n_rows < 0 || out_capacity < 0)
         return HOPH_ERR_PARAM;
@@ -1434,10 +1440,12 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
             bump.take(8);                                               // n_cand
             bump.take((size_t)n_rows * 4);                              // cand
         }
-        bump.take(cap1 * 16);  // sort A
-        bump.take(cap1 * 16);  // sort B
+        if (last) {
+            bump.take(cap1 * 16);  // sort A
+            bump.take(cap1 * 16);  // sort B
+        }
         if (pass == 0) {
-            unsigned char *base = (unsigned char *)hoph_scratch(plan, bump.off);
+            unsigned char *base = (unsigned char *)hoph_scratch(plan, bump.off, lane);
             if (!base) return HOPH_ERR_NOMEM;
             bump.base = base;
         }
@@ -1460,8 +1468,8 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         n_cand = (unsigned long long *)bump.take(8);
         cand = (uint32_t *)bump.take((size_t)n_rows * 4);
     }
-    ulonglong2 *sortA = (ulonglong2 *)bump.take(cap1 * 16);
-    ulonglong2 *sortB = (ulonglong2 *)bump.take(cap1 * 16);
+    ulonglong2 *sortA = last ? (ulonglong2 *)bump.take(cap1 * 16) : nullptr;
+    ulonglong2 *sortB = last ? (ulonglong2 *)bump.take(cap1 * 16) : nullptr;
 
     PairArgs pa;
     pa.coll = d_coll_planes;
@@ -1710,16 +1718,54 @@ int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int
     if (!d_planes) return HOPH_ERR_PARAM;
     const int64_t kg = plan->P.k_group;
     const int64_t cstride = n_rows * kg;
-    for (int64_t q0 = 0; q0 < n_rows - 1; q0 += batch) {
-        const int64_t nb = std::min(batch, n_rows - 1 - q0);
-        // rows q0 .. n_rows-1 against queries q0 .. q0+nb-1, both read in place
-        const bool last = q0 + batch >= n_rows - 1;
-        const uint32_t *blk = d_planes + q0 * kg;
-        const int rc = query_batch_impl<uint32_t>(plan, mode, blk, nb, blk, n_rows - q0, d_out,
-                                                  out_capacity, d_out_count, d_stats, stream,
-                                                  cstride, cstride, q0, false, last);
-        if (rc != HOPH_OK) return rc;
+    const int64_t n_blocks = (n_rows - 1 + batch - 1) / batch;
+    const int want = plan->exec.join_lanes > 0 ? plan->exec.join_lanes : 3;
+    const int lanes = (int)std::min<int64_t>(std::min(want, (int)hoph_plan::kMaxLanes), n_blocks);
+    // blocks in flight: block b runs on lane b % lanes, each lane a stream and
+    // a scratch of the plan's own, forked from and joined back to `stream`
+    if (lanes > 1) {
+        for (int i = 0; i < lanes; ++i) {
+            if (!plan->lane_stream[i])
+                HOPH_CUDA_TRY(cudaStreamCreateWithFlags(&plan->lane_stream[i], cudaStreamNonBlocking));
+            if (!plan->lane_event[i])
+                HOPH_CUDA_TRY(cudaEventCreateWithFlags(&plan->lane_event[i], cudaEventDisableTiming));
+        }
+        if (!plan->fork_event)
+            HOPH_CUDA_TRY(cudaEventCreateWithFlags(&plan->fork_event, cudaEventDisableTiming));
+        HOPH_CUDA_TRY(cudaEventRecord(plan->fork_event, s));
+        for (int i = 0; i < lanes; ++i)
+            HOPH_CUDA_TRY(cudaStreamWaitEvent(plan->lane_stream[i], plan->fork_event, 0));
     }
+    int rc = HOPH_OK;
+    for (int64_t blk = 0; blk < n_blocks && rc == HOPH_OK; ++blk) {
+        const int64_t q0 = blk * batch;
+        const int64_t nb = std::min(batch, n_rows - 1 - q0);
+        const int lane = (int)(blk % lanes);
+        cudaStream_t ls = lanes > 1 ? plan->lane_stream[lane] : s;
+        // rows q0 .. n_rows-1 against queries q0 .. q0+nb-1, both read in place
+        const uint32_t *bp = d_planes + q0 * kg;
+        rc = query_batch_impl<uint32_t>(plan, mode, bp, nb, bp, n_rows - q0, d_out, out_capacity,
+                                        d_out_count, d_stats, ls, cstride, cstride, q0, false,
+                                        false, lane);
+    }
+    if (lanes > 1) {  // join every lane back, also after an error
+        for (int i = 0; i < lanes; ++i) {
+            HOPH_CUDA_TRY(cudaEventRecord(plan->lane_event[i], plan->lane_stream[i]));
+            HOPH_CUDA_TRY(cudaStreamWaitEvent(s, plan->lane_event[i], 0));
+        }
+    }
+    if (rc != HOPH_OK) return rc;
+    // one sort of all blocks' pairs (lane 0's scratch is free again here)
+    const size_t cap1 = (size_t)std::max<int64_t>(out_capacity, 1);
+    ulonglong2 *sortA = (ulonglong2 *)hoph_scratch(plan, 2 * cap1 * 16, 0);
+    if (!sortA) return HOPH_ERR_NOMEM;
+    StatsFold none{};
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
+    sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(
+        d_out, reinterpret_cast<const unsigned long long *>(d_out_count), out_capacity, sortA,
+        sortA + cap1, plan->d_status, none);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    plan->launches += 1;
     return HOPH_OK;
 }
 

@@ -85,7 +85,7 @@ class hoph_exec(ctypes.Structure):
     _fields_ = [("strategy", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
                 ("consumer_warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32),
-                ("sketch_cta_bits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sketch_cta_bits", ctypes.c_int32), ("join_lanes", ctypes.c_int32)]
 
 
 class HophError(RuntimeError):
@@ -369,15 +369,15 @@ class Plan:
         self.close()
 
     def set_exec(self, strategy=-1, tile_rows=0, consumer_warps=0, ctas_per_sm=0, stages=0,
-                 lanes_per_row=0, sketch_cta_bits=0):
+                 lanes_per_row=0, sketch_cta_bits=0, join_lanes=0):
         """Replace all execution knobs (kept in self.exec_kwargs)."""
         hoph_plan_set_exec(self.handle, hoph_exec(strategy, tile_rows, consumer_warps,
                                                   ctas_per_sm, stages, lanes_per_row,
-                                                  sketch_cta_bits))
+                                                  sketch_cta_bits, join_lanes))
         self.exec_kwargs = dict(strategy=strategy, tile_rows=tile_rows,
                                 consumer_warps=consumer_warps, ctas_per_sm=ctas_per_sm,
                                 stages=stages, lanes_per_row=lanes_per_row,
-                                sketch_cta_bits=sketch_cta_bits)
+                                sketch_cta_bits=sketch_cta_bits, join_lanes=join_lanes)
 
     def update_exec(self, **knobs):
         """Change some execution knobs, keeping the others."""

@@ -402,6 +402,90 @@ def test_self_join_is_the_upper_triangle_of_the_all_pairs_query(small, mode, ab,
         assert stats.rejected[g] == np.count_nonzero((grp == g + 1) & (dec == 2)), ("rej", g)
 
 
+@pytest.fixture(scope="module")
+def self_join_case(small):
+    """(1:2)HOPH, k' = 64 over the 5,000 sets plus the 50 planted near
+    duplicates: the collection and the oracle's accepted upper-triangle pairs
+    with per-group decision counts."""
+    D, k, kg, ab = small["D"], 128, 64, (1, 2)
+    ids = np.concatenate([small["ids"], small["q_ids"]])
+    off = np.concatenate([small["off"], small["off"][-1] + small["q_off"][1:]])
+    n = len(off) - 1
+    lo = oc.layout(D, k, kg, *ab)
+    rows = oc.sketch(ids, off, lo, perm=oc.permutation(D, 1))
+    z = np.diff(lo[::kg]).astype(np.uint64)
+    full = oc.query("hoph", rows, rows, kg, T[0], T[1], EPS, z=z, per_pair=True)
+    want = full["accepted"]
+    want = [tuple(int(x) for x in w) for w in want[want[:, 0] < want[:, 1]]]
+    iu = np.triu_indices(n, 1)
+    dec, grp = full["dec"][iu], full["groups"][iu]
+    acc = [int(np.count_nonzero((grp == g + 1) & (dec == 1))) for g in range(k // kg)]
+    rej = [int(np.count_nonzero((grp == g + 1) & (dec == 2))) for g in range(k // kg)]
+    return dict(D=D, k=k, kg=kg, ab=ab, ids=ids, off=off, n=n, want=want, acc=acc, rej=rej)
+
+
+def _run_self_join(plan, c, n, batch, cap, dev, stream=None):
+    out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    st = torch.zeros(hoph.STATS_WORDS, dtype=torch.int64, device=dev)
+    hoph.hoph_self_join(plan.handle, hoph.HOPH_MODE_HOPH, c, n, batch, out, cap, cnt, st, stream)
+    return out, cnt, st
+
+
+def _self_join_result(out, cnt, st):
+    m = int(cnt.item())
+    got = out[:m].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+    stats = hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes())
+    return ([(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"])) for p in got],
+            stats)
+
+
+@pytest.mark.parametrize("lanes", [1, 3, 4])
+def test_self_join_blocks_in_flight_keep_the_result(self_join_case, lanes):
+    """join_lanes = 1, 3, 4 (blocks of 300 rows on that many of the plan's
+    streams at once): the oracle's upper-triangle pairs, in order, and its
+    per-group decision counts."""
+    dev = device()
+    w = self_join_case
+    with hoph.Plan(w["D"], w["k"], w["kg"], *w["ab"], seed=1, thr=T, epsilon=EPS) as plan:
+        c = plan.sketch(to_dev(w["ids"], dev), to_dev(w["off"], dev), w["n"])
+        plan.update_exec(join_lanes=lanes)
+        got, stats = _self_join_result(*_run_self_join(plan, c, w["n"], 300, 1 << 14, dev))
+        plan.check()
+    assert got == w["want"]
+    assert stats.entering[0] == w["n"] * (w["n"] - 1) // 2
+    assert list(stats.accepted[:len(w["acc"])]) == w["acc"]
+    assert list(stats.rejected[:len(w["rej"])]) == w["rej"]
+
+
+def test_self_join_with_lanes_replays_from_a_graph(self_join_case):
+    """The self-join's fork onto the plan's streams and join back, captured
+    in a CUDA graph (after one eager call has created the streams) and
+    replayed twice: the oracle's pairs each time."""
+    dev = device()
+    w = self_join_case
+    with hoph.Plan(w["D"], w["k"], w["kg"], *w["ab"], seed=1, thr=T, epsilon=EPS) as plan:
+        c = plan.sketch(to_dev(w["ids"], dev), to_dev(w["off"], dev), w["n"])
+        plan.update_exec(join_lanes=2)
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            bufs = _run_self_join(plan, c, w["n"], 400, 1 << 14, dev, side)
+            side.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                hoph.hoph_self_join(plan.handle, hoph.HOPH_MODE_HOPH, c, w["n"], 400, bufs[0],
+                                    1 << 14, bufs[1], None, side)
+        torch.cuda.synchronize()
+        for _ in range(2):
+            bufs[0].zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            got, _ = _self_join_result(*bufs)
+            assert got == w["want"]
+        plan.check()
+
+
 def test_compact_planes_with_a_hashed_join():
     """Compact planes over a key space that needs the hashed group map and
     the key table (D = 256 x 65,535, k = 256 bins of 65,535 values, the
