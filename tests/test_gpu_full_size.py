@@ -73,15 +73,19 @@ def test_full_size_query_matches_the_oracle_on_sampled_rows():
         plan.check()
         plan.set_exec(strategy=1, lanes_per_row=0, consumer_warps=16, stages=3)
         pairs, m, st = plan.query(hoph.HOPH_MODE_HOPH, q, nq, planes, n, stats=True)
-        # compact 16-bit planes in the shape the benchmark tunes for them
-        plan.set_exec(strategy=1, lanes_per_row=4, consumer_warps=31, stages=2)
-        pairs16, m16, _ = plan.query(hoph.HOPH_MODE_HOPH, q16, nq, planes16, n)
+        # compact 16-bit planes, in both shapes the benchmark's tuner has picked
+        # for them (16 warps, two lanes per row; 31 warps, four lanes per row)
+        compact = []
+        for lpr, cw, stg in ((0, 16, 3), (4, 31, 2)):
+            plan.set_exec(strategy=1, lanes_per_row=lpr, consumer_warps=cw, stages=stg)
+            compact.append(plan.query(hoph.HOPH_MODE_HOPH, q16, nq, planes16, n)[:2])
         G = plan.G
         rng = np.random.default_rng(5)
         src = qw["src"][qw["src"] >= 0]
         sample = np.unique(np.concatenate([rng.choice(n, 4096, replace=False),
                                            pairs["row"].astype(np.int64),
-                                           pairs16["row"].astype(np.int64), src]))
+                                           *[p["row"].astype(np.int64) for p, _ in compact],
+                                           src]))
         got_rows = _device_rows(planes, sample, dev)
         idx = torch.from_numpy(sample).to(dev)
         got_rows16 = planes16.index_select(1, idx).cpu().numpy().view(np.uint16) \
@@ -103,8 +107,9 @@ def test_full_size_query_matches_the_oracle_on_sampled_rows():
     # compact planes: the offsets in 16 bits (empty 0xFFFF), the same pairs
     want16 = np.where(want_rows == hoph.HOPH_EMPTY_VALUE, hoph.HOPH_EMPTY_VALUE16, want_rows)
     assert np.array_equal(got_rows16, want16.astype(np.uint16))
-    assert m16 == m and {(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"]))
-                         for p in pairs16} == want_set
+    for pairs16, m16 in compact:
+        assert m16 == m and {(int(p["query"]), int(p["row"]), int(p["groups"]),
+                              int(p["matches"])) for p in pairs16} == want_set
     assert sum(1 for p in want_set if p[1] in set(src.tolist())) > 0
     assert st.entering[0] == nq * n
     assert sum(st.accepted[g] for g in range(G)) == m
