@@ -238,9 +238,12 @@ __device__ __forceinline__ void flush_stats(const unsigned long long *s_stats,
 __device__ void produce_tiles(const CUtensorMap *map, unsigned char *stages, uint64_t *full,
                               uint64_t *empty, volatile int32_t *abort_flag, int nstages,
                               uint32_t stage_bytes, uint32_t stage_stride, int64_t n_tiles,
-                              int R, int32_t *status, bool four_d = false) {
+                              int R, int32_t *status, bool four_d = false, int prefetch = 0) {
     tma_prefetch_desc(map);
     int64_t it = 0;
+    // 4-D maps: as each tile is issued, the CTA's tile `prefetch` strides
+    // ahead is asked into L2, so more of the stream is in flight than the
+    // shared-memory stages hold
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
         const int s = (int)(it % nstages);
         const uint32_t use = (uint32_t)(it / nstages);
@@ -250,9 +253,13 @@ __device__ void produce_tiles(const CUtensorMap *map, unsigned char *stages, uin
             break;
         }
         mbar_arrive_expect_tx(full + s, stage_bytes);
-        if (four_d)
+        if (four_d) {
+            const int64_t ahead = tile + (int64_t)prefetch * gridDim.x;
+            if (prefetch > 0 && ahead < n_tiles)
+                tma_prefetch_l2_4d(map, 0, 0, (int32_t)(ahead * R), 0);
             tma_load_4d(stages + (size_t)s * stage_stride, map, full + s, 0, 0,
                         (int32_t)(tile * R), 0);
+        }
         else
             tma_load_3d(stages + (size_t)s * stage_stride, map, full + s, 0, (int32_t)(tile * R),
                         0);
@@ -587,6 +594,9 @@ struct FilterArgs {
     int32_t *status;
 };
 
+// join filter: tiles per CTA prefetched into L2 ahead of the TMA loads
+constexpr int kFilterPrefetch = 1;
+
 struct FilterSmem {
     uint32_t bars, abort_flag, row_min, gmap, stages, total;
 };
@@ -641,7 +651,7 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
     if (warp == a.n_cons) {
         if (lane == 0)
             produce_tiles(&map, stages, full, empty, abort_flag, a.stages, a.stage_bytes,
-                          a.stage_stride, a.n_tiles, R, a.status, true);
+                          a.stage_stride, a.n_tiles, R, a.status, true, kFilterPrefetch);
         return;
     }
     {
