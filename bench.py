@@ -532,8 +532,13 @@ def run_native(args):
                       "join_hits": int(stats.join_hits), "strategy": int(stats.strategy),
                       "rows_counted": int(stats.rows_counted)}}
 
-    if rank == 0 and not args.no_extras:
-        line["e2e"] = e2e_leg(args, plan, qw, planes, dev, stream)
+    if not args.no_extras:  # every rank: the end-to-end step is timed over all of them
+        def sync(x):
+            barrier()
+            return max_over_ranks(x)
+        line["e2e"] = e2e_leg(args, plan, qw, planes, dev, stream, world, sync)
+    # the other legs are single-GPU studies: rank 0 of a one-GPU run only
+    if rank == 0 and world == 1 and not args.no_extras:
         line["sketch"] = sketch_leg(dev, stream, peaks)
         rq = recall_queries(off, coll_seed)
         line["oph_full_scan_baseline"], oph_pairs, oph_rq_pairs = oph_baseline_leg(
@@ -566,9 +571,11 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
-def e2e_leg(args, plan, qw, planes, dev, stream):
+def e2e_leg(args, plan, qw, planes, dev, stream, world=1, sync=None):
     """Same step through the public API from pinned host buffers: H2D of the
-    query sets, sketch, query, D2H of the count and the accepted pairs."""
+    query sets, sketch, query, D2H of the count and the accepted pairs.  On
+    several ranks every rank runs it between barriers (`sync(x)`: barrier and
+    max over ranks of x) and the value counts all ranks' pairs."""
     import torch
     from paper_1805_11254_gb300 import hoph
     nq = args.queries
@@ -598,15 +605,18 @@ def e2e_leg(args, plan, qw, planes, dev, stream):
         stream.synchronize()
         d2h = 8 + 16 * n
 
+    sync = sync or (lambda x: x)
     for _ in range(3):
         once()
+    sync(0.0)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         once()
-    dt = (time.perf_counter() - t0) / args.e2e_steps
+    dt = sync((time.perf_counter() - t0) / args.e2e_steps)
     h2d = int(h_ids.numel() * 4 + h_off.numel() * 8)
-    serial = {"value": nq * args.rows / dt, "ms_per_step": dt * 1e3, "d2h_bytes_per_step": d2h}
-    pipe = e2e_in_flight(args, plan, h_ids, h_off, planes, dev)
+    serial = {"value": nq * args.rows * world / dt, "ms_per_step": dt * 1e3,
+              "d2h_bytes_per_step": d2h}
+    pipe = e2e_in_flight(args, plan, h_ids, h_off, planes, dev, world=world, sync=sync)
     best = pipe if pipe["value"] > serial["value"] else serial
     return {"value": best["value"], "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": int(best["d2h_bytes_per_step"]),
@@ -616,7 +626,8 @@ def e2e_leg(args, plan, qw, planes, dev, stream):
             "path": "pinned host sets -> oph_build_sketches -> hoph_query_batch -> host pairs"}
 
 
-def e2e_in_flight(args, plan, h_ids, h_off, planes, dev, n_lanes=3, window=4096):
+def e2e_in_flight(args, plan, h_ids, h_off, planes, dev, n_lanes=3, window=4096, world=1,
+                  sync=None):
     """The end-to-end step with several batches in flight: each lane (its own
     plan and stream) copies a batch's sets in, sketches and queries them and
     copies the count and the first `window` pairs back; a lane's results are
@@ -669,17 +680,19 @@ def e2e_in_flight(args, plan, h_ids, h_off, planes, dev, n_lanes=3, window=4096)
         for ln in lanes:
             if ln["busy"]:
                 finish(ln)
+    sync = sync or (lambda x: x)
     run(3 * n_lanes)
     for ln in lanes:
         ln["extra"] = 0
+    sync(0.0)
     t0 = time.perf_counter()
     run(args.e2e_steps)
-    dt = (time.perf_counter() - t0) / args.e2e_steps
+    dt = sync((time.perf_counter() - t0) / args.e2e_steps)
     extra = sum(ln["extra"] for ln in lanes) / args.e2e_steps
     for ln in lanes:
         ln["plan"].check()
         ln["plan"].close()
-    return {"value": nq * args.rows / dt, "ms_per_step": dt * 1e3,
+    return {"value": nq * args.rows * world / dt, "ms_per_step": dt * 1e3,
             "d2h_bytes_per_step": 8 + 16 * window + extra,
             "schedule": "%d batches in flight (one plan and stream each)" % n_lanes}
 
