@@ -800,7 +800,7 @@ __host__ __device__ inline CountSmem count_smem(const CountArgs &a) {
 // passes, and the next candidate row's values are loaded while the current
 // one is counted.
 template <int NCH, typename E>
-__global__ void __launch_bounds__(kCountThreads, 4) count_kernel(const __grid_constant__ CountArgs a) {
+__global__ void __launch_bounds__(kCountThreads, 3) count_kernel(const __grid_constant__ CountArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const CountSmem L = count_smem(a);
     const PairArgs &P = a.p;

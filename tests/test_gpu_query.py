@@ -486,6 +486,39 @@ def test_self_join_with_lanes_replays_from_a_graph(self_join_case):
         plan.check()
 
 
+def test_self_join_edges_capacity_and_arguments(self_join_case):
+    """Fewer than two rows: no pairs.  An output buffer of 3 pairs: the
+    device reports HOPH_ERR_CAPACITY, the count is the oracle's full count,
+    and the 3 kept pairs are genuine (sorted among themselves).  Bad batch
+    sizes and MinWise are refused on the host before anything runs."""
+    dev = device()
+    w = self_join_case
+    with hoph.Plan(w["D"], w["k"], w["kg"], *w["ab"], seed=1, thr=T, epsilon=EPS) as plan:
+        c = plan.sketch(to_dev(w["ids"], dev), to_dev(w["off"], dev), w["n"])
+        plan.check()
+        for n in (0, 1):
+            out, cnt, _ = _run_self_join(plan, c, n, 64, 4, dev)
+            plan.check()
+            assert int(cnt.item()) == 0
+        out, cnt, _ = _run_self_join(plan, c, w["n"], 500, 3, dev)
+        assert hoph.hoph_sync_status(plan.handle) == hoph.HOPH_ERR_CAPACITY
+        assert int(cnt.item()) == len(w["want"])
+        kept = [(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"]))
+                for p in out.cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)]
+        assert kept == sorted(kept) and set(kept) <= set(w["want"])
+        out = torch.empty((4, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        for batch in (0, 4097):
+            with pytest.raises(hoph.HophError) as e:
+                hoph.hoph_self_join(plan.handle, hoph.HOPH_MODE_HOPH, c, w["n"], batch, out, 4,
+                                    cnt)
+            assert e.value.code == hoph.HOPH_ERR_PARAM
+        with pytest.raises(hoph.HophError) as e:
+            hoph.hoph_self_join(plan.handle, "minwise_full", c, w["n"], 64, out, 4, cnt)
+        assert e.value.code == hoph.HOPH_ERR_UNSUPPORTED
+        plan.check()
+
+
 def test_compact_planes_with_a_hashed_join():
     """Compact planes over a key space that needs the hashed group map and
     the key table (D = 256 x 65,535, k = 256 bins of 65,535 values, the
