@@ -1426,7 +1426,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     if (strategy < 0) strategy = (join_ok && n_queries >= 16) ? 1 : 0;
 
     const int mask_words = (W + 31) / 32;
-    // group map words (+ the zero word), padded for the filter's bulk copy
+    // group map words (+ the zero word), padded for the filter's 16-byte copy
     const uint64_t gmap_alloc = (map_slots / 16 + 2 + 3) & ~3ull;
     int wshift = 0;  // bits of a scanned-bin index (join index entries)
     while ((1 << wshift) < W) ++wshift;
