@@ -434,3 +434,22 @@ class Plan:
             s = hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes())
             st_out = s
         return pairs, n, st_out
+
+    def self_join(self, mode, planes, n_rows, batch=1536, capacity=1 << 16, stream=None,
+                  stats=False, check=True):
+        """Run hoph_self_join over one collection's planes; returns (pairs
+        structured ndarray with query < row, count, stats)."""
+        import torch
+        dev = planes.device
+        out = torch.empty((max(capacity, 1), 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        st = torch.zeros(STATS_WORDS, dtype=torch.int64, device=dev) if stats else None
+        hoph_self_join(self.handle, mode, planes, n_rows, batch, out, capacity, cnt, st, stream)
+        if check:
+            rc = hoph_sync_status(self.handle, stream)
+            if rc not in (HOPH_OK, HOPH_ERR_CAPACITY):
+                raise HophError(rc, "hoph_self_join (device)")
+        n = int(cnt.item())
+        pairs = out[:min(n, capacity)].cpu().numpy().view(PAIR_DTYPE).reshape(-1)
+        st_out = hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes()) if stats else None
+        return pairs, n, st_out

@@ -443,15 +443,17 @@ def _self_join_result(out, cnt, st):
 @pytest.mark.parametrize("lanes", [1, 3, 4])
 def test_self_join_blocks_in_flight_keep_the_result(self_join_case, lanes):
     """join_lanes = 1, 3, 4 (blocks of 300 rows on that many of the plan's
-    streams at once): the oracle's upper-triangle pairs, in order, and its
-    per-group decision counts."""
+    streams at once), through Plan.self_join: the oracle's upper-triangle
+    pairs, in order, and its per-group decision counts."""
     dev = device()
     w = self_join_case
     with hoph.Plan(w["D"], w["k"], w["kg"], *w["ab"], seed=1, thr=T, epsilon=EPS) as plan:
         c = plan.sketch(to_dev(w["ids"], dev), to_dev(w["off"], dev), w["n"])
         plan.update_exec(join_lanes=lanes)
-        got, stats = _self_join_result(*_run_self_join(plan, c, w["n"], 300, 1 << 14, dev))
-        plan.check()
+        pairs, m, stats = plan.self_join("hoph", c, w["n"], batch=300, stats=True)
+        got = [(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"]))
+               for p in pairs]
+    assert m == len(got)
     assert got == w["want"]
     assert stats.entering[0] == w["n"] * (w["n"] - 1) // 2
     assert list(stats.accepted[:len(w["acc"])]) == w["acc"]
