@@ -546,10 +546,14 @@ def run_native(args):
         line["quality"] = quality(qw, {"hoph": pairs, "oph_full_scan": oph_pairs}, off,
                                   coll_seed, args)
         eps_runs = eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq)
+        thr_runs = eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq,
+                                variants=[(t, EPS) for t in EQUAL_RECALL_T])
         methods = {"oph_full_scan": oph_rq_pairs}
         methods.update({"hoph_eps_%g" % e: r["pairs"] for e, r in eps_runs.items()})
+        methods.update({"hoph_T_%d_%d" % t: r["pairs"] for t, r in thr_runs.items()})
         study = quality(rq, methods, off, coll_seed, args, n_random_rows=500)
-        line["equal_recall"] = equal_recall(study, eps_runs, nq, args.rows, len(rq["q_off"]) - 1)
+        line["equal_recall"] = equal_recall(study, eps_runs, nq, args.rows, len(rq["q_off"]) - 1,
+                                            thr_runs)
         line["cpu_baseline"] = cpu_baseline(qw, off, coll_seed, args.cpu_seconds, args.rows)
         if not args.no_serve:
             line["serving"] = serving_leg(args, planes, dev, line["oph_full_scan_baseline"])
@@ -698,6 +702,8 @@ def e2e_in_flight(args, plan, h_ids, h_off, planes, dev, n_lanes=3, window=4096,
 
 
 EQUAL_RECALL_EPS = (1e-4, 1e-5, 1e-6, 1e-8, 0.0)
+EQUAL_RECALL_T = ((699, 1000), (698, 1000), (697, 1000), (696, 1000), (695, 1000), (69, 100),
+                  (68, 100), (67, 100))
 RECALL_QUERIES = 4096
 
 
@@ -709,12 +715,15 @@ def recall_queries(off, coll_seed):
                              PLANT_SEED + 50)
 
 
-def eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq, reps=20):
+def eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq, reps=20,
+                 variants=None):
     """The same step (sketch the query sets, HOPH query) at smaller error
-    tolerances: the sketches do not depend on eps, only the decisions do.
-    Returns {eps: {"pairs", "ms"}}: the pairs of the recall query set `rq`
-    (one call of 4,096 queries) and the eager CUDA-event time of the
-    benchmark's 1,024-query step."""
+    tolerances (or, with `variants` = [(thr, eps)], at other decision
+    thresholds): the sketches do not depend on eps or the threshold, only the
+    decisions do.  Returns {key: {"pairs", "ms"}} (key eps, or thr with
+    variants): the pairs of the recall query set `rq` (one call of 4,096
+    queries) and the eager CUDA-event time of the benchmark's 1,024-query
+    step."""
     import torch
     from paper_1805_11254_gb300 import hoph
     rq_ids, rq_off = to_dev(rq["q_ids"], dev), to_dev(rq["q_off"], dev)
@@ -723,8 +732,10 @@ def eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq, reps=20):
     cap = 1 << 20
     o = torch.empty((cap, 2), dtype=torch.int64, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-    for eps in EQUAL_RECALL_EPS:
-        with hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=eps) as p:
+    runs = variants if variants is not None else [(T, e) for e in EQUAL_RECALL_EPS]
+    for thr, eps in runs:
+        key = thr if variants is not None else eps
+        with hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=thr, epsilon=eps) as p:
             qp = torch.empty((p.G, nq, KG), dtype=torch.int32, device=dev)
 
             def step():
@@ -748,14 +759,18 @@ def eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq, reps=20):
                                   cap, cnt, None, stream)
             p.check(stream)
             n = int(cnt.item())
-            out[eps] = {"pairs": o[:min(n, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+            out[key] = {"pairs": o[:min(n, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
                         .copy(), "ms": ms}
     return out
 
 
-def equal_recall(q, eps_runs, nq, rows, n_rq):
+def equal_recall(q, eps_runs, nq, rows, n_rq, thr_runs=None):
     """The largest eps at which HOPH's recall on the recall query set reaches
-    plain OPH's, with the benchmark step's eager throughput at each eps."""
+    plain OPH's, with the benchmark step's eager throughput at each eps.  The
+    recall gap is the final estimator's (Lemma 3 weighs the groups by their
+    space; OPH pools all bins), which no eps closes; so the largest decision
+    threshold T' <= T at which HOPH (eps = 1e-4) reaches OPH's recall, ground
+    truth still exact Jaccard >= T, is reported too."""
     target = q["oph_full_scan"]["recall"]
     pts = []
     for eps, r in eps_runs.items():
@@ -764,9 +779,22 @@ def equal_recall(q, eps_runs, nq, rows, n_rq):
                     "ms_per_step_eager": r["ms"], "value": nq * rows / (r["ms"] / 1e3)})
     ok = [p for p in pts if p["recall"] >= target]
     best = max(ok, key=lambda p: p["eps"]) if ok else None
-    return {"oph_full_scan_recall": target, "points": pts,
+    tpts = []
+    for thr, r in (thr_runs or {}).items():
+        m = q["hoph_T_%d_%d" % thr]
+        tpts.append({"T": "%d/%d" % thr, "t": thr[0] / thr[1], "recall": m["recall"],
+                     "precision": m["precision"], "ms_per_step_eager": r["ms"],
+                     "value": nq * rows / (r["ms"] / 1e3)})
+    tok = [p for p in tpts if p["recall"] >= target]
+    tbest = max(tok, key=lambda p: p["t"]) if tok else None
+    return {"oph_full_scan_recall": target,
+            "oph_full_scan_precision": q["oph_full_scan"]["precision"], "points": pts,
             "eps_at_equal_recall": best["eps"] if best else None,
             "value_at_equal_recall": best["value"] if best else None,
+            "threshold_points": tpts,
+            "decision_threshold_at_equal_recall": tbest["T"] if tbest else None,
+            "precision_at_equal_recall": tbest["precision"] if tbest else None,
+            "value_at_equal_recall_by_threshold": tbest["value"] if tbest else None,
             "unit": UNIT, "recall_queries": n_rq, "truly_similar": q["truly_similar"],
             "how": "recall of %d query sets (half planted) against exact Jaccard; eps only "
                    "changes the decisions; throughput = eager step timing (sketch + query) of "
