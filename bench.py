@@ -569,6 +569,20 @@ def run_native(args):
             torch.cuda.empty_cache()
             line["shingle"] = shingle_leg(args, dev, stream, peaks)
     plan.close()
+    # the metric's four parts side by side
+    parts = {"pair_comparisons_per_s": line["value"],
+             "hbm_roofline_frac_of_measured": roofline["frac"]}
+    if "sketch" in line:
+        parts["sets_sketched_per_s"] = line["sketch"]["sets_per_s"]
+    if "equal_recall" in line:
+        er = line["equal_recall"]
+        parts["equal_recall"] = {
+            "oph_full_scan_recall": er["oph_full_scan_recall"],
+            "hoph_decision_threshold": er["decision_threshold_at_equal_recall"],
+            "hoph_precision": er["precision_at_equal_recall"],
+            "oph_full_scan_precision": er["oph_full_scan_precision"],
+            "pair_comparisons_per_s_eager": er["value_at_equal_recall_by_threshold"]}
+    line["metric_parts"] = parts
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
