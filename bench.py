@@ -890,7 +890,11 @@ def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
                         " k = 256 OPH",
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": gbs / peaks["hbm_gbs"], "traffic": None,
-                         "algorithmic_bytes_per_launch": bytes_}}
+                         "algorithmic_bytes_per_launch": bytes_,
+                         "binding_limit": "L1 data pipe: one random psi gather and one shared "
+                                          "atomicMin per ID, 84% of its peak in the ncu capture "
+                                          "(profiles/oph_sketch_kernel_1e6sets.md); DRAM moves "
+                                          "only the algorithmic bytes"}}
 
 
 def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
