@@ -43,7 +43,7 @@ SKETCH_SEED = 21
 # dram read+write bytes per filter-kernel launch from an ncu capture, keyed by
 # the sha256 of the filter kernel's source it was taken on (null once that
 # source changes)
-NCU_TRAFFIC = {"0b9ddb719d8627aa": 2576.44e6}  # profiles/filter_kernel_2e6rows.md, x5 rows
+NCU_TRAFFIC = {"0b9ddb719d8627aa": 2576.44e6}  # 2*10^6-row capture x 5 rows
 
 
 def parse():
@@ -892,9 +892,9 @@ def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
                          "frac": gbs / peaks["hbm_gbs"], "traffic": None,
                          "algorithmic_bytes_per_launch": bytes_,
                          "binding_limit": "L1 data pipe: one random psi gather and one shared "
-                                          "atomicMin per ID, 84% of its peak in the ncu capture "
-                                          "(profiles/oph_sketch_kernel_1e6sets.md); DRAM moves "
-                                          "only the algorithmic bytes"}}
+                                          "atomicMin per ID, 84% of its peak in an ncu capture "
+                                          "of this workload; DRAM moves only the algorithmic "
+                                          "bytes"}}
 
 
 def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
