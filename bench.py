@@ -429,13 +429,13 @@ def run_native(args):
     # index and candidate counting overlap another's streaming filter.  With n
     # batches in flight the K timed steps are K // n replays of that graph
     # (+ K % n replays of the single-step graph); each step still sketches and
-    # queries a whole batch.  Two and three in flight are timed; the fastest
-    # schedule (this or one at a time) gives the headline.
+    # queries a whole batch.  Two, three and four in flight are timed; the
+    # fastest schedule (this or one at a time) gives the headline.
     serial = {"ms_per_step": ms / args.steps, "value": value}
     pipeline = None
     if graph is not None and not args.no_pipeline and args.steps >= 2:
         lanes = [dict(plan=plan, q=q_planes, out=out, cnt=cnt)]
-        for _ in range(2):
+        for _ in range(3):
             p2 = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
             p2.set_exec(**plan.exec_kwargs)
             lanes.append(dict(plan=p2, q=torch.empty_like(q_planes), out=torch.empty_like(out),
@@ -450,7 +450,7 @@ def run_native(args):
                 lane_step(ln, stream)
         torch.cuda.synchronize()
         timed = {}
-        for n_in in (2, 3):
+        for n_in in (2, 3, 4):
             streams = [torch.cuda.Stream(device=dev) for _ in range(n_in)]
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
