@@ -58,9 +58,11 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=100)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-extras", action="store_true", help="skip sketch/OPH/CPU legs")
-    p.add_argument("--profile", nargs="?", const="query", choices=("query", "sketch", "oph1"),
-                   help="few launches of the query step (or of the 10^6-set sketch, or of the "
-                        "one-query OPH full scan with its tuned knobs), for ncu")
+    p.add_argument("--profile", nargs="?", const="query",
+                   choices=("query", "sketch", "oph1", "self_join"),
+                   help="few launches of the query step (or of the 10^6-set sketch, of the "
+                        "one-query OPH full scan with its tuned knobs, or one self-join of "
+                        "the first --rows rows), for ncu")
     p.add_argument("--no-graph", action="store_true", help="eager launches instead of a graph")
     p.add_argument("--no-pipeline", action="store_true",
                    help="one batch at a time (no second batch in flight on a second stream)")
@@ -307,6 +309,9 @@ def run_native(args):
     off, coll_seed = collection_host(args.rows, rank)
     if args.profile == "oph1":
         profile_oph1(args, off, coll_seed, dev, stream)
+        return
+    if args.profile == "self_join":
+        profile_self_join(args, off, coll_seed, dev, stream)
         return
     n_ids = int(off[-1])
     plan = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
@@ -895,6 +900,23 @@ def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
                                           "atomicMin per ID, 84% of its peak in an ncu capture "
                                           "of this workload; DRAM moves only the algorithmic "
                                           "bytes"}}
+
+
+def profile_self_join(args, off, coll_seed, dev, stream, batch=1536):
+    """One hoph_self_join over the collection's first --rows rows ((1:2)HOPH,
+    blocks of 1,536 rows, the library's default blocks in flight), for an ncu
+    launch list."""
+    import torch
+    from paper_1805_11254_gb300 import hoph
+    n = args.rows
+    with hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS) as plan:
+        n_ids = int(off[n])
+        d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+        hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
+        planes = plan.sketch(d_ids, to_dev(off[:n + 1], dev), n, stream=stream)
+        del d_ids
+        pairs, m, _ = plan.self_join("hoph", planes, n, batch=batch, stream=stream)
+        print(json.dumps({"self_join_rows": n, "batch": batch, "accepted": m}), flush=True)
 
 
 def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
