@@ -44,6 +44,29 @@ def test_struct_sizes_match_header_layout():
     assert hoph.PAIR_DTYPE.itemsize == 16
     assert ctypes.sizeof(hoph.hoph_stats) == 8 * (3 * 16 + 4)
     assert ctypes.sizeof(hoph.hoph_params) == 64
+    assert ctypes.sizeof(hoph.hoph_exec) == 32
+
+
+def _header_fields(struct_name):
+    """Member names of `typedef struct {...} struct_name;` in include/hoph.h."""
+    text = open(os.path.join(ROOT, "include", "hoph.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct\s*\{([^{}]*)\}\s*%s\s*;" % struct_name, text)
+    assert m, struct_name
+    names = []
+    for decl in m.group(1).split(";"):
+        decl = " ".join(decl.split())
+        if decl:  # "type name[, name...]" with optional array suffixes
+            _, declarators = decl.split(" ", 1)
+            names += [re.sub(r"\[.*\]", "", d).strip(" *") for d in declarators.split(",")]
+    return names
+
+
+@pytest.mark.parametrize("name", ["hoph_params", "hoph_exec", "hoph_stats", "hoph_plan_info"])
+def test_binding_structs_follow_the_header(name):
+    """The ctypes mirrors of the ABI structs name the same members in the
+    same order as include/hoph.h."""
+    assert [f[0] for f in getattr(hoph, name)._fields_] == _header_fields(name)
 
 
 @pytest.mark.parametrize("kw", [dict(k=100, k_group=32), dict(k=128, k_group=0),
