@@ -346,7 +346,8 @@ def run_native(args):
 
     from paper_1805_11254_gb300 import autotune
     best, tune_ms = None, {}
-    if not args.no_tune:
+    if not args.no_tune:  # tuned on this batch's own sketches
+        hoph.oph_build_sketches(plan.handle, dq_ids, dq_off, nq, q_planes, stream)
         best, tune_ms = autotune.tune_query(plan, hoph.HOPH_MODE_HOPH, q_planes, nq, planes,
                                             args.rows, out, cap, cnt, stream)
     for _ in range(args.warmup):

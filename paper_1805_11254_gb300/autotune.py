@@ -32,9 +32,12 @@ def _lanes(cand, W):
 
 
 def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
-               stream=None, reps=3, candidates=None):
+               stream=None, reps=3, candidates=None, finalists=3, rounds=4):
     """Pick the fastest execution setting for this batch shape; returns
-    (best setting, {setting index: ms}).  Compact (16-bit) planes go through
+    (best setting, {setting index: ms}).  Every candidate is timed once; the
+    `finalists` fastest are then timed again, interleaved, `rounds` times,
+    and the lowest median wins (one short timing per candidate cannot tell
+    settings a few percent apart).  Compact (16-bit) planes go through
     hoph_query_batch16."""
     import torch
     call = hoph.hoph_query_batch16 if c_planes.element_size() == 2 else hoph.hoph_query_batch
@@ -48,8 +51,24 @@ def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity,
     stream = stream or torch.cuda.current_stream()
     times = {}
     ref = None
-    best, best_ms = None, None
+    best = None
+    tried = {}
     W = plan.k if mode in (0, "oph_full") else plan.kg
+
+    def timed(cand):
+        plan.update_exec(**{**QUERY_DEFAULTS, **cand})
+        call(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
+             None, stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
+                 None, stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
     for i, cand in enumerate(candidates):
         cand = _lanes(cand, W)
         if cand["strategy"] == 0 and n_queries >= 256 and n_rows >= 1 << 20:
@@ -67,18 +86,20 @@ def tune_query(plan, mode, q_planes, n_queries, c_planes, n_rows, out, capacity,
             ref = (n, got)
         elif n != ref[0] or not np.array_equal(got, ref[1]):
             raise RuntimeError("execution setting %r changed the result" % cand)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            call(plan.handle, mode, q_planes, n_queries, c_planes, n_rows, out, capacity, count,
-                 None, stream)
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        times[i] = ms
-        if best_ms is None or ms < best_ms:
-            best, best_ms = cand, ms
+        times[i] = timed(cand)
+        tried[i] = cand
+    if len(tried) > 1 and finalists > 1 and rounds > 0:
+        top = sorted(tried, key=times.get)[:finalists]
+        runs = {i: [] for i in top}
+        for _ in range(rounds):
+            for i in top:
+                runs[i].append(timed(tried[i]))
+        for i in top:
+            times[i] = float(np.median(runs[i]))
+        best_i = min(top, key=times.get)
+        best = tried[best_i]
+    elif tried:
+        best = tried[min(tried, key=times.get)]
     if best is None:
         plan.update_exec(**QUERY_DEFAULTS)
         return None, times
@@ -91,7 +112,7 @@ SKETCH_CANDIDATES = (0, 10, 11, 12, 13, 14, 64)
 
 
 def tune_sketch(plan, d_ids, d_offsets, n_sets, out, stream=None, reps=3,
-                candidates=SKETCH_CANDIDATES):
+                candidates=SKETCH_CANDIDATES, finalists=3, rounds=4):
     """Pick the size (bits of a set's ID count) from which a set gets a whole
     CTA instead of one warp, for this batch; 0 is the library's own choice,
     64 warps only.  Every setting must give the same sketches.  Returns
@@ -103,7 +124,19 @@ def tune_sketch(plan, d_ids, d_offsets, n_sets, out, stream=None, reps=3,
         return _cache[key], {}
     stream = stream or torch.cuda.current_stream()
     call = hoph.oph_build_sketches16 if out.element_size() == 2 else hoph.oph_build_sketches
-    times, ref, best, best_ms = {}, None, None, None
+    def timed(bits):
+        plan.update_exec(sketch_cta_bits=bits)
+        call(plan.handle, d_ids, d_offsets, n_sets, out, stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call(plan.handle, d_ids, d_offsets, n_sets, out, stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    times, ref = {}, None
     for bits in candidates:
         plan.update_exec(sketch_cta_bits=bits)
         call(plan.handle, d_ids, d_offsets, n_sets, out, stream)
@@ -113,16 +146,17 @@ def tune_sketch(plan, d_ids, d_offsets, n_sets, out, stream=None, reps=3,
             ref = got
         elif not torch.equal(got, ref):
             raise RuntimeError("sketch_cta_bits=%d changed the sketches" % bits)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            call(plan.handle, d_ids, d_offsets, n_sets, out, stream)
-        e1.record(stream)
-        e1.synchronize()
-        times[bits] = e0.elapsed_time(e1) / reps
-        if best_ms is None or times[bits] < best_ms:
-            best, best_ms = bits, times[bits]
+        times[bits] = timed(bits)
+    # the closest settings again, interleaved (as for the query knobs)
+    top = sorted(times, key=times.get)[:finalists]
+    runs = {b: [] for b in top}
+    for _ in range(rounds if len(top) > 1 else 0):
+        for b in top:
+            runs[b].append(timed(b))
+    for b in top:
+        if runs[b]:
+            times[b] = float(np.median(runs[b]))
+    best = min(top, key=times.get)
     plan.update_exec(sketch_cta_bits=best)
     _cache[key] = best
     return best, times

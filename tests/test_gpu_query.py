@@ -545,3 +545,32 @@ def test_compact_planes_with_a_hashed_join():
         pairs, n, st = plan.query("oph_full", q16, q16.shape[1], c16, c16.shape[1], stats=True)
         assert st.strategy == 1
         assert pairs_tuples(pairs) == oracle_tuples(want)
+
+
+def test_autotuner_keeps_the_result_and_sets_the_fastest_knobs(small):
+    """autotune.tune_query over the join and dense settings: every setting
+    it times returns the oracle's pairs (it raises otherwise), the chosen one
+    is left on the plan, and the pairs after tuning are still the oracle's;
+    tune_sketch likewise for the sketch's CTA-size knob."""
+    from paper_1805_11254_gb300 import autotune
+    dev = device()
+    D, k, kg, ab = small["D"], 128, 32, (1, 1)
+    with hoph.Plan(D, k, kg, *ab, seed=1, thr=T, epsilon=EPS) as plan:
+        q, c = _sketch_both(plan, small, dev)
+        nq, nr = q.shape[1], c.shape[1]
+        cap = 1 << 14
+        out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        best, times = autotune.tune_query(plan, "hoph", q, nq, c, nr, out, cap, cnt,
+                                          finalists=2, rounds=2)
+        assert best is not None and len(times) >= 2
+        assert all(plan.exec_kwargs[kk] == v for kk, v in best.items())
+        pairs, n, _ = plan.query("hoph", q, nq, c, nr)
+        z = [plan.info.group_size[g] for g in range(plan.G)]
+        want = _oracle_query("hoph", planes_to_rows(q), planes_to_rows(c), kg, z)
+        assert pairs_tuples(pairs) == oracle_tuples(want)
+        d_ids, d_off = to_dev(small["ids"], dev), to_dev(small["off"], dev)
+        sk = torch.empty_like(c)
+        bits, btimes = autotune.tune_sketch(plan, d_ids, d_off, nr, sk, finalists=2, rounds=2)
+        assert plan.exec_kwargs["sketch_cta_bits"] == bits and len(btimes) >= 2
+        assert torch.equal(sk, c)
