@@ -302,16 +302,6 @@ __device__ __forceinline__ void tma_prefetch_l2_4d(const CUtensorMap *map, int32
                  : "memory");
 }
 
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialization may start while the previous kernel of its stream still runs;
-// pdl_wait() returns once that kernel has completed and its writes are
-// visible (a no-op for a normal launch); pdl_trigger() lets the next such
-// kernel be scheduled.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }

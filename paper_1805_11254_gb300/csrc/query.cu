@@ -39,31 +39,10 @@
 
 #include <algorithm>
 #include <mutex>
-#include <utility>
 
 #include "common.cuh"
 
 namespace {
-
-// Launch a kernel with programmatic stream serialization: it may be scheduled
-// while the previous kernel of the stream runs (that kernel calls
-// pdl_trigger); it calls pdl_wait before reading anything that kernel writes.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_after_previous(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                                  cudaStream_t s, Args &&...args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
-
 
 constexpr int kSurvCap = 32;  // per-warp survivor list (one entry per lane)
 constexpr int kMaxW = 1024;   // scanned bins per row
@@ -539,7 +518,6 @@ struct IndexArgs {
 __global__ void join_init_kernel(uint32_t *head, int64_t n_head, uint32_t *gmap, int64_t n_gmap,
                                  unsigned long long *st, int n_st, uint32_t *n_allempty,
                                  unsigned long long *n_cand, int64_t *out_count) {
-    pdl_trigger();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t T = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = t; i < n_head; i += T) head[i] = kNil;
@@ -557,8 +535,6 @@ __global__ void join_init_kernel(uint32_t *head, int64_t n_head, uint32_t *gmap,
 // the key's list)
 template <typename E>
 __global__ void join_count_kernel(const IndexArgs a) {
-    pdl_trigger();
-    pdl_wait();  // join_init has reset the lists, the map and the counters
     const int lane = threadIdx.x & 31;
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= a.n_q) return;
@@ -672,15 +648,12 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
     }
     __syncthreads();
 
-    pdl_trigger();
     if (warp == a.n_cons) {
-        // the planes are not written by the join index: stream them at once
         if (lane == 0)
             produce_tiles(&map, stages, full, empty, abort_flag, a.stages, a.stage_bytes,
                           a.stage_stride, a.n_tiles, R, a.status, true, kFilterPrefetch);
         return;
     }
-    pdl_wait();  // the group map and the candidate counter come from the join index
     {
         // the consumers copy the group map (16-byte pieces; the map is padded
         // to a multiple of four words) while the first tiles are in flight
@@ -848,8 +821,6 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(const __grid_co
     for (int i = tid; i < kCountWarps * cwords; i += blockDim.x) s_cnt[i] = 0;
     for (int i = tid; i < kCountWarps; i += blockDim.x) s_nsurv[i] = 0;
     for (int i = tid; i < kStatWords; i += blockDim.x) s_stats[i] = 0;
-    pdl_trigger();
-    pdl_wait();  // candidates from the filter, lists from the join index
     __syncthreads();
 
     uint32_t *cnt = s_cnt + warp * cwords;
@@ -1018,8 +989,7 @@ int launch_count(const CountArgs &ca, uint32_t smem, int num_sms, cudaStream_t s
     int per = 0;
     HOPH_CUDA_TRY(hoph_occupancy(&per, (const void *)kern, kCountThreads, smem));
     if (per < 1) return HOPH_ERR_UNSUPPORTED;
-    HOPH_CUDA_TRY(launch_after_previous(kern, dim3((unsigned)(num_sms * per)), dim3(kCountThreads),
-                                        smem, s, ca));
+    kern<<<(unsigned)(num_sms * per), kCountThreads, smem, s>>>(ca);
     HOPH_CUDA_TRY(cudaGetLastError());
     return HOPH_OK;
 }
@@ -1104,7 +1074,6 @@ __global__ void __launch_bounds__(kSortThreads) sort_pairs_kernel(
     ulonglong2 *bufB, int32_t *status, const StatsFold f) {
     extern __shared__ __align__(1024) unsigned char smem[];
     ulonglong2 *sv = reinterpret_cast<ulonglong2 *>(smem);
-    pdl_wait();  // the pairs and statistics of the calls before
     if (threadIdx.x == 0) stats_fold(f);
     const unsigned long long total = *count;
     if (total > (unsigned long long)cap && threadIdx.x == 0) hoph_flag(status, HOPH_ERR_CAPACITY);
@@ -1283,7 +1252,7 @@ int launch_filter_c(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem,
     if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
     if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
     const int64_t grid = std::min<int64_t>(fa.n_tiles, (int64_t)num_sms * per_sm);
-    HOPH_CUDA_TRY(launch_after_previous(kern, dim3((unsigned)grid), dim3(threads), smem, s, fa, map));
+    kern<<<(unsigned)grid, threads, smem, s>>>(fa, map);
     HOPH_CUDA_TRY(cudaGetLastError());
     return HOPH_OK;
 }
@@ -1568,10 +1537,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
             n_allempty, n_cand, first ? d_out_count : nullptr);
         if (keys_hashed) HOPH_CUDA_TRY(cudaMemsetAsync(tkey, 0xFF, head_slots * 8, s));
         const unsigned qb = (unsigned)((n_queries * 32 + 255) / 256);
-        if (keys_hashed)  // a memset sits between the two kernels
-            join_count_kernel<E><<<qb, 256, 0, s>>>(ia);
-        else
-            HOPH_CUDA_TRY(launch_after_previous(join_count_kernel<E>, dim3(qb), dim3(256), 0, s, ia));
+        join_count_kernel<E><<<qb, 256, 0, s>>>(ia);
         HOPH_CUDA_TRY(cudaGetLastError());
         launches += 2;
 
@@ -1715,10 +1681,8 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     sf.out = d_stats;
     if (last) {
         HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
-        HOPH_CUDA_TRY(launch_after_previous(sort_pairs_kernel, dim3(1), dim3(kSortThreads),
-                                            kSortSmem * 16, s, d_out,
-                                            (const unsigned long long *)pa.out_count,
-                                            out_capacity, sortA, sortB, plan->d_status, sf));
+        sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(
+            d_out, pa.out_count, out_capacity, sortA, sortB, plan->d_status, sf);
     } else if (d_stats) {
         stats_fold_kernel<<<1, 32, 0, s>>>(sf);
     } else {

@@ -227,7 +227,6 @@ __global__ void __launch_bounds__(kSketchThreads, 6) oph_sketch_kernel(const Ske
     }
     const uint32_t regions = (PHASES & 2) ? kSketchWarps : 1;
     for (uint32_t i = threadIdx.x; i < regions * a.k; i += blockDim.x) s_sk[i] = HOPH_EMPTY_VALUE;
-    pdl_wait();  // the work list (and the IDs) of the kernels before
     __syncthreads();
     bool bad = false;
     const int64_t n_big = a.n_big ? (int64_t)*a.n_big : 0;
@@ -318,7 +317,6 @@ __global__ void __launch_bounds__(1024) bucket_small_kernel(const int64_t *off, 
                                                             uint32_t *n_big, int32_t *order,
                                                             int64_t warps, int bits) {
     __shared__ uint32_t h[kBuckets], cur[kBuckets];
-    pdl_trigger();
     for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) h[i] = 0;
     __syncthreads();
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
@@ -503,21 +501,7 @@ int launch_phases(hoph_plan *plan, const SketchArgs &a, cudaStream_t s) {
     if (per < 1) return HOPH_ERR_UNSUPPORTED;
     const int64_t want = PHASES == 1 ? a.n_sets : (a.n_sets + kSketchWarps - 1) / kSketchWarps;
     const int64_t blocks = std::min<int64_t>(want, (int64_t)grid_for(plan, per));
-    if (PHASES == 3) {  // after the work list: scheduled while it finishes
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)blocks);
-        cfg.blockDim = dim3(kSketchThreads);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        HOPH_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
-    } else {
-        kern<<<(unsigned)blocks, kSketchThreads, smem, s>>>(a);
-    }
+    kern<<<(unsigned)blocks, kSketchThreads, smem, s>>>(a);
     HOPH_CUDA_TRY(cudaGetLastError());
     plan->launches += 1;
     return HOPH_OK;
