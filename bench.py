@@ -640,13 +640,16 @@ def e2e_leg(args, plan, qw, planes, dev, stream, world=1, sync=None):
     h2d = int(h_ids.numel() * 4 + h_off.numel() * 8)
     serial = {"value": nq * args.rows * world / dt, "ms_per_step": dt * 1e3,
               "d2h_bytes_per_step": d2h}
-    pipe = e2e_in_flight(args, plan, h_ids, h_off, planes, dev, world=world, sync=sync)
+    pipes = [e2e_in_flight(args, plan, h_ids, h_off, planes, dev, n_lanes=n, world=world,
+                           sync=sync) for n in (3, 4)]
+    pipe = max(pipes, key=lambda r: r["value"])
     best = pipe if pipe["value"] > serial["value"] else serial
     return {"value": best["value"], "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": int(best["d2h_bytes_per_step"]),
             "ms_per_step": best["ms_per_step"],
             "schedule": best.get("schedule", "one batch at a time"),
             "serial": serial, "in_flight": pipe,
+            "ms_per_step_by_lanes": {p_["schedule"].split()[0]: p_["ms_per_step"] for p_ in pipes},
             "path": "pinned host sets -> oph_build_sketches -> hoph_query_batch -> host pairs"}
 
 
