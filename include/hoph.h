@@ -20,6 +20,11 @@
  *   - A plan owns its permutation table, bin layout, decision thresholds and
  *     scratch memory.  Calls that use one plan must be ordered on one stream
  *     (they share its scratch); use one plan per concurrent stream.
+ *   - The scratch grows on demand (a call that needs more synchronises the
+ *     device and reallocates it).  A CUDA graph captured from calls on a
+ *     plan keeps the scratch addresses of its capture, so before capturing,
+ *     make one uncaptured call of the largest shape the plan will serve;
+ *     after that no call of a shape up to it grows the scratch.
  */
 #ifndef HOPH_H
 #define HOPH_H

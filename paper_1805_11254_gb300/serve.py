@@ -126,8 +126,11 @@ class GpuExecutor:
             lane["h_cnt"] = torch.zeros(1, dtype=torch.int64).pin_memory()
             lane["graphs"] = {}
             self.lanes.append(lane)
+        # largest batch first: its eager call sizes the plan's scratch for every
+        # bucket, so the scratch never grows (and moves) under a graph that
+        # was already captured
         for lane in self.lanes:
-            for b in self.buckets:
+            for b in reversed(self.buckets):
                 lane["graphs"][b] = self._capture(lane, b)
 
     def _device_step(self, lane, bucket, stream):
