@@ -74,7 +74,7 @@ def parse():
                    help="skip the all-pairs self-join of a 10^6-row collection")
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the threshold / tolerance sweep on the 5,000-set workload")
-    p.add_argument("--serve-rates", default="2000,20000,100000",
+    p.add_argument("--serve-rates", default="2000,20000,100000,150000",
                    help="Poisson arrival rates (query sets per second)")
     p.add_argument("--serve-seconds", type=float, default=1.5)
     p.add_argument("--no-shingle", action="store_true", help="skip the D=2^32 shingle workload")
@@ -1052,7 +1052,6 @@ def serving_leg(args, planes, dev, oph_leg):
     plan_kw = dict(D=D, k=K, k_group=KG, a=AB[0], b=AB[1], seed=PERM_SEED, thr=T, epsilon=EPS)
     buckets = (64, 256, 1024)
     id_cap = 4 << 20
-    ex = serve.GpuExecutor(plan_kw, planes, args.rows, "hoph", buckets, id_cap)
     ctr = [0]
 
     def sets_for(rng, n):
@@ -1063,28 +1062,34 @@ def serving_leg(args, planes, dev, oph_leg):
             ctr[0] += int(sz)
         return out
 
-    results = []
-    try:
-        for i, rate in enumerate(float(x) for x in args.serve_rates.split(",")):
-            reqs = serve.poisson_requests(rate, args.serve_seconds, 100 + i, sets_for)
-            t0 = time.perf_counter()
-            done = serve.serve(ex, serve.Batcher(buckets, id_cap), reqs)
-            wall = time.perf_counter() - t0
-            ok = [r for r in done if r.error is None]
-            n_sets = sum(len(r.sets) for r in ok)
-            summ = serve.latency_summary(ok)
-            summ.update({"rate_query_sets_per_s": rate, "query_sets": n_sets,
-                         "throughput_query_sets_per_s": n_sets / wall,
-                         "pair_comparisons_per_s": n_sets * args.rows / wall,
-                         "rejected": len(done) - len(ok)})
-            results.append(summ)
-    finally:
-        ex.close()
-    return {"rates": results, "collection_rows": args.rows, "batch_slots": list(buckets),
+    by_streams = {}
+    for n_streams in (2, 4):
+        ex = serve.GpuExecutor(plan_kw, planes, args.rows, "hoph", buckets, id_cap,
+                               n_streams=n_streams)
+        results = []
+        try:
+            for i, rate in enumerate(float(x) for x in args.serve_rates.split(",")):
+                reqs = serve.poisson_requests(rate, args.serve_seconds, 100 + i, sets_for)
+                t0 = time.perf_counter()
+                done = serve.serve(ex, serve.Batcher(buckets, id_cap), reqs)
+                wall = time.perf_counter() - t0
+                ok = [r for r in done if r.error is None]
+                n_sets = sum(len(r.sets) for r in ok)
+                summ = serve.latency_summary(ok)
+                summ.update({"rate_query_sets_per_s": rate, "query_sets": n_sets,
+                             "throughput_query_sets_per_s": n_sets / wall,
+                             "pair_comparisons_per_s": n_sets * args.rows / wall,
+                             "rejected": len(done) - len(ok)})
+                results.append(summ)
+        finally:
+            ex.close()
+        by_streams[n_streams] = results
+    return {"rates": by_streams[4], "rates_by_streams": by_streams,
+            "collection_rows": args.rows, "batch_slots": list(buckets),
             "one_request_per_launch_oph_capacity_query_sets_per_s":
                 1e3 / oph_leg["ms_per_query_launch"],
-            "how": "2 streams x 1 plan each, one CUDA graph per (stream, batch size); H2D of a "
-                   "batch's sets and its sketching overlap the query of the other stream"}
+            "how": "2 or 4 streams x 1 plan each, one CUDA graph per (stream, batch size); H2D "
+                   "of a batch's sets and its sketching overlap other streams' queries"}
 
 
 def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream, peaks,

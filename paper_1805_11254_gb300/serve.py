@@ -5,8 +5,9 @@ waiting requests into the next batch while query slots and the reserved
 device memory for IDs last; each batch is padded to a fixed slot count so
 its whole device work (H2D of the sets, OPH/HOPH sketching, the HOPH query
 against the resident collection, D2H of the accepted pairs) replays as one
-captured CUDA graph.  Two streams with a plan each keep two batches in
-flight: the copies and sketching of one overlap the query of the other.
+captured CUDA graph.  Several streams (two by default) with a plan each keep
+that many batches in flight: the copies and sketching of one overlap the
+queries of the others.
 Results are scattered back per request; a request's pairs do not depend on
 which other requests shared its batch (padding sets are empty and their
 pairs are dropped).
@@ -99,7 +100,7 @@ def pack_batch(reqs, bucket, h_ids, h_off):
 
 
 class GpuExecutor:
-    """Two streams, one plan each, one graph per (stream, bucket)."""
+    """`n_streams` streams, one plan each, one graph per (stream, bucket)."""
 
     def __init__(self, plan_kwargs, planes, n_rows, mode, slot_buckets, id_capacity,
                  out_capacity=1 << 14, n_streams=2, device=None):
