@@ -24,7 +24,10 @@
  *     device and reallocates it).  A CUDA graph captured from calls on a
  *     plan keeps the scratch addresses of its capture, so before capturing,
  *     make one uncaptured call of the largest shape the plan will serve;
- *     after that no call of a shape up to it grows the scratch.
+ *     after that no call of a shape up to it grows the scratch.  A call that
+ *     would grow the scratch (or build a decision table, or create the
+ *     self-join's streams) while its stream is being captured returns
+ *     HOPH_ERR_CAPTURE before enqueuing anything.
  */
 #ifndef HOPH_H
 #define HOPH_H
@@ -46,6 +49,8 @@ extern "C" {
 #define HOPH_ERR_NOMEM (-6)       /* host or device allocation failed        */
 #define HOPH_ERR_UNSUPPORTED (-7) /* valid parameters this build cannot run  */
 #define HOPH_ERR_TOO_LARGE (-8)   /* input exceeds a fixed-size scratch area  */
+#define HOPH_ERR_CAPTURE (-9)     /* the call would (re)allocate plan memory
+                                     while its stream is being captured      */
 
 /* ---- enumerations ------------------------------------------------------ */
 /* comparison modes of hoph_query_batch */

@@ -201,8 +201,13 @@ cudaError_t hoph_ensure_smem(const void *func, int bytes);
 cudaError_t hoph_occupancy(int *blocks, const void *func, int threads, size_t smem);
 
 // grow-only scratch owned by the plan (one per lane, lane 0 for every call
-// but a self-join's other blocks in flight); returns nullptr on failure
-void *hoph_scratch(hoph_plan *plan, size_t bytes, int lane = 0);
+// but a self-join's other blocks in flight): *out = at least `bytes`;
+// HOPH_ERR_CAPTURE when it would have to grow while `stream` is being
+// captured, HOPH_ERR_NOMEM when the allocation fails
+int hoph_scratch(hoph_plan *plan, size_t bytes, int lane, cudaStream_t stream, void **out);
+
+// true while `stream` is being captured into a graph
+bool hoph_capturing(cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -346,10 +346,22 @@ cudaError_t hoph_occupancy(int *blocks, const void *func, int threads, size_t sm
     return cudaSuccess;
 }
 
-void *hoph_scratch(hoph_plan *plan, size_t bytes, int lane) {
+bool hoph_capturing(cudaStream_t stream) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st != cudaStreamCaptureStatusNone;
+}
+
+int hoph_scratch(hoph_plan *plan, size_t bytes, int lane, cudaStream_t stream, void **out) {
     void *&buf = lane > 0 ? plan->lane_scratch[lane] : plan->d_scratch;
     size_t &have = lane > 0 ? plan->lane_scratch_bytes[lane] : plan->scratch_bytes;
-    if (bytes <= have) return buf;
+    *out = buf;
+    if (bytes <= have) return HOPH_OK;
+    // growing would free memory a captured graph may already point at
+    if (hoph_capturing(stream)) return HOPH_ERR_CAPTURE;
     size_t want = std::max(bytes, have * 2);
     want = (want + 255) & ~(size_t)255;
     if (buf) {
@@ -358,12 +370,14 @@ void *hoph_scratch(hoph_plan *plan, size_t bytes, int lane) {
         buf = nullptr;
         have = 0;
     }
+    *out = nullptr;
     if (cudaMalloc(&buf, want) != cudaSuccess) {
         cudaGetLastError();
-        return nullptr;
+        return HOPH_ERR_NOMEM;
     }
     have = want;
-    return buf;
+    *out = buf;
+    return HOPH_OK;
 }
 
 void hoph_timing_mark(hoph_plan *plan, int which, cudaStream_t s) {
@@ -498,6 +512,9 @@ const char *hoph_status_string(int status) {
         case HOPH_ERR_NOMEM: return "allocation failed";
         case HOPH_ERR_UNSUPPORTED: return "parameters not supported by this build";
         case HOPH_ERR_TOO_LARGE: return "input larger than the fixed scratch of this entry point";
+        case HOPH_ERR_CAPTURE:
+            return "the call needs new plan memory while its stream is captured (make one "
+                   "uncaptured call of the largest shape first)";
         default: return "unknown status";
     }
 }

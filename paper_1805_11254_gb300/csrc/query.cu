@@ -1375,6 +1375,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     if (!d_query_planes || !d_coll_planes) return HOPH_ERR_PARAM;
 
     if (plan->table_W[mode] != W) {
+        if (hoph_capturing(s)) return HOPH_ERR_CAPTURE;  // it allocates and copies
         plan->table_ok[mode] = build_table(fp, W, 1, plan->h_table[mode]);
         plan->table_W[mode] = W;
         cudaFree(plan->d_table[mode]);
@@ -1455,8 +1456,10 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
             bump.take(cap1 * 16);  // sort B
         }
         if (pass == 0) {
-            unsigned char *base = (unsigned char *)hoph_scratch(plan, bump.off, lane);
-            if (!base) return HOPH_ERR_NOMEM;
+            void *p = nullptr;
+            const int src = hoph_scratch(plan, bump.off, lane, s, &p);
+            if (src != HOPH_OK) return src;
+            unsigned char *base = static_cast<unsigned char *>(p);
             bump.base = base;
         }
     }
@@ -1734,6 +1737,8 @@ int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int
     // blocks in flight: block b runs on lane b % lanes, each lane a stream and
     // a scratch of the plan's own, forked from and joined back to `stream`
     if (lanes > 1) {
+        for (int i = 0; i < lanes; ++i)
+            if (!plan->lane_stream[i] && hoph_capturing(s)) return HOPH_ERR_CAPTURE;
         for (int i = 0; i < lanes; ++i) {
             if (!plan->lane_stream[i])
                 HOPH_CUDA_TRY(cudaStreamCreateWithFlags(&plan->lane_stream[i], cudaStreamNonBlocking));
@@ -1767,8 +1772,10 @@ int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int
     if (rc != HOPH_OK) return rc;
     // one sort of all blocks' pairs (lane 0's scratch is free again here)
     const size_t cap1 = (size_t)std::max<int64_t>(out_capacity, 1);
-    ulonglong2 *sortA = (ulonglong2 *)hoph_scratch(plan, 2 * cap1 * 16, 0);
-    if (!sortA) return HOPH_ERR_NOMEM;
+    void *sp = nullptr;
+    const int src = hoph_scratch(plan, 2 * cap1 * 16, 0, s, &sp);
+    if (src != HOPH_OK) return src;
+    ulonglong2 *sortA = static_cast<ulonglong2 *>(sp);
     StatsFold none{};
     HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
     sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(

@@ -542,8 +542,10 @@ int build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_offs
     a.compact = compact ? 1 : 0;
     if (n_sets >= kWorkListMin) {
         const size_t bytes = (3 * kBuckets + 1) * sizeof(uint32_t) + (size_t)n_sets * sizeof(int32_t);
-        uint32_t *wl = (uint32_t *)hoph_scratch(plan, bytes);
-        if (!wl) return HOPH_ERR_NOMEM;
+        void *p = nullptr;
+        const int src = hoph_scratch(plan, bytes, 0, s, &p);
+        if (src != HOPH_OK) return src;
+        uint32_t *wl = static_cast<uint32_t *>(p);
         const int rc = build_work_list(plan, d_offsets, n_sets, wl, a, s);
         if (rc != HOPH_OK) return rc;
     }
@@ -576,8 +578,10 @@ int hoph_synth_sketch(hoph_plan *plan, uint64_t seed, uint64_t D, const int64_t 
     a.gen_D = D;
     if (n_sets >= kWorkListMin) {
         const size_t bytes = (3 * kBuckets + 1) * sizeof(uint32_t) + (size_t)n_sets * sizeof(int32_t);
-        uint32_t *wl = (uint32_t *)hoph_scratch(plan, bytes);
-        if (!wl) return HOPH_ERR_NOMEM;
+        void *p = nullptr;
+        const int src = hoph_scratch(plan, bytes, 0, s, &p);
+        if (src != HOPH_OK) return src;
+        uint32_t *wl = static_cast<uint32_t *>(p);
         const int rc = build_work_list(plan, d_offsets, n_sets, wl, a, s);
         if (rc != HOPH_OK) return rc;
     }

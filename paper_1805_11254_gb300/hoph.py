@@ -26,6 +26,7 @@ HOPH_ERR_CUDA = -5
 HOPH_ERR_NOMEM = -6
 HOPH_ERR_UNSUPPORTED = -7
 HOPH_ERR_TOO_LARGE = -8
+HOPH_ERR_CAPTURE = -9
 
 HOPH_MODE_OPH_FULL = 0
 HOPH_MODE_GOPH = 1

@@ -109,3 +109,48 @@ def test_two_batches_in_flight_match_the_oracle(strategy):
     finally:
         for p in plans:
             p.close()
+
+
+def test_capture_refuses_new_plan_memory_then_works_after_a_warm_call():
+    """A query captured on a fresh plan would have to allocate its scratch and
+    decision table inside the capture: the call returns HOPH_ERR_CAPTURE
+    before enqueuing anything.  After one uncaptured call of the same shape
+    the capture succeeds and its replay gives that call's pairs."""
+    dev = device()
+    w = synth.small_parity_workload()
+    D, k, kg = w["D"], 128, 32
+    with hoph.Plan(D, k, kg, 1, 1, seed=1, thr=(7, 10), epsilon=1e-4) as plan:
+        c = plan.sketch(to_dev(w["ids"], dev), to_dev(w["off"], dev), 3000)
+        q = plan.sketch(to_dev(w["q_ids"], dev), to_dev(w["q_off"], dev), 40)
+        plan.check()
+        cap = 4096
+        out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        with hoph.Plan(D, k, kg, 1, 1, seed=1, thr=(7, 10), epsilon=1e-4) as fresh:
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(g, stream=side):
+                    with pytest.raises(hoph.HophError) as e:
+                        hoph.hoph_query_batch(fresh.handle, "hoph", q, 40, c, 3000, out, cap, cnt,
+                                              None, side)
+                    cnt.zero_()  # keep the capture non-empty
+            assert e.value.code == hoph.HOPH_ERR_CAPTURE
+            torch.cuda.synchronize()
+            with torch.cuda.stream(side):
+                hoph.hoph_query_batch(fresh.handle, "hoph", q, 40, c, 3000, out, cap, cnt, None,
+                                      side)  # warm: scratch and table sized here
+                side.synchronize()
+                want = out[:int(cnt.item())].clone()
+                g2 = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g2, stream=side):
+                    hoph.hoph_query_batch(fresh.handle, "hoph", q, 40, c, 3000, out, cap, cnt,
+                                          None, side)
+            torch.cuda.synchronize()
+            out.zero_()
+            g2.replay()
+            torch.cuda.synchronize()
+            fresh.check()
+            assert int(cnt.item()) == len(want) > 0
+            assert torch.equal(out[:len(want)], want)
