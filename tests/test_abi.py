@@ -88,6 +88,7 @@ def test_invalid_parameters_rejected_before_any_cuda_call(lib, kw):
 def test_status_strings(lib):
     assert hoph.hoph_status_string(0) == "ok"
     assert "capacity" in hoph.hoph_status_string(hoph.HOPH_ERR_CAPACITY)
+    assert "captured" in hoph.hoph_status_string(hoph.HOPH_ERR_CAPTURE)
     assert hoph.hoph_status_string(12345) == "unknown status"
 
 
@@ -95,3 +96,17 @@ def test_null_plan_is_a_parameter_error(lib):
     assert lib.oph_build_sketches(None, None, None, 0, None, None) == hoph.HOPH_ERR_PARAM
     assert lib.hoph_query_batch(None, 0, None, 0, None, 0, None, 0, None, None, None) == \
         hoph.HOPH_ERR_PARAM
+
+
+def test_binding_constants_follow_the_header():
+    """Every HOPH_* integer #define of include/hoph.h has the same value in
+    the Python binding."""
+    text = open(os.path.join(ROOT, "include", "hoph.h")).read()
+    found = re.findall(r"#define (HOPH_\w+) \(?(-?\d+)\)?\s", text)
+    assert len(found) >= 9
+    for name, val in found:
+        if hasattr(hoph, name):
+            assert getattr(hoph, name) == int(val), name
+    for name, _ in found:
+        if name.startswith("HOPH_ERR_"):
+            assert hasattr(hoph, name), name
