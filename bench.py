@@ -1217,7 +1217,7 @@ def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream
 
 
 def self_join_leg(off, coll_seed, dev, stream, n_base=1_000_000, n_planted=1000,
-                  batches=(1024, 1536, 2048), lanes=(2, 3, 4), reps=3):
+                  batches=(1024, 1536, 2048), lanes=(3, 4, 6, 8), reps=3):
     """All near-duplicate pairs inside one collection (hoph_self_join): the
     first 10^6 rows of the query workload's collection plus 1,000 planted
     near duplicates of random rows among them (J ~ U[0.6, 0.95]), (1:2)HOPH;

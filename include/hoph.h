@@ -160,7 +160,7 @@ typedef struct {
                               * 0 = library choice, 64 = warps only      */
     int32_t join_lanes;      /* hoph_self_join: blocks in flight at once,
                               * each on a stream and scratch of the plan's
-                              * own (1-4; 0 = library choice, 4)         */
+                              * own (1-8; 0 = library choice, 8)         */
 } hoph_exec;
 
 typedef struct hoph_plan hoph_plan;
@@ -273,7 +273,7 @@ int hoph_query_batch16(hoph_plan *plan, uint32_t mode, const uint16_t *d_query_p
  *               n_rows (n_rows - 1) / 2): a block skips the pairs i >= j
  *               among its own rows before counting or deciding them.
  * Modes GOPH, HOPH and OPH_FULL (not MinWise).  A block reads its query
- * planes in place (no copy).  Up to exec.join_lanes blocks (default 4) are
+ * planes in place (no copy).  Up to exec.join_lanes blocks (default 8) are
  * in flight at once, each on a stream and a scratch buffer the plan owns,
  * forked from `stream` and joined back to it before the final sort, so the
  * call stays ordered on `stream` (and can be captured into a graph).  The

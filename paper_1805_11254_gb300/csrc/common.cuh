@@ -164,7 +164,7 @@ struct hoph_plan {
     // flight, each on a stream of the plan's own)
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
-    static constexpr int kMaxLanes = 4;
+    static constexpr int kMaxLanes = 8;
     void *lane_scratch[kMaxLanes] = {};
     size_t lane_scratch_bytes[kMaxLanes] = {};
     cudaStream_t lane_stream[kMaxLanes] = {};

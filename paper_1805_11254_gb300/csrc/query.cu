@@ -1732,7 +1732,7 @@ int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int
     const int64_t kg = plan->P.k_group;
     const int64_t cstride = n_rows * kg;
     const int64_t n_blocks = (n_rows - 1 + batch - 1) / batch;
-    const int want = plan->exec.join_lanes > 0 ? plan->exec.join_lanes : 4;
+    const int want = plan->exec.join_lanes > 0 ? plan->exec.join_lanes : 8;
     const int lanes = (int)std::min<int64_t>(std::min(want, (int)hoph_plan::kMaxLanes), n_blocks);
     // blocks in flight: block b runs on lane b % lanes, each lane a stream and
     // a scratch of the plan's own, forked from and joined back to `stream`

@@ -440,7 +440,7 @@ def _self_join_result(out, cnt, st):
             stats)
 
 
-@pytest.mark.parametrize("lanes", [1, 3, 4])
+@pytest.mark.parametrize("lanes", [1, 3, 4, 8])
 def test_self_join_blocks_in_flight_keep_the_result(self_join_case, lanes):
     """join_lanes = 1, 3, 4 (blocks of 300 rows on that many of the plan's
     streams at once), through Plan.self_join: the oracle's upper-triangle
