@@ -1390,8 +1390,10 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     if (!plan->table_ok[mode]) return HOPH_ERR_UNSUPPORTED;
     const std::vector<uint16_t> &tab = plan->h_table[mode];
 
+    // (TMA tile coordinates are 32-bit signed: rows beyond 2^31 take the plain loads)
     const bool tma_base_ok = ((kg * ES) % 16 == 0) && kg <= 256 && Gs <= 256 &&
-                             ((uintptr_t)d_coll_planes & 15) == 0 && get_encode_fn() != nullptr;
+                             n_rows < (1ll << 31) && ((uintptr_t)d_coll_planes & 15) == 0 &&
+                             get_encode_fn() != nullptr;
 
     // join: needs "no match => reject" for every K >= 1, TMA tiles, a rule
     // whose K == 0 pairs are the all-empty ones, and a key space (the psi-space
