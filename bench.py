@@ -284,19 +284,22 @@ def run_native(args):
     import torch
     from paper_1805_11254_gb300 import build_lib, hoph, shard, synth
     rank, world, local = env_rank()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    build_lib.build()
-    hoph.load()
-    stream = torch.cuda.current_stream()
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+
+    if rank == 0:  # one rank compiles (when the library is not up to date), all load it
+        build_lib.build()
+    barrier()
+    hoph.load()
+    stream = torch.cuda.current_stream()
 
     def max_over_ranks(x):
         return shard.max_over_ranks(x, device=dev)
