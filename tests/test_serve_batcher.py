@@ -1,6 +1,7 @@
 """Host-side admission rules of the continuous-batching service (no GPU)."""
 import numpy as np
 
+from paper_1805_11254_gb300 import serve
 from paper_1805_11254_gb300.serve import Batcher, Request, pack_batch
 
 
@@ -53,3 +54,71 @@ def test_pack_batch_pads_with_empty_sets():
     assert h_off.tolist() == [0, 3, 3, 5, 5, 5, 5, 5, 5]
     assert h_ids[:5].tolist() == [0, 1, 2, 7, 8]
     assert [(r.rid, j) for r, j in owner] == [(0, 0), (0, 1), (7, 0)]
+
+
+class _FakeExecutor:
+    """The executor's interface on the host: `n` lanes, each batch takes
+    `service` seconds of the fake clock; a batch's requests get one pair per
+    query set (the set's own index), so results can be checked per request."""
+
+    def __init__(self, clock, n=2, service=0.004):
+        self.lanes = [dict(busy=None) for _ in range(n)]
+        self.clock, self.service, self.launched = clock, service, []
+
+    def free_lane(self):
+        return next((ln for ln in self.lanes if ln["busy"] is None), None)
+
+    def launch(self, lane, reqs, bucket):
+        self.launched.append((len(reqs), bucket))
+        lane["busy"] = (reqs, self.clock() + self.service)
+
+    def poll(self, now_fn, block=False):
+        done = []
+        for ln in self.lanes:
+            if ln["busy"] is not None and self.clock() >= ln["busy"][1]:
+                for r in ln["busy"][0]:
+                    r.pairs = [(j, 0, 1, 0) for j in range(len(r.sets))]
+                    r.done = now_fn()
+                    done.append(r)
+                ln["busy"] = None
+        return done
+
+
+def test_serve_loop_completes_every_request_once_with_its_own_results():
+    """serve() over a fake clock and executor: every admitted request
+    completes exactly once, after its arrival, with results for each of its
+    own sets; oversized requests come back rejected; batches never exceed
+    the largest bucket, and at most `n` are in flight."""
+    t = [0.0]
+
+    def clock():
+        t[0] += 1e-4  # each look at the clock advances it
+        return t[0]
+
+    rng = np.random.default_rng(3)
+    reqs = [serve.Request(i, [np.arange(int(rng.integers(1, 50)), dtype=np.uint32)
+                              for _ in range(int(rng.integers(1, 40)))], 0.002 * i)
+            for i in range(60)]
+    reqs.append(serve.Request(60, [np.arange(5, dtype=np.uint32)] * 300, 0.05))  # > 256 sets
+    ex = _FakeExecutor(clock)
+    done = serve.serve(ex, serve.Batcher((16, 64, 256), 1 << 20), reqs, clock=clock)
+    assert sorted(r.rid for r in done) == list(range(61))
+    rejected = [r for r in done if r.error is not None]
+    assert [r.rid for r in rejected] == [60]
+    for r in done:
+        if r.error is None:
+            assert r.done is not None and r.done >= r.arrival
+            assert r.pairs == [(j, 0, 1, 0) for j in range(len(r.sets))]
+    assert all(bucket <= 256 and n >= 1 for n, bucket in ex.launched)
+
+
+def test_latency_summary_and_poisson_arrivals():
+    reqs = serve.poisson_requests(5000.0, 0.5, 7, lambda rng, n: [np.zeros(3, np.uint32)] * n)
+    assert reqs and all(a.arrival < b.arrival for a, b in zip(reqs, reqs[1:]))
+    sets = sum(len(r.sets) for r in reqs)
+    assert 1500 < sets < 3500  # 5,000 sets/s for 0.5 s
+    for i, r in enumerate(reqs):
+        r.done = r.arrival + 0.001 * (1 + i % 10)
+    s = serve.latency_summary(reqs)
+    assert s["requests"] == len(reqs)
+    assert 1.0 <= s["p50_ms"] <= 10.0 and s["p99_ms"] <= 10.0 + 1e-9
