@@ -310,3 +310,129 @@ def test_decision_monotone_in_matches():
 def test_precision_recall_definitions():
     p, r = hr.precision_recall({1, 2, 3, 4}, {2, 3, 5})
     assert (p, r) == (Fraction(2, 4), Fraction(2, 3))
+
+
+# --- (a:b)HOPH with r != 1/2: Lemma 3 and Algorithm 2 pinned by the mathematics ---
+
+@pytest.mark.parametrize("a,b", [(1, 2), (2, 1)])
+@pytest.mark.parametrize("A,B", [([0, 1, 2, 4], [1, 2, 5, 6]),   # groups rarely empty
+                                 ([0, 1], [1, 2]),                # union of 3: groups often empty
+                                 ([3], [3, 6])])                  # one shared element of two
+def test_hoph_space_weighted_estimator_unbiased_exhaustive(a, b, A, B):
+    """Lemma 3 (Sec. 4.2) with the a:b space weights: within a group of equal
+    bins a non-empty bin's minimum is a uniformly drawn element of the union
+    given where the union's elements fall, so E[M_j / K_j] = J for every
+    group, and the space-weighted mean over the groups that have a non-empty
+    bin is exactly J whatever the weights.  Exhaustive over all 7!
+    permutations for a 1:2 and a 2:1 layout (D = 7, k = 4, k' = 2; group
+    sizes 2+5 and 4+3), including permutations that leave a group empty."""
+    D, k, kg = 7, 4, 2
+    lo, z = hr.layout(D, k, kg, a, b)
+    assert z == ([2, 5] if (a, b) == (1, 2) else [4, 3])
+    J = hr.exact_jaccard(A, B)
+    total = Fraction(0)
+    n = 0
+    empty_groups = 0
+    for p in permutations(range(D)):
+        psi = p.__getitem__
+        sa = hr.oph_sketch(A, psi, lo)
+        sb = hr.oph_sketch(B, psi, lo)
+        for g in range(2):
+            if all(v == E for v in sa[g * kg:(g + 1) * kg] + sb[g * kg:(g + 1) * kg]):
+                empty_groups += 1
+        total += hr.hoph_estimate(sa, sb, kg, z)
+        n += 1
+    assert total / n == J
+    if len(set(A) | set(B)) <= 3:
+        assert empty_groups > 0  # the case where a group drops out of the weights is covered
+
+
+def _expected_by_completion(s, t, kg, z, T, eps, bt):
+    """The Algorithm 2 decision derived from Lemma 3's estimator alone.
+    After l groups the remaining requirement is the smallest number c of
+    matched bins that every remaining group (all bins non-empty) must reach
+    for the final estimator to be >= T; the pair is already similar when the
+    compared groups' own estimate exceeds T and P(X < c) <= eps, and already
+    dissimilar otherwise when P(X >= c) <= eps (X ~ Bin(k', T); Def. 1).
+    c is found by trying every completion, never from the P_r formula."""
+    G = len(z)
+    for l in range(1, G):
+        pre_s, pre_t = s[:l * kg], t[:l * kg]
+        done = hr.hoph_estimate(pre_s, pre_t, kg, z[:l])
+        c_star = kg + 1
+        for c in range(kg + 1):
+            comp_s = pre_s + [0] * ((G - l) * kg)
+            comp_t = pre_t + [0 if i % kg < c else 1 for i in range((G - l) * kg)]
+            if hr.hoph_estimate(comp_s, comp_t, kg, z) >= T:
+                c_star = c
+                break
+        if done is not None and done > T:
+            if bt.lower(c_star) <= eps:
+                return hr.ACCEPT, l
+        else:
+            if bt.upper(c_star) <= eps:
+                return hr.REJECT, l
+    est = hr.hoph_estimate(s, t, kg, z)
+    return (hr.ACCEPT if est is not None and est >= T else hr.REJECT), G
+
+
+@pytest.mark.parametrize("D,a,b", [(1 << 12, 1, 2), (1 << 12, 2, 1), (3000, 1, 3),
+                                   (1 << 12, 1, 1)])
+def test_hoph_space_rule_equals_the_requirement_from_lemma_3(D, a, b):
+    """Every early accept / reject of the space-weighted (a:b)HOPH rule, for
+    r != 1/2 as well as 1/2, equals the decision derived from completions of
+    Lemma 3's estimator (above): catches a wrong remaining size Z_rem, a
+    wrong group weight or a wrong tail.  Group states cover empty bins and
+    whole empty groups."""
+    import random
+    rng = random.Random(17 + a * 7 + b)
+    kg, G = 10, 4
+    lo, z = hr.layout(D, kg * G, kg, a, b)
+    seen = set()
+    for T in (Fraction(7, 10), Fraction(1, 2), Fraction(3, 5)):
+        bt = hr.BinomialTails(kg, T)
+        for eps in (1e-4, 1e-2, 0.2, 0.5):
+            for _ in range(150):
+                s, t = [], []
+                for g in range(G):
+                    kind = rng.random()
+                    for i in range(kg):
+                        if kind < 0.1:                        # the whole group empty
+                            s.append(E)
+                            t.append(E)
+                        elif rng.random() < 0.1:              # an empty bin on one side
+                            s.append(E if rng.random() < 0.5 else 0)
+                            t.append(0 if s[-1] == E and rng.random() < 0.5 else E)
+                        else:
+                            s.append(0)
+                            t.append(0 if rng.random() < rng.choice((0.2, 0.6, 0.9)) else 1)
+                got = hr.hoph_compare(s, t, kg, z, T, eps)
+                want = _expected_by_completion(s, t, kg, z, T, eps, bt)
+                assert got[:2] == want, (a, b, T, eps, s, t, got, want)
+                seen.add(want)
+    # early accepts, early rejects and full scans all occurred
+    assert {d for d, l in seen if l < G} == {hr.ACCEPT, hr.REJECT}
+    assert any(l == G for _, l in seen)
+
+
+@pytest.mark.parametrize("a,b", [(1, 2), (2, 1)])
+def test_decision_reductions_on_unequal_layouts(a, b):
+    """On 1:2 and 2:1 layouts: eps = 0 makes the early-terminating HOPH rule
+    decide exactly as Lemma 3's full estimator >= T, and eps >= 1 ends every
+    pair after the first group."""
+    import random
+    rng = random.Random(23 + a)
+    D, k, kg = 729, 32, 8
+    lo, z = hr.layout(D, k, kg, a, b)
+    perm = hr.permutation_table(D, 13)
+    base = [rng.sample(range(D), rng.randint(3, 90)) for _ in range(12)]
+    sets = base + [bs[: len(bs) // 2] + rng.sample(range(D), 4) for bs in base]
+    for T in (Fraction(1, 2), Fraction(7, 10)):
+        for A in sets:
+            for B in sets:
+                sa, sb = (hr.oph_sketch(S, perm.__getitem__, lo) for S in (A, B))
+                est = hr.hoph_estimate(sa, sb, kg, z)
+                full = hr.ACCEPT if est is not None and est >= T else hr.REJECT
+                assert hr.hoph_compare(sa, sb, kg, z, T, 0.0)[0] == full
+                assert hr.hoph_compare(sa, sb, kg, z, T, 1.0)[1] == 1
+                assert hr.hoph_compare(sa, sb, kg, z, T, 2.5)[1] == 1
