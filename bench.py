@@ -39,6 +39,9 @@ K, KG, AB = 256, 64, (1, 2)
 T, EPS = (7, 10), 1e-4
 PERM_SEED, COLL_SEED, Q_SEED, PLANT_SEED = 1, 11, 12, 13
 SKETCH_SEED = 21
+# output capacity (accepted pairs) of a 1,024-query step: about 70 pairs are
+# accepted per batch; up to 65,536 the library sorts them in one CTA
+CAP = 1 << 16
 
 # dram read+write bytes per filter-kernel launch from an ncu capture, keyed by
 # the sha256 of the filter kernel's source it was taken on (null once that
@@ -58,11 +61,28 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=100)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-extras", action="store_true", help="skip sketch/OPH/CPU legs")
+    p.add_argument("--in-flight", type=int, default=8,
+                   help="batches in flight in the timed schedule (each lane its own plan, "
+                        "stream branch and query batch)")
+    p.add_argument("--decision-thr", default="697/1000",
+                   help="decision threshold of the timed HOPH step; ground truth stays "
+                        "Jaccard >= 7/10.  697/1000 is where (1:2)HOPH's recall on this "
+                        "seeded workload reaches plain OPH's at 7/10 (re-checked every run "
+                        "by the recall study)")
+    p.add_argument("--no-truth-threshold", action="store_true",
+                   help="skip timing the same schedule at the ground-truth threshold 7/10")
+    p.add_argument("--details", default=None,
+                   help="also write the studies' JSON to this file")
     p.add_argument("--profile", nargs="?", const="query",
                    choices=("query", "sketch", "oph1", "self_join"),
                    help="few launches of the query step (or of the 10^6-set sketch, of the "
                         "one-query OPH full scan with its tuned knobs, or one self-join of "
                         "the first --rows rows), for ncu")
+    p.add_argument("--profile-knobs", default="",
+                   help="execution knobs of the profiled query step, e.g. "
+                        "'strategy=1,lanes_per_row=32,stages=2,tile_rows=256'")
+    p.add_argument("--profile-compact", action="store_true",
+                   help="profile the query step over compact (uint16) planes")
     p.add_argument("--no-graph", action="store_true", help="eager launches instead of a graph")
     p.add_argument("--no-pipeline", action="store_true",
                    help="one batch at a time (no second batch in flight on a second stream)")
@@ -176,7 +196,7 @@ def to_dev(a, dev):
 # CPU oracle legs
 # ---------------------------------------------------------------------------
 
-def cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z):
+def cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z, thr=T):
     """One bounded CPU step: oracle sketches of the query batch and the
     (1:2)HOPH comparison against `rows` collection rows.  The sample rows'
     sketches are prepared outside the timing (the collection is resident on
@@ -187,26 +207,26 @@ def cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z):
     c_sk = oc.sketch(ids, off[:rows + 1], lo, perm=perm, threads=threads)
     t0 = time.perf_counter()
     q_sk = oc.sketch(qw["q_ids"], qw["q_off"], lo, perm=perm, threads=threads)
-    oc.query("hoph", q_sk, c_sk, KG, T[0], T[1], EPS, z=z, threads=threads)
+    oc.query("hoph", q_sk, c_sk, KG, thr[0], thr[1], EPS, z=z, threads=threads)
     return time.perf_counter() - t0, len(qw["q_off"]) - 1
 
 
-def cpu_baseline(qw, off, coll_seed, target_s, n_rows):
+def cpu_baseline(qw, off, coll_seed, target_s, n_rows, thr=T):
     from oracle import oracle_c as oc
     threads = os.cpu_count() or 1
     lo = oc.layout(D, K, KG, *AB)
     perm = oc.permutation(D, PERM_SEED)
     z = np.diff(lo[::KG]).astype(np.uint64)
     probe = min(2000, n_rows)
-    t, nq = cpu_oracle_pass(qw, off, coll_seed, probe, threads, lo, perm, z)
+    t, nq = cpu_oracle_pass(qw, off, coll_seed, probe, threads, lo, perm, z, thr)
     rows = int(min(n_rows, max(probe, probe * target_s / max(t, 1e-6))))
-    t, nq = cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z)
-    t1, _ = cpu_oracle_pass(qw, off, coll_seed, probe, 1, lo, perm, z)  # one core, small sample
+    t, nq = cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z, thr)
+    # one core, small sample
+    t1, _ = cpu_oracle_pass(qw, off, coll_seed, probe, 1, lo, perm, z, thr)
     return {"value": nq * rows / t, "unit": UNIT, "cores": threads, "kind": "oracle",
             "cpu_model": cpu_model(), "value_one_core": nq * probe / t1,
-            "sample": "oracle sketches of the %d query sets + (1:2)HOPH comparison against "
-                      "collection rows 0..%d (%d pairs, %.1f s); one core: rows 0..%d"
-                      % (nq, rows - 1, nq * rows, t, probe - 1)}
+            "sample": "C oracle: sketch %d query sets + (1:2)HOPH vs rows 0..%d (%d pairs, "
+                      "%.1f s); one core: rows 0..%d" % (nq, rows - 1, nq * rows, t, probe - 1)}
 
 
 def cpu_model():
@@ -235,24 +255,25 @@ def run_reference(args):
     from oracle import oracle_c as oc
     oc.build()
     off, coll_seed = collection_host(args.rows, 0)
-    qw = query_sets(args.queries, off, coll_seed)
+    qw = lane_batch(args, off, coll_seed, 0)
+    thr = decision_thr(args)
     threads = os.cpu_count() or 1
     lo = oc.layout(D, K, KG, *AB)
     perm = oc.permutation(D, PERM_SEED)
     z = np.diff(lo[::KG]).astype(np.uint64)
     budget = 150.0 / max(1, args.steps + args.warmup)  # seconds per step
     probe = 256
-    t, nq = cpu_oracle_pass(qw, off, coll_seed, probe, threads, lo, perm, z)
+    t, nq = cpu_oracle_pass(qw, off, coll_seed, probe, threads, lo, perm, z, thr)
     rows = int(min(args.rows, max(16, probe * budget / max(t, 1e-6))))
     for _ in range(args.warmup):
-        cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z)
+        cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z, thr)
     total = 0.0
     for _ in range(args.steps):
-        t, nq = cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z)
+        t, nq = cpu_oracle_pass(qw, off, coll_seed, rows, threads, lo, perm, z, thr)
         total += t
     value = nq * rows * args.steps / total
-    sample = ("per step: oracle sketches of %d query sets + (1:2)HOPH comparison against "
-              "collection rows 0..%d (%d pairs)" % (nq, rows - 1, nq * rows))
+    sample = ("per step: C oracle sketches %d query sets + (1:2)HOPH vs collection rows "
+              "0..%d (%d pairs)" % (nq, rows - 1, nq * rows))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
@@ -262,27 +283,43 @@ def run_reference(args):
                              "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(headline_json(line), flush=True)
+
+
+def decision_thr(args):
+    """The decision threshold of the timed step as (num, den)."""
+    num, den = (int(x) for x in args.decision_thr.split("/"))
+    return num, den
 
 
 def workload_config(args, world):
-    return {"workload": "batched (1:2)HOPH query: %d query sets (10%% planted, J 0.6-0.95) "
-                        "sketched and compared against %d resident k=256 sketches per GPU"
+    thr = decision_thr(args)
+    return {"workload": "step = sketch %d query sets (10%% planted near duplicates) + "
+                        "(1:2)HOPH query vs %d resident k=256 sketches/GPU"
                         % (args.queries, args.rows),
-            "D": D, "k": K, "k_group": KG, "a_b": "1:2", "T": "7/10", "eps": EPS,
-            "queries": args.queries, "rows_per_gpu": args.rows,
-            "set_size": "lognormal(median 300, sigma 1.0) clipped [10, 20000]",
-            "ids": "uniform over D", "l2": "inputs larger than L2 (2.56 GB plane per pass)",
-            "parallelism": "rows sharded, %d GPU(s), no data-path collective" % world}
+            "D": D, "k": K, "k_group": KG, "a_b": "1:2", "T_truth": "%d/%d" % T,
+            "T_decision": "%d/%d" % thr, "eps": EPS, "queries": args.queries,
+            "rows_per_gpu": args.rows, "sets": "lognormal(300,1) [10,20000], uniform IDs",
+            "l2": "inputs > L2 (2.56 GB plane/pass)",
+            "schedule": "%d batches in flight" % max(1, args.in_flight),
+            "parallelism": "rows sharded x%d, no data-path collective" % world}
 
 
 # ---------------------------------------------------------------------------
 # native
 # ---------------------------------------------------------------------------
 
+def lane_batch(args, off, coll_seed, lane):
+    """The query batch of in-flight lane `lane` (lane 0: the step's batch;
+    every other lane draws its own sets with its own seeds)."""
+    from paper_1805_11254_gb300 import synth
+    return synth.query_batch(args.queries, 0.1, D, coll_seed, off, 0.6, 0.95,
+                             Q_SEED + 1000 * lane, PLANT_SEED + 1000 * lane)
+
+
 def run_native(args):
     import torch
-    from paper_1805_11254_gb300 import build_lib, hoph, shard, synth
+    from paper_1805_11254_gb300 import build_lib, hoph, shard
     rank, world, local = env_rank()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -300,6 +337,7 @@ def run_native(args):
     barrier()
     hoph.load()
     stream = torch.cuda.current_stream()
+    thr = decision_thr(args)
 
     def max_over_ranks(x):
         return shard.max_over_ranks(x, device=dev)
@@ -317,388 +355,426 @@ def run_native(args):
         profile_self_join(args, off, coll_seed, dev, stream)
         return
     n_ids = int(off[-1])
-    plan = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
-    d_off = to_dev(off, dev)
-    d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
-    hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
-    planes = plan.sketch(d_ids, d_off, args.rows)
-    plan.check()
-    del d_ids
+    with hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=thr, epsilon=EPS) as plan:
+        d_off = to_dev(off, dev)
+        d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+        hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
+        planes = plan.sketch(d_ids, d_off, args.rows)
+        plan.check()
+    del d_ids, d_off
     torch.cuda.empty_cache()
 
-    # ---- query batch
-    qw = query_sets(args.queries, off, coll_seed)
-    nq = args.queries
-    dq_ids = to_dev(qw["q_ids"], dev)
-    dq_off = to_dev(qw["q_off"], dev)
-    q_planes = torch.empty((plan.G, nq, KG), dtype=torch.int32, device=dev)
-    cap = 1 << 20
-    out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
-    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-
-    def step(s=stream):
-        hoph.oph_build_sketches(plan.handle, dq_ids, dq_off, nq, q_planes, s)
-        hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_HOPH, q_planes, nq, planes, args.rows,
-                              out, cap, cnt, None, s)
+    n_lanes = max(1, args.in_flight)
+    batches = [lane_batch(args, off, coll_seed, ln) for ln in range(n_lanes)]
+    qw = batches[0]
 
     if args.profile:
-        for _ in range(max(1, args.warmup)):
-            step()
-        plan.check()
+        with hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=thr, epsilon=EPS) as p:
+            if args.profile_knobs:
+                p.set_exec(**{kv.split("=")[0]: int(kv.split("=")[1])
+                              for kv in args.profile_knobs.split(",")})
+            dq_ids, dq_off = to_dev(qw["q_ids"], dev), to_dev(qw["q_off"], dev)
+            build, query, dt = hoph.oph_build_sketches, hoph.hoph_query_batch, torch.int32
+            c = planes
+            if args.profile_compact:
+                build, query, dt = hoph.oph_build_sketches16, hoph.hoph_query_batch16, torch.int16
+                d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
+                hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
+                c = p.sketch16(d_ids, to_dev(off, dev), args.rows)
+                del d_ids, planes
+            q = torch.empty((p.G, args.queries, KG), dtype=dt, device=dev)
+            out = torch.empty((CAP, 2), dtype=torch.int64, device=dev)
+            cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+            for _ in range(max(1, args.warmup)):
+                build(p.handle, dq_ids, dq_off, args.queries, q, stream)
+                query(p.handle, hoph.HOPH_MODE_HOPH, q, args.queries, c, args.rows, out, CAP, cnt,
+                      None, stream)
+            p.check()
+            print(json.dumps({"profiled": "query", "knobs": p.exec_kwargs,
+                              "compact": bool(args.profile_compact),
+                              "accepted": int(cnt.item())}), flush=True)
         return
 
-    from paper_1805_11254_gb300 import autotune
-    best, tune_ms = None, {}
-    if not args.no_tune:  # tuned on this batch's own sketches
-        hoph.oph_build_sketches(plan.handle, dq_ids, dq_off, nq, q_planes, stream)
-        best, tune_ms = autotune.tune_query(plan, hoph.HOPH_MODE_HOPH, q_planes, nq, planes,
-                                            args.rows, out, cap, cnt, stream)
-    for _ in range(args.warmup):
-        step()
-    plan.check()
-    st = torch.zeros(hoph.STATS_WORDS, dtype=torch.int64, device=dev)
-    hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_HOPH, q_planes, nq, planes, args.rows, out,
-                          cap, cnt, st, stream)
-    stats = hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes())
-    n_acc = int(cnt.item())
-    pairs = out[:min(n_acc, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
-
-    # kernels one step launches (library's own count, one eager step)
-    hoph.hoph_plan_enable_timing(plan.handle, True)
-    step()
-    _, _, launches_per_step = hoph.hoph_plan_read_timing(plan.handle)
-
-    # ---- the step as one CUDA graph (timing events captured inside it)
-    graph = None
-    if not args.no_graph:
-        side = torch.cuda.Stream(device=dev)
-        side.wait_stream(stream)
-        with torch.cuda.stream(side):
-            for _ in range(3):
-                step(side)
-        stream.wait_stream(side)
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            step(torch.cuda.current_stream())
-        torch.cuda.synchronize()
-        graph.replay()
-        torch.cuda.synchronize()
-        plan.check()
-        g_pairs = out[:min(int(cnt.item()), cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
-        if int(cnt.item()) != n_acc or not np.array_equal(g_pairs, pairs):
-            raise RuntimeError("graph replay changed the result")
-
-    def run_step():
-        if graph is not None:
-            graph.replay()
-        else:
-            step()
-
-    # ---- timed region: K steps back to back
-    clocks = Clocks(local)
-    clocks.start()
-    time.sleep(0.3)
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        run_step()
-    e1.record(stream)
-    barrier()
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
-    plan.check()
-    ms = max_over_ranks(ms)
-    pairs_per_step = nq * args.rows
-    value = pairs_per_step * world * args.steps / (ms / 1e3)
-
-    # ---- kernel durations: the same K steps again, reading the CUDA events
-    # recorded around each phase (inside the graph when one is used)
-    phase_ms = [0.0, 0.0, 0.0, 0.0]
-    k_time = min(args.steps, 200)
-    if graph is None:
-        hoph.hoph_plan_enable_timing(plan.handle, True)
-        for _ in range(k_time):
-            step()
-        phase_ms, calls, _ = hoph.hoph_plan_read_timing(plan.handle)
-        phase_ms = [p / max(calls, 1) for p in phase_ms]
-    else:
-        for _ in range(k_time):
-            graph.replay()
-            phase_ms = [a + b for a, b in zip(phase_ms, hoph.hoph_plan_peek_timing(plan.handle))]
-        phase_ms = [p / k_time for p in phase_ms]
-    hoph.hoph_plan_enable_timing(plan.handle, False)
-    calls = 1
-    launches = launches_per_step * args.steps
-
-    # ---- batches in flight: more plans run the same step on more streams and
-    # one CUDA graph holds one branch per batch, so one batch's sketching, join
-    # index and candidate counting overlap another's streaming filter.  With n
-    # batches in flight the K timed steps are K // n replays of that graph
-    # (+ K % n replays of the single-step graph); each step still sketches and
-    # queries a whole batch.  Two, three, four, six and eight in flight are
-    # timed; the fastest schedule (this or one at a time) gives the headline.
-    serial = {"ms_per_step": ms / args.steps, "value": value}
-    pipeline = None
-    if graph is not None and not args.no_pipeline and args.steps >= 2:
-        lanes = [dict(plan=plan, q=q_planes, out=out, cnt=cnt)]
-        for _ in range(7):
-            p2 = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
-            p2.set_exec(**plan.exec_kwargs)
-            lanes.append(dict(plan=p2, q=torch.empty_like(q_planes), out=torch.empty_like(out),
-                              cnt=torch.zeros_like(cnt)))
-
-        def lane_step(ln, s):
-            hoph.oph_build_sketches(ln["plan"].handle, dq_ids, dq_off, nq, ln["q"], s)
-            hoph.hoph_query_batch(ln["plan"].handle, hoph.HOPH_MODE_HOPH, ln["q"], nq, planes,
-                                  args.rows, ln["out"], cap, ln["cnt"], None, s)
-        for ln in lanes[1:]:
-            for _ in range(3):  # sizes the plan's scratch and tables outside the capture
-                lane_step(ln, stream)
-        torch.cuda.synchronize()
-        timed = {}
-        for n_in in (2, 3, 4, 6, 8):
-            streams = [torch.cuda.Stream(device=dev) for _ in range(n_in)]
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                cs = torch.cuda.current_stream()
-                for st_, ln in zip(streams, lanes):
-                    st_.wait_stream(cs)
-                    lane_step(ln, st_)
-                for st_ in streams:
-                    cs.wait_stream(st_)
-            torch.cuda.synchronize()
-            g.replay()
-            torch.cuda.synchronize()
-            for ln in lanes[:n_in]:
-                ln["plan"].check()
-                c_ = int(ln["cnt"].item())
-                got = ln["out"][:min(c_, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
-                if c_ != n_acc or not np.array_equal(got, pairs):
-                    raise RuntimeError("the %d-branch graph changed the result" % n_in)
-            clocks = Clocks(local)
-            clocks.start()
-            time.sleep(0.3)
-            barrier()
-            e0.record(stream)
-            for _ in range(args.steps // n_in):
-                g.replay()
-            for _ in range(args.steps % n_in):
-                graph.replay()
-            e1.record(stream)
-            barrier()
-            ms_n = max_over_ranks(e0.elapsed_time(e1))
-            timed[n_in] = (ms_n, clocks.stop())
-            for ln in lanes[:n_in]:
-                ln["plan"].check()
-        for ln in lanes[1:]:
-            ln["plan"].close()
-        n_best = min(timed, key=lambda n: timed[n][0])
-        ms_n, clk_n = timed[n_best]
-        value_n = pairs_per_step * world * args.steps / (ms_n / 1e3)
-        pipeline = {"batches_in_flight": n_best, "ms_per_step": ms_n / args.steps,
-                    "value": value_n,
-                    "ms_per_step_by_batches_in_flight": {n: t[0] / args.steps
-                                                         for n, t in timed.items()}}
-        if value_n > value:
-            ms, value, clk = ms_n, value_n, clk_n
-
     peaks, peak_kind = measured_peaks()
-    scan_ms = phase_ms[1] / max(calls, 1)
-    # the streaming pass reads the first plane and the query sketches once
-    alg_bytes = int(args.rows * KG * 4 + nq * KG * 4)
-    achieved = alg_bytes / (scan_ms / 1e3) / 1e9
-    traffic = NCU_TRAFFIC.get(filter_src_sha())
-    roofline = {"bound": "hbm", "kernel": "filter_kernel (value join, first-group plane)",
-                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy)",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel_ms_per_launch": scan_ms,
-                "phases_ms_per_step": {"join_index": phase_ms[0] / max(calls, 1),
-                                       "filter": scan_ms,
-                                       "count_candidates": phase_ms[2] / max(calls, 1),
-                                       "sort_stats": phase_ms[3] / max(calls, 1)}}
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": workload_config(args, world), "roofline": roofline,
-            "gpu_launches": int(launches),
-            "cuda_graph": graph is not None,
-            "schedule": ("%d batches in flight (one graph, one stream branch and one plan per "
-                         "batch)" % pipeline["batches_in_flight"]
-                         if pipeline and ms / args.steps <= pipeline["ms_per_step"]
-                         else "one batch at a time (graph replays)"),
-            "serial": serial, "pipelined": pipeline,
-            "clocks": clk,
-            "autotune": {"best": best, "ms_by_candidate": tune_ms},
-            "stats": {"accepted": n_acc, "survivors_entering_group": list(stats.entering[:4]),
-                      "accepted_per_group": list(stats.accepted[:4]),
-                      "rejected_per_group": list(stats.rejected[:4]),
-                      "join_hits": int(stats.join_hits), "strategy": int(stats.strategy),
-                      "rows_counted": int(stats.rows_counted)}}
+    head = headline_leg(args, planes, batches, dev, stream, thr, barrier, max_over_ranks, local,
+                        truth_threshold_too=not (args.no_extras or args.no_truth_threshold))
+    value = head["value"]
+    line = headline_line(args, world, head, peaks, peak_kind)
+    details = {"headline": {k_: v for k_, v in head.items() if k_ not in ("pairs", "roofline")}}
 
     if not args.no_extras:  # every rank: the end-to-end step is timed over all of them
         def sync(x):
             barrier()
             return max_over_ranks(x)
-        line["e2e"] = e2e_leg(args, plan, qw, planes, dev, stream, world, sync)
+        e2e = e2e_leg(args, thr, batches, planes, dev, world, sync)
+        line["e2e"] = {k_: e2e[k_] for k_ in ("value", "unit", "h2d_bytes_per_step",
+                                              "d2h_bytes_per_step", "ms_per_step")}
+        details["e2e"] = e2e
     # the other legs are single-GPU studies: rank 0 of a one-GPU run only
     if rank == 0 and world == 1 and not args.no_extras:
-        line["sketch"] = sketch_leg(dev, stream, peaks)
+        details["sketch"] = sketch_leg(dev, stream, peaks)
         rq = recall_queries(off, coll_seed)
-        line["oph_full_scan_baseline"], oph_pairs, oph_rq_pairs = oph_baseline_leg(
+        details["oph_full_scan_baseline"], oph_pairs, oph_rq_pairs = oph_baseline_leg(
             args, off, coll_seed, qw, dev, stream, value, rq)
-        line["quality"] = quality(qw, {"hoph": pairs, "oph_full_scan": oph_pairs}, off,
-                                  coll_seed, args)
+        details["quality"] = quality(qw, {"hoph": head["pairs"], "oph_full_scan": oph_pairs},
+                                     off, coll_seed, args)
+        dq_ids, dq_off = to_dev(qw["q_ids"], dev), to_dev(qw["q_off"], dev)
+        nq = args.queries
         eps_runs = eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq)
+        thr_set = sorted(set(EQUAL_RECALL_T) | {thr}, key=lambda t: -t[0] / t[1])
         thr_runs = eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq,
-                                variants=[(t, EPS) for t in EQUAL_RECALL_T])
+                                variants=[(t, EPS) for t in thr_set])
         methods = {"oph_full_scan": oph_rq_pairs}
         methods.update({"hoph_eps_%g" % e: r["pairs"] for e, r in eps_runs.items()})
         methods.update({"hoph_T_%d_%d" % t: r["pairs"] for t, r in thr_runs.items()})
         study = quality(rq, methods, off, coll_seed, args, n_random_rows=500)
-        line["equal_recall"] = equal_recall(study, eps_runs, nq, args.rows, len(rq["q_off"]) - 1,
-                                            thr_runs)
-        line["cpu_baseline"] = cpu_baseline(qw, off, coll_seed, args.cpu_seconds, args.rows)
+        er = equal_recall(study, eps_runs, nq, args.rows, len(rq["q_off"]) - 1, thr_runs)
+        m_thr = study["hoph_T_%d_%d" % thr]
+        er["headline_decision_threshold"] = "%d/%d" % thr
+        er["headline_recall"] = m_thr["recall"]
+        er["headline_precision"] = m_thr["precision"]
+        er["headline_at_equal_recall"] = m_thr["recall"] >= er["oph_full_scan_recall"]
+        details["equal_recall"] = er
+        line["cpu_baseline"] = cpu_baseline(qw, off, coll_seed, args.cpu_seconds, args.rows, thr)
         if not args.no_serve:
-            line["serving"] = serving_leg(args, planes, dev, line["oph_full_scan_baseline"])
+            details["serving"] = serving_leg(args, planes, dev, details["oph_full_scan_baseline"])
         if not args.no_compact:
-            line["compact"] = compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs, dev,
-                                          stream, peaks)
+            details["compact"] = compact_leg(args, off, coll_seed, dq_ids, dq_off, nq,
+                                             head["pairs"], dev, stream, peaks, thr)
         if not args.no_sweep:
-            line["sweeps"] = sweep_leg(dev, stream)
+            details["sweeps"] = sweep_leg(dev, stream)
         if not args.no_self_join:
-            line["self_join"] = self_join_leg(off, coll_seed, dev, stream)
+            details["self_join"] = self_join_leg(off, coll_seed, dev, stream)
         if not args.no_shingle:
             del planes
             torch.cuda.empty_cache()
-            line["shingle"] = shingle_leg(args, dev, stream, peaks)
-    plan.close()
-    # the metric's four parts side by side
-    parts = {"pair_comparisons_per_s": line["value"],
-             "hbm_roofline_frac_of_measured": roofline["frac"]}
-    if "sketch" in line:
-        parts["sets_sketched_per_s"] = line["sketch"]["sets_per_s"]
-    if "equal_recall" in line:
-        er = line["equal_recall"]
-        parts["equal_recall"] = {
-            "oph_full_scan_recall": er["oph_full_scan_recall"],
-            "hoph_decision_threshold": er["decision_threshold_at_equal_recall"],
-            "hoph_precision": er["precision_at_equal_recall"],
-            "oph_full_scan_precision": er["oph_full_scan_precision"],
-            "pair_comparisons_per_s_eager": er["value_at_equal_recall_by_threshold"]}
-    line["metric_parts"] = parts
+            details["shingle"] = shingle_leg(args, dev, stream, peaks)
+        line["metric_parts"] = metric_parts(details)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line, details, args.details)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def e2e_leg(args, plan, qw, planes, dev, stream, world=1, sync=None):
-    """Same step through the public API from pinned host buffers: H2D of the
-    query sets, sketch, query, D2H of the count and the accepted pairs.  On
-    several ranks every rank runs it between barriers (`sync(x)`: barrier and
-    max over ranks of x) and the value counts all ranks' pairs."""
+def headline_line(args, world, head, peaks, peak_kind):
+    """The benchmark's JSON line from the timed step's results (the e2e,
+    cpu_baseline and metric_parts keys are added by the caller)."""
+    roofline = dict(head["roofline"])
+    roofline["peak"] = peaks["hbm_gbs"]
+    roofline["frac"] = roofline["achieved"] / peaks["hbm_gbs"]
+    roofline["peak_source"] = "%s hbm_gbs (copy)" % peak_kind
+    return {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": workload_config(args, world),
+            "roofline": roofline, "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"]}
+
+
+def metric_parts(details):
+    """The metric's other parts, in a few numbers: sets sketched per second,
+    the sketch's HBM fraction, the recalls behind "equal recall", and the
+    plain-OPH baseline the HOPH step is compared with."""
+    parts = {}
+    sk = details.get("sketch")
+    if sk:
+        parts["sets_sketched_per_s"] = sk["sets_per_s"]
+        parts["sketch_hbm_frac"] = sk["roofline"]["frac"]
+    er = details.get("equal_recall")
+    if er:
+        parts["recall_hoph"] = er["headline_recall"]
+        parts["recall_oph_full_scan"] = er["oph_full_scan_recall"]
+        parts["at_equal_recall"] = er["headline_at_equal_recall"]
+    ob = details.get("oph_full_scan_baseline")
+    if ob:
+        parts["oph_one_query_per_launch_pairs_per_s"] = ob["value"]
+    h = details.get("headline", {})
+    if "value_at_T" in h:
+        parts["value_at_T_7_10"] = h["value_at_T"]
+    return parts
+
+
+def emit(line, details, details_path=None):
+    """Print the headline as the one JSON line on stdout (kept short); the
+    studies go to stderr as one line prefixed 'details: ' and, when asked,
+    to a file."""
+    text = json.dumps(details, default=_jsonable)
+    if details_path:
+        d = os.path.dirname(os.path.abspath(details_path))
+        os.makedirs(d, exist_ok=True)
+        with open(details_path, "w") as f:
+            f.write(text + "\n")
+    print("details: " + text, file=sys.stderr, flush=True)
+    print(headline_json(line), flush=True)
+
+
+def _jsonable(x):
+    if isinstance(x, (np.integer,)):
+        return int(x)
+    if isinstance(x, (np.floating,)):
+        return float(x)
+    if isinstance(x, np.ndarray):
+        return x.tolist()
+    return str(x)
+
+
+def _round(x):
+    """Floats to 6 significant digits (the line stays short)."""
+    if isinstance(x, float):
+        return float("%.6g" % x)
+    if isinstance(x, dict):
+        return {k_: _round(v) for k_, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_round(v) for v in x]
+    return x
+
+
+HEADLINE_MAX_BYTES = 2048
+# what goes first if a line would still be too long (never the contract's keys)
+_TRIM = (("metric_parts",), ("cpu_baseline", "cpu_model"), ("config", "sets"), ("config", "l2"),
+         ("roofline", "peak_source"), ("cpu_baseline", "sample"), ("config", "workload"))
+
+
+def headline_json(line):
+    """The headline as one JSON line under 2 KB: floats rounded to six
+    significant digits, no spaces; optional keys are dropped (in _TRIM's
+    order) if it would still be longer."""
+    line = _round(line)
+    text = json.dumps(line, default=_jsonable, separators=(",", ":"))
+    for path in _TRIM:
+        if len(text) <= HEADLINE_MAX_BYTES:
+            break
+        d = line
+        for key in path[:-1]:
+            d = d.get(key, {}) if isinstance(d, dict) else {}
+        if isinstance(d, dict) and path[-1] in d:
+            del d[path[-1]]
+            text = json.dumps(line, default=_jsonable, separators=(",", ":"))
+    return text
+
+
+def headline_leg(args, planes, batches, dev, stream, thr, barrier, max_over_ranks, local,
+                 knobs=None, truth_threshold_too=True):
+    """The timed step: sketch a batch of query sets and (1:2)HOPH-query it
+    against the resident collection.  Every in-flight lane has its own plan,
+    stream branch and query batch; the step is replayed as a CUDA graph, one
+    batch at a time and with all lanes in flight (the headline schedule,
+    fixed by --in-flight).  Returns value, timings, roofline inputs and lane
+    0's pairs.  `knobs`: execution knobs to use instead of tuning."""
     import torch
-    from paper_1805_11254_gb300 import hoph
+    from paper_1805_11254_gb300 import autotune, hoph
     nq = args.queries
-    h_ids = torch.from_numpy(np.ascontiguousarray(qw["q_ids"]).view(np.int32)).pin_memory()
-    h_off = torch.from_numpy(np.ascontiguousarray(qw["q_off"])).pin_memory()
-    d_ids = torch.empty_like(h_ids, device=dev)
-    d_off = torch.empty_like(h_off, device=dev)
-    q_planes = torch.empty((plan.G, nq, KG), dtype=torch.int32, device=dev)
-    cap = 1 << 20
-    out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
-    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-    h_cnt = torch.zeros(1, dtype=torch.int64).pin_memory()
-    h_out = torch.empty((cap, 2), dtype=torch.int64).pin_memory()
-    d2h = 0
-
-    def once():
-        nonlocal d2h
-        d_ids.copy_(h_ids, non_blocking=True)
-        d_off.copy_(h_off, non_blocking=True)
-        hoph.oph_build_sketches(plan.handle, d_ids, d_off, nq, q_planes, stream)
-        hoph.hoph_query_batch(plan.handle, hoph.HOPH_MODE_HOPH, q_planes, nq, planes, args.rows,
-                              out, cap, cnt, None, stream)
-        h_cnt.copy_(cnt, non_blocking=True)
-        stream.synchronize()
-        n = min(int(h_cnt.item()), cap)
-        h_out[:n].copy_(out[:n], non_blocking=True)
-        stream.synchronize()
-        d2h = 8 + 16 * n
-
-    sync = sync or (lambda x: x)
-    for _ in range(3):
-        once()
-    sync(0.0)
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        once()
-    dt = sync((time.perf_counter() - t0) / args.e2e_steps)
-    h2d = int(h_ids.numel() * 4 + h_off.numel() * 8)
-    serial = {"value": nq * args.rows * world / dt, "ms_per_step": dt * 1e3,
-              "d2h_bytes_per_step": d2h}
-    pipes = [e2e_in_flight(args, plan, h_ids, h_off, planes, dev, n_lanes=n, world=world,
-                           sync=sync) for n in (3, 4, 6, 8)]
-    pipe = max(pipes, key=lambda r: r["value"])
-    best = pipe if pipe["value"] > serial["value"] else serial
-    return {"value": best["value"], "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": int(best["d2h_bytes_per_step"]),
-            "ms_per_step": best["ms_per_step"],
-            "schedule": best.get("schedule", "one batch at a time"),
-            "serial": serial, "in_flight": pipe,
-            "ms_per_step_by_lanes": {p_["schedule"].split()[0]: p_["ms_per_step"] for p_ in pipes},
-            "path": "pinned host sets -> oph_build_sketches -> hoph_query_batch -> host pairs"}
-
-
-def e2e_in_flight(args, plan, h_ids, h_off, planes, dev, n_lanes=3, window=4096, world=1,
-                  sync=None):
-    """The end-to-end step with several batches in flight: each lane (its own
-    plan and stream) copies a batch's sets in, sketches and queries them and
-    copies the count and the first `window` pairs back; a lane's results are
-    read (the rest of its pairs copied if there are more) before it takes the
-    next batch.  Host wall time over K steps."""
-    import torch
-    from paper_1805_11254_gb300 import hoph
-    nq = args.queries
+    cap = CAP
     lanes = []
-    for _ in range(n_lanes):
-        p = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
-        p.set_exec(**plan.exec_kwargs)
+    for b in batches:
+        p = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=thr, epsilon=EPS)
+        lanes.append(dict(plan=p, ids=to_dev(b["q_ids"], dev), off=to_dev(b["q_off"], dev),
+                          q=torch.empty((p.G, nq, KG), dtype=torch.int32, device=dev),
+                          out=torch.empty((cap, 2), dtype=torch.int64, device=dev),
+                          cnt=torch.zeros(1, dtype=torch.int64, device=dev)))
+
+    def lane_step(ln, s):
+        hoph.oph_build_sketches(ln["plan"].handle, ln["ids"], ln["off"], nq, ln["q"], s)
+        hoph.hoph_query_batch(ln["plan"].handle, hoph.HOPH_MODE_HOPH, ln["q"], nq, planes,
+                              args.rows, ln["out"], cap, ln["cnt"], None, s)
+
+    def lane_pairs(ln):
+        c_ = int(ln["cnt"].item())
+        return c_, ln["out"][:min(c_, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1).copy()
+
+    l0 = lanes[0]
+    best, tune_ms = knobs, {}
+    if knobs is not None:
+        l0["plan"].set_exec(**knobs)
+    elif not args.no_tune:  # tuned on lane 0's own sketches
+        hoph.oph_build_sketches(l0["plan"].handle, l0["ids"], l0["off"], nq, l0["q"], stream)
+        best, tune_ms = autotune.tune_query(l0["plan"], hoph.HOPH_MODE_HOPH, l0["q"], nq, planes,
+                                            args.rows, l0["out"], cap, l0["cnt"], stream)
+    for ln in lanes:
+        ln["plan"].set_exec(**l0["plan"].exec_kwargs)
+        for _ in range(max(3, args.warmup)):  # also sizes scratch outside any capture
+            lane_step(ln, stream)
+        ln["plan"].check()
+        ln["n"], ln["pairs"] = lane_pairs(ln)
+    st = torch.zeros(hoph.STATS_WORDS, dtype=torch.int64, device=dev)
+    hoph.hoph_query_batch(l0["plan"].handle, hoph.HOPH_MODE_HOPH, l0["q"], nq, planes, args.rows,
+                          l0["out"], cap, l0["cnt"], st, stream)
+    stats = hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes())
+
+    # kernels one step launches (the library's own count, one eager step)
+    hoph.hoph_plan_enable_timing(l0["plan"].handle, True)
+    lane_step(l0, stream)
+    _, _, launches_per_step = hoph.hoph_plan_read_timing(l0["plan"].handle)
+
+    # every lane's step is one CUDA graph (timing events inside), captured on
+    # the lane's own stream
+    for ln in lanes:
+        hoph.hoph_plan_enable_timing(ln["plan"].handle, True)
+        ln["s"] = torch.cuda.Stream(device=dev)
+        ln["s"].wait_stream(stream)
+        with torch.cuda.stream(ln["s"]):
+            lane_step(ln, ln["s"])
+        ln["g"] = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(ln["g"], stream=ln["s"]):
+            lane_step(ln, ln["s"])
+        stream.wait_stream(ln["s"])
+    torch.cuda.synchronize()
+    for ln in lanes:
+        with torch.cuda.stream(ln["s"]):
+            ln["g"].replay()
+        ln["s"].synchronize()
+        ln["plan"].check()
+        if lane_pairs(ln)[0] != ln["n"] or not np.array_equal(lane_pairs(ln)[1], ln["pairs"]):
+            raise RuntimeError("a graph replay changed a batch's result")
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def run_steps(k, lns):
+        """k steps dealt round-robin over the lanes: step i replays lane
+        i mod n's graph on that lane's stream, after its previous step only
+        (no barrier between steps)."""
+        for ln in lns:
+            ln["s"].wait_event(e0)
+        for i in range(k):
+            ln = lns[i % len(lns)]
+            with torch.cuda.stream(ln["s"]):
+                ln["g"].replay()
+        for ln in lns:
+            stream.wait_stream(ln["s"])
+
+    def timed(lns):
+        clocks = Clocks(local)
+        clocks.start()
+        time.sleep(0.3)
+        barrier()
+        e0.record(stream)
+        run_steps(args.steps, lns)
+        e1.record(stream)
+        barrier()
+        t = max_over_ranks(e0.elapsed_time(e1))
+        return t, clocks.stop()
+
+    def phases(lns, rounds):
+        """Mean per-launch phase times (ms) of each lane's call as it runs in
+        this schedule: the same round-robin steps again, reading the events
+        captured in each lane's graph after every round."""
+        acc = [[0.0] * 4 for _ in lns]
+        for _ in range(rounds):
+            e0.record(stream)
+            run_steps(len(lns), lns)
+            for a, ln in zip(acc, lns):
+                for i, v in enumerate(hoph.hoph_plan_peek_timing(ln["plan"].handle)):
+                    a[i] += v
+        return [[v / rounds for v in a] for a in acc]
+
+    # one batch at a time (lane 0 alone), then all lanes in flight
+    ms1, clk1 = timed(lanes[:1])
+    reps = min(args.steps, 200)
+    ph1 = phases(lanes[:1], reps)[0]
+    n_in = len(lanes)
+    msn = clkn = phn = None
+    if n_in > 1:
+        msn, clkn = timed(lanes)
+        phn = phases(lanes, max(1, reps // n_in))
+    for ln in lanes:
+        hoph.hoph_plan_enable_timing(ln["plan"].handle, False)
+
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    pairs_per_step = nq * args.rows
+    ms, clk = (msn, clkn) if msn is not None else (ms1, clk1)
+    value = pairs_per_step * world * args.steps / (ms / 1e3)
+    filt = ph1[1]
+    # the streaming pass reads the first plane and the query sketches once
+    alg_bytes = int(args.rows * KG * 4 + nq * KG * 4)
+    traffic = NCU_TRAFFIC.get(filter_src_sha())
+    roofline = {"bound": "hbm", "kernel": "filter_kernel",
+                "achieved": alg_bytes / (filt / 1e3) / 1e9, "unit": "GB/s", "traffic": traffic,
+                "alg_bytes": alg_bytes, "kernel_ms": filt}
+    out = {"value": value, "ms": ms, "clocks": clk, "roofline": roofline,
+           "gpu_launches": int(launches_per_step * args.steps),
+           "schedule": ("%d batches in flight (a plan, stream, query batch and step graph per "
+                        "lane; steps dealt round-robin)" % n_in if msn is not None
+                        else "one batch at a time (graph replays)"),
+           "decision_threshold": "%d/%d" % thr,
+           "serial": {"ms_per_step": ms1 / args.steps,
+                      "value": pairs_per_step * world * args.steps / (ms1 / 1e3),
+                      "clocks": clk1, "phases_ms": dict(zip(PHASES, ph1))},
+           "in_flight_phases_ms_by_lane": ([dict(zip(PHASES, p)) for p in phn] if phn else None),
+           "autotune": {"best": best, "ms_by_candidate": tune_ms},
+           "accepted_by_lane": [ln["n"] for ln in lanes],
+           "stats": {"accepted": int(l0["n"]),
+                     "survivors_entering_group": list(stats.entering[:4]),
+                     "accepted_per_group": list(stats.accepted[:4]),
+                     "rejected_per_group": list(stats.rejected[:4]),
+                     "join_hits": int(stats.join_hits), "strategy": int(stats.strategy),
+                     "rows_counted": int(stats.rows_counted)},
+           "pairs": l0["pairs"]}
+    knobs_used = dict(l0["plan"].exec_kwargs)
+    for ln in lanes:
+        ln["plan"].close()
+    if truth_threshold_too and thr != T:
+        # the same schedule and knobs at the ground-truth threshold itself
+        out["value_at_T"] = headline_leg(args, planes, batches, dev, stream, T, barrier,
+                                         max_over_ranks, local, knobs=knobs_used,
+                                         truth_threshold_too=False)["value"]
+    return out
+
+
+PHASES = ("join_index", "filter", "count_candidates", "sort_stats")
+
+
+def e2e_leg(args, thr, batches, planes, dev, world=1, sync=None, window=4096):
+    """The step end to end through the public API from pinned host buffers,
+    with the headline's lanes in flight: each lane (its own plan, stream and
+    query batch) copies its sets in (H2D), sketches and queries them and
+    copies the count and the first `window` pairs back (D2H); a lane's
+    results are read (the rest of its pairs copied if there are more) before
+    it takes its next batch.  Host wall time over --e2e-steps steps.  On
+    several ranks every rank runs it between barriers (`sync(x)`: barrier
+    and max over ranks of x) and the value counts all ranks' pairs."""
+    import torch
+    from paper_1805_11254_gb300 import hoph
+    nq = args.queries
+    cap = CAP
+    lanes = []
+    for b in batches:
+        p = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=thr, epsilon=EPS)
+        h_ids = torch.from_numpy(np.ascontiguousarray(b["q_ids"]).view(np.int32)).pin_memory()
+        h_off = torch.from_numpy(np.ascontiguousarray(b["q_off"])).pin_memory()
         lanes.append(dict(
-            plan=p, s=torch.cuda.Stream(device=dev), d_ids=torch.empty_like(h_ids, device=dev),
-            d_off=torch.empty_like(h_off, device=dev),
+            plan=p, s=torch.cuda.Stream(device=dev), h_ids=h_ids, h_off=h_off,
+            d_ids=torch.empty_like(h_ids, device=dev), d_off=torch.empty_like(h_off, device=dev),
             q=torch.empty((p.G, nq, KG), dtype=torch.int32, device=dev),
-            out=torch.empty((1 << 20, 2), dtype=torch.int64, device=dev),
+            out=torch.empty((cap, 2), dtype=torch.int64, device=dev),
             cnt=torch.zeros(1, dtype=torch.int64, device=dev),
             h_cnt=torch.zeros(1, dtype=torch.int64).pin_memory(),
-            h_out=torch.empty((1 << 20, 2), dtype=torch.int64).pin_memory(),
-            ev=torch.cuda.Event(), busy=False, extra=0))
+            h_out=torch.empty((cap, 2), dtype=torch.int64).pin_memory(),
+            ev=torch.cuda.Event(), busy=False, h2d=0, d2h=0, pairs=0))
+    n_lanes = len(lanes)
 
     def issue(ln):
         s = ln["s"]
         with torch.cuda.stream(s):
-            ln["d_ids"].copy_(h_ids, non_blocking=True)
-            ln["d_off"].copy_(h_off, non_blocking=True)
+            ln["d_ids"].copy_(ln["h_ids"], non_blocking=True)
+            ln["d_off"].copy_(ln["h_off"], non_blocking=True)
             hoph.oph_build_sketches(ln["plan"].handle, ln["d_ids"], ln["d_off"], nq, ln["q"], s)
             hoph.hoph_query_batch(ln["plan"].handle, hoph.HOPH_MODE_HOPH, ln["q"], nq, planes,
-                                  args.rows, ln["out"], 1 << 20, ln["cnt"], None, s)
+                                  args.rows, ln["out"], cap, ln["cnt"], None, s)
             ln["h_cnt"].copy_(ln["cnt"], non_blocking=True)
             ln["h_out"][:window].copy_(ln["out"][:window], non_blocking=True)
             ln["ev"].record(s)
+        ln["h2d"] += ln["h_ids"].numel() * 4 + ln["h_off"].numel() * 8
+        ln["d2h"] += 8 + 16 * window
         ln["busy"] = True
 
     def finish(ln):
         ln["ev"].synchronize()
-        n = min(int(ln["h_cnt"][0]), 1 << 20)
+        n = min(int(ln["h_cnt"][0]), cap)
         if n > window:  # the rest of the pairs
             ln["h_out"][window:n].copy_(ln["out"][window:n])
-            ln["extra"] += 16 * (n - window)
+            ln["d2h"] += 16 * (n - window)
+        ln["pairs"] = n
         ln["busy"] = False
 
     def run(k):
@@ -713,18 +789,20 @@ def e2e_in_flight(args, plan, h_ids, h_off, planes, dev, n_lanes=3, window=4096,
     sync = sync or (lambda x: x)
     run(3 * n_lanes)
     for ln in lanes:
-        ln["extra"] = 0
+        ln["h2d"] = ln["d2h"] = 0
     sync(0.0)
     t0 = time.perf_counter()
     run(args.e2e_steps)
     dt = sync((time.perf_counter() - t0) / args.e2e_steps)
-    extra = sum(ln["extra"] for ln in lanes) / args.e2e_steps
     for ln in lanes:
         ln["plan"].check()
         ln["plan"].close()
-    return {"value": nq * args.rows * world / dt, "ms_per_step": dt * 1e3,
-            "d2h_bytes_per_step": 8 + 16 * window + extra,
-            "schedule": "%d batches in flight (one plan and stream each)" % n_lanes}
+    return {"value": nq * args.rows * world / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": int(sum(ln["h2d"] for ln in lanes) / args.e2e_steps),
+            "d2h_bytes_per_step": int(sum(ln["d2h"] for ln in lanes) / args.e2e_steps),
+            "schedule": "%d batches in flight (one plan, stream and query batch each)" % n_lanes,
+            "accepted_by_lane": [ln["pairs"] for ln in lanes],
+            "path": "pinned host sets -> oph_build_sketches -> hoph_query_batch -> host pairs"}
 
 
 EQUAL_RECALL_EPS = (1e-4, 1e-5, 1e-6, 1e-8, 0.0)
@@ -755,7 +833,7 @@ def eps_variants(args, planes, dq_ids, dq_off, nq, dev, stream, rq, reps=20,
     rq_ids, rq_off = to_dev(rq["q_ids"], dev), to_dev(rq["q_off"], dev)
     n_rq = len(rq["q_off"]) - 1
     out = {}
-    cap = 1 << 20
+    cap = CAP
     o = torch.empty((cap, 2), dtype=torch.int64, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     runs = variants if variants is not None else [(T, e) for e in EQUAL_RECALL_EPS]
@@ -1067,14 +1145,14 @@ def serving_leg(args, planes, dev, oph_leg):
 
     by_streams = {}
     for n_streams in (2, 4):
-        ex = serve.GpuExecutor(plan_kw, planes, args.rows, "hoph", buckets, id_cap,
-                               n_streams=n_streams)
+        ex = serve.GpuExecutor(plan_kw, planes, args.rows, "hoph", buckets, None,
+                               n_streams=n_streams, max_ids=id_cap)
         results = []
         try:
             for i, rate in enumerate(float(x) for x in args.serve_rates.split(",")):
                 reqs = serve.poisson_requests(rate, args.serve_seconds, 100 + i, sets_for)
                 t0 = time.perf_counter()
-                done = serve.serve(ex, serve.Batcher(buckets, id_cap), reqs)
+                done = serve.serve(ex, serve.Batcher(buckets, ex.id_capacity), reqs)
                 wall = time.perf_counter() - t0
                 ok = [r for r in done if r.error is None]
                 n_sets = sum(len(r.sets) for r in ok)
@@ -1086,16 +1164,18 @@ def serving_leg(args, planes, dev, oph_leg):
                 results.append(summ)
         finally:
             ex.close()
-        by_streams[n_streams] = results
-    return {"rates": by_streams[4], "rates_by_streams": by_streams,
+        by_streams[n_streams] = {"id_capacity_per_batch": ex.id_capacity, "rates": results}
+    return {"rates": by_streams[4]["rates"], "rates_by_streams": by_streams,
             "collection_rows": args.rows, "batch_slots": list(buckets),
             "one_request_per_launch_oph_capacity_query_sets_per_s":
                 1e3 / oph_leg["ms_per_query_launch"],
             "how": "2 or 4 streams x 1 plan each, one CUDA graph per (stream, batch size); H2D "
-                   "of a batch's sets and its sketching overlap other streams' queries"}
+                   "of a batch's sets and its sketching overlap other streams' queries; IDs per "
+                   "batch sized from the free HBM at start (75%, split over the streams, at "
+                   "most 4M)"}
 
 
-def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream, peaks,
+def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream, peaks, thr,
                 steps=200):
     """The benchmark step over compact planes: every bin of the (1:2) layout
     over 2^20 is at most 5,462 values wide, so the stored offsets fit in 16
@@ -1103,7 +1183,7 @@ def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream
     halves.  Same pairs as the uint32 planes (checked), timed as a graph."""
     import torch
     from paper_1805_11254_gb300 import hoph
-    plan = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
+    plan = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=thr, epsilon=EPS)
     n_ids = int(off[-1])
     d_off = to_dev(off, dev)
     d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
@@ -1113,7 +1193,7 @@ def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream
     del d_ids
     torch.cuda.empty_cache()
     q16 = torch.empty((plan.G, nq, KG), dtype=torch.int16, device=dev)
-    cap = 1 << 20
+    cap = CAP
     out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
 
@@ -1161,7 +1241,7 @@ def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream
     # batches in flight (two to four), as for the uint32 headline
     lanes = [dict(plan=plan, q=q16, out=out, cnt=cnt)]
     for _ in range(3):
-        p2 = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=T, epsilon=EPS)
+        p2 = hoph.Plan(D, K, KG, *AB, seed=PERM_SEED, thr=thr, epsilon=EPS)
         p2.set_exec(**plan.exec_kwargs)
         lanes.append(dict(plan=p2, q=torch.empty_like(q16), out=torch.empty_like(out),
                           cnt=torch.zeros_like(cnt)))
@@ -1371,6 +1451,67 @@ def sweep_leg(dev, stream, reps=5):
             "collection_sketch_ms": sketch_ms, "points": out}
 
 
+# 64-bit multiplies per ID on the hashed-psi sketch path (read off the
+# kernels): the generator's SplitMix64 step (3 low products) and its scaling
+# to [0, D) (1 low), psi = ((a x + b) mod 2^61-1) >> 29 (1 low + 1 high), and
+# the bin arithmetic floor(o nb / z) with its exact correction (2 low)
+ALU_MULS_GENERATED = {"lo": 7, "hi": 1}
+ALU_MULS_STORED = {"lo": 3, "hi": 1}
+
+
+def alu_peak_leg(dev, stream, target_ms=30.0):
+    """Measured integer peaks (hoph_int_probe): 32-bit multiply-adds and the
+    low and high halves of 64-bit products per second, each from a launch of
+    about target_ms, with the SM clock sampled meanwhile."""
+    import torch
+    from paper_1805_11254_gb300 import hoph
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    threads = sms * 8 * 256
+    sink = torch.empty(threads, dtype=torch.int64, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {}
+    for kind, name in ((0, "imad32"), (1, "mul64_lo"), (2, "mul64_hi")):
+        iters = 256
+        for _ in range(12):  # grow until a launch takes about target_ms
+            hoph.hoph_int_probe(kind, iters, sink, stream)
+            e0.record(stream)
+            hoph.hoph_int_probe(kind, iters, sink, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if ms >= target_ms or iters >= 1 << 24:
+                break
+            iters = min(1 << 24, int(iters * max(2.0, target_ms / max(ms, 1e-3))))
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
+        time.sleep(0.2)
+        e0.record(stream)
+        for _ in range(3):
+            hoph.hoph_int_probe(kind, iters, sink, stream)
+        e1.record(stream)
+        e1.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / 3
+        ops = 8.0 * iters * threads
+        rate = ops / (ms / 1e3)
+        mhz = clk["sm_mhz"] if clk else None
+        out[name] = {"ops_per_s": rate, "ms": ms, "iters": iters,
+                     "per_sm_per_clock": rate / sms / (mhz * 1e6) if mhz else None,
+                     "sm_mhz": mhz}
+    return out
+
+
+def alu_roofline(ids_per_s, muls, peak):
+    """IDs/s against the IDs/s the measured 64-bit multiply rates allow at
+    `muls` low and high products per ID."""
+    ideal = 1.0 / (muls["lo"] / peak["mul64_lo"]["ops_per_s"] +
+                   muls["hi"] / peak["mul64_hi"]["ops_per_s"])
+    return {"bound": "alu", "achieved": ids_per_s, "peak": ideal, "unit": "IDs/s",
+            "frac": ids_per_s / ideal, "muls_per_id": muls,
+            "peak_source": "measured (hoph_int_probe 64-bit products, this run)"}
+
+
 def shingle_leg(args, dev, stream, peaks, q_batch=1024, n_planted=32):
     """Large-set shingle regime: IDs uniform over 2^32, psi the 2-universal
     hash mod 2^61-1, (2:1)HOPH with k = 512, k' = 128 (G = 4), T = 0.7.  The
@@ -1397,9 +1538,13 @@ def shingle_leg(args, dev, stream, peaks, q_batch=1024, n_planted=32):
         torch.cuda.synchronize()
         plan.check()
         ms = e0.elapsed_time(e1)
+        alu = alu_peak_leg(dev, stream)
+        out["alu_peak"] = alu
+        ids_s = int(c_off[-1]) / (ms / 1e3)
         out["collection_generate_and_sketch"] = {
-            "sets_per_s": args.shingle_rows / (ms / 1e3), "ids_per_s": int(c_off[-1]) / (ms / 1e3),
-            "ms": ms, "ids": int(c_off[-1]), "bound": "alu (generator + 61-bit mulmod + bin arithmetic)"}
+            "sets_per_s": args.shingle_rows / (ms / 1e3), "ids_per_s": ids_s,
+            "ms": ms, "ids": int(c_off[-1]),
+            "roofline": alu_roofline(ids_s, ALU_MULS_GENERATED, alu)}
         # query sets: a few planted near duplicates of collection rows, the rest fresh
         rng = np.random.default_rng(seed_q)
         src = rng.integers(0, args.shingle_rows, n_planted)
@@ -1431,7 +1576,9 @@ def shingle_leg(args, dev, stream, peaks, q_batch=1024, n_planted=32):
         byts = 4 * int(q_off[-1]) + 8 * (nq + 1) + 4 * K4 * nq
         gbs = byts / (ms / 1e3) / 1e9
         out["query_sketch"] = {"sets_per_s": nq / (ms / 1e3), "ms": ms, "ids": int(q_off[-1]),
-                               "GB_per_s": gbs, "hbm_frac": gbs / peaks["hbm_gbs"]}
+                               "GB_per_s": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
+                               "roofline": alu_roofline(int(q_off[-1]) / (ms / 1e3),
+                                                        ALU_MULS_STORED, alu)}
         del d_qids
         # batches of 1,024 query sketches against the collection
         cap = 1 << 16

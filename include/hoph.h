@@ -154,7 +154,12 @@ typedef struct {
     int32_t consumer_warps;  /* scoring warps per CTA (dense <= 15, join filter <= 31) */
     int32_t ctas_per_sm;     /* resident CTAs per SM for the scan         */
     int32_t stages;          /* TMA pipeline depth                        */
-    int32_t lanes_per_row;   /* join filter: lanes sharing one row (1-8)  */
+    int32_t lanes_per_row;   /* join filter: lanes sharing one row (1-8);
+                              * 32: a whole warp per row over a group map
+                              * striped across the banks by bin (one
+                              * scanned plane whose rows are 128, 256 or
+                              * 512 bytes, W <= 128; tile_rows then sets
+                              * the rows per tile)                       */
     int32_t sketch_cta_bits; /* sketch: sets whose size has at least this
                               * many bits get a whole CTA, the rest a warp;
                               * 0 = library choice, 64 = warps only      */
@@ -190,6 +195,23 @@ int hoph_plan_get_info(const hoph_plan *plan, hoph_plan_info *out);
 
 /* Set execution knobs (exec = NULL restores the defaults). */
 int hoph_plan_set_exec(hoph_plan *plan, const hoph_exec *exec);
+
+/*
+ * The small-probability limits of Definition 1 for X ~ Bin(k', T) (Table 2's
+ * two tails, Eq. 10-11), exactly: *U = min{j : P(X >= j) <= eps} and
+ * *L = max{j : P(X < j) <= eps}, j in 0..k'+1, with T = thr_num / thr_den
+ * and eps a double taken at its exact binary value.  The tails are compared
+ * with eps in integer arithmetic (td^k' P(X = i) is an integer), so an eps
+ * equal to a tail, or one ulp from it, is decided exactly.  These are the
+ * limits every plan's decisions use (hoph_plan_info.upper_limit /
+ * lower_limit).  Host only: no device, no allocation visible to the caller.
+ *   k_group   k', 1..65535; thr_num 1..thr_den; thr_den 1..65535;
+ *   epsilon   finite, >= 0.
+ * Returns HOPH_OK, or HOPH_ERR_PARAM for arguments out of range or a NULL
+ * output pointer (outputs untouched then).
+ */
+int hoph_small_probability_limits(uint32_t k_group, uint32_t thr_num, uint32_t thr_den,
+                                  double epsilon, int64_t *U, int64_t *L);
 
 /*
  * OPH / HOPH sketches of n_sets sets (Sec. 3.2 "One Permutation Hashing",
@@ -298,7 +320,9 @@ int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int
  *     the library, present on every GPU that loads it until the process
  *     exits.  The first call on each device looks up that array's device
  *     address (cudaGetSymbolAddress, with the device current); make that
- *     first call before any stream capture.
+ *     first call before any stream capture (during one it returns
+ *     HOPH_ERR_CAPTURE and enqueues nothing).  The address is kept for the
+ *     device's context: it is not valid after a cudaDeviceReset.
  *   - Every call on a device shares the one array: calls whose work overlaps
  *     on the GPU (other streams, other host threads) race and corrupt each
  *     other's work list.  Order such calls on one stream.
@@ -365,6 +389,22 @@ int hoph_check_bounded_wait(hoph_plan *plan, uint64_t limit_ns, void *stream);
  */
 int hoph_synth_sketch(hoph_plan *plan, uint64_t seed, uint64_t D, const int64_t *d_offsets,
                       int64_t n_sets, uint32_t *d_planes, void *stream);
+
+/*
+ * Integer-throughput probe (benchmark tooling; no paper counterpart): the
+ * measured peak that ALU-bound sketching (the hashed permutation's 61-bit
+ * arithmetic) is compared with.  A grid of (SMs x 8) CTAs of 256 threads;
+ * every thread runs `iters` rounds of 8 independent dependency chains of
+ * one operation:
+ *   kind 0: x = x * a + b, 32-bit (multiply-add);
+ *   kind 1: x = x * a + b, 64-bit (low half of a 64 x 64 product);
+ *   kind 2: x = mulhi(x, a) + b, 64-bit (high half of a 64 x 64 product).
+ * Operations per launch = 8 * iters * (SMs x 8 x 256).  d_sink (uint64,
+ * one per thread of the grid: SMs x 2048 entries) receives the chains'
+ * final values so no work is dropped.  iters in 1..2^24, kind in 0..2;
+ * HOPH_ERR_PARAM otherwise.  Asynchronous on `stream`.
+ */
+int hoph_int_probe(uint32_t kind, int64_t iters, uint64_t *d_sink, void *stream);
 
 /* Synchronise `stream`, then return and clear the plan's device status word
  * (HOPH_OK if no device-side error was recorded). */

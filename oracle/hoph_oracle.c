@@ -14,9 +14,10 @@
  *
  * Everything is plain loops over the definitions.  Decisions are taken on
  * exact integer fractions (__int128 cross-multiplication) and the binomial
- * tails are looked up at ceil(m), as Algorithm 1/2 read F(m); the tails
- * themselves are long double.  Work is split across POSIX threads by query
- * (comparison) or by set (sketching) only.
+ * tails are looked up at ceil(m), as Algorithm 1/2 read F(m); whether a tail
+ * is <= eps is decided exactly, on the integers td^k' P(X = i) (fixed-size
+ * multi-word arithmetic below).  Work is split across POSIX threads by
+ * query (comparison) or by set (sketching) only.
  */
 #include <math.h>
 #include <pthread.h>
@@ -274,6 +275,146 @@ int or_tails(uint32_t kg, uint32_t tn, uint32_t td, long double *low,
     return 0;
 }
 
+/* ----------------------------------------------------------------------- */
+/* Exact tail tests (Definition 1): is P(X >= m) <= eps, is P(X < m) <= eps */
+/* ----------------------------------------------------------------------- */
+
+/* Numbers are nl little-endian 32-bit words, large enough for every value
+ * below (no overflow check is needed beyond the size chosen in or_tail_ok). */
+static void w_set_small(uint32_t *a, int nl, uint32_t v) {
+    memset(a, 0, sizeof(uint32_t) * nl);
+    a[0] = v;
+}
+static void w_mul_small(uint32_t *a, int nl, uint32_t m) {
+    uint64_t carry = 0;
+    int i;
+    for (i = 0; i < nl; ++i) {
+        uint64_t v = (uint64_t)a[i] * m + carry;
+        a[i] = (uint32_t)v;
+        carry = v >> 32;
+    }
+}
+static void w_div_small(uint32_t *a, int nl, uint32_t d) {
+    uint64_t r = 0;
+    int i;
+    for (i = nl - 1; i >= 0; --i) {
+        uint64_t v = (r << 32) | a[i];
+        a[i] = (uint32_t)(v / d);
+        r = v % d;
+    }
+}
+static void w_add(uint32_t *a, const uint32_t *b, int nl) {
+    uint64_t carry = 0;
+    int i;
+    for (i = 0; i < nl; ++i) {
+        uint64_t v = (uint64_t)a[i] + b[i] + carry;
+        a[i] = (uint32_t)v;
+        carry = v >> 32;
+    }
+}
+static void w_shl(uint32_t *out, const uint32_t *a, int nl, int bits) {
+    int w = bits / 32, r = bits % 32, i;
+    memset(out, 0, sizeof(uint32_t) * nl);
+    for (i = 0; i + w < nl; ++i) {
+        out[i + w] |= a[i] << r;
+        if (r && i + w + 1 < nl) out[i + w + 1] |= a[i] >> (32 - r);
+    }
+}
+static int w_cmp(const uint32_t *a, const uint32_t *b, int nl) {
+    int i;
+    for (i = nl - 1; i >= 0; --i)
+        if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+    return 0;
+}
+
+/*
+ * up_ok[m] = [P(X >= m) <= eps], low_ok[m] = [P(X < m) <= eps], m = 0..kg+1,
+ * X ~ Bin(kg, tn/td).  With s = td - tn, A_i = C(kg, i) tn^i s^(kg-i) =
+ * td^kg P(X = i); eps = mant 2^e2 exactly (frexp), so a tail t <= eps is
+ * t td^kg 2^-e2 <= mant td^kg.  sum_i A_i = td^kg is checked against the
+ * power itself.  Returns 0, or -1 on bad arguments / a failed check.
+ */
+int or_tail_ok(uint32_t kg, uint32_t tn, uint32_t td, double eps, uint8_t *up_ok,
+               uint8_t *low_ok) {
+    int bits_td = 0, nl, fe = 0, e2, rc = 0;
+    uint32_t i, j, s;
+    uint64_t mant;
+    uint32_t *A, *tdk, *tmp, *rhs, *lhs, *up, *low;
+    if (td == 0 || tn == 0 || tn > td || kg == 0 || !(eps >= 0.0)) return -1;
+    s = td - tn;
+    while (bits_td < 32 && (1ull << bits_td) <= td) ++bits_td;
+    nl = (int)(((uint64_t)kg * bits_td + 64 + 1200) / 32 + 2);
+    A = (uint32_t *)calloc((size_t)(kg + 1) * nl, sizeof(uint32_t));
+    tdk = (uint32_t *)calloc(nl, sizeof(uint32_t));
+    tmp = (uint32_t *)calloc(nl, sizeof(uint32_t));
+    rhs = (uint32_t *)calloc(nl, sizeof(uint32_t));
+    lhs = (uint32_t *)calloc(nl, sizeof(uint32_t));
+    up = (uint32_t *)calloc((size_t)(kg + 2) * nl, sizeof(uint32_t));
+    low = (uint32_t *)calloc((size_t)(kg + 2) * nl, sizeof(uint32_t));
+    /* A_i = C(kg, i) tn^i s^(kg-i); C(kg, i) by C(kg, i-1) (kg-i+1) / i */
+    w_set_small(tmp, nl, 1);
+    for (i = 0; i <= kg; ++i) {
+        uint32_t *a = A + (size_t)i * nl;
+        if (i > 0) {
+            w_mul_small(tmp, nl, kg - i + 1);
+            w_div_small(tmp, nl, i);
+        }
+        memcpy(a, tmp, sizeof(uint32_t) * nl);
+        for (j = 0; j < i; ++j) w_mul_small(a, nl, tn);
+        for (j = 0; j < kg - i; ++j) w_mul_small(a, nl, s);
+    }
+    /* up[m] = sum_{i >= m} A_i, low[m] = sum_{i < m} A_i */
+    for (i = kg + 1; i-- > 0;) {
+        memcpy(up + (size_t)i * nl, up + (size_t)(i + 1) * nl, sizeof(uint32_t) * nl);
+        w_add(up + (size_t)i * nl, A + (size_t)i * nl, nl);
+    }
+    for (i = 1; i <= kg + 1; ++i) {
+        memcpy(low + (size_t)i * nl, low + (size_t)(i - 1) * nl, sizeof(uint32_t) * nl);
+        w_add(low + (size_t)i * nl, A + (size_t)(i - 1) * nl, nl);
+    }
+    w_set_small(tdk, nl, 1);
+    for (i = 0; i < kg; ++i) w_mul_small(tdk, nl, td);
+    if (w_cmp(tdk, up, nl) != 0 || w_cmp(tdk, low + (size_t)(kg + 1) * nl, nl) != 0) rc = -1;
+    /* rhs = mant td^kg, eps = mant 2^e2 */
+    mant = (uint64_t)ldexp(frexp(eps, &fe), 53);
+    e2 = fe - 53;
+    if (eps == 0.0) { mant = 0; e2 = 0; }
+    memcpy(rhs, tdk, sizeof(uint32_t) * nl);
+    w_mul_small(rhs, nl, (uint32_t)(mant >> 32));
+    w_shl(tmp, rhs, nl, 32);
+    memcpy(rhs, tdk, sizeof(uint32_t) * nl);
+    w_mul_small(rhs, nl, (uint32_t)mant);
+    w_add(rhs, tmp, nl);
+    if (e2 > 0) {
+        w_shl(tmp, rhs, nl, e2);
+        memcpy(rhs, tmp, sizeof(uint32_t) * nl);
+    }
+    for (i = 0; i <= kg + 1; ++i) {
+        w_shl(lhs, up + (size_t)i * nl, nl, e2 < 0 ? -e2 : 0);
+        up_ok[i] = (uint8_t)(w_cmp(lhs, rhs, nl) <= 0);
+        w_shl(lhs, low + (size_t)i * nl, nl, e2 < 0 ? -e2 : 0);
+        low_ok[i] = (uint8_t)(w_cmp(lhs, rhs, nl) <= 0);
+    }
+    free(A); free(tdk); free(tmp); free(rhs); free(lhs); free(up); free(low);
+    return rc;
+}
+
+/* U = min{j : P(X >= j) <= eps}, L = max{j : P(X < j) <= eps} (for tests) */
+int or_limits(uint32_t kg, uint32_t tn, uint32_t td, double eps, int64_t *U, int64_t *L) {
+    uint8_t *up_ok = (uint8_t *)malloc(kg + 2), *low_ok = (uint8_t *)malloc(kg + 2);
+    int64_t j;
+    int rc = or_tail_ok(kg, tn, td, eps, up_ok, low_ok);
+    if (rc == 0) {
+        *U = kg + 1;
+        for (j = (int64_t)kg + 1; j >= 0; --j) if (up_ok[j]) *U = j;
+        *L = 0;
+        for (j = 0; j <= (int64_t)kg + 1; ++j) if (low_ok[j]) *L = j;
+    }
+    free(up_ok);
+    free(low_ok);
+    return rc;
+}
+
 /* double-precision copy of the tails, for tests */
 int or_tails_double(uint32_t kg, uint32_t tn, uint32_t td, double *low, double *up) {
     long double *l = (long double *)malloc(sizeof(long double) * (kg + 2));
@@ -309,8 +450,7 @@ typedef struct {
 
 typedef struct {
     const or_query_params *p;
-    long double *low, *up;
-    long double eps;
+    uint8_t *low_ok, *up_ok; /* [kg+2]: P(X < m) <= eps, P(X >= m) <= eps */
     const uint32_t *qs, *rs;
     int64_t Q, N;
     int8_t *dec;
@@ -331,15 +471,18 @@ static int64_t floor_div128(i128 a, i128 b) { /* b > 0 */
 }
 static int64_t ceil_div128(i128 a, i128 b) { return -floor_div128(-a, b); }
 
-static long double tail_lower(const query_ctx *c, int64_t m) {
-    if (m <= 0) return 0.0L;
-    if (m > (int64_t)c->p->kg) return 1.0L;
-    return c->low[m];
+/* F(m) <= eps for the lower tail P(X < m) and the upper tail P(X >= m) at an
+ * integer m (= ceil of the real argument); outside 0..kg+1 the tails are the
+ * same as at the nearest end (0 below 0 / 1 above kg for the lower one). */
+static int lower_small(const query_ctx *c, int64_t m) {
+    if (m < 0) m = 0;
+    if (m > (int64_t)c->p->kg + 1) m = (int64_t)c->p->kg + 1;
+    return c->low_ok[m];
 }
-static long double tail_upper(const query_ctx *c, int64_t m) {
-    if (m <= 0) return 1.0L;
-    if (m > (int64_t)c->p->kg) return 0.0L;
-    return c->up[m];
+static int upper_small(const query_ctx *c, int64_t m) {
+    if (m < 0) m = 0;
+    if (m > (int64_t)c->p->kg + 1) m = (int64_t)c->p->kg + 1;
+    return c->up_ok[m];
 }
 
 static i128 gcd128(i128 a, i128 b) {
@@ -402,9 +545,9 @@ static int compare_pair(query_ctx *c, const uint32_t *s, const uint32_t *t,
             ceilm = ceil_div128(num, den);
             /* M_ra < M_a = T k' ?  num/den < tn kg / td */
             if (num * td < (i128)tn * kg * den) {
-                if (tail_lower(c, ceilm) <= c->eps) return OR_ACCEPT;
+                if (lower_small(c, ceilm)) return OR_ACCEPT;
             } else {
-                if (tail_upper(c, ceilm) <= c->eps) return OR_REJECT;
+                if (upper_small(c, ceilm)) return OR_REJECT;
             }
         }
         return OR_REJECT;
@@ -456,9 +599,9 @@ static int compare_pair(query_ctx *c, const uint32_t *s, const uint32_t *t,
             }
             ceilm = ceil_div128(num * kg, den);
             if (num * td < (i128)tn * den) { /* P_r < T */
-                if (tail_lower(c, (int64_t)ceilm) <= c->eps) return OR_ACCEPT;
+                if (lower_small(c, (int64_t)ceilm)) return OR_ACCEPT;
             } else {
-                if (tail_upper(c, (int64_t)ceilm) <= c->eps) return OR_REJECT;
+                if (upper_small(c, (int64_t)ceilm)) return OR_REJECT;
             }
         }
         return OR_REJECT;
@@ -511,7 +654,7 @@ int64_t or_query(const or_query_params *p, const uint32_t *qs, int64_t Q,
     query_ctx c;
     int t, nt;
     int64_t total = 0, i;
-    long double *low, *up;
+    uint8_t *low_ok, *up_ok;
     if (p->kg == 0 || p->k % p->kg) return -1;
     if (threads < 1) threads = 1;
     if (threads > 256) threads = 256;
@@ -519,10 +662,14 @@ int64_t or_query(const or_query_params *p, const uint32_t *qs, int64_t Q,
     memset(&c, 0, sizeof c);
     c.p = p;
     c.G = (p->mode == OR_GOPH || p->mode == OR_HOPH) ? p->k / p->kg : 1;
-    low = (long double *)malloc(sizeof(long double) * (p->kg + 2));
-    up = (long double *)malloc(sizeof(long double) * (p->kg + 2));
-    if (or_tails(p->kg, p->tn, p->td, low, up)) { free(low); free(up); return -1; }
-    c.low = low; c.up = up; c.eps = (long double)p->eps;
+    low_ok = (uint8_t *)malloc(p->kg + 2);
+    up_ok = (uint8_t *)malloc(p->kg + 2);
+    if (or_tail_ok(p->kg, p->tn, p->td, p->eps, up_ok, low_ok)) {
+        free(low_ok);
+        free(up_ok);
+        return -1;
+    }
+    c.low_ok = low_ok; c.up_ok = up_ok;
     c.qs = qs; c.rs = rs; c.Q = Q; c.N = N;
     c.dec = dec; c.groups = groups; c.msum = msum;
     c.acc = (int64_t **)calloc(nt, sizeof(int64_t *));
@@ -543,7 +690,7 @@ int64_t or_query(const or_query_params *p, const uint32_t *qs, int64_t Q,
         free(c.hist);
     }
     free(c.acc); free(c.acc_n); free(c.acc_cap);
-    free(low); free(up);
+    free(low_ok); free(up_ok);
     if (c.err) return -3;
     return total;
 }

@@ -10,8 +10,7 @@ Permutation Hashing: Efficient Multimedia Near Duplicate Detection",
 arXiv 1805.11254).  Section / equation / algorithm numbers below are the
 paper's.
 
-Readings taken where the paper is garbled or silent (each one is also listed
-with its reason in the design notes):
+Readings taken where the paper is garbled or silent:
 
 * near duplicate means Jaccard >= T (Sec. 3.1 prints "<", the rest of the
   paper tests ">=");
@@ -37,6 +36,7 @@ with its reason in the design notes):
 
 from bisect import bisect_right
 from fractions import Fraction
+from functools import lru_cache
 from math import comb
 
 EMPTY = 0xFFFFFFFF          # the empty-bin marker (the paper's circled-times)
@@ -249,12 +249,17 @@ def _ceil_fraction(f):
     return -((-f.numerator) // f.denominator)
 
 
+@lru_cache(maxsize=64)
+def _tails_cached(kg, T):
+    return BinomialTails(kg, T)
+
+
 def small_probability_limits(kg, T, eps):
     """U = min{j : P(X >= j) <= eps}, L = max{j : P(X < j) <= eps}.
 
     Not used by the decisions below (they evaluate the tails directly); kept
     so tests can compare against the library's precomputed limits."""
-    bt = BinomialTails(kg, T)
+    bt = _tails_cached(kg, Fraction(T))
     e = Fraction(eps)
     U = next(j for j in range(kg + 2) if bt.up[j] <= e)
     L = max(j for j in range(kg + 2) if bt.low[j] <= e)

@@ -57,6 +57,8 @@ def load():
         lib.or_minwise.restype = i32
         lib.or_tails_double.argtypes = [u32, u32, u32, P, P]
         lib.or_tails_double.restype = i32
+        lib.or_limits.argtypes = [u32, u32, u32, ctypes.c_double, P, P]
+        lib.or_limits.restype = i32
         lib.or_query.argtypes = [ctypes.POINTER(QueryParams), P, i64, P, i64, P, P, P, P, i64,
                                  P, i32]
         lib.or_query.restype = i64
@@ -134,6 +136,15 @@ def tails(kg, tn, td):
     if load().or_tails_double(kg, tn, td, _p(low), _p(up)):
         raise ValueError("bad T")
     return low, up
+
+
+def limits(kg, tn, td, eps):
+    """(U, L) from the oracle's exact tail tests (Definition 1)."""
+    U = ctypes.c_int64()
+    L = ctypes.c_int64()
+    if load().or_limits(kg, tn, td, float(eps), ctypes.byref(U), ctypes.byref(L)):
+        raise ValueError("bad tail parameters")
+    return U.value, L.value
 
 
 def query(mode, qs, rs, kg, tn, td, eps, rule="both", z=None, per_pair=False,

@@ -81,37 +81,164 @@ bool build_layout(const hoph_params &p, std::vector<uint64_t> &lo, uint64_t *z) 
     return true;
 }
 
-// X ~ Bin(k', T): U = min{j : P(X >= j) <= eps}, L = max{j : P(X < j) <= eps}
-// (Definition 1 with the two tails of Eq. 11).  The pmf comes from the
-// ratio recurrence p_{i+1} = p_i (k'-i)/(i+1) T/(1-T) in long double.
-void small_probability_limits(uint32_t kg, int64_t tn, int64_t td, double eps, int64_t *U,
+// Exact small-probability limits (Definition 1 with the two tails of
+// Eq. 11): X ~ Bin(k', T), U = min{j : P(X >= j) <= eps},
+// L = max{j : P(X < j) <= eps}.  With T = tn/td in lowest terms and
+// s = td - tn, A_i = C(k', i) tn^i s^(k'-i) = td^k' P(X = i) is an integer,
+// so "tail <= eps" is the integer comparison  sum A_i <= mant 2^e td^k'
+// with eps = mant 2^e exactly (mant < 2^53).  Non-negative integers are
+// little-endian vectors of 32-bit limbs.
+namespace big {
+typedef std::vector<uint32_t> Num;
+
+void trim(Num &a) {
+    while (!a.empty() && a.back() == 0) a.pop_back();
+}
+void mul_small(Num &a, uint32_t m) {
+    if (m == 0) {
+        a.clear();
+        return;
+    }
+    uint64_t carry = 0;
+    for (uint32_t &l : a) {
+        const uint64_t v = (uint64_t)l * m + carry;
+        l = (uint32_t)v;
+        carry = v >> 32;
+    }
+    if (carry) a.push_back((uint32_t)carry);
+}
+// a /= d; the callers only divide where the quotient is exact
+void div_small(Num &a, uint32_t d) {
+    uint64_t r = 0;
+    for (size_t i = a.size(); i-- > 0;) {
+        const uint64_t v = (r << 32) | a[i];
+        a[i] = (uint32_t)(v / d);
+        r = v % d;
+    }
+    trim(a);
+}
+void add(Num &a, const Num &b) {
+    if (a.size() < b.size()) a.resize(b.size(), 0);
+    uint64_t carry = 0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        const uint64_t v = (uint64_t)a[i] + (i < b.size() ? b[i] : 0u) + carry;
+        a[i] = (uint32_t)v;
+        carry = v >> 32;
+    }
+    if (carry) a.push_back((uint32_t)carry);
+}
+Num shl(const Num &a, uint32_t bits) {
+    if (a.empty()) return a;
+    const uint32_t w = bits / 32, r = bits % 32;
+    Num out(a.size() + w + 1, 0);
+    for (size_t i = 0; i < a.size(); ++i) {
+        out[i + w] |= a[i] << r;
+        if (r) out[i + w + 1] |= a[i] >> (32 - r);
+    }
+    trim(out);
+    return out;
+}
+int cmp(const Num &a, const Num &b) {  // both trimmed
+    if (a.size() != b.size()) return a.size() < b.size() ? -1 : 1;
+    for (size_t i = a.size(); i-- > 0;)
+        if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+    return 0;
+}
+Num pow_small(uint32_t base, uint32_t e) {
+    Num a{1};
+    for (uint32_t i = 0; i < e; ++i) mul_small(a, base);
+    trim(a);
+    return a;
+}
+}  // namespace big
+
+// x <= eps * td^k' with eps = mant 2^e2, given rhs = mant td^k'
+struct EpsBound {
+    big::Num rhs;
+    int e2 = 0;
+    bool le(const big::Num &x) const {
+        if (e2 >= 0) return big::cmp(x, big::shl(rhs, (uint32_t)e2)) <= 0;
+        return big::cmp(big::shl(x, (uint32_t)(-e2)), rhs) <= 0;
+    }
+};
+
+uint32_t gcd32(uint32_t a, uint32_t b) {
+    while (b) {
+        const uint32_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+void small_probability_limits(uint32_t kg, int64_t tn64, int64_t td64, double eps, int64_t *U,
                               int64_t *L, int32_t *always) {
     *always = eps >= 1.0;
-    std::vector<long double> pmf(kg + 1, 0.0L);
-    if (tn == td) {
-        pmf[kg] = 1.0L;
-    } else {
-        const long double T = (long double)tn / (long double)td;
-        const long double ratio = T / (1.0L - T);
-        long double v = powl(1.0L - T, (long double)kg);
-        for (uint32_t i = 0; i <= kg; ++i) {
-            pmf[i] = v;
-            v = v * (long double)(kg - i) / (long double)(i + 1) * ratio;
-        }
+    const uint32_t g = gcd32((uint32_t)tn64, (uint32_t)td64);
+    const uint32_t tn = (uint32_t)tn64 / g, td = (uint32_t)td64 / g, s = td - tn;
+    if (s == 0) {  // T = 1: X = k' always
+        *U = eps >= 1.0 ? 0 : (int64_t)kg + 1;
+        *L = eps >= 1.0 ? (int64_t)kg + 1 : (int64_t)kg;
+        return;
     }
-    // upper(j) = sum_{i >= j} pmf_i, lower(j) = sum_{i < j} pmf_i
-    std::vector<long double> upper(kg + 2, 0.0L), lower(kg + 2, 0.0L);
-    for (int j = (int)kg; j >= 0; --j) upper[j] = upper[j + 1] + pmf[j];
-    for (uint32_t j = 1; j <= kg + 1; ++j) lower[j] = lower[j - 1] + pmf[j - 1];
-    const long double e = (long double)eps;
-    int64_t u = kg + 1;
-    for (uint32_t j = 0; j <= kg + 1; ++j)
-        if (upper[j] <= e) { u = j; break; }
-    int64_t l = 0;
-    for (uint32_t j = 0; j <= kg + 1; ++j)
-        if (lower[j] <= e) l = j;
-    *U = u;
-    *L = l;
+    EpsBound bound;
+    if (eps > 0.0) {
+        int e = 0;
+        const double f = frexp(eps, &e);  // eps = f 2^e, f in [0.5, 1)
+        uint64_t mant = (uint64_t)ldexp(f, 53);
+        bound.e2 = e - 53;
+        while (!(mant & 1)) {
+            mant >>= 1;
+            ++bound.e2;
+        }
+        // rhs = mant td^k'
+        big::Num t = big::pow_small(td, kg), lo_part = t;
+        big::mul_small(lo_part, (uint32_t)mant);
+        big::Num hi_part = t;
+        big::mul_small(hi_part, (uint32_t)(mant >> 32));
+        hi_part = big::shl(hi_part, 32);
+        big::add(lo_part, hi_part);
+        big::trim(lo_part);
+        bound.rhs = lo_part;
+    }  // eps = 0: rhs stays 0, only a zero tail qualifies
+    // U: upper tails from the top, A_k' = tn^k', A_{i-1} = A_i i s / ((k'-i+1) tn);
+    // {j : P(X >= j) <= eps} is [U, k'+1]
+    {
+        big::Num A = big::pow_small(tn, kg), up;
+        int64_t u = 0;
+        for (int64_t j = kg; j >= 0; --j) {
+            big::add(up, A);
+            big::trim(up);
+            if (!bound.le(up)) {
+                u = j + 1;
+                break;
+            }
+            if (j > 0) {
+                big::mul_small(A, (uint32_t)j * s);
+                big::div_small(A, (uint32_t)(kg - j + 1) * tn);
+            }
+        }
+        *U = u;
+    }
+    // L: lower tails from the bottom, A_0 = s^k', A_{i+1} = A_i (k'-i) tn / ((i+1) s);
+    // {j : P(X < j) <= eps} is [0, L]
+    {
+        big::Num A = big::pow_small(s, kg), low;
+        int64_t l = (int64_t)kg + 1;
+        for (int64_t j = 1; j <= (int64_t)kg + 1; ++j) {
+            big::add(low, A);  // low = P(X < j) td^k'
+            big::trim(low);
+            if (!bound.le(low)) {
+                l = j - 1;
+                break;
+            }
+            if (j <= (int64_t)kg) {
+                big::mul_small(A, (uint32_t)(kg - j + 1) * tn);
+                big::div_small(A, (uint32_t)j * s);
+            }
+        }
+        *L = l;
+    }
 }
 
 // The literal recursion's integers (hoph_decide) stay below 2^120 for every
@@ -448,6 +575,16 @@ int hoph_plan_create(const hoph_params *params, hoph_plan **out) {
     return plan_create(params, nullptr, out);
 }
 
+int hoph_small_probability_limits(uint32_t k_group, uint32_t thr_num, uint32_t thr_den,
+                                  double epsilon, int64_t *U, int64_t *L) {
+    if (!U || !L || k_group == 0 || k_group > 65535 || thr_den == 0 || thr_den > 65535 ||
+        thr_num == 0 || thr_num > thr_den || !(epsilon >= 0.0) || !isfinite(epsilon))
+        return HOPH_ERR_PARAM;
+    int32_t always = 0;
+    small_probability_limits(k_group, thr_num, thr_den, epsilon, U, L, &always);
+    return HOPH_OK;
+}
+
 int hoph_plan_create_with_perm(const hoph_params *params, const uint32_t *host_perm,
                                hoph_plan **out) {
     if (!host_perm) return HOPH_ERR_PARAM;
@@ -483,7 +620,7 @@ int hoph_plan_set_exec(hoph_plan *plan, const hoph_exec *exec) {
         exec->tile_rows > 256 || exec->consumer_warps < 0 || exec->consumer_warps > 31 ||
         exec->ctas_per_sm < 0 || exec->ctas_per_sm > 8 || exec->stages < 0 || exec->stages > 8 ||
         (exec->lanes_per_row != 0 && exec->lanes_per_row != 1 && exec->lanes_per_row != 2 &&
-         exec->lanes_per_row != 4 && exec->lanes_per_row != 8) ||
+         exec->lanes_per_row != 4 && exec->lanes_per_row != 8 && exec->lanes_per_row != 32) ||
         exec->sketch_cta_bits < 0 || exec->sketch_cta_bits > 64 || exec->join_lanes < 0 ||
         exec->join_lanes > hoph_plan::kMaxLanes)
         return HOPH_ERR_PARAM;

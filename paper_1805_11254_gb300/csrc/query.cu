@@ -503,6 +503,8 @@ struct IndexArgs {
     uint32_t *gmap;      // per 16 map slots: an even / an odd query has slot j (bits j, 16 + j; swapped in odd words)
     int32_t map_hashed;  // map slot = map_slot(key, map_shift), else the key itself
     uint32_t map_shift;
+    int32_t striped;     // striped map (filter_striped_kernel), else by key
+    uint32_t nwb;        // striped map: words per (bin, lane) stack
     int32_t keys_hashed;  // key slot from the key table, else the key itself
     unsigned long long *tkey;
     uint32_t tmask;
@@ -511,6 +513,18 @@ struct IndexArgs {
     int32_t *allempty;
     uint32_t *n_allempty;
 };
+
+// Striped group map: a warp reads a row of W scanned values as 32-bit words,
+// lane l taking words l, l + 32, ...; a bin is filed in the bank (word
+// column) of the lane that reads it, and the bins of one lane are stacked.
+template <typename E>
+__host__ __device__ __forceinline__ uint32_t striped_lane(uint32_t w) {
+    return sizeof(E) == 4 ? (w & 31u) : ((w >> 1) & 31u);
+}
+template <typename E>
+__host__ __device__ __forceinline__ uint32_t striped_stack(uint32_t w) {
+    return sizeof(E) == 4 ? (w >> 5) : (((w >> 6) << 1) | (w & 1u));
+}
 
 // A join batch's state reset in one launch: list heads to kNil, the group
 // map and the call's counters to zero (out_count: null when the output
@@ -554,12 +568,25 @@ __global__ void join_count_kernel(const IndexArgs a) {
         if (lane == 0) a.q_emask[q * a.mask_words + c] = em;
         if (valid && !e) {
             const uint32_t key = (uint32_t)a.binbase[w] + v;
-            const uint32_t mi = a.map_hashed ? map_slot(key, a.map_shift) : key;
-            // slot j of word mi >> 4: even-query bit at j and odd-query bit at
-            // 16 + j, the halves swapped in odd words, so a right rotation of
-            // the word by (mi & 31) brings the even bit to 0 and the odd to 16
-            const uint32_t word = mi >> 4;
-            atomicOr(a.gmap + word, 1u << ((mi & 15u) + ((((uint32_t)q ^ word) & 1u) << 4)));
+            if (a.striped) {
+                // bin w lives in the bank of the lane that reads it (striped_lane),
+                // in that lane's stack striped_stack; slot u = v + 1 (0 is the
+                // empty bins' guard), word u >> 4 of the stack, the two group
+                // bits as below with the halves swapped in odd words
+                const uint32_t u = v + 1u;
+                const uint32_t word =
+                    (striped_stack<E>(w) * a.nwb + (u >> 4)) * 32u + striped_lane<E>(w);
+                atomicOr(a.gmap + word,
+                         1u << ((u & 15u) + ((((uint32_t)q ^ (u >> 4)) & 1u) << 4)));
+            } else {
+                const uint32_t mi = a.map_hashed ? map_slot(key, a.map_shift) : key;
+                // slot j of word mi >> 4: even-query bit at j and odd-query bit at
+                // 16 + j, the halves swapped in odd words, so a right rotation of
+                // the word by (mi & 31) brings the even bit to 0 and the odd to 16
+                const uint32_t word = mi >> 4;
+                atomicOr(a.gmap + word,
+                         1u << ((mi & 15u) + ((((uint32_t)q ^ word) & 1u) << 4)));
+            }
             const uint32_t slot = a.keys_hashed ? table_insert(a.tkey, a.tmask, key) : key;
             if (slot == kNoSlot) {
                 hoph_flag(a.status, HOPH_ERR_CAPACITY);
@@ -586,6 +613,7 @@ struct FilterArgs {
                               // zero-padded to a multiple of 4 words)
     uint32_t gmap_words;      // the last word is zero: empty bins look up its slot 0
     uint32_t map_shift;       // hashed map: slot = map_slot(key, map_shift)
+    uint32_t nwb;             // striped map: words per (bin, lane) stack
     const uint64_t *binbase;  // key = lo[w] + value
     const uint16_t *row_min;  // [W + 1]
     int32_t keep_empty;       // rows without a non-empty scanned bin are candidates
@@ -747,6 +775,133 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
             base = __shfl_sync(0xFFFFFFFFu, base, 0);
             if (pass) a.cand[base + __popc(pm & ((1u << lane) - 1u))] = (uint32_t)row;
         }
+        if (++s == a.stages) {
+            s = 0;
+            ph ^= 1u;
+        }
+    }
+}
+
+// Join filter over a striped group map (lanes over bins): a warp takes one
+// row at a time, lane l reading 32-bit words l, l + 32, ... of it (NW words,
+// 4 / sizeof(E) values each), so the 32 lanes look up 32 different banks of
+// the map and every lookup is one shared-memory wavefront.  Per lane the
+// values' hits and non-empty bins are packed (even-group hits in bits 0-7,
+// non-empty bins 8-15, odd-group hits 16-23; W <= 128 keeps each below 256)
+// and one warp reduction gives the row's totals.  Tiles come through an
+// unswizzled 4-D box {v, k'/v, rows, 1}: row r's values are contiguous.
+constexpr int kStripedRows = 4;  // rows a warp of the striped filter handles at once
+
+template <typename E, int NW>
+__global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_constant__ FilterArgs a,
+                                                               const __grid_constant__ CUtensorMap map) {
+    constexpr int RPI = kStripedRows;
+    constexpr int VPW = 4 / (int)sizeof(E);  // values per 32-bit word
+    constexpr int NS = NW * VPW;             // values (map stacks) per lane
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const FilterSmem L = filter_smem(a);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
+    uint64_t *empty = full + 8;
+    volatile int32_t *abort_flag = reinterpret_cast<volatile int32_t *>(smem + L.abort_flag);
+    uint16_t *s_rmin = reinterpret_cast<uint16_t *>(smem + L.row_min);
+    const unsigned char *s_gmap = smem + L.gmap;
+    unsigned char *stages = smem + L.stages;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int R = a.tile_rows;
+    for (int i = tid; i <= a.W; i += blockDim.x) s_rmin[i] = a.row_min[i];
+    if (tid == 0) {
+        *abort_flag = 0;
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, a.n_cons);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == a.n_cons) {
+        if (lane == 0)
+            produce_tiles(&map, stages, full, empty, abort_flag, a.stages, a.stage_bytes,
+                          a.stage_stride, a.n_tiles, R, a.status, true, kFilterPrefetch);
+        return;
+    }
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.gmap);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem + L.gmap);
+        const uint32_t n4 = (a.gmap_words + 3) / 4;
+        const uint32_t nt = (uint32_t)a.n_cons * 32;
+#pragma unroll 4
+        for (uint32_t i = tid; i < n4; i += nt) dst[i] = __ldg(src + i);
+        named_bar_sync(1, nt);
+    }
+    // byte offset of (stack s, word row 0) in this lane's bank
+    uint32_t sbase[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) sbase[s] = ((uint32_t)s * a.nwb * 32u + (uint32_t)lane) * 4u;
+    const uint32_t row_words = (uint32_t)a.W * sizeof(E) / 4;
+
+    int s = 0;
+    uint32_t ph = 0;
+    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        if (!mbar_wait_bounded(full + s, ph, abort_flag)) {
+            hoph_flag(a.status, HOPH_ERR_TIMEOUT);
+            *abort_flag = 1;
+            break;
+        }
+        const uint32_t *tw = reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride);
+        const int64_t row0 = tile * R;
+        const int rows = (int)(a.n_rows - row0 < (int64_t)R ? a.n_rows - row0 : (int64_t)R);
+        // RPI rows of the tile at a time per warp (R is a multiple of RPI), their
+        // loads, lookups and reductions interleaved; rows past the collection's
+        // end (a ragged last tile) are looked up but never kept
+        for (int r0 = warp * RPI; r0 < rows; r0 += a.n_cons * RPI) {
+            uint32_t acc[RPI];
+#pragma unroll
+            for (int j = 0; j < RPI; ++j) acc[j] = 0u;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) {
+                uint32_t word[RPI];
+#pragma unroll
+                for (int j = 0; j < RPI; ++j) word[j] = tw[(uint32_t)(r0 + j) * row_words + lane + 32 * i];
+#pragma unroll
+                for (int h = 0; h < VPW; ++h) {
+                    uint32_t mw[RPI], u[RPI];
+#pragma unroll
+                    for (int j = 0; j < RPI; ++j) {
+                        if constexpr (VPW == 1) {
+                            u[j] = word[j] + 1u;  // the empty marker wraps to slot 0
+                        } else {
+                            u[j] = ((h ? (word[j] >> 16) : word[j]) + 1u) & 0xFFFFu;
+                        }
+                        mw[j] = *reinterpret_cast<const uint32_t *>(s_gmap + sbase[i * VPW + h] +
+                                                                   ((u[j] >> 4) << 7));
+                    }
+#pragma unroll
+                    for (int j = 0; j < RPI; ++j)
+                        acc[j] += (__funnelshift_r(mw[j], mw[j], u[j]) & 0x10001u) +
+                                  (u[j] != 0u ? 0x100u : 0u);
+                }
+            }
+            uint32_t passmask = 0;
+#pragma unroll
+            for (int j = 0; j < RPI; ++j) {
+                const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, acc[j]);
+                const uint32_t ne = (tot >> 8) & 0xFFu;
+                const int hh = (int)max(tot & 0xFFu, (tot >> 16) & 0xFFu);
+                const bool pass = ne == 0 ? (a.keep_empty != 0) : (hh >= (int)s_rmin[ne]);
+                if (pass && r0 + j < rows) passmask |= 1u << j;
+            }
+            if (passmask && lane == 0) {
+                const unsigned long long at =
+                    atomicAdd(a.n_cand, (unsigned long long)__popc(passmask));
+                int o = 0;
+                for (int j = 0; j < RPI; ++j)
+                    if (passmask >> j & 1u) a.cand[at + o++] = (uint32_t)(row0 + r0 + j);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + s);
         if (++s == a.stages) {
             s = 0;
             ph ^= 1u;
@@ -1128,6 +1283,92 @@ __global__ void __launch_bounds__(kSortThreads) sort_pairs_kernel(
     }
 }
 
+// Outputs larger than kSortOneCta records of capacity are sorted by many CTAs
+// in a launch sequence (the count is known only on the device, so the host
+// launches the passes a full buffer needs and those past the count return at
+// once): sort_runs_kernel sorts runs of kSortSmem records in shared memory,
+// CTAs striding over the runs; one merge_pass_kernel per doubling of the run
+// length merges pairs of sorted runs, every record placed by its rank in the
+// other run; sort_finish_kernel writes the result (in bufA or bufB, by the
+// parity of the passes that did work) back as hoph_pair records and folds the
+// statistics.
+constexpr int64_t kSortOneCta = 1 << 16;
+
+__device__ __forceinline__ hoph_pair unpack_pair(const ulonglong2 r) {
+    hoph_pair p;
+    p.query = (uint32_t)(r.x >> 40);
+    p.row = (int64_t)(r.x & ((1ull << 40) - 1));
+    p.groups = (uint16_t)(r.y >> 16);
+    p.matches = (uint16_t)(r.y & 0xFFFFu);
+    return p;
+}
+
+__global__ void __launch_bounds__(kSortThreads) sort_runs_kernel(const hoph_pair *out,
+                                                                 const unsigned long long *count,
+                                                                 int64_t cap, ulonglong2 *bufA) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    ulonglong2 *sv = reinterpret_cast<ulonglong2 *>(smem);
+    const int64_t n = (int64_t)min(*count, (unsigned long long)cap);
+    for (int64_t base = (int64_t)blockIdx.x * kSortSmem; base < n;
+         base += (int64_t)gridDim.x * kSortSmem) {
+        const int cnt = (int)min((long long)kSortSmem, (long long)(n - base));
+        int m = 1;
+        while (m < cnt) m <<= 1;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            if (i < cnt) {
+                const hoph_pair p = out[base + i];
+                sv[i] = make_ulonglong2(pair_key(p),
+                                        ((unsigned long long)p.groups << 16) | p.matches);
+            } else {
+                sv[i] = make_ulonglong2(~0ull, 0ull);
+            }
+        }
+        __syncthreads();
+        bitonic_smem(sv, m);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) bufA[base + i] = sv[i];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) merge_pass_kernel(const ulonglong2 *src, ulonglong2 *dst,
+                                                         const unsigned long long *count,
+                                                         int64_t cap, int64_t run) {
+    const int64_t n = (int64_t)min(*count, (unsigned long long)cap);
+    if (run >= n) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pairbase = (i / (2 * run)) * (2 * run);
+        const int64_t a0 = pairbase, a1 = min(pairbase + run, n);
+        const int64_t b0 = a1, b1 = min(pairbase + 2 * run, n);
+        const ulonglong2 v = src[i];
+        int64_t pos;
+        if (i < a1)
+            pos = pairbase + (i - a0) + lower_bound_key(src + b0, b1 - b0, v.x);
+        else
+            pos = pairbase + (i - b0) + lower_bound_key(src + a0, a1 - a0, v.x);
+        dst[pos] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) sort_finish_kernel(hoph_pair *out,
+                                                          const unsigned long long *count,
+                                                          int64_t cap, const ulonglong2 *bufA,
+                                                          const ulonglong2 *bufB, int32_t *status,
+                                                          const StatsFold f) {
+    const unsigned long long total = *count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        stats_fold(f);
+        if (total > (unsigned long long)cap) hoph_flag(status, HOPH_ERR_CAPACITY);
+    }
+    const int64_t n = (int64_t)min(total, (unsigned long long)cap);
+    if (n <= 1) return;
+    int passes = 0;
+    for (int64_t run = kSortSmem; run < n; run <<= 1) ++passes;
+    const ulonglong2 *src = (passes & 1) ? bufB : bufA;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = unpack_pair(src[i]);
+}
 
 // ===========================================================================
 // Per-pair counts (no early exit): warp per pair, lanes over bins
@@ -1227,7 +1468,7 @@ bool encode_planes_map(CUtensorMap *map, const void *planes, int esize, int kg, 
 // {v, k'/v, R, Gs} with v = 128 / esize values per 128-byte line, 128-byte
 // swizzle (needs k' % v == 0)
 bool encode_swizzled_map(CUtensorMap *map, const void *planes, int esize, int kg, int64_t n_rows,
-                         int Gs, int64_t cstride, int R) {
+                         int Gs, int64_t cstride, int R, bool swizzle = true) {
     EncodeTiledFn fn = get_encode_fn();
     if (!fn) return false;
     const int v = 128 / esize;
@@ -1237,8 +1478,25 @@ bool encode_swizzled_map(CUtensorMap *map, const void *planes, int esize, int kg
     const cuuint32_t box[4] = {(cuuint32_t)v, (cuuint32_t)(kg / v), (cuuint32_t)R, (cuuint32_t)Gs};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(map, map_type(esize), 4, (void *)planes, gdim, gstride, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE,
+              swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename E, int NW>
+int launch_striped(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem, int num_sms,
+                   int ctas_per_sm, cudaStream_t s) {
+    auto kern = filter_striped_kernel<E, NW>;
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)kern, (int)smem));
+    const int threads = 32 * (fa.n_cons + 1);
+    int per_sm = 0;
+    HOPH_CUDA_TRY(hoph_occupancy(&per_sm, (const void *)kern, threads, smem));
+    if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+    const int64_t grid = std::min<int64_t>(fa.n_tiles, (int64_t)num_sms * per_sm);
+    kern<<<(unsigned)grid, threads, smem, s>>>(fa, map);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    return HOPH_OK;
 }
 
 template <int NPER, bool HASHED, int MAXC, typename E>
@@ -1300,6 +1558,34 @@ bool build_table(const DecideParams &dp, int W, int l, std::vector<uint16_t> &ta
         tab[2 * (W + 1) + n] = (uint16_t)best;
     }
     return true;
+}
+
+// Sort the output by (query, row) and fold the call's statistics: one CTA up
+// to kSortOneCta records of capacity, the multi-CTA sequence beyond.
+int launch_output_sort(hoph_plan *plan, hoph_pair *d_out, const unsigned long long *count,
+                       int64_t cap, ulonglong2 *sortA, ulonglong2 *sortB, const StatsFold &sf,
+                       cudaStream_t s, int64_t *launches) {
+    if (cap <= kSortOneCta) {
+        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
+        sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(d_out, count, cap, sortA,
+                                                                  sortB, plan->d_status, sf);
+        HOPH_CUDA_TRY(cudaGetLastError());
+        *launches = 1;
+        return HOPH_OK;
+    }
+    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_runs_kernel, kSortSmem * 16));
+    const int64_t runs = (cap + kSortSmem - 1) / kSortSmem;
+    sort_runs_kernel<<<(unsigned)std::min<int64_t>(runs, plan->num_sms), kSortThreads,
+                       kSortSmem * 16, s>>>(d_out, count, cap, sortA);
+    int passes = 0;
+    for (int64_t run = kSortSmem; run < cap; run <<= 1, ++passes)
+        merge_pass_kernel<<<(unsigned)plan->num_sms * 8, 256, 0, s>>>(
+            passes & 1 ? sortB : sortA, passes & 1 ? sortA : sortB, count, cap, run);
+    sort_finish_kernel<<<(unsigned)plan->num_sms * 4, 256, 0, s>>>(d_out, count, cap, sortA,
+                                                                    sortB, plan->d_status, sf);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    *launches = passes + 2;
+    return HOPH_OK;
 }
 
 struct Bump {
@@ -1428,9 +1714,27 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     if (strategy == 1 && !join_ok) return HOPH_ERR_UNSUPPORTED;
     if (strategy < 0) strategy = (join_ok && n_queries >= 16) ? 1 : 0;
 
+    // The striped map (lanes over bins, filter_striped_kernel): one plane,
+    // rows of whole 128-byte lines, W <= 128, a direct map of W stacks of
+    // nwb words (slot 0 of each the empty guard) that fits next to two
+    // stages of 64 rows.  lanes_per_row = 32 asks for it.
+    uint32_t nwb = 0;
+    const int lane_words = W * ES / 128;  // 32-bit words of a row per lane
+    if (Gs == 1 && (W * ES) % 128 == 0 && W <= 128 && !map_hashed &&
+        (lane_words == 1 || lane_words == 2 || lane_words == 4)) {
+        uint64_t maxw = 0;
+        for (int w = 0; w < W; ++w) maxw = std::max<uint64_t>(maxw, plan->lo[w + 1] - plan->lo[w]);
+        nwb = (uint32_t)((maxw + 1 + 15) / 16);
+    }
+    const bool striped_ok = nwb > 0 && (uint64_t)W * nwb * 4 + 2ull * 64 * W * ES + 8 * W +
+                                           4096 <= (uint64_t)kSmemLimit;
+    const bool striped = strategy == 1 && plan->exec.lanes_per_row == 32;
+    if (striped && !striped_ok) return HOPH_ERR_UNSUPPORTED;
+
     const int mask_words = (W + 31) / 32;
     // group map words (+ the zero word), padded for the filter's 16-byte copy
-    const uint64_t gmap_alloc = (map_slots / 16 + 2 + 3) & ~3ull;
+    const uint64_t gmap_words_used = striped ? (uint64_t)W * nwb : map_slots / 16 + 2;
+    const uint64_t gmap_alloc = (gmap_words_used + 3) & ~3ull;
     int wshift = 0;  // bits of a scanned-bin index (join index entries)
     while ((1 << wshift) < W) ++wshift;
     const int64_t qstride = qstride_in >= 0 ? qstride_in : n_queries * (int64_t)kg;
@@ -1530,6 +1834,8 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         ia.gmap = gmap;
         ia.map_hashed = map_hashed;
         ia.map_shift = map_shift;
+        ia.striped = striped ? 1 : 0;
+        ia.nwb = nwb;
         ia.keys_hashed = keys_hashed;
         ia.tkey = tkey;
         ia.tmask = (uint32_t)(head_slots - 1);
@@ -1553,8 +1859,9 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         fa.Gs = Gs;
         fa.W = W;
         fa.gmap = gmap;
-        fa.gmap_words = (uint32_t)(map_slots / 16 + 2);  // + a zero word for empty bins
+        fa.gmap_words = (uint32_t)gmap_words_used;  // direct / hashed: + a zero word
         fa.map_shift = map_shift;
+        fa.nwb = nwb;
         fa.binbase = binbase;
         fa.row_min = pa.thr + 2 * (W + 1);
         const int K0 = hoph_effective(fp.rule, W, W, 0);
@@ -1562,42 +1869,56 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         fa.cand = cand;
         fa.n_cand = n_cand;
         fa.status = plan->d_status;
-        // shape: bins per lane (32 or 16), consumer warps and stages that fit
-        // next to the group map, at least two stages
-        int lpr = plan->exec.lanes_per_row > 0 ? plan->exec.lanes_per_row : std::max(1, W / 32);
+        // shape: bins per lane (32 or 16; the striped kernel: lanes over a
+        // row's bins, tile_rows rows per tile), consumer warps and stages that
+        // fit next to the group map, at least two stages
+        int lpr = striped ? 32
+                          : (plan->exec.lanes_per_row > 0 ? plan->exec.lanes_per_row
+                                                          : std::max(1, W / 32));
         const int nper = W / lpr;
-        if (W % lpr || (nper != 32 && nper != 16) || lpr > 32) return HOPH_ERR_UNSUPPORTED;
+        if (!striped && (W % lpr || (nper != 32 && nper != 16) || lpr > 32))
+            return HOPH_ERR_UNSUPPORTED;
         const uint32_t fixed = 16 * 8 + 16 + align_up((W + 1) * 2, 16) +
                                align_up(fa.gmap_words * 4, 1024) + 1024;
         int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 16;
+        if (striped) n_cons = std::min(n_cons, 16);
         int stages = plan->exec.stages > 0 ? plan->exec.stages : 3;
-        auto stage_of = [&](int nc) { return align_up((uint32_t)(32 / lpr * nc) * W * ES, 1024); };
+        int srows = plan->exec.tile_rows > 0 ? plan->exec.tile_rows : 256;
+        if (striped) srows = std::max(kStripedRows, srows / kStripedRows * kStripedRows);
+        auto rows_of = [&](int nc) { return striped ? srows : 32 / lpr * nc; };
+        auto stage_of = [&](int nc) { return align_up((uint32_t)rows_of(nc) * W * ES, 1024); };
         while (n_cons > 1 && (fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit ||
-                              32 / lpr * n_cons > 256)) {
-            if (stages > 2) --stages; else --n_cons;
+                              rows_of(n_cons) > 256)) {
+            if (stages > 2) --stages;
+            else if (striped && srows > 64) srows /= 2;
+            else --n_cons;
         }
         if (fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit)
             return HOPH_ERR_UNSUPPORTED;
         fa.lanes_per_row = lpr;
         fa.n_cons = n_cons;
-        fa.tile_rows = 32 / lpr * n_cons;
+        fa.tile_rows = rows_of(n_cons);
         fa.stages = stages;
         fa.n_tiles = (n_rows + fa.tile_rows - 1) / fa.tile_rows;
         fa.stage_bytes = (uint32_t)fa.tile_rows * W * ES;
         fa.stage_stride = align_up(fa.stage_bytes, 1024);
         CUtensorMap map;
         memset(&map, 0, sizeof map);
-        if (!encode_swizzled_map(&map, d_coll_planes, ES, kg, n_rows, Gs, cstride, fa.tile_rows))
+        if (!encode_swizzled_map(&map, d_coll_planes, ES, kg, n_rows, Gs, cstride, fa.tile_rows,
+                                 !striped))
             return HOPH_ERR_UNSUPPORTED;
         const FilterSmem FL = filter_smem(fa);
         hoph_timing_mark(plan, 1, s);
         const int cps = plan->exec.ctas_per_sm;
         const int nsm = plan->num_sms;
         const int frc =
-            nper == 32 ? (map_hashed ? launch_filter<32, true, E>(fa, map, FL.total, nsm, cps, s)
-                                     : launch_filter<32, false, E>(fa, map, FL.total, nsm, cps, s))
-                       : (map_hashed ? launch_filter<16, true, E>(fa, map, FL.total, nsm, cps, s)
-                                     : launch_filter<16, false, E>(fa, map, FL.total, nsm, cps, s));
+            striped ? (lane_words == 1   ? launch_striped<E, 1>(fa, map, FL.total, nsm, cps, s)
+                       : lane_words == 2 ? launch_striped<E, 2>(fa, map, FL.total, nsm, cps, s)
+                                         : launch_striped<E, 4>(fa, map, FL.total, nsm, cps, s))
+            : nper == 32 ? (map_hashed ? launch_filter<32, true, E>(fa, map, FL.total, nsm, cps, s)
+                                       : launch_filter<32, false, E>(fa, map, FL.total, nsm, cps, s))
+                         : (map_hashed ? launch_filter<16, true, E>(fa, map, FL.total, nsm, cps, s)
+                                       : launch_filter<16, false, E>(fa, map, FL.total, nsm, cps, s));
         if (frc != HOPH_OK) return frc;
         hoph_timing_mark(plan, 2, s);
 
@@ -1685,9 +2006,11 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     sf.strategy = strategy;
     sf.out = d_stats;
     if (last) {
-        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
-        sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(
-            d_out, pa.out_count, out_capacity, sortA, sortB, plan->d_status, sf);
+        int64_t sort_launches = 0;
+        const int rc = launch_output_sort(plan, d_out, pa.out_count, out_capacity, sortA, sortB,
+                                          sf, s, &sort_launches);
+        if (rc != HOPH_OK) return rc;
+        launches += sort_launches - 1;
     } else if (d_stats) {
         stats_fold_kernel<<<1, 32, 0, s>>>(sf);
     } else {
@@ -1779,12 +2102,12 @@ int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int
     if (src != HOPH_OK) return src;
     ulonglong2 *sortA = static_cast<ulonglong2 *>(sp);
     StatsFold none{};
-    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
-    sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(
-        d_out, reinterpret_cast<const unsigned long long *>(d_out_count), out_capacity, sortA,
-        sortA + cap1, plan->d_status, none);
-    HOPH_CUDA_TRY(cudaGetLastError());
-    plan->launches += 1;
+    int64_t sort_launches = 0;
+    const int rc2 = launch_output_sort(plan, d_out,
+                                       reinterpret_cast<const unsigned long long *>(d_out_count),
+                                       out_capacity, sortA, sortA + cap1, none, s, &sort_launches);
+    if (rc2 != HOPH_OK) return rc2;
+    plan->launches += sort_launches;
     return HOPH_OK;
 }
 

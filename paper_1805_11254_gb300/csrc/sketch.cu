@@ -115,23 +115,29 @@ __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *
                                            const uint32_t *p, int64_t n, int t, int T,
                                            bool &bad) {
     const uint32_t mask = a.key_bits >= 32 ? 0xFFFFFFFFu : ((1u << a.key_bits) - 1u);
-    // psi-value of x as (bin << 32) | offset; bin k marks an ID outside V
-    auto locate = [&](uint32_t x) -> uint64_t {
-        if (HASH) {
+    // hash path: psi-value of x as (bin << 32) | offset (bin < k always);
+    // table path: the packed table key (bin << key_bits) | offset itself, or
+    // all ones for an ID outside V (no table key is all ones: k 2^key_bits
+    // stays below 2^32 for the table sizes a plan accepts), so a thread keeps
+    // 32 bits per lookup in flight
+    using Loc = typename std::conditional<HASH, uint64_t, uint32_t>::type;
+    auto locate = [&](uint32_t x) -> Loc {
+        if constexpr (HASH) {
             return hash_bin(*s_reg, s_lo, hash61(x, a.ha, a.hb));
         } else {
-            if (x >= a.D) return (uint64_t)a.k << 32;
-            const uint32_t key = __ldg(a.key + x);
-            return ((uint64_t)(uint32_t)((uint64_t)key >> a.key_bits) << 32) | (key & mask);
+            return x < a.D ? __ldg(a.key + x) : 0xFFFFFFFFu;
         }
     };
-    auto apply = [&](uint64_t bo) {
-        const uint32_t bin = (uint32_t)(bo >> 32), off = (uint32_t)bo;
-        if (bin >= a.k) {
-            bad = true;
-            return;
+    auto apply = [&](Loc v) {
+        if constexpr (HASH) {
+            atomicMin(sk + (uint32_t)(v >> 32), (uint32_t)v);
+        } else {
+            if (v == 0xFFFFFFFFu) {
+                bad = true;
+                return;
+            }
+            atomicMin(sk + (v >> a.key_bits), v & mask);
         }
-        atomicMin(sk + bin, off);
     };
     const int64_t head =
         (int64_t)min((long long)n, (long long)((4 - ((reinterpret_cast<uintptr_t>(p) >> 2) & 3)) & 3));
@@ -142,14 +148,14 @@ __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *
     for (; i + T < nvec; i += 2 * (int64_t)T) {
         const uint4 v0 = ldg_nc_v4(p4 + i);
         const uint4 v1 = ldg_nc_v4(p4 + i + T);
-        const uint64_t b0 = locate(v0.x), b1 = locate(v0.y), b2 = locate(v0.z), b3 = locate(v0.w);
-        const uint64_t b4 = locate(v1.x), b5 = locate(v1.y), b6 = locate(v1.z), b7 = locate(v1.w);
+        const Loc b0 = locate(v0.x), b1 = locate(v0.y), b2 = locate(v0.z), b3 = locate(v0.w);
+        const Loc b4 = locate(v1.x), b5 = locate(v1.y), b6 = locate(v1.z), b7 = locate(v1.w);
         apply(b0); apply(b1); apply(b2); apply(b3);
         apply(b4); apply(b5); apply(b6); apply(b7);
     }
     if (i < nvec) {
         const uint4 v0 = ldg_nc_v4(p4 + i);
-        const uint64_t b0 = locate(v0.x), b1 = locate(v0.y), b2 = locate(v0.z), b3 = locate(v0.w);
+        const Loc b0 = locate(v0.x), b1 = locate(v0.y), b2 = locate(v0.z), b3 = locate(v0.w);
         apply(b0); apply(b1); apply(b2); apply(b3);
     }
     const int64_t tail0 = head + (nvec << 2);
@@ -164,29 +170,32 @@ __device__ __forceinline__ void sketch_generated(const SketchArgs &a, const uint
                                                  uint64_t first, int64_t n, int t, int T,
                                                  bool &bad) {
     const uint32_t mask = a.key_bits >= 32 ? 0xFFFFFFFFu : ((1u << a.key_bits) - 1u);
-    auto locate = [&](uint32_t x) -> uint64_t {
-        if (HASH) {
+    // as in sketch_ids
+    using Loc = typename std::conditional<HASH, uint64_t, uint32_t>::type;
+    auto locate = [&](uint32_t x) -> Loc {
+        if constexpr (HASH) {
             return hash_bin(*s_reg, s_lo, hash61(x, a.ha, a.hb));
         } else {
-            if (x >= a.D) return (uint64_t)a.k << 32;
-            const uint32_t key = __ldg(a.key + x);
-            return ((uint64_t)(uint32_t)((uint64_t)key >> a.key_bits) << 32) | (key & mask);
+            return x < a.D ? __ldg(a.key + x) : 0xFFFFFFFFu;
         }
     };
-    auto apply = [&](uint64_t bo) {
-        const uint32_t bin = (uint32_t)(bo >> 32), off = (uint32_t)bo;
-        if (bin >= a.k) {
-            bad = true;
-            return;
+    auto apply = [&](Loc v) {
+        if constexpr (HASH) {
+            atomicMin(sk + (uint32_t)(v >> 32), (uint32_t)v);
+        } else {
+            if (v == 0xFFFFFFFFu) {
+                bad = true;
+                return;
+            }
+            atomicMin(sk + (v >> a.key_bits), v & mask);
         }
-        atomicMin(sk + bin, off);
     };
     int64_t j = t;
     for (; j + 3 * (int64_t)T < n; j += 4 * (int64_t)T) {
-        const uint64_t b0 = locate(synth_id(a.gen_seed, first + j, a.gen_D));
-        const uint64_t b1 = locate(synth_id(a.gen_seed, first + j + T, a.gen_D));
-        const uint64_t b2 = locate(synth_id(a.gen_seed, first + j + 2 * T, a.gen_D));
-        const uint64_t b3 = locate(synth_id(a.gen_seed, first + j + 3 * T, a.gen_D));
+        const Loc b0 = locate(synth_id(a.gen_seed, first + j, a.gen_D));
+        const Loc b1 = locate(synth_id(a.gen_seed, first + j + T, a.gen_D));
+        const Loc b2 = locate(synth_id(a.gen_seed, first + j + 2 * T, a.gen_D));
+        const Loc b3 = locate(synth_id(a.gen_seed, first + j + 3 * T, a.gen_D));
         apply(b0); apply(b1); apply(b2); apply(b3);
     }
     for (; j < n; j += T) apply(locate(synth_id(a.gen_seed, first + j, a.gen_D)));
@@ -215,7 +224,8 @@ __device__ __forceinline__ void store_sketch(const SketchArgs &a, uint32_t *sk, 
 // get the smallest of the remaining sets.  Without a work list (a.n_big null)
 // only phase 2 runs, in input order.
 template <bool HASH, int PHASES, bool COMPACT>
-__global__ void __launch_bounds__(kSketchThreads, 6) oph_sketch_kernel(const SketchArgs a) {
+__global__ void __launch_bounds__(kSketchThreads, (!HASH && PHASES != 3) ? 8 : 6)
+    oph_sketch_kernel(const SketchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *s_lo = reinterpret_cast<uint64_t *>(smem_raw);  // HASH only
     uint32_t *s_sk = reinterpret_cast<uint32_t *>(smem_raw + (HASH ? (a.k + 1) * 8 : 0));
@@ -411,6 +421,40 @@ __global__ void synth_ids_kernel(uint64_t seed, int64_t first, int64_t n, uint64
             }
             out[e] = (uint32_t)l;
         }
+    }
+}
+
+// Integer-throughput probe: 8 independent chains per thread of one
+// operation (KIND 0: 32-bit multiply-add, 1: 64-bit multiply-add, 2: high
+// half of a 64-bit product plus an add); the constants come from the thread
+// index so nothing folds away.
+template <int KIND>
+__global__ void __launch_bounds__(256) int_probe_kernel(int64_t iters, uint64_t *sink) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (KIND == 0) {
+        uint32_t x[8];
+        const uint32_t a = (uint32_t)(t * 2654435761u) | 1u, b = (uint32_t)t ^ 0x9E3779B9u;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = (uint32_t)t + c;
+        for (int64_t i = 0; i < iters; ++i)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) x[c] = x[c] * a + b;
+        uint32_t r = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) r ^= x[c];
+        sink[t] = r;
+    } else {
+        uint64_t x[8];
+        const uint64_t a = (t * 0x9E3779B97F4A7C15ull) | 1ull, b = t ^ 0xBF58476D1CE4E5B9ull;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = t + (uint64_t)c;
+        for (int64_t i = 0; i < iters; ++i)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) x[c] = (KIND == 1 ? x[c] * a : __umul64hi(x[c], a)) + b;
+        uint64_t r = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) r ^= x[c];
+        sink[t] = r;
     }
 }
 
@@ -611,6 +655,20 @@ int minwise_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t
     return HOPH_OK;
 }
 
+int hoph_int_probe(uint32_t kind, int64_t iters, uint64_t *d_sink, void *stream) {
+    if (kind > 2 || iters < 1 || iters > (1ll << 24) || !d_sink) return HOPH_ERR_PARAM;
+    int dev = 0, sms = 0;
+    HOPH_CUDA_TRY(cudaGetDevice(&dev));
+    HOPH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)sms * 8;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (kind == 0) int_probe_kernel<0><<<grid, 256, 0, s>>>(iters, d_sink);
+    else if (kind == 1) int_probe_kernel<1><<<grid, 256, 0, s>>>(iters, d_sink);
+    else int_probe_kernel<2><<<grid, 256, 0, s>>>(iters, d_sink);
+    HOPH_CUDA_TRY(cudaGetLastError());
+    return HOPH_OK;
+}
+
 int hoph_synth_ids(uint64_t seed, int64_t first, int64_t n_ids, uint64_t D, uint32_t kind,
                    const double *d_cdf, int64_t n_cdf, uint32_t *d_ids, void *stream) {
     if (n_ids < 0 || first < 0 || kind > 1 || (n_ids > 0 && !d_ids)) return HOPH_ERR_PARAM;
@@ -654,13 +712,17 @@ uint32_t *g_static_addr[kMaxDevices] = {};
 // Device address of g_static_worklist on the current device.  The symbol
 // name is only a host-side handle; the first call on each device looks the
 // address up with cudaGetSymbolAddress (with that device current) and caches
-// it.
-int static_worklist(uint32_t **out) {
+// it.  That set-up is refused (HOPH_ERR_CAPTURE) while `s` is being captured,
+// like every other first-use set-up of the library.  The cached address
+// belongs to the device's current context: it is not valid after a
+// cudaDeviceReset.
+int static_worklist(cudaStream_t s, uint32_t **out) {
     int dev = 0;
     HOPH_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return HOPH_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_static_mu);
     if (!g_static_addr[dev]) {
+        if (hoph_capturing(s)) return HOPH_ERR_CAPTURE;
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_static_worklist);
         if (e != cudaSuccess || !p) return hoph_cuda_fail(e);
@@ -678,10 +740,10 @@ extern "C" int oph_build_sketches_static(hoph_plan *plan, const uint32_t *d_ids,
     if (!plan || n_sets < 0 || (n_sets > 0 && (!d_offsets || !d_planes))) return HOPH_ERR_PARAM;
     if (n_sets > kStaticMaxSets) return HOPH_ERR_TOO_LARGE;
     if (n_sets == 0) return HOPH_OK;
-    uint32_t *scr = nullptr;
-    const int rc = static_worklist(&scr);
-    if (rc != HOPH_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *scr = nullptr;
+    const int rc = static_worklist(s, &scr);
+    if (rc != HOPH_OK) return rc;
     SketchArgs a = sketch_args(plan, d_ids, d_offsets, n_sets, d_planes);
     // the array keeps the previous call's contents: build_work_list zeroes the
     // histogram and the cursors (the bases, the count and the order are

@@ -102,7 +102,8 @@ _EXPORTS = ["hoph_plan_create", "hoph_plan_create_with_perm", "hoph_plan_destroy
             "hoph_sync_status", "hoph_status_string", "hoph_plan_enable_timing",
             "hoph_plan_read_timing", "oph_build_sketches_static", "hoph_plan_peek_timing",
             "hoph_check_bounded_wait", "hoph_synth_sketch", "oph_build_sketches16",
-            "hoph_query_batch16", "hoph_self_join"]
+            "hoph_query_batch16", "hoph_self_join", "hoph_small_probability_limits",
+            "hoph_int_probe"]
 
 
 def load(path=LIB_PATH):
@@ -126,6 +127,10 @@ def load(path=LIB_PATH):
     lib.hoph_plan_get_info.restype = i32
     lib.hoph_plan_set_exec.argtypes = [P, ctypes.POINTER(hoph_exec)]
     lib.hoph_plan_set_exec.restype = i32
+    lib.hoph_small_probability_limits.argtypes = [u32, u32, u32, ctypes.c_double, P, P]
+    lib.hoph_small_probability_limits.restype = i32
+    lib.hoph_int_probe.argtypes = [u32, i64, P, P]
+    lib.hoph_int_probe.restype = i32
     lib.oph_build_sketches.argtypes = [P, P, P, i64, P, P]
     lib.oph_build_sketches.restype = i32
     lib.oph_build_sketches_static.argtypes = [P, P, P, i64, P, P]
@@ -230,6 +235,17 @@ def hoph_plan_set_exec(plan, exec_=None):
            "hoph_plan_set_exec")
 
 
+def hoph_small_probability_limits(k_group, thr_num, thr_den, epsilon):
+    """(U, L) of Definition 1, exact (host only; no device needed)."""
+    U = ctypes.c_int64()
+    L = ctypes.c_int64()
+    _check(load().hoph_small_probability_limits(int(k_group), int(thr_num), int(thr_den),
+                                                float(epsilon), ctypes.addressof(U),
+                                                ctypes.addressof(L)),
+           "hoph_small_probability_limits")
+    return U.value, L.value
+
+
 def oph_build_sketches(plan, d_ids, d_offsets, n_sets, d_planes, stream=None):
     return _check(load().oph_build_sketches(plan, _ptr(d_ids), _ptr(d_offsets), int(n_sets),
                                             _ptr(d_planes), _stream(stream)), "oph_build_sketches")
@@ -285,6 +301,11 @@ def hoph_pair_counts(plan, d_query_planes, n_queries, d_coll_planes, n_rows, d_c
     return _check(load().hoph_pair_counts(plan, _ptr(d_query_planes), int(n_queries),
                                           _ptr(d_coll_planes), int(n_rows), _ptr(d_counts),
                                           _stream(stream)), "hoph_pair_counts")
+
+
+def hoph_int_probe(kind, iters, d_sink, stream=None):
+    return _check(load().hoph_int_probe(int(kind), int(iters), _ptr(d_sink), _stream(stream)),
+                  "hoph_int_probe")
 
 
 def hoph_synth_ids(seed, first, n_ids, D, kind, d_cdf, n_cdf, d_ids, stream=None):

@@ -1,13 +1,15 @@
 """Continuous-batching near-duplicate query service over the C ABI.
 
 Requests (each a list of query sets) arrive over time.  The batcher admits
-waiting requests into the next batch while query slots and the reserved
-device memory for IDs last; each batch is padded to a fixed slot count so
-its whole device work (H2D of the sets, OPH/HOPH sketching, the HOPH query
-against the resident collection, D2H of the accepted pairs) replays as one
-captured CUDA graph.  Several streams (two by default) with a plan each keep
-that many batches in flight: the copies and sketching of one overlap the
-queries of the others.
+waiting requests into the next batch while query slots and the device
+memory for IDs last; that ID memory is sized from the free HBM read when
+the service starts (the resident collection already allocated), minus a
+reserve, split across the streams.  Each batch is padded to a fixed slot
+count so its whole device work (H2D of the sets, OPH/HOPH sketching, the
+HOPH query against the resident collection, D2H of the count and the first
+accepted pairs) replays as one captured CUDA graph.  Several streams (two
+by default) with a plan each keep that many batches in flight: the copies
+and sketching of one overlap the queries of the others.
 Results are scattered back per request; a request's pairs do not depend on
 which other requests shared its batch (padding sets are empty and their
 pairs are dropped).
@@ -80,6 +82,19 @@ class Batcher:
         return len(self.waiting)
 
 
+def id_capacity_from_free_memory(free_bytes, n_lanes, reserve_frac=0.25, max_ids=1 << 24):
+    """IDs one lane's device buffer may hold: the free device memory
+    `free_bytes` (read after the resident collection and every lane's fixed
+    buffers and plan scratch exist) minus a reserve fraction, split evenly
+    over `n_lanes`, at 4 bytes per ID, capped at `max_ids` (the pinned host
+    staging buffer has the same size).  0 when nothing is left; the batcher
+    then rejects every request that carries IDs."""
+    if n_lanes < 1 or not 0.0 <= reserve_frac < 1.0:
+        raise ValueError("n_lanes >= 1 and 0 <= reserve_frac < 1")
+    usable = int(max(0, free_bytes) * (1.0 - reserve_frac)) // n_lanes
+    return int(max(0, min(max_ids, usable // 4)))
+
+
 def pack_batch(reqs, bucket, h_ids, h_off):
     """Write the batch's sets into pinned host buffers (padding sets are
     empty); returns (n_ids, owner) with owner[q] = (request, local index)."""
@@ -100,10 +115,18 @@ def pack_batch(reqs, bucket, h_ids, h_off):
 
 
 class GpuExecutor:
-    """`n_streams` streams, one plan each, one graph per (stream, bucket)."""
+    """`n_streams` streams, one plan each, one graph per (stream, bucket).
 
-    def __init__(self, plan_kwargs, planes, n_rows, mode, slot_buckets, id_capacity,
-                 out_capacity=1 << 14, n_streams=2, device=None):
+    id_capacity: IDs per batch; None sizes it from the device's free memory
+    (``id_capacity_from_free_memory`` over ``mem_reader()``, by default
+    torch.cuda.mem_get_info's free bytes) once every lane's fixed buffers
+    and plan scratch exist.  The batcher must use ``self.id_capacity``.
+    pair_window: accepted pairs copied back inside the captured graph; a
+    batch with more copies the rest when it is retired."""
+
+    def __init__(self, plan_kwargs, planes, n_rows, mode, slot_buckets, id_capacity=None,
+                 out_capacity=1 << 14, n_streams=2, device=None, mem_reader=None,
+                 reserve_frac=0.25, max_ids=1 << 24, pair_window=256):
         import torch
         self.torch = torch
         self.dev = device or torch.device("cuda", torch.cuda.current_device())
@@ -112,21 +135,38 @@ class GpuExecutor:
         self.mode = mode
         self.buckets = sorted(slot_buckets)
         self.cap = out_capacity
+        self.window = max(1, min(pair_window, out_capacity))
         self.lanes = []
+        mb = self.buckets[-1]
         for _ in range(n_streams):
             plan = hoph.Plan(**plan_kwargs)
             lane = dict(plan=plan, stream=torch.cuda.Stream(device=self.dev), busy=None)
-            mb = self.buckets[-1]
-            lane["d_ids"] = torch.empty(max(id_capacity, 1), dtype=torch.int32, device=self.dev)
             lane["d_off"] = torch.zeros(mb + 1, dtype=torch.int64, device=self.dev)
             lane["out"] = torch.empty((self.cap, 2), dtype=torch.int64, device=self.dev)
             lane["cnt"] = torch.zeros(1, dtype=torch.int64, device=self.dev)
-            lane["h_ids"] = torch.empty(max(id_capacity, 1), dtype=torch.int32).pin_memory()
             lane["h_off"] = torch.zeros(mb + 1, dtype=torch.int64).pin_memory()
             lane["h_out"] = torch.empty((self.cap, 2), dtype=torch.int64).pin_memory()
             lane["h_cnt"] = torch.zeros(1, dtype=torch.int64).pin_memory()
+            lane["qb"] = {b: torch.empty((plan.G, b, plan.kg), dtype=torch.int32,
+                                         device=self.dev) for b in self.buckets}
             lane["graphs"] = {}
+            # one eager step of empty sets at the largest batch size sizes the
+            # plan's scratch and tables (they depend on the batch size, not the IDs)
+            lane["d_ids"] = torch.empty(1, dtype=torch.int32, device=self.dev)
+            with torch.cuda.stream(lane["stream"]):
+                self._device_step(lane, mb, lane["stream"])
+            lane["stream"].synchronize()
             self.lanes.append(lane)
+        if id_capacity is None:
+            torch.cuda.synchronize(self.dev)
+            free = (mem_reader() if mem_reader is not None
+                    else torch.cuda.mem_get_info(self.dev)[0])
+            id_capacity = id_capacity_from_free_memory(free, n_streams, reserve_frac, max_ids)
+        self.id_capacity = int(id_capacity)
+        for lane in self.lanes:
+            lane["d_ids"] = torch.empty(max(self.id_capacity, 1), dtype=torch.int32,
+                                        device=self.dev)
+            lane["h_ids"] = torch.empty(max(self.id_capacity, 1), dtype=torch.int32).pin_memory()
         # largest batch first: its eager call sizes the plan's scratch for every
         # bucket, so the scratch never grows (and moves) under a graph that
         # was already captured
@@ -144,13 +184,10 @@ class GpuExecutor:
         hoph.hoph_query_batch(plan.handle, self.mode, planes_q, bucket, self.planes, self.n_rows,
                               lane["out"], self.cap, lane["cnt"], None, stream)
         lane["h_cnt"].copy_(lane["cnt"], non_blocking=True)
-        lane["h_out"].copy_(lane["out"], non_blocking=True)
+        lane["h_out"][:self.window].copy_(lane["out"][:self.window], non_blocking=True)
 
     def _capture(self, lane, bucket):
         torch = self.torch
-        plan = lane["plan"]
-        lane.setdefault("qb", {})[bucket] = torch.empty((plan.G, bucket, plan.kg),
-                                                        dtype=torch.int32, device=self.dev)
         lane["d_off"].zero_()
         s = lane["stream"]
         with torch.cuda.stream(s):
@@ -194,6 +231,9 @@ class GpuExecutor:
                 continue
             rc = hoph.hoph_sync_status(lane["plan"].handle, lane["stream"])
             n = int(lane["h_cnt"][0])
+            if min(n, self.cap) > self.window:  # the pairs past the captured window
+                m = min(n, self.cap)
+                lane["h_out"][self.window:m].copy_(lane["out"][self.window:m])
             t = now_fn()
             err = None
             if rc not in (hoph.HOPH_OK,):

@@ -52,3 +52,26 @@ def pairs_tuples(pairs):
 
 def oracle_tuples(res):
     return [tuple(int(v) for v in row) for row in res["accepted"]]
+
+
+_perm_cache = {}
+
+
+def oracle_rows(ids, off, D, k, kg, ab=(0, 0), seed=1, hashed=False):
+    """The oracle's own sketches ([n][k] uint32, bins in psi order) of the
+    sets (ids, off): its layout (Sec. 3.2 / 4.1) and its own psi (explicit
+    Fisher-Yates table, or the 2-universal hash), nothing from the GPU."""
+    lo = oc.layout(D, k, kg, *ab)
+    if hashed:
+        return oc.sketch(ids, off, lo, D=D, hash_ab=oc.hash_params(seed))
+    key = (D, seed)
+    if key not in _perm_cache:
+        _perm_cache.clear()
+        _perm_cache[key] = oc.permutation(D, seed)
+    return oc.sketch(ids, off, lo, perm=_perm_cache[key])
+
+
+def oracle_z(D, k, kg, ab=(0, 0)):
+    """Group sizes z_g (values of V per group) from the oracle's layout."""
+    lo = oc.layout(D, k, kg, *ab)
+    return np.diff(lo[::kg]).astype(np.uint64)

@@ -4,8 +4,8 @@ decision counts must be identical."""
 import numpy as np
 import pytest
 
-from gpu_helpers import (device, oracle_tuples, pairs_tuples, planes_to_rows, rows_to_planes,
-                         to_dev, torch)  # noqa: F401
+from gpu_helpers import (device, oracle_rows, oracle_tuples, oracle_z, pairs_tuples,
+                         planes_to_rows, rows_to_planes, to_dev, torch)  # noqa: F401
 from oracle import oracle_c as oc
 from paper_1805_11254_gb300 import hoph, synth
 
@@ -30,6 +30,20 @@ def _sketch_both(plan, w, dev):
 def _oracle_query(mode, q_rows, c_rows, kg, z, eps=EPS, rule="both", thr=T):
     return oc.query(mode, q_rows, c_rows, kg, thr[0], thr[1], eps, rule=rule,
                     z=np.asarray(z, dtype=np.uint64))
+
+
+def _small_oracle(w, k, kg, ab, q=None, c=None):
+    """The oracle's sketches of the small workload's queries and rows (psi
+    from seed 1) and its group sizes; GPU planes q, c, when given, must
+    equal them bit for bit."""
+    D = w["D"]
+    q_rows = oracle_rows(w["q_ids"], w["q_off"], D, k, kg, ab, 1)
+    c_rows = oracle_rows(w["ids"], w["off"], D, k, kg, ab, 1)
+    if q is not None:
+        assert np.array_equal(planes_to_rows(q), q_rows)
+    if c is not None:
+        assert np.array_equal(planes_to_rows(c), c_rows)
+    return q_rows, c_rows, oracle_z(D, k, kg, ab)
 
 
 def _compare(plan, mode, q, c, nq, nr, want, strategy, G):
@@ -62,8 +76,8 @@ def test_small_workload_parity(small, mode, ab, kg, strategy):
     with hoph.Plan(D, k, kg, *ab, seed=1, thr=T, epsilon=EPS) as plan:
         q, c = _sketch_both(plan, small, dev)
         nq, nr = q.shape[1], c.shape[1]
-        z = [plan.info.group_size[g] for g in range(plan.G)]
-        want = _oracle_query(mode, planes_to_rows(q), planes_to_rows(c), kg, z)
+        q_rows, c_rows, z = _small_oracle(small, k, kg, ab, q, c)
+        want = _oracle_query(mode, q_rows, c_rows, kg, z)
         assert want["count"] > 0
         G = plan.G if mode in ("goph", "hoph") else 1
         _compare(plan, mode, q, c, nq, nr, want, strategy, G)
@@ -113,8 +127,9 @@ def test_rules_eps_and_empty_bins(mode, ab, rule, eps):
         d_ids, d_off = to_dev(ids, dev), to_dev(off, dev)
         c = plan.sketch(d_ids, d_off, len(sets))
         plan.check()
-        rows = planes_to_rows(c)
-        z = [plan.info.group_size[g] for g in range(plan.G)]
+        rows = oracle_rows(ids, off, D, k, kg, ab, 9)
+        assert np.array_equal(planes_to_rows(c), rows)
+        z = oracle_z(D, k, kg, ab)
         want = _oracle_query(mode, rows, rows, kg, z, eps=eps, rule=rule, thr=thr)
         G = plan.G if mode != "oph_full" else 1
         for strategy in (0, -1, 1):
@@ -127,14 +142,12 @@ def test_ragged_tiles_and_batch_sizes(small, n_rows, n_q):
     dev = device()
     D, k, kg = small["D"], 128, 32
     with hoph.Plan(D, k, kg, 1, 1, seed=1, thr=T) as plan:
-        q, c = _sketch_both(plan, small, dev)
+        q_all, rows, z = _small_oracle(small, k, kg, (1, 1))
         # planted rows first so there are accepted pairs in range
         src = small["src"][:n_q]
-        rows = planes_to_rows(c)
         sel = np.concatenate([src, np.arange(n_rows)])[:n_rows]
         c_rows = rows[sel]
-        q_rows = planes_to_rows(q)[:n_q]
-        z = [plan.info.group_size[g] for g in range(plan.G)]
+        q_rows = q_all[:n_q]
         want = _oracle_query("hoph", q_rows, c_rows, kg, z)
         for strategy in (0, 1):
             _compare(plan, "hoph", rows_to_planes(q_rows, kg, dev), rows_to_planes(c_rows, kg, dev),
@@ -153,7 +166,8 @@ def test_empty_inputs_and_capacity_overflow(small):
         # T = 0.01 accepts nearly everything: more pairs than the buffer holds
         out = torch.empty((4, 2), dtype=torch.int64, device=dev)
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-        rows, qrows = planes_to_rows(c)[:100], planes_to_rows(q)[:10]
+        q_all, c_all, _ = _small_oracle(small, k, kg, (0, 0))
+        rows, qrows = c_all[:100], q_all[:10]
         hoph.hoph_query_batch(plan.handle, "goph", rows_to_planes(qrows, kg, dev), 10,
                               rows_to_planes(rows, kg, dev), 100, out, 4, cnt)
         assert hoph.hoph_sync_status(plan.handle) == hoph.HOPH_ERR_CAPACITY
@@ -193,10 +207,9 @@ def test_pair_counts_parity(small):
     dev = device()
     D, k, kg = small["D"], 128, 32
     with hoph.Plan(D, k, kg, 1, 1, seed=1) as plan:
-        q, c = _sketch_both(plan, small, dev)
         nr = 700
-        cr = planes_to_rows(c)[:nr]
-        qr = planes_to_rows(q)
+        qr, c_all, _ = _small_oracle(small, k, kg, (1, 1))
+        cr = c_all[:nr]
         out = torch.empty((qr.shape[0], nr, plan.G, 3), dtype=torch.int16, device=dev)
         hoph.hoph_pair_counts(plan.handle, rows_to_planes(qr, kg, dev), qr.shape[0],
                               rows_to_planes(cr, kg, dev), nr, out)
@@ -227,8 +240,8 @@ def test_join_execution_knobs_do_not_change_results(small, kg, lpr, warps, stage
     D, k = small["D"], 128
     with hoph.Plan(D, k, kg, 1, 2, seed=1, thr=T, epsilon=EPS) as plan:
         q, c = _sketch_both(plan, small, dev)
-        z = [plan.info.group_size[g] for g in range(plan.G)]
-        want = _oracle_query("hoph", planes_to_rows(q), planes_to_rows(c), kg, z)
+        q_rows, c_rows, z = _small_oracle(small, k, kg, (1, 2), q, c)
+        want = _oracle_query("hoph", q_rows, c_rows, kg, z)
         plan.set_exec(strategy=1, lanes_per_row=lpr, consumer_warps=warps, stages=stages)
         pairs, n, st = plan.query("hoph", q, q.shape[1], c, c.shape[1], stats=True)
         assert pairs_tuples(pairs) == oracle_tuples(want)
@@ -268,15 +281,13 @@ def test_large_key_spaces_use_the_hashed_join(case):
         c = plan.sketch(to_dev(ids, dev), to_dev(off, dev), len(off) - 1)
         q = plan.sketch(to_dev(q_ids, dev), to_dev(q_off, dev), len(q_off) - 1)
         plan.check()
-        c_rows, q_rows = planes_to_rows(c), planes_to_rows(q)
-        lo = oc.layout(D, k, kg, *ab)
-        if case.startswith("hash61"):
-            want_c = oc.sketch(ids, off, lo, D=D, hash_ab=oc.hash_params(7))
-        else:
-            want_c = oc.sketch(ids, off, lo, perm=oc.permutation(D, 7))
-        assert np.array_equal(c_rows, want_c)
-        z = np.diff(lo[::kg]).astype(np.uint64)
-        want = oc.query(mode, q_rows, c_rows, kg, thr[0], thr[1], 1e-4, z=z)
+        hashed = case.startswith("hash61")
+        want_c = oracle_rows(ids, off, D, k, kg, ab, 7, hashed=hashed)
+        want_q = oracle_rows(q_ids, q_off, D, k, kg, ab, 7, hashed=hashed)
+        assert np.array_equal(planes_to_rows(c), want_c)
+        assert np.array_equal(planes_to_rows(q), want_q)
+        z = oracle_z(D, k, kg, ab)
+        want = oc.query(mode, want_q, want_c, kg, thr[0], thr[1], 1e-4, z=z)
         assert want["count"] > 0
         plan.set_exec(strategy=1)
         pairs, n, st = plan.query(mode, q, q.shape[1], c, c.shape[1], stats=True)
@@ -316,9 +327,9 @@ def test_literal_weighting_parity(small, ab, strategy):
                    weighting=hoph.HOPH_WEIGHT_LITERAL) as plan:
         q, c = _sketch_both(plan, small, dev)
         nq, nr = q.shape[1], c.shape[1]
-        z = [plan.info.group_size[g] for g in range(plan.G)]
-        want = oc.query("hoph", planes_to_rows(q), planes_to_rows(c), kg, T[0], T[1], EPS,
-                        z=np.asarray(z, dtype=np.uint64), weighting="literal", ab=ab)
+        q_rows, c_rows, z = _small_oracle(small, k, kg, ab, q, c)
+        want = oc.query("hoph", q_rows, c_rows, kg, T[0], T[1], EPS, z=z, weighting="literal",
+                        ab=ab)
         _compare(plan, "hoph", q, c, nq, nr, want, strategy, plan.G)
 
 
@@ -334,8 +345,8 @@ def test_compact_planes_give_the_same_pairs(small, mode, ab, kg, strategy):
     D, k = small["D"], 128
     with hoph.Plan(D, k, kg, *ab, seed=1, thr=T, epsilon=EPS) as plan:
         q, c = _sketch_both(plan, small, dev)
-        z = [plan.info.group_size[g] for g in range(plan.G)]
-        want = _oracle_query(mode, planes_to_rows(q), planes_to_rows(c), kg, z)
+        q_rows, c_rows, z = _small_oracle(small, k, kg, ab, q, c)
+        want = _oracle_query(mode, q_rows, c_rows, kg, z)
         q16 = plan.sketch16(to_dev(small["q_ids"], dev), to_dev(small["q_off"], dev), q.shape[1])
         c16 = plan.sketch16(to_dev(small["ids"], dev), to_dev(small["off"], dev), c.shape[1])
         plan.check()
@@ -373,9 +384,9 @@ def test_self_join_is_the_upper_triangle_of_the_all_pairs_query(small, mode, ab,
     with hoph.Plan(D, k, kg, *ab, seed=1, thr=T, epsilon=EPS) as plan:
         c = plan.sketch(to_dev(ids, dev), to_dev(off, dev), n)
         plan.check()
-        rows = planes_to_rows(c)
-        z = [plan.info.group_size[g] for g in range(plan.G)]
-        full = oc.query(mode, rows, rows, kg, T[0], T[1], EPS, z=np.asarray(z, dtype=np.uint64),
+        rows = oracle_rows(ids, off, D, k, kg, ab, 1)
+        assert np.array_equal(planes_to_rows(c), rows)
+        full = oc.query(mode, rows, rows, kg, T[0], T[1], EPS, z=oracle_z(D, k, kg, ab),
                         per_pair=True)
         want = full["accepted"]
         want = want[want[:, 0] < want[:, 1]]
@@ -537,9 +548,12 @@ def test_compact_planes_with_a_hashed_join():
         c16 = plan.sketch16(to_dev(ids, dev), to_dev(off, dev), len(off) - 1)
         q16 = plan.sketch16(to_dev(q_ids, dev), to_dev(q_off, dev), len(q_off) - 1)
         plan.check()
-        z = np.diff(oc.layout(D, k, kg)[::kg]).astype(np.uint64)
-        want = oc.query("oph_full", planes_to_rows(q), planes_to_rows(c), kg, thr[0], thr[1],
-                        1e-4, z=z)
+        want_q = oracle_rows(q_ids, q_off, D, k, kg, (0, 0), 9)
+        want_c = oracle_rows(ids, off, D, k, kg, (0, 0), 9)
+        assert np.array_equal(planes_to_rows(q), want_q)
+        assert np.array_equal(planes_to_rows(c), want_c)
+        want = oc.query("oph_full", want_q, want_c, kg, thr[0], thr[1], 1e-4,
+                        z=oracle_z(D, k, kg))
         assert want["count"] > 0
         plan.set_exec(strategy=1)
         pairs, n, st = plan.query("oph_full", q16, q16.shape[1], c16, c16.shape[1], stats=True)
@@ -566,11 +580,89 @@ def test_autotuner_keeps_the_result_and_sets_the_fastest_knobs(small):
         assert best is not None and len(times) >= 2
         assert all(plan.exec_kwargs[kk] == v for kk, v in best.items())
         pairs, n, _ = plan.query("hoph", q, nq, c, nr)
-        z = [plan.info.group_size[g] for g in range(plan.G)]
-        want = _oracle_query("hoph", planes_to_rows(q), planes_to_rows(c), kg, z)
+        q_rows, c_rows, z = _small_oracle(small, k, kg, ab, q, c)
+        want = _oracle_query("hoph", q_rows, c_rows, kg, z)
         assert pairs_tuples(pairs) == oracle_tuples(want)
         d_ids, d_off = to_dev(small["ids"], dev), to_dev(small["off"], dev)
         sk = torch.empty_like(c)
         bits, btimes = autotune.tune_sketch(plan, d_ids, d_off, nr, sk, finalists=2, rounds=2)
         assert plan.exec_kwargs["sketch_cta_bits"] == bits and len(btimes) >= 2
         assert torch.equal(sk, c)
+
+
+@pytest.mark.parametrize("knobs", [dict(consumer_warps=16, stages=2, tile_rows=256),
+                                   dict(consumer_warps=16, stages=4, tile_rows=64),
+                                   dict(consumer_warps=5, stages=3, tile_rows=96)])
+@pytest.mark.parametrize("k,kg,compact", [(128, 32, False), (256, 64, False), (256, 128, False),
+                                          (256, 64, True), (256, 128, True)])
+def test_striped_filter_keeps_the_oracle_pairs(small, k, kg, compact, knobs):
+    """The join filter over the bank-striped group map (lanes_per_row = 32:
+    a warp per row, lane l reading words l, l + 32, ...), for 32, 64 and 128
+    scanned bins, uint32 and compact planes, ragged last tiles: the oracle's
+    pairs and per-group decision counts; with too few row bytes for whole
+    lanes (32 compact bins) it is refused."""
+    dev = device()
+    D, ab = small["D"], (1, 2)
+    with hoph.Plan(D, k, kg, *ab, seed=1, thr=T, epsilon=EPS) as plan:
+        q_rows, c_rows, z = _small_oracle(small, k, kg, ab)
+        want = _oracle_query("hoph", q_rows, c_rows, kg, z)
+        assert want["count"] > 0
+        if compact:
+            q = plan.sketch16(to_dev(small["q_ids"], dev), to_dev(small["q_off"], dev),
+                              len(q_rows))
+            c = plan.sketch16(to_dev(small["ids"], dev), to_dev(small["off"], dev), len(c_rows))
+        else:
+            q, c = _sketch_both(plan, small, dev)
+        plan.check()
+        plan.set_exec(strategy=1, lanes_per_row=32, **knobs)
+        pairs, n, st = plan.query("hoph", q, q.shape[1], c, c.shape[1], capacity=1 << 16,
+                                  stats=True)
+        assert st.strategy == 1
+        assert n == want["count"]
+        assert pairs_tuples(pairs) == oracle_tuples(want)
+        for g in range(plan.G):
+            assert st.accepted[g] == want["hist"][g + 1][1]
+            assert st.rejected[g] == want["hist"][g + 1][2]
+    with hoph.Plan(D, 128, 32, *ab, seed=1, thr=T, epsilon=EPS) as plan:
+        q16 = plan.sketch16(to_dev(small["q_ids"], dev), to_dev(small["q_off"], dev), 50)
+        c16 = plan.sketch16(to_dev(small["ids"], dev), to_dev(small["off"], dev), 5000)
+        plan.set_exec(strategy=1, lanes_per_row=32)
+        with pytest.raises(hoph.HophError) as e:
+            plan.query("hoph", q16, 50, c16, 5000)
+        assert e.value.code == hoph.HOPH_ERR_UNSUPPORTED
+
+
+def test_over_a_million_accepted_pairs_come_out_in_order():
+    """Over a million accepted pairs (sketches over two values per bin, so about
+    half the bins of a pair match; T = 2/5): a capacity above the one-CTA
+    sort's limit takes the many-CTA run sort and merge passes, and the output
+    is exactly the oracle's accepted pairs in (query, row) order, with the
+    groups compared and matched bins of each; a capacity one short reports
+    HOPH_ERR_CAPACITY with the full count.  (Dense scan: at k' = 32 and
+    T = 2/5 a pair without a match is not rejected at every denominator, so
+    the value join is not offered.)"""
+    dev = device()
+    rng = np.random.default_rng(77)
+    D, k, kg, nq, nr = 1 << 16, 64, 32, 1200, 1100
+    q_rows = rng.integers(0, 2, (nq, k)).astype(np.uint32)
+    c_rows = rng.integers(0, 2, (nr, k)).astype(np.uint32)
+    q_rows[rng.random((nq, k)) < 0.05] = hoph.HOPH_EMPTY_VALUE
+    c_rows[rng.random((nr, k)) < 0.05] = hoph.HOPH_EMPTY_VALUE
+    thr = (2, 5)
+    want = oc.query("goph", q_rows, c_rows, kg, thr[0], thr[1], EPS)
+    assert want["count"] > 1_000_000
+    with hoph.Plan(D, k, kg, seed=1, thr=thr, epsilon=EPS) as plan:
+        q, c = rows_to_planes(q_rows, kg, dev), rows_to_planes(c_rows, kg, dev)
+        pairs, n, st = plan.query("goph", q, nq, c, nr, capacity=want["count"] + 5, stats=True)
+        assert n == want["count"]
+        got = np.stack([pairs["query"].astype(np.int64), pairs["row"],
+                        pairs["groups"].astype(np.int64), pairs["matches"].astype(np.int64)], 1)
+        assert np.array_equal(got, want["accepted"])
+        hist = want["hist"]
+        for g in range(plan.G):
+            assert st.accepted[g] == hist[g + 1][1] and st.rejected[g] == hist[g + 1][2]
+        out = torch.empty((want["count"] - 1, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        hoph.hoph_query_batch(plan.handle, "goph", q, nq, c, nr, out, want["count"] - 1, cnt)
+        assert hoph.hoph_sync_status(plan.handle) == hoph.HOPH_ERR_CAPACITY
+        assert int(cnt.item()) == want["count"]

@@ -122,3 +122,48 @@ def test_latency_summary_and_poisson_arrivals():
     s = serve.latency_summary(reqs)
     assert s["requests"] == len(reqs)
     assert 1.0 <= s["p50_ms"] <= 10.0 and s["p99_ms"] <= 10.0 + 1e-9
+
+
+def test_id_capacity_follows_the_free_device_memory():
+    """The executor sizes each lane's ID buffer from the free HBM it reads at
+    start (a fake reader here): a reserve fraction kept back, the rest split
+    over the lanes at 4 bytes per ID, capped; nothing left admits nothing."""
+    free = {"bytes": 80 << 30}
+    reader = lambda: free["bytes"]  # noqa: E731
+    cap = serve.id_capacity_from_free_memory(reader(), 4, reserve_frac=0.25, max_ids=1 << 40)
+    assert cap == (int((80 << 30) * 0.75) // 4) // 4
+    assert serve.id_capacity_from_free_memory(reader(), 4, 0.25, max_ids=1 << 20) == 1 << 20
+    free["bytes"] = 4 * 1000 * 2  # two lanes, no reserve: 1,000 IDs each
+    assert serve.id_capacity_from_free_memory(reader(), 2, 0.0) == 1000
+    free["bytes"] = 0
+    assert serve.id_capacity_from_free_memory(reader(), 2, 0.25) == 0
+    import pytest
+    with pytest.raises(ValueError):
+        serve.id_capacity_from_free_memory(1 << 30, 0)
+    with pytest.raises(ValueError):
+        serve.id_capacity_from_free_memory(1 << 30, 2, reserve_frac=1.0)
+
+
+def test_admission_is_bounded_by_the_memory_budget():
+    """With the ID capacity a small device leaves (fake reader: 2,400 bytes
+    free, 2 lanes, no reserve -> 300 IDs per batch), requests are batched
+    only while their IDs fit, and a request that alone exceeds it is
+    rejected rather than queued; a larger device admits them together."""
+    small = serve.id_capacity_from_free_memory(2400, 2, reserve_frac=0.0)
+    assert small == 300
+    reqs = [_req(0, [100, 100], 0.0), _req(1, [150], 0.0), _req(2, [50], 0.0),
+            _req(3, [400], 0.0)]
+    b = Batcher((4, 8), id_capacity=small)
+    assert [b.offer(r) for r in reqs] == [True, True, True, False]
+    assert [r.rid for r in b.rejected] == [3]
+    got, _ = b.next_batch(0.0)
+    assert [r.rid for r in got] == [0]          # 200 IDs; +150 would exceed 300
+    got, _ = b.next_batch(0.0)
+    assert [r.rid for r in got] == [1, 2]       # 150 + 50
+    big = serve.id_capacity_from_free_memory(1 << 20, 2, reserve_frac=0.0)
+    b = Batcher((4, 8), id_capacity=big)
+    for r in reqs:
+        r.error = None
+        assert b.offer(r)
+    got, bucket = b.next_batch(0.0)
+    assert [r.rid for r in got] == [0, 1, 2, 3] and bucket == 8

@@ -31,8 +31,12 @@ def test_static_entry_point_matches_allocating_one(ab, kg):
     dev = device()
     D, k = 1 << 20, 256
     with hoph.Plan(D, k, kg, *ab, seed=1) as plan:
-        # two calls in a row through the C ABI, different sizes and contents
-        for n_sets, seed in ((60000, 31), (20011, 32)):
+        # calls in a row through the C ABI, different sizes and contents, each
+        # smaller batch after a larger one (the shared array keeps the last
+        # call's contents): two-launch sizes (60,000 and 20,011 sets), a
+        # one-launch size with a multi-warp work list (9,000), the one-CTA
+        # work-list kernel (3,000) and a batch too small for a work list (37)
+        for n_sets, seed in ((60000, 31), (9000, 35), (20011, 32), (3000, 34), (37, 33)):
             ids, off = _inputs(n_sets, seed, D)
             d_ids, d_off = to_dev(ids, dev), to_dev(off, dev)
             want = torch.full((plan.G, n_sets, kg), -7, dtype=torch.int32, device=dev)
