@@ -46,7 +46,7 @@ CAP = 1 << 16
 # dram read+write bytes per filter-kernel launch from an ncu capture, keyed by
 # the sha256 of the filter kernel's source it was taken on (null once that
 # source changes)
-NCU_TRAFFIC = {"5f5a7d980fdb1192": 2577.06e6}  # 2*10^6-row capture x 5 rows
+NCU_TRAFFIC = {"e447e4d9d8de52fd": 2577.20e6}  # 2*10^6-row capture x 5 rows
 
 
 def parse():
@@ -74,7 +74,7 @@ def parse():
     p.add_argument("--details", default=None,
                    help="also write the studies' JSON to this file")
     p.add_argument("--profile", nargs="?", const="query",
-                   choices=("query", "sketch", "oph1", "self_join"),
+                   choices=("query", "sketch", "oph1", "self_join", "shingle"),
                    help="few launches of the query step (or of the 10^6-set sketch, of the "
                         "one-query OPH full scan with its tuned knobs, or one self-join of "
                         "the first --rows rows), for ncu")
@@ -109,11 +109,12 @@ def env_rank():
 
 
 def filter_src_sha():
-    """sha256[:16] of the join filter's source (FilterArgs through the kernel)."""
+    """sha256[:16] of the uint32 join filter's source (FilterArgs through
+    filter_kernel)."""
     with open(os.path.join(ROOT, "paper_1805_11254_gb300", "csrc", "query.cu")) as f:
         text = f.read()
     a = text.index("struct FilterArgs {")
-    b = text.index("// Join strategy, part 3")
+    b = text.index("// Join filter over a striped group map")
     return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 
 
@@ -345,6 +346,9 @@ def run_native(args):
     if args.profile == "sketch":
         sketch_leg(dev, stream, measured_peaks()[0], steps=2)
         return
+    if args.profile == "shingle":
+        profile_shingle(args, dev, stream)
+        return
 
     # ---- collection (setup, untimed)
     off, coll_seed = collection_host(args.rows, rank)
@@ -443,6 +447,7 @@ def run_native(args):
                                              head["pairs"], dev, stream, peaks, thr)
         if not args.no_sweep:
             details["sweeps"] = sweep_leg(dev, stream)
+            details["large_output"] = large_output_leg(dev, stream)
         if not args.no_self_join:
             details["self_join"] = self_join_leg(off, coll_seed, dev, stream)
         if not args.no_shingle:
@@ -987,6 +992,32 @@ def sketch_leg(dev, stream, peaks, n_sets=1_000_000, steps=20):
                                           "bytes"}}
 
 
+def profile_shingle(args, dev, stream, reps=2):
+    """The shingle regime's two sketches for ncu: --shingle-rows collection
+    sets generated and sketched in the kernel (hoph_synth_sketch), then
+    --shingle-queries stored query sets sketched, each `reps` times."""
+    import torch
+    from paper_1805_11254_gb300 import hoph, synth
+    D4, K4, KG4, AB4 = 1 << 32, 512, 128, (2, 1)
+    with hoph.Plan(D4, K4, KG4, *AB4, perm_kind=hoph.HOPH_PERM_HASH61, seed=PERM_SEED, thr=T,
+                   epsilon=EPS) as plan:
+        c_off = synth.offsets_from_sizes(synth.uniform_sizes(args.shingle_rows, 1000, 100000, 31))
+        d_coff = to_dev(c_off, dev)
+        planes = torch.empty((plan.G, args.shingle_rows, KG4), dtype=torch.int32, device=dev)
+        for _ in range(reps):
+            hoph.hoph_synth_sketch(plan.handle, 31, D4, d_coff, args.shingle_rows, planes, stream)
+        q_off = synth.offsets_from_sizes(synth.uniform_sizes(args.shingle_queries, 1000, 100000,
+                                                             34))
+        d_qids = torch.empty(int(q_off[-1]), dtype=torch.int32, device=dev)
+        hoph.hoph_synth_ids(35, 0, int(q_off[-1]), D4, 0, None, 0, d_qids, stream)
+        qp = torch.empty((plan.G, args.shingle_queries, KG4), dtype=torch.int32, device=dev)
+        for _ in range(reps):
+            plan.sketch(d_qids, to_dev(q_off, dev), args.shingle_queries, out=qp, stream=stream)
+        plan.check(stream)
+        print(json.dumps({"profiled": "shingle", "collection_ids": int(c_off[-1]),
+                          "query_ids": int(q_off[-1])}), flush=True)
+
+
 def profile_self_join(args, off, coll_seed, dev, stream, batch=1536):
     """One hoph_self_join over the collection's first --rows rows ((1:2)HOPH,
     blocks of 1,536 rows, the library's default blocks in flight), for an ncu
@@ -1376,6 +1407,48 @@ def self_join_leg(off, coll_seed, dev, stream, n_base=1_000_000, n_planted=1000,
 
 SWEEP_T = ((1, 2), (3, 5), (7, 10), (4, 5), (9, 10))
 SWEEP_EPS = (1e-3, 1e-4, 1e-5)
+
+
+def large_output_leg(dev, stream, reps=5):
+    """A query whose output is over a million accepted pairs (1,200 x 1,100
+    sketches over two values per bin, GOPH k = 64, k' = 32, T = 2/5, the
+    case of the tests): the comparison's and the output sort's phase times
+    from the library's CUDA events, with the capacity above the one-CTA
+    sort's limit (many-CTA runs and merges)."""
+    import torch
+    from paper_1805_11254_gb300 import hoph
+    rng = np.random.default_rng(77)
+    Dl, k, kg, nq, nr = 1 << 16, 64, 32, 1200, 1100
+    q_rows = rng.integers(0, 2, (nq, k)).astype(np.uint32)
+    c_rows = rng.integers(0, 2, (nr, k)).astype(np.uint32)
+    q_rows[rng.random((nq, k)) < 0.05] = hoph.HOPH_EMPTY_VALUE
+    c_rows[rng.random((nr, k)) < 0.05] = hoph.HOPH_EMPTY_VALUE
+
+    def planes(rows):
+        p = np.ascontiguousarray(rows.reshape(len(rows), k // kg, kg).transpose(1, 0, 2))
+        return to_dev(p, dev)
+    q, c = planes(q_rows), planes(c_rows)
+    cap = 1 << 21
+    out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    with hoph.Plan(Dl, k, kg, seed=1, thr=(2, 5), epsilon=EPS) as plan:
+        hoph.hoph_query_batch(plan.handle, "goph", q, nq, c, nr, out, cap, cnt, None, stream)
+        plan.check(stream)
+        n = int(cnt.item())
+        got = out[:min(n, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+        key = got["query"].astype(np.int64) * nr + got["row"]
+        ordered = bool(np.all(np.diff(key) > 0))
+        hoph.hoph_plan_enable_timing(plan.handle, True)
+        for _ in range(reps):
+            hoph.hoph_query_batch(plan.handle, "goph", q, nq, c, nr, out, cap, cnt, None, stream)
+        ph, calls, launches = hoph.hoph_plan_read_timing(plan.handle)
+        hoph.hoph_plan_enable_timing(plan.handle, False)
+        plan.check(stream)
+    return {"accepted": n, "in_order": ordered, "capacity": cap,
+            "compare_ms": (ph[0] + ph[1] + ph[2]) / max(calls, 1),
+            "sort_ms": ph[3] / max(calls, 1), "launches_per_call": launches / max(calls, 1),
+            "how": "GOPH, 1,200 queries x 1,100 rows, dense scan; sort = many-CTA run sort and "
+                   "merge passes (16 B records)"}
 
 
 def sweep_leg(dev, stream, reps=5):

@@ -159,7 +159,9 @@ typedef struct {
                               * striped across the banks by bin (one
                               * scanned plane whose rows are 128, 256 or
                               * 512 bytes, W <= 128; tile_rows then sets
-                              * the rows per tile)                       */
+                              * the rows per tile, a multiple of 32);
+                              * 0: the library's choice (32 for 16-bit
+                              * planes where it applies, else W / 32)   */
     int32_t sketch_cta_bits; /* sketch: sets whose size has at least this
                               * many bits get a whole CTA, the rest a warp;
                               * 0 = library choice, 64 = warps only      */

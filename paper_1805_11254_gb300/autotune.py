@@ -18,10 +18,11 @@ QUERY_DEFAULTS = dict(strategy=-1, tile_rows=0, consumer_warps=0, ctas_per_sm=0,
 JOIN_CANDIDATES = [dict(strategy=1, lanes_per_row=l, consumer_warps=c, stages=s)
                    for l, c, s in ((0, 16, 2), (0, 12, 2), (0, 8, 3), (0, 16, 3), (-2, 16, 2),
                                    (-2, 16, 3), (-2, 16, 4), (-2, 31, 2), (-2, 24, 2))]
-# the striped-map filter (a warp per row): rows per tile x stages x warps
+# the striped-map filter (lanes over a row's bins): warps x stages x rows per tile
+# (0: a 64 KB stage)
 JOIN_CANDIDATES += [dict(strategy=1, lanes_per_row=32, consumer_warps=c, stages=s, tile_rows=r)
-                    for c, s, r in ((16, 2, 256), (16, 3, 128), (16, 4, 128), (12, 3, 128),
-                                    (16, 4, 64), (8, 4, 128))]
+                    for c, s, r in ((16, 2, 0), (16, 3, 0), (16, 3, 256), (16, 4, 256),
+                                    (8, 3, 256), (12, 3, 384))]
 DENSE_CANDIDATES = [dict(strategy=0, consumer_warps=c, stages=s, tile_rows=r)
                     for c, s, r in ((8, 4, 0), (15, 4, 0), (8, 6, 0), (4, 4, 0), (15, 2, 64),
                                     (8, 4, 32), (15, 3, 32), (8, 2, 64), (4, 8, 16), (6, 4, 32))]

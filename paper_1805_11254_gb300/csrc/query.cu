@@ -238,7 +238,8 @@ __device__ __forceinline__ void flush_stats(const unsigned long long *s_stats,
 __device__ void produce_tiles(const CUtensorMap *map, unsigned char *stages, uint64_t *full,
                               uint64_t *empty, volatile int32_t *abort_flag, int nstages,
                               uint32_t stage_bytes, uint32_t stage_stride, int64_t n_tiles,
-                              int R, int32_t *status, bool four_d = false, int prefetch = 0) {
+                              int R, int32_t *status, bool four_d = false, int prefetch = 0,
+                              int boxes = 1) {
     tma_prefetch_desc(map);
     int64_t it = 0;
     // 4-D maps: as each tile is issued, the CTA's tile `prefetch` strides
@@ -254,11 +255,16 @@ __device__ void produce_tiles(const CUtensorMap *map, unsigned char *stages, uin
         }
         mbar_arrive_expect_tx(full + s, stage_bytes);
         if (four_d) {
+            // a tile of R rows as `boxes` boxes of R / boxes rows each
             const int64_t ahead = tile + (int64_t)prefetch * gridDim.x;
-            if (prefetch > 0 && ahead < n_tiles)
-                tma_prefetch_l2_4d(map, 0, 0, (int32_t)(ahead * R), 0);
-            tma_load_4d(stages + (size_t)s * stage_stride, map, full + s, 0, 0,
-                        (int32_t)(tile * R), 0);
+            const int br = R / boxes;
+            const uint32_t bb = stage_bytes / (uint32_t)boxes;
+            for (int b = 0; b < boxes; ++b) {
+                if (prefetch > 0 && ahead < n_tiles)
+                    tma_prefetch_l2_4d(map, 0, 0, (int32_t)(ahead * R + b * br), 0);
+                tma_load_4d(stages + (size_t)s * stage_stride + (size_t)b * bb, map, full + s, 0,
+                            0, (int32_t)(tile * R + b * br), 0);
+            }
         }
         else
             tma_load_3d(stages + (size_t)s * stage_stride, map, full + s, 0, (int32_t)(tile * R),
@@ -614,6 +620,7 @@ struct FilterArgs {
     uint32_t gmap_words;      // the last word is zero: empty bins look up its slot 0
     uint32_t map_shift;       // hashed map: slot = map_slot(key, map_shift)
     uint32_t nwb;             // striped map: words per (bin, lane) stack
+    int32_t boxes;            // TMA boxes per tile (striped: tiles above 256 rows)
     const uint64_t *binbase;  // key = lo[w] + value
     const uint16_t *row_min;  // [W + 1]
     int32_t keep_empty;       // rows without a non-empty scanned bin are candidates
@@ -782,20 +789,20 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
     }
 }
 
-// Join filter over a striped group map (lanes over bins): a warp takes one
-// row at a time, lane l reading 32-bit words l, l + 32, ... of it (NW words,
-// 4 / sizeof(E) values each), so the 32 lanes look up 32 different banks of
-// the map and every lookup is one shared-memory wavefront.  Per lane the
-// values' hits and non-empty bins are packed (even-group hits in bits 0-7,
-// non-empty bins 8-15, odd-group hits 16-23; W <= 128 keeps each below 256)
-// and one warp reduction gives the row's totals.  Tiles come through an
-// unswizzled 4-D box {v, k'/v, rows, 1}: row r's values are contiguous.
-constexpr int kStripedRows = 4;  // rows a warp of the striped filter handles at once
-
+// Join filter over a striped group map (lanes over bins).  A warp takes 32
+// rows at a time; for each, lane l reads 32-bit words l, l + 32, ... of the row
+// (NW words, 4 / sizeof(E) values each), so the 32 lanes look up 32 different
+// banks of the map and every lookup is one shared-memory wavefront.  A lane
+// keeps one packed partial count per row (even-group hits in bits 0-7,
+// non-empty bins 8-15, odd-group hits 16-23, and for 16-bit values the
+// non-empty high halves in 24-31; W <= 128 keeps each below 256)
+// and five butterfly steps (exchange half of the rows with the partner lane,
+// add the other half) leave lane r with row r's totals, so every lane decides
+// one row.  Tiles come through an unswizzled 4-D box {v, k'/v, rows, 1}: row
+// r's values are contiguous; tile_rows is a multiple of 32.
 template <typename E, int NW>
 __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_constant__ FilterArgs a,
                                                                const __grid_constant__ CUtensorMap map) {
-    constexpr int RPI = kStripedRows;
     constexpr int VPW = 4 / (int)sizeof(E);  // values per 32-bit word
     constexpr int NS = NW * VPW;             // values (map stacks) per lane
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -823,7 +830,8 @@ __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_co
     if (warp == a.n_cons) {
         if (lane == 0)
             produce_tiles(&map, stages, full, empty, abort_flag, a.stages, a.stage_bytes,
-                          a.stage_stride, a.n_tiles, R, a.status, true, kFilterPrefetch);
+                          a.stage_stride, a.n_tiles, R, a.status, true, kFilterPrefetch,
+                          a.boxes);
         return;
     }
     {
@@ -840,6 +848,7 @@ __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_co
 #pragma unroll
     for (int s = 0; s < NS; ++s) sbase[s] = ((uint32_t)s * a.nwb * 32u + (uint32_t)lane) * 4u;
     const uint32_t row_words = (uint32_t)a.W * sizeof(E) / 4;
+    const int keep_empty = a.keep_empty;
 
     int s = 0;
     uint32_t ph = 0;
@@ -849,55 +858,69 @@ __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_co
             *abort_flag = 1;
             break;
         }
-        const uint32_t *tw = reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride);
+        const uint32_t *tw =
+            reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride) + lane;
         const int64_t row0 = tile * R;
         const int rows = (int)(a.n_rows - row0 < (int64_t)R ? a.n_rows - row0 : (int64_t)R);
-        // RPI rows of the tile at a time per warp (R is a multiple of RPI), their
-        // loads, lookups and reductions interleaved; rows past the collection's
-        // end (a ragged last tile) are looked up but never kept
-        for (int r0 = warp * RPI; r0 < rows; r0 += a.n_cons * RPI) {
-            uint32_t acc[RPI];
+        // groups of 32 rows, dealt round-robin over the warps; rows past the
+        // collection's end (a ragged last tile) are looked up but never kept
+        for (int r0 = warp * 32; r0 < rows; r0 += a.n_cons * 32) {
+            uint32_t acc[32];
 #pragma unroll
-            for (int j = 0; j < RPI; ++j) acc[j] = 0u;
+            for (int j = 0; j < 32; ++j) {
+                uint32_t t = 0;
 #pragma unroll
-            for (int i = 0; i < NW; ++i) {
-                uint32_t word[RPI];
-#pragma unroll
-                for (int j = 0; j < RPI; ++j) word[j] = tw[(uint32_t)(r0 + j) * row_words + lane + 32 * i];
-#pragma unroll
-                for (int h = 0; h < VPW; ++h) {
-                    uint32_t mw[RPI], u[RPI];
-#pragma unroll
-                    for (int j = 0; j < RPI; ++j) {
-                        if constexpr (VPW == 1) {
-                            u[j] = word[j] + 1u;  // the empty marker wraps to slot 0
-                        } else {
-                            u[j] = ((h ? (word[j] >> 16) : word[j]) + 1u) & 0xFFFFu;
-                        }
-                        mw[j] = *reinterpret_cast<const uint32_t *>(s_gmap + sbase[i * VPW + h] +
-                                                                   ((u[j] >> 4) << 7));
+                for (int i = 0; i < NW; ++i) {
+                    const uint32_t word = tw[(uint32_t)(r0 + j) * row_words + 32 * i];
+                    // slot u = value + 1 (the empty marker wraps to slot 0, the guard);
+                    // the word of slot u in its stack is u >> 4, 128 bytes a row
+                    if constexpr (VPW == 1) {
+                        const uint32_t u = word + 1u;
+                        const uint32_t mw = *reinterpret_cast<const uint32_t *>(
+                            s_gmap + sbase[i] + ((u & ~15u) << 3));
+                        t += (__funnelshift_r(mw, mw, u) & 0x10001u) + (u != 0u ? 0x100u : 0u);
+                    } else {
+                        // both 16-bit slots at once; the rotation only reads the low
+                        // five bits of its amount, so the low slot needs no mask
+                        const uint32_t w1 = __vadd2(word, 0x00010001u);
+                        const uint32_t uh = w1 >> 16;
+                        const uint32_t m0 = *reinterpret_cast<const uint32_t *>(
+                            s_gmap + sbase[2 * i] + ((w1 & 0xFFF0u) << 3));
+                        const uint32_t m1 = *reinterpret_cast<const uint32_t *>(
+                            s_gmap + sbase[2 * i + 1] + ((uh & ~15u) << 3));
+                        // non-empty slots: 1 per half, the low one counted in bits
+                        // 8-15, the high one in bits 24-31
+                        t += (__funnelshift_r(m0, m0, w1) & 0x10001u) +
+                             (__funnelshift_r(m1, m1, uh) & 0x10001u) +
+                             (__vsetne2(w1, 0u) << 8);
                     }
+                }
+                acc[j] = t;
+            }
+            // butterfly: after step `o` a lane holds the partial sums of the rows
+            // whose index agrees with its own lane index in the bits done so far
 #pragma unroll
-                    for (int j = 0; j < RPI; ++j)
-                        acc[j] += (__funnelshift_r(mw[j], mw[j], u[j]) & 0x10001u) +
-                                  (u[j] != 0u ? 0x100u : 0u);
+            for (int o = 16, n = 16; o >= 1; o >>= 1, n >>= 1) {
+                const bool upper = (lane & o) != 0;
+#pragma unroll
+                for (int j = 0; j < n; ++j) {
+                    const uint32_t send = upper ? acc[j] : acc[j + n];
+                    const uint32_t keep = upper ? acc[j + n] : acc[j];
+                    acc[j] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, o);
                 }
             }
-            uint32_t passmask = 0;
-#pragma unroll
-            for (int j = 0; j < RPI; ++j) {
-                const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, acc[j]);
-                const uint32_t ne = (tot >> 8) & 0xFFu;
-                const int hh = (int)max(tot & 0xFFu, (tot >> 16) & 0xFFu);
-                const bool pass = ne == 0 ? (a.keep_empty != 0) : (hh >= (int)s_rmin[ne]);
-                if (pass && r0 + j < rows) passmask |= 1u << j;
-            }
-            if (passmask && lane == 0) {
-                const unsigned long long at =
-                    atomicAdd(a.n_cand, (unsigned long long)__popc(passmask));
-                int o = 0;
-                for (int j = 0; j < RPI; ++j)
-                    if (passmask >> j & 1u) a.cand[at + o++] = (uint32_t)(row0 + r0 + j);
+            const uint32_t tot = acc[0];  // row r0 + lane
+            const uint32_t ne = ((tot >> 8) & 0xFFu) + (VPW == 1 ? 0u : tot >> 24);
+            const uint32_t hh = max(tot & 0xFFu, (tot >> 16) & 0xFFu);
+            const bool pass = (r0 + lane < rows) &&
+                              (ne == 0 ? keep_empty != 0 : hh >= (uint32_t)s_rmin[ne]);
+            const uint32_t pm = __ballot_sync(0xFFFFFFFFu, pass);
+            if (pm) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.n_cand, (unsigned long long)__popc(pm));
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (pass)
+                    a.cand[base + __popc(pm & ((1u << lane) - 1u))] = (uint32_t)(row0 + r0 + lane);
             }
         }
         __syncwarp();
@@ -1717,7 +1740,7 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     // The striped map (lanes over bins, filter_striped_kernel): one plane,
     // rows of whole 128-byte lines, W <= 128, a direct map of W stacks of
     // nwb words (slot 0 of each the empty guard) that fits next to two
-    // stages of 64 rows.  lanes_per_row = 32 asks for it.
+    // stages of 64 rows.  lanes_per_row = 32 asks for it
     uint32_t nwb = 0;
     const int lane_words = W * ES / 128;  // 32-bit words of a row per lane
     if (Gs == 1 && (W * ES) % 128 == 0 && W <= 128 && !map_hashed &&
@@ -1728,7 +1751,9 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     }
     const bool striped_ok = nwb > 0 && (uint64_t)W * nwb * 4 + 2ull * 64 * W * ES + 8 * W +
                                            4096 <= (uint64_t)kSmemLimit;
-    const bool striped = strategy == 1 && plan->exec.lanes_per_row == 32;
+    // (the library's own choice for 16-bit planes, where it is the faster filter)
+    const bool striped = strategy == 1 && (plan->exec.lanes_per_row == 32 ||
+                                           (plan->exec.lanes_per_row == 0 && ES == 2 && striped_ok));
     if (striped && !striped_ok) return HOPH_ERR_UNSUPPORTED;
 
     const int mask_words = (W + 31) / 32;
@@ -1883,29 +1908,39 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 16;
         if (striped) n_cons = std::min(n_cons, 16);
         int stages = plan->exec.stages > 0 ? plan->exec.stages : 3;
-        int srows = plan->exec.tile_rows > 0 ? plan->exec.tile_rows : 256;
-        if (striped) srows = std::max(kStripedRows, srows / kStripedRows * kStripedRows);
+        // striped: rows per tile a multiple of 32 (a warp's group), loaded as
+        // boxes of at most 256 rows; the default fills a 64 KB stage
+        int srows = plan->exec.tile_rows > 0 ? plan->exec.tile_rows : 65536 / (W * ES);
+        if (striped) {
+            srows = std::min(1024, std::max(32, srows / 32 * 32));
+            if (srows > 256) srows = srows / 256 * 256;
+            n_cons = std::min(n_cons, srows / 32);
+        }
         auto rows_of = [&](int nc) { return striped ? srows : 32 / lpr * nc; };
+        auto too_many_rows = [&](int nc) { return striped ? false : rows_of(nc) > 256; };
         auto stage_of = [&](int nc) { return align_up((uint32_t)rows_of(nc) * W * ES, 1024); };
         while (n_cons > 1 && (fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit ||
-                              rows_of(n_cons) > 256)) {
+                              too_many_rows(n_cons))) {
             if (stages > 2) --stages;
-            else if (striped && srows > 64) srows /= 2;
-            else --n_cons;
+            else if (striped && srows > 64) {
+                srows = srows > 256 ? srows / 2 / 256 * 256 : srows / 2 / 32 * 32;
+                n_cons = std::min(n_cons, srows / 32);
+            } else --n_cons;
         }
         if (fixed + (uint32_t)stages * stage_of(n_cons) > (uint32_t)kSmemLimit)
             return HOPH_ERR_UNSUPPORTED;
         fa.lanes_per_row = lpr;
         fa.n_cons = n_cons;
         fa.tile_rows = rows_of(n_cons);
+        fa.boxes = striped && fa.tile_rows > 256 ? fa.tile_rows / 256 : 1;
         fa.stages = stages;
         fa.n_tiles = (n_rows + fa.tile_rows - 1) / fa.tile_rows;
         fa.stage_bytes = (uint32_t)fa.tile_rows * W * ES;
         fa.stage_stride = align_up(fa.stage_bytes, 1024);
         CUtensorMap map;
         memset(&map, 0, sizeof map);
-        if (!encode_swizzled_map(&map, d_coll_planes, ES, kg, n_rows, Gs, cstride, fa.tile_rows,
-                                 !striped))
+        if (!encode_swizzled_map(&map, d_coll_planes, ES, kg, n_rows, Gs, cstride,
+                                 fa.tile_rows / fa.boxes, !striped))
             return HOPH_ERR_UNSUPPORTED;
         const FilterSmem FL = filter_smem(fa);
         hoph_timing_mark(plan, 1, s);
