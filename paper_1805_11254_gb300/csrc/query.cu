@@ -952,7 +952,9 @@ struct CountArgs {
     const uint32_t *n_allempty;
 };
 
-constexpr int kCountThreads = 256;
+// four warps and about 11 KB of shared memory a CTA (1,024 queries), so that
+// counting CTAs fit on an SM beside a running filter CTA of another batch
+constexpr int kCountThreads = 128;
 constexpr int kCountWarps = kCountThreads / 32;
 
 struct CountSmem {
@@ -978,7 +980,7 @@ __host__ __device__ inline CountSmem count_smem(const CountArgs &a) {
 // passes, and the next candidate row's values are loaded while the current
 // one is counted.
 template <int NCH, typename E>
-__global__ void __launch_bounds__(kCountThreads, 3) count_kernel(const __grid_constant__ CountArgs a) {
+__global__ void __launch_bounds__(kCountThreads, 6) count_kernel(const __grid_constant__ CountArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const CountSmem L = count_smem(a);
     const PairArgs &P = a.p;
@@ -1176,7 +1178,11 @@ int launch_count(const CountArgs &ca, uint32_t smem, int num_sms, cudaStream_t s
 // Deterministic output order: sort the accepted pairs by (query, row)
 // ===========================================================================
 constexpr int kSortThreads = 1024;
-constexpr int kSortSmem = 8192;  // records sorted in shared memory at once
+constexpr int kSortSmem = 8192;  // records sorted in shared memory at once (many-CTA sort)
+// the one-CTA sort (capacities up to kSortOneCta): runs of 512 records in 8 KB
+// and 256 threads, small enough to share an SM with a running filter CTA
+constexpr int kSmallSortThreads = 256;
+constexpr int kSmallSortRun = 512;
 
 __device__ __forceinline__ unsigned long long pair_key(const hoph_pair &p) {
     return ((unsigned long long)p.query << 40) | (unsigned long long)p.row;
@@ -1247,7 +1253,7 @@ __global__ void stats_fold_kernel(const StatsFold f) {
 }
 
 // Sort the accepted pairs by (query, row); thread 0 also folds the statistics.
-__global__ void __launch_bounds__(kSortThreads) sort_pairs_kernel(
+__global__ void __launch_bounds__(kSmallSortThreads) sort_pairs_kernel(
     hoph_pair *out, const unsigned long long *count, int64_t cap, ulonglong2 *bufA,
     ulonglong2 *bufB, int32_t *status, const StatsFold f) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -1257,9 +1263,9 @@ __global__ void __launch_bounds__(kSortThreads) sort_pairs_kernel(
     if (total > (unsigned long long)cap && threadIdx.x == 0) hoph_flag(status, HOPH_ERR_CAPACITY);
     const int64_t n = (int64_t)min(total, (unsigned long long)cap);
     if (n <= 1) return;
-    // sort runs of kSortSmem records in shared memory into bufA
-    for (int64_t base = 0; base < n; base += kSortSmem) {
-        const int cnt = (int)min((long long)kSortSmem, (long long)(n - base));
+    // sort runs of kSmallSortRun records in shared memory into bufA
+    for (int64_t base = 0; base < n; base += kSmallSortRun) {
+        const int cnt = (int)min((long long)kSmallSortRun, (long long)(n - base));
         int m = 1;
         while (m < cnt) m <<= 1;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -1278,7 +1284,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pairs_kernel(
     }
     // merge sorted runs (keys are unique: rank = own index + rank in the other run)
     ulonglong2 *src = bufA, *dst = bufB;
-    for (int64_t run = kSortSmem; run < n; run <<= 1) {
+    for (int64_t run = kSmallSortRun; run < n; run <<= 1) {
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
             const int64_t pairbase = (i / (2 * run)) * (2 * run);
             const int64_t a0 = pairbase, a1 = min(pairbase + run, n);
@@ -1589,8 +1595,8 @@ int launch_output_sort(hoph_plan *plan, hoph_pair *d_out, const unsigned long lo
                        int64_t cap, ulonglong2 *sortA, ulonglong2 *sortB, const StatsFold &sf,
                        cudaStream_t s, int64_t *launches) {
     if (cap <= kSortOneCta) {
-        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSortSmem * 16));
-        sort_pairs_kernel<<<1, kSortThreads, kSortSmem * 16, s>>>(d_out, count, cap, sortA,
+        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)sort_pairs_kernel, kSmallSortRun * 16));
+        sort_pairs_kernel<<<1, kSmallSortThreads, kSmallSortRun * 16, s>>>(d_out, count, cap, sortA,
                                                                   sortB, plan->d_status, sf);
         HOPH_CUDA_TRY(cudaGetLastError());
         *launches = 1;
