@@ -103,17 +103,42 @@ __device__ __forceinline__ uint64_t hash_bin(const RegionTable &t, const uint64_
     return ((uint64_t)bin << 32) | (uint32_t)(v - s_lo[bin]);
 }
 
+// Table path: the IDs below kHotIds (the most frequent words of a
+// frequency-ranked vocabulary) are collected as bits of `hot` instead of
+// being gathered and applied one by one; kSkipKey marks them, kBadKey an ID
+// outside V (no table key reaches either: k 2^key_bits stays below 2^32 for
+// the table sizes a plan accepts).
+constexpr uint32_t kHotIds = 32;
+constexpr uint32_t kSkipKey = 0xFFFFFFFEu;
+constexpr uint32_t kBadKey = 0xFFFFFFFFu;
+
+// The hot IDs of a set (bits of hm, collected by its warp or CTA), applied
+// to its sketch once each by lanes 0..31; one at or beyond D (a universe of
+// fewer than 32 IDs) is flagged instead.
+__device__ __forceinline__ void apply_hot(const SketchArgs &a, uint32_t *sk, uint32_t hm,
+                                          int lane, bool &bad) {
+    if (hm >> lane & 1u) {
+        if ((uint64_t)lane >= a.D) {
+            bad = true;
+            return;
+        }
+        const uint32_t mask = a.key_bits >= 32 ? 0xFFFFFFFFu : ((1u << a.key_bits) - 1u);
+        const uint32_t key = __ldg(a.key + lane);
+        atomicMin(sk + (key >> a.key_bits), key & mask);
+    }
+}
+
 // One thread's share of the IDs [p, p+n) (thread t of a group of T threads):
 // a scalar head up to a 16-byte boundary, a 128-bit body whose eight table
 // gathers are issued before any of their minima is applied, a scalar tail.
 // Each ID updates the shared sketch `sk` with an atomicMin (no read first: one
 // shared-memory operation per ID instead of a read and, when it improves, an
 // atomic).
-template <bool HASH>
+template <bool HASH, bool WIDE = true>
 __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *s_lo,
                                            const RegionTable *s_reg, uint32_t *sk,
                                            const uint32_t *p, int64_t n, int t, int T,
-                                           bool &bad) {
+                                           bool &bad, uint32_t &hot) {
     const uint32_t mask = a.key_bits >= 32 ? 0xFFFFFFFFu : ((1u << a.key_bits) - 1u);
     // hash path: psi-value of x as (bin << 32) | offset (bin < k always);
     // table path: the packed table key (bin << key_bits) | offset itself, or
@@ -125,15 +150,19 @@ __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *
         if constexpr (HASH) {
             return hash_bin(*s_reg, s_lo, hash61(x, a.ha, a.hb));
         } else {
-            return x < a.D ? __ldg(a.key + x) : 0xFFFFFFFFu;
+            // the most frequent IDs of a frequency-ranked vocabulary (x < 32)
+            // only set a bit; the set's bits are applied once at its end
+            const bool h = x < kHotIds;
+            hot |= h ? (1u << (x & 31u)) : 0u;
+            return h ? kSkipKey : (x < a.D ? __ldg(a.key + x) : kBadKey);
         }
     };
     auto apply = [&](Loc v) {
         if constexpr (HASH) {
             atomicMin(sk + (uint32_t)(v >> 32), (uint32_t)v);
         } else {
-            if (v == 0xFFFFFFFFu) {
-                bad = true;
+            if (v >= kSkipKey) {
+                if (v == kBadKey) bad = true;
                 return;
             }
             atomicMin(sk + (v >> a.key_bits), v & mask);
@@ -145,7 +174,8 @@ __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *
     const uint4 *p4 = reinterpret_cast<const uint4 *>(p + head);
     const int64_t nvec = (n - head) >> 2;
     int64_t i = t;
-    for (; i + T < nvec; i += 2 * (int64_t)T) {
+    // WIDE: two 128-bit loads (eight lookups) in flight per iteration, else one
+    for (; WIDE && i + T < nvec; i += 2 * (int64_t)T) {
         const uint4 v0 = ldg_nc_v4(p4 + i);
         const uint4 v1 = ldg_nc_v4(p4 + i + T);
         const Loc b0 = locate(v0.x), b1 = locate(v0.y), b2 = locate(v0.z), b3 = locate(v0.w);
@@ -153,10 +183,11 @@ __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *
         apply(b0); apply(b1); apply(b2); apply(b3);
         apply(b4); apply(b5); apply(b6); apply(b7);
     }
-    if (i < nvec) {
+    for (; i < nvec; i += T) {
         const uint4 v0 = ldg_nc_v4(p4 + i);
         const Loc b0 = locate(v0.x), b1 = locate(v0.y), b2 = locate(v0.z), b3 = locate(v0.w);
         apply(b0); apply(b1); apply(b2); apply(b3);
+        if (WIDE) break;  // the wide loop leaves at most one vector per thread
     }
     const int64_t tail0 = head + (nvec << 2);
     for (int64_t j = tail0 + t; j < n; j += T) apply(locate(p[j]));
@@ -168,7 +199,7 @@ template <bool HASH>
 __device__ __forceinline__ void sketch_generated(const SketchArgs &a, const uint64_t *s_lo,
                                                  const RegionTable *s_reg, uint32_t *sk,
                                                  uint64_t first, int64_t n, int t, int T,
-                                                 bool &bad) {
+                                                 bool &bad, uint32_t &hot) {
     const uint32_t mask = a.key_bits >= 32 ? 0xFFFFFFFFu : ((1u << a.key_bits) - 1u);
     // as in sketch_ids
     using Loc = typename std::conditional<HASH, uint64_t, uint32_t>::type;
@@ -176,15 +207,19 @@ __device__ __forceinline__ void sketch_generated(const SketchArgs &a, const uint
         if constexpr (HASH) {
             return hash_bin(*s_reg, s_lo, hash61(x, a.ha, a.hb));
         } else {
-            return x < a.D ? __ldg(a.key + x) : 0xFFFFFFFFu;
+            // the most frequent IDs of a frequency-ranked vocabulary (x < 32)
+            // only set a bit; the set's bits are applied once at its end
+            const bool h = x < kHotIds;
+            hot |= h ? (1u << (x & 31u)) : 0u;
+            return h ? kSkipKey : (x < a.D ? __ldg(a.key + x) : kBadKey);
         }
     };
     auto apply = [&](Loc v) {
         if constexpr (HASH) {
             atomicMin(sk + (uint32_t)(v >> 32), (uint32_t)v);
         } else {
-            if (v == 0xFFFFFFFFu) {
-                bad = true;
+            if (v >= kSkipKey) {
+                if (v == kBadKey) bad = true;
                 return;
             }
             atomicMin(sk + (v >> a.key_bits), v & mask);
@@ -239,6 +274,9 @@ __global__ void __launch_bounds__(kSketchThreads, (!HASH && PHASES != 3) ? 8 : 6
     for (uint32_t i = threadIdx.x; i < regions * a.k; i += blockDim.x) s_sk[i] = HOPH_EMPTY_VALUE;
     __syncthreads();
     bool bad = false;
+    uint32_t hot = 0;
+    __shared__ uint32_t s_hot;
+    if (threadIdx.x == 0) s_hot = 0;
     const int64_t n_big = a.n_big ? (int64_t)*a.n_big : 0;
     // phase 1 (warp 0's sketch region serves the CTA; store_sketch resets it)
     for (int64_t item = (PHASES & 1) ? blockIdx.x : n_big; item < n_big; item += gridDim.x) {
@@ -246,11 +284,19 @@ __global__ void __launch_bounds__(kSketchThreads, (!HASH && PHASES != 3) ? 8 : 6
         const int64_t beg = a.off[set], end = a.off[set + 1];
         if (a.generate)
             sketch_generated<HASH>(a, s_lo, &s_reg, s_sk, (uint64_t)beg, end - beg, threadIdx.x,
-                                   blockDim.x, bad);
+                                   blockDim.x, bad, hot);
         else
             sketch_ids<HASH>(a, s_lo, &s_reg, s_sk, a.ids + beg, end - beg, threadIdx.x,
-                             blockDim.x, bad);
+                             blockDim.x, bad, hot);
+        if (!HASH) {
+            const uint32_t hm = __reduce_or_sync(0xFFFFFFFFu, hot);
+            hot = 0;
+            if (lane == 0 && hm) atomicOr(&s_hot, hm);
+            __syncthreads();
+            if (warp == 0) apply_hot(a, s_sk, s_hot, lane, bad);
+        }
         __syncthreads();
+        if (!HASH && threadIdx.x == 0) s_hot = 0;  // every read of it is behind the barrier
         store_sketch<COMPACT>(a, s_sk, set, threadIdx.x, blockDim.x);
         __syncthreads();
     }
@@ -266,9 +312,15 @@ __global__ void __launch_bounds__(kSketchThreads, (!HASH && PHASES != 3) ? 8 : 6
         const int64_t set = a.order ? a.order[item] : item;
         const int64_t beg = a.off[set], end = a.off[set + 1];
         if (a.generate)
-            sketch_generated<HASH>(a, s_lo, &s_reg, sk, (uint64_t)beg, end - beg, lane, 32, bad);
+            sketch_generated<HASH>(a, s_lo, &s_reg, sk, (uint64_t)beg, end - beg, lane, 32, bad,
+                                   hot);
         else
-            sketch_ids<HASH>(a, s_lo, &s_reg, sk, a.ids + beg, end - beg, lane, 32, bad);
+            sketch_ids<HASH, (HASH || PHASES != 2)>(a, s_lo, &s_reg, sk, a.ids + beg, end - beg,
+                                                    lane, 32, bad, hot);
+        if (!HASH) {
+            apply_hot(a, sk, __reduce_or_sync(0xFFFFFFFFu, hot), lane, bad);
+            hot = 0;
+        }
         __syncwarp();
         store_sketch<COMPACT>(a, sk, set, lane, 32);
         __syncwarp();

@@ -257,3 +257,32 @@ def test_work_list_shapes_at_their_boundaries(n):
         got = _gpu_sketch(plan, ids, off, dev)
     want = oc.sketch(ids, off, oc.layout(D, k, kg, 1, 1), perm=oc.permutation(D, 4))
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("D,k", [(1 << 20, 256), (24, 8)])
+def test_frequent_small_ids_take_the_bitmask_path(D, k):
+    """IDs below 32 (the most frequent words of a frequency-ranked
+    vocabulary) are collected as bits and applied once per set: sets made
+    mostly of them, on the warp and the CTA paths and in a one-launch batch,
+    give the oracle's sketches; with a universe smaller than 32 the IDs at or
+    beyond it are still flagged and skipped."""
+    dev = device()
+    rng = np.random.default_rng(55)
+    sizes = list(rng.integers(1, 200, 150)) + [5000, 12000, 0, 3]
+    sets = []
+    for s in sizes:
+        x = rng.integers(0, 32, s)
+        tail = rng.integers(0, min(D, 1 << 20), s)
+        sets.append(np.where(rng.random(s) < 0.8, x, tail).astype(np.uint32))
+    valid = [st[st < D] for st in sets]
+    ids, off = synth.pack_sets(sets)
+    vids, voff = synth.pack_sets(valid)
+    for n_rep in (1, 130):  # one launch with a work list, then two launches
+        ids_r, off_r = synth.pack_sets([st for st in sets for _ in range(1)] * n_rep)
+        with hoph.Plan(D, k, k, seed=4) as plan:
+            planes = plan.sketch(to_dev(ids_r, dev), to_dev(off_r, dev), len(off_r) - 1)
+            rc = hoph.hoph_sync_status(plan.handle)
+            assert rc == (hoph.HOPH_ERR_ID_RANGE if D < 32 else hoph.HOPH_OK)
+            got = planes_to_rows(planes)
+        want = oc.sketch(vids, voff, oc.layout(D, k, k), perm=oc.permutation(D, 4))
+        assert np.array_equal(got, np.tile(want, (n_rep, 1)))
