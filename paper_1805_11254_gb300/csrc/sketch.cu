@@ -112,6 +112,13 @@ constexpr uint32_t kHotIds = 32;
 constexpr uint32_t kSkipKey = 0xFFFFFFFEu;
 constexpr uint32_t kBadKey = 0xFFFFFFFFu;
 
+// 1 << x, or 0 for x >= 32 (PTX shl clamps the shift amount to the width)
+__device__ __forceinline__ uint32_t bit_or_zero(uint32_t x) {
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(1u), "r"(x));
+    return r;
+}
+
 // The hot IDs of a set (bits of hm, collected by its warp or CTA), applied
 // to its sketch once each by lanes 0..31; one at or beyond D (a universe of
 // fewer than 32 IDs) is flagged instead.
@@ -152,9 +159,8 @@ __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *
         } else {
             // the most frequent IDs of a frequency-ranked vocabulary (x < 32)
             // only set a bit; the set's bits are applied once at its end
-            const bool h = x < kHotIds;
-            hot |= h ? (1u << (x & 31u)) : 0u;
-            return h ? kSkipKey : (x < a.D ? __ldg(a.key + x) : kBadKey);
+            hot |= bit_or_zero(x);
+            return x < kHotIds ? kSkipKey : (x < a.D ? __ldg(a.key + x) : kBadKey);
         }
     };
     auto apply = [&](Loc v) {
@@ -209,9 +215,8 @@ __device__ __forceinline__ void sketch_generated(const SketchArgs &a, const uint
         } else {
             // the most frequent IDs of a frequency-ranked vocabulary (x < 32)
             // only set a bit; the set's bits are applied once at its end
-            const bool h = x < kHotIds;
-            hot |= h ? (1u << (x & 31u)) : 0u;
-            return h ? kSkipKey : (x < a.D ? __ldg(a.key + x) : kBadKey);
+            hot |= bit_or_zero(x);
+            return x < kHotIds ? kSkipKey : (x < a.D ? __ldg(a.key + x) : kBadKey);
         }
     };
     auto apply = [&](Loc v) {
@@ -275,8 +280,6 @@ __global__ void __launch_bounds__(kSketchThreads, (!HASH && PHASES != 3) ? 8 : 6
     __syncthreads();
     bool bad = false;
     uint32_t hot = 0;
-    __shared__ uint32_t s_hot;
-    if (threadIdx.x == 0) s_hot = 0;
     const int64_t n_big = a.n_big ? (int64_t)*a.n_big : 0;
     // phase 1 (warp 0's sketch region serves the CTA; store_sketch resets it)
     for (int64_t item = (PHASES & 1) ? blockIdx.x : n_big; item < n_big; item += gridDim.x) {
@@ -288,15 +291,11 @@ __global__ void __launch_bounds__(kSketchThreads, (!HASH && PHASES != 3) ? 8 : 6
         else
             sketch_ids<HASH>(a, s_lo, &s_reg, s_sk, a.ids + beg, end - beg, threadIdx.x,
                              blockDim.x, bad, hot);
-        if (!HASH) {
-            const uint32_t hm = __reduce_or_sync(0xFFFFFFFFu, hot);
+        if (!HASH) {  // each warp applies the hot IDs its own lanes met
+            apply_hot(a, s_sk, __reduce_or_sync(0xFFFFFFFFu, hot), lane, bad);
             hot = 0;
-            if (lane == 0 && hm) atomicOr(&s_hot, hm);
-            __syncthreads();
-            if (warp == 0) apply_hot(a, s_sk, s_hot, lane, bad);
         }
         __syncthreads();
-        if (!HASH && threadIdx.x == 0) s_hot = 0;  // every read of it is behind the barrier
         store_sketch<COMPACT>(a, s_sk, set, threadIdx.x, blockDim.x);
         __syncthreads();
     }
