@@ -436,3 +436,40 @@ def test_decision_reductions_on_unequal_layouts(a, b):
                 assert hr.hoph_compare(sa, sb, kg, z, T, 0.0)[0] == full
                 assert hr.hoph_compare(sa, sb, kg, z, T, 1.0)[1] == 1
                 assert hr.hoph_compare(sa, sb, kg, z, T, 2.5)[1] == 1
+
+
+@pytest.mark.parametrize("a,b", [(1, 1), (1, 2), (2, 1), (3, 2)])
+def test_literal_recursion_matches_its_closed_form(a, b):
+    """Algorithm 2's printed recursion P_l = (P_{l-1} - (M_l/k') r^l) / r^l
+    from P_0 = T unrolls to P_l = T / r^{s_l} - sum_j (M_j/k') / r^{s_l - s_j}
+    with s_l = 1 + 2 + ... + l.  Every early decision of the oracle's literal
+    weighting (Def. 1's tails at P_l k') must agree with that closed form, for
+    r = a/(a+b) with a:b = 1:1, 1:2, 2:1, 3:2 and random match counts over
+    four groups (no empty bins, so K = k')."""
+    import random
+    rng = random.Random(5 + 10 * a + b)
+    kg, G = 8, 4
+    lo, z = hr.layout(4096, kg * G, kg, a, b)
+    r = Fraction(a, a + b)
+    for T in (Fraction(7, 10), Fraction(1, 2)):
+        bt = hr.BinomialTails(kg, T)
+        for eps in (1e-3, 0.05, 0.3):
+            for _ in range(60):
+                ms = [rng.randint(0, kg) for _ in range(G)]
+                s_, t_ = _pair_with_matches(kg, ms, G)
+                got = hr.hoph_compare(s_, t_, kg, z, T, eps, weighting="literal", ab=(a, b))
+                want = None
+                for l in range(1, G):
+                    sl = l * (l + 1) // 2
+                    P = T / r ** sl - sum(Fraction(ms[j - 1], kg) / r ** (sl - j * (j + 1) // 2)
+                                          for j in range(1, l + 1))
+                    if P < T and bt.lower(P * kg) <= eps:
+                        want = (hr.ACCEPT, l)
+                        break
+                    if P >= T and bt.upper(P * kg) <= eps:
+                        want = (hr.REJECT, l)
+                        break
+                if want is None:  # all groups: the space-weighted estimator (Lemma 3)
+                    est = hr.hoph_estimate(s_, t_, kg, z)
+                    want = ((hr.ACCEPT if est is not None and est >= T else hr.REJECT), G)
+                assert got[:2] == want, (a, b, T, eps, ms, got, want)
