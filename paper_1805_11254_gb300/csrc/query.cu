@@ -789,6 +789,12 @@ __global__ void __launch_bounds__(32 * (MAXC + 1)) filter_kernel(const __grid_co
     }
 }
 
+__device__ __forceinline__ uint32_t umad(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+
 // Join filter over a striped group map (lanes over bins).  A warp takes 32
 // rows at a time; for each, lane l reads 32-bit words l, l + 32, ... of the row
 // (NW words, 4 / sizeof(E) values each), so the 32 lanes look up 32 different
@@ -849,6 +855,8 @@ __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_co
     for (int s = 0; s < NS; ++s) sbase[s] = ((uint32_t)s * a.nwb * 32u + (uint32_t)lane) * 4u;
     const uint32_t row_words = (uint32_t)a.W * sizeof(E) / 4;
     const int keep_empty = a.keep_empty;
+    // 1, 8, 128 and 256 as values the compiler cannot fold into shifts and adds
+    const uint32_t one = a.stages > 0 ? 1u : 0u, k8 = one << 3, k128 = one << 7, k256 = one << 8;
 
     int s = 0;
     uint32_t ph = 0;
@@ -865,13 +873,16 @@ __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_co
         // groups of 32 rows, dealt round-robin over the warps; rows past the
         // collection's end (a ragged last tile) are looked up but never kept
         for (int r0 = warp * 32; r0 < rows; r0 += a.n_cons * 32) {
+            // acc[j] of lane l counts row r0 + (j ^ l): the butterfly below then
+            // always keeps the low half of its slots and sends the high half
             uint32_t acc[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 uint32_t t = 0;
 #pragma unroll
                 for (int i = 0; i < NW; ++i) {
-                    const uint32_t word = tw[(uint32_t)(r0 + j) * row_words + 32 * i];
+                    const uint32_t word =
+                        tw[(uint32_t)(r0 + (j ^ lane)) * row_words + 32 * i];
                     // slot u = value + 1 (the empty marker wraps to slot 0, the guard);
                     // the word of slot u in its stack is u >> 4, 128 bytes a row
                     if constexpr (VPW == 1) {
@@ -884,30 +895,29 @@ __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_co
                         // five bits of its amount, so the low slot needs no mask
                         const uint32_t w1 = __vadd2(word, 0x00010001u);
                         const uint32_t uh = w1 >> 16;
+                        // the multiply-adds run on the FMA pipe, beside the ALU
+                        // pipe that the shifts, rotates and masks keep busy
                         const uint32_t m0 = *reinterpret_cast<const uint32_t *>(
-                            s_gmap + sbase[2 * i] + ((w1 & 0xFFF0u) << 3));
+                            s_gmap + umad(w1 & 0xFFF0u, k8, sbase[2 * i]));
                         const uint32_t m1 = *reinterpret_cast<const uint32_t *>(
-                            s_gmap + sbase[2 * i + 1] + ((uh & ~15u) << 3));
+                            s_gmap + umad(w1 >> 20, k128, sbase[2 * i + 1]));
                         // non-empty slots: 1 per half, the low one counted in bits
                         // 8-15, the high one in bits 24-31
-                        t += (__funnelshift_r(m0, m0, w1) & 0x10001u) +
-                             (__funnelshift_r(m1, m1, uh) & 0x10001u) +
-                             (__vsetne2(w1, 0u) << 8);
+                        t = umad(__funnelshift_r(m0, m0, w1) & 0x10001u, one, t);
+                        t = umad(__funnelshift_r(m1, m1, uh) & 0x10001u, one, t);
+                        t = umad(__vsetne2(w1, 0u), k256, t);
                     }
                 }
                 acc[j] = t;
             }
-            // butterfly: after step `o` a lane holds the partial sums of the rows
-            // whose index agrees with its own lane index in the bits done so far
+            // butterfly: at step o, slot j < o of lane l holds row r0 + (j ^ l), whose
+            // partner-lane share sits in the partner's slot j + o (the same row:
+            // (j + o) ^ (l ^ o) = j ^ l); after the last step slot 0 is row r0 + l
 #pragma unroll
-            for (int o = 16, n = 16; o >= 1; o >>= 1, n >>= 1) {
-                const bool upper = (lane & o) != 0;
+            for (int o = 16; o >= 1; o >>= 1) {
 #pragma unroll
-                for (int j = 0; j < n; ++j) {
-                    const uint32_t send = upper ? acc[j] : acc[j + n];
-                    const uint32_t keep = upper ? acc[j + n] : acc[j];
-                    acc[j] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, o);
-                }
+                for (int j = 0; j < o; ++j)
+                    acc[j] = umad(__shfl_xor_sync(0xFFFFFFFFu, acc[j + o], o), one, acc[j]);
             }
             const uint32_t tot = acc[0];  // row r0 + lane
             const uint32_t ne = ((tot >> 8) & 0xFFu) + (VPW == 1 ? 0u : tot >> 24);
