@@ -621,6 +621,7 @@ struct FilterArgs {
     uint32_t map_shift;       // hashed map: slot = map_slot(key, map_shift)
     uint32_t nwb;             // striped map: words per (bin, lane) stack
     int32_t boxes;            // TMA boxes per tile (striped: tiles above 256 rows)
+    uint32_t stage_align;     // alignment of the stages' offset in shared memory
     const uint64_t *binbase;  // key = lo[w] + value
     const uint16_t *row_min;  // [W + 1]
     int32_t keep_empty;       // rows without a non-empty scanned bin are candidates
@@ -642,7 +643,7 @@ __host__ __device__ inline FilterSmem filter_smem(const FilterArgs &a) {
     L.bars = o;       o += 16 * 8;
     L.abort_flag = o; o += 16;
     L.row_min = o;    o = align_up(o + (a.W + 1) * 2, 16);
-    L.gmap = o;       o = align_up(o + a.gmap_words * 4, 1024);
+    L.gmap = o;       o = align_up(o + a.gmap_words * 4, a.stage_align);
     L.stages = o;     o += a.stages * a.stage_stride;
     L.total = o;
     return L;
@@ -800,24 +801,25 @@ __device__ __forceinline__ uint32_t umad(uint32_t a, uint32_t b, uint32_t c) {
 // (NW words, 4 / sizeof(E) values each), so the 32 lanes look up 32 different
 // banks of the map and every lookup is one shared-memory wavefront.  A lane
 // keeps one packed partial count per row (even-group hits in bits 0-7,
-// non-empty bins 8-15, odd-group hits 16-23, and for 16-bit values the
-// non-empty high halves in 24-31; W <= 128 keeps each below 256)
-// and five butterfly steps (exchange half of the rows with the partner lane,
-// add the other half) leave lane r with row r's totals, so every lane decides
-// one row.  Tiles come through an unswizzled 4-D box {v, k'/v, rows, 1}: row
-// r's values are contiguous; tile_rows is a multiple of 32.
+// odd-group hits 16-23; uint32 values: non-empty bins in 8-15; 16-bit values:
+// empty low halves in 8-15 and empty high halves in 24-31; W <= 128 keeps each
+// below 256) and five butterfly steps (exchange half of the rows with the
+// partner lane, add the other half) leave lane r with row r's totals, so every
+// lane decides one row.  Tiles come through an unswizzled 4-D box
+// {v, k'/v, rows, 1}: row r's values are contiguous; tile_rows is a multiple
+// of 32 and the stages start on a multiple of 32 rows' bytes.
 template <typename E, int NW>
 __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_constant__ FilterArgs a,
                                                                const __grid_constant__ CUtensorMap map) {
     constexpr int VPW = 4 / (int)sizeof(E);  // values per 32-bit word
     constexpr int NS = NW * VPW;             // values (map stacks) per lane
+    constexpr uint32_t RB = 128u * NW;       // bytes of a row
     extern __shared__ __align__(1024) unsigned char smem[];
     const FilterSmem L = filter_smem(a);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint64_t *empty = full + 8;
     volatile int32_t *abort_flag = reinterpret_cast<volatile int32_t *>(smem + L.abort_flag);
     uint16_t *s_rmin = reinterpret_cast<uint16_t *>(smem + L.row_min);
-    const unsigned char *s_gmap = smem + L.gmap;
     unsigned char *stages = smem + L.stages;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -849,14 +851,21 @@ __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_co
         for (uint32_t i = tid; i < n4; i += nt) dst[i] = __ldg(src + i);
         named_bar_sync(1, nt);
     }
-    // byte offset of (stack s, word row 0) in this lane's bank
+    // offset in shared memory of (stack s, word row 0) in this lane's bank
     uint32_t sbase[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) sbase[s] = ((uint32_t)s * a.nwb * 32u + (uint32_t)lane) * 4u;
-    const uint32_t row_words = (uint32_t)a.W * sizeof(E) / 4;
+    for (int s = 0; s < NS; ++s)
+        sbase[s] = L.gmap + ((uint32_t)s * a.nwb * 32u + (uint32_t)lane) * 4u;
     const int keep_empty = a.keep_empty;
-    // 1, 8, 128 and 256 as values the compiler cannot fold into shifts and adds
-    const uint32_t one = a.stages > 0 ? 1u : 0u, k8 = one << 3, k128 = one << 7, k256 = one << 8;
+    const uint32_t W = (uint32_t)a.W;
+    // 1, 8, 128 and 2^16 as values the compiler cannot fold into shifts and
+    // adds (the multiply-adds run on the FMA pipe, beside the ALU pipe that
+    // the shifts, rotates and masks keep busy)
+    const uint32_t one = a.stages > 0 ? 1u : 0u, k8 = one << 3, k128 = one << 7, k64k = one << 16;
+    // this lane's word l of row (32-row group base) ^ (j << 7): the group's
+    // offset is a multiple of 32 rows' bytes, so OR-ing in the lane's row and
+    // word is an addition
+    const uint32_t lane_off = (uint32_t)lane * RB | (uint32_t)lane * 4u;
 
     int s = 0;
     uint32_t ph = 0;
@@ -866,46 +875,46 @@ __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_co
             *abort_flag = 1;
             break;
         }
-        const uint32_t *tw =
-            reinterpret_cast<const uint32_t *>(stages + (size_t)s * a.stage_stride) + lane;
+        const uint32_t st_off = L.stages + (uint32_t)s * a.stage_stride;
         const int64_t row0 = tile * R;
         const int rows = (int)(a.n_rows - row0 < (int64_t)R ? a.n_rows - row0 : (int64_t)R);
         // groups of 32 rows, dealt round-robin over the warps; rows past the
         // collection's end (a ragged last tile) are looked up but never kept
         for (int r0 = warp * 32; r0 < rows; r0 += a.n_cons * 32) {
+            const uint32_t q_off = (st_off + (uint32_t)r0 * RB) | lane_off;
             // acc[j] of lane l counts row r0 + (j ^ l): the butterfly below then
             // always keeps the low half of its slots and sends the high half
             uint32_t acc[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
+                const unsigned char *rp = smem + (q_off ^ ((uint32_t)j * RB));
                 uint32_t t = 0;
 #pragma unroll
                 for (int i = 0; i < NW; ++i) {
-                    const uint32_t word =
-                        tw[(uint32_t)(r0 + (j ^ lane)) * row_words + 32 * i];
+                    const uint32_t word = *reinterpret_cast<const uint32_t *>(rp + 128 * i);
                     // slot u = value + 1 (the empty marker wraps to slot 0, the guard);
                     // the word of slot u in its stack is u >> 4, 128 bytes a row
                     if constexpr (VPW == 1) {
                         const uint32_t u = word + 1u;
                         const uint32_t mw = *reinterpret_cast<const uint32_t *>(
-                            s_gmap + sbase[i] + ((u & ~15u) << 3));
+                            smem + sbase[i] + ((u & ~15u) << 3));
                         t += (__funnelshift_r(mw, mw, u) & 0x10001u) + (u != 0u ? 0x100u : 0u);
                     } else {
-                        // both 16-bit slots at once; the rotation only reads the low
-                        // five bits of its amount, so the low slot needs no mask
-                        const uint32_t w1 = __vadd2(word, 0x00010001u);
-                        const uint32_t uh = w1 >> 16;
-                        // the multiply-adds run on the FMA pipe, beside the ALU
-                        // pipe that the shifts, rotates and masks keep busy
+                        // low slot: word + 1 (a carry into the high half is never
+                        // read); high slot: word + 2^16, wrapping out of the word.
+                        // The rotations read only the low five bits of their amount
+                        const uint32_t w1 = umad(word, one, one);
+                        const uint32_t w2 = umad(one, k64k, word);
                         const uint32_t m0 = *reinterpret_cast<const uint32_t *>(
-                            s_gmap + umad(w1 & 0xFFF0u, k8, sbase[2 * i]));
+                            smem + umad(w1 & 0xFFF0u, k8, sbase[2 * i]));
                         const uint32_t m1 = *reinterpret_cast<const uint32_t *>(
-                            s_gmap + umad(w1 >> 20, k128, sbase[2 * i + 1]));
-                        // non-empty slots: 1 per half, the low one counted in bits
-                        // 8-15, the high one in bits 24-31
-                        t = umad(__funnelshift_r(m0, m0, w1) & 0x10001u, one, t);
-                        t = umad(__funnelshift_r(m1, m1, uh) & 0x10001u, one, t);
-                        t = umad(__vsetne2(w1, 0u), k256, t);
+                            smem + umad(w2 >> 20, k128, sbase[2 * i + 1]));
+                        t += (__funnelshift_r(m0, m0, w1) & 0x10001u) +
+                             (__funnelshift_r(m1, m1, w2 >> 16) & 0x10001u);
+                        // empty halves: a stored offset is below 2^15 (a bin has at
+                        // most nwb * 16 - 1 <= 32767 values), the empty marker has
+                        // bit 15 set; bits 15 and 31 land on 8 and 24
+                        t += (word >> 7) & 0x01000100u;
                     }
                 }
                 acc[j] = t;
@@ -920,7 +929,8 @@ __global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_co
                     acc[j] = umad(__shfl_xor_sync(0xFFFFFFFFu, acc[j + o], o), one, acc[j]);
             }
             const uint32_t tot = acc[0];  // row r0 + lane
-            const uint32_t ne = ((tot >> 8) & 0xFFu) + (VPW == 1 ? 0u : tot >> 24);
+            const uint32_t ne =
+                VPW == 1 ? (tot >> 8) & 0xFFu : W - (((tot >> 8) & 0xFFu) + (tot >> 24));
             const uint32_t hh = max(tot & 0xFFu, (tot >> 16) & 0xFFu);
             const bool pass = (r0 + lane < rows) &&
                               (ne == 0 ? keep_empty != 0 : hh >= (uint32_t)s_rmin[ne]);
@@ -1525,17 +1535,21 @@ bool encode_swizzled_map(CUtensorMap *map, const void *planes, int esize, int kg
 template <typename E, int NW>
 int launch_striped(const FilterArgs &fa, const CUtensorMap &map, uint32_t smem, int num_sms,
                    int ctas_per_sm, cudaStream_t s) {
-    auto kern = filter_striped_kernel<E, NW>;
-    HOPH_CUDA_TRY(hoph_ensure_smem((const void *)kern, (int)smem));
-    const int threads = 32 * (fa.n_cons + 1);
-    int per_sm = 0;
-    HOPH_CUDA_TRY(hoph_occupancy(&per_sm, (const void *)kern, threads, smem));
-    if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
-    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
-    const int64_t grid = std::min<int64_t>(fa.n_tiles, (int64_t)num_sms * per_sm);
-    kern<<<(unsigned)grid, threads, smem, s>>>(fa, map);
-    HOPH_CUDA_TRY(cudaGetLastError());
-    return HOPH_OK;
+    if constexpr (sizeof(E) == 2 && NW == 4) {
+        return HOPH_ERR_UNSUPPORTED;  // 256 16-bit bins: W <= 128 never gets here
+    } else {
+        auto kern = filter_striped_kernel<E, NW>;
+        HOPH_CUDA_TRY(hoph_ensure_smem((const void *)kern, (int)smem));
+        const int threads = 32 * (fa.n_cons + 1);
+        int per_sm = 0;
+        HOPH_CUDA_TRY(hoph_occupancy(&per_sm, (const void *)kern, threads, smem));
+        if (per_sm < 1) return HOPH_ERR_UNSUPPORTED;
+        if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+        const int64_t grid = std::min<int64_t>(fa.n_tiles, (int64_t)num_sms * per_sm);
+        kern<<<(unsigned)grid, threads, smem, s>>>(fa, map);
+        HOPH_CUDA_TRY(cudaGetLastError());
+        return HOPH_OK;
+    }
 }
 
 template <int NPER, bool HASHED, int MAXC, typename E>
@@ -1765,8 +1779,9 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         for (int w = 0; w < W; ++w) maxw = std::max<uint64_t>(maxw, plan->lo[w + 1] - plan->lo[w]);
         nwb = (uint32_t)((maxw + 1 + 15) / 16);
     }
-    const bool striped_ok = nwb > 0 && (uint64_t)W * nwb * 4 + 2ull * 64 * W * ES + 8 * W +
-                                           4096 <= (uint64_t)kSmemLimit;
+    const bool striped_ok = nwb > 0 && (ES == 4 || nwb * 16 <= 0x8000) &&
+                            (uint64_t)W * nwb * 4 + 2ull * 64 * W * ES + 8 * W + 4096 +
+                                    4096ull * lane_words <= (uint64_t)kSmemLimit;
     // (the library's own choice for 16-bit planes, where it is the faster filter)
     const bool striped = strategy == 1 && (plan->exec.lanes_per_row == 32 ||
                                            (plan->exec.lanes_per_row == 0 && ES == 2 && striped_ok));
@@ -1919,8 +1934,11 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
         const int nper = W / lpr;
         if (!striped && (W % lpr || (nper != 32 && nper != 16) || lpr > 32))
             return HOPH_ERR_UNSUPPORTED;
+        // striped: the stages start on a multiple of 32 rows' bytes (lane l
+        // then finds row r0 + (j ^ l) of a group at one XOR off its base)
+        fa.stage_align = striped ? 4096u * (uint32_t)lane_words : 1024u;
         const uint32_t fixed = 16 * 8 + 16 + align_up((W + 1) * 2, 16) +
-                               align_up(fa.gmap_words * 4, 1024) + 1024;
+                               align_up(fa.gmap_words * 4, fa.stage_align) + fa.stage_align;
         int n_cons = plan->exec.consumer_warps > 0 ? plan->exec.consumer_warps : 16;
         if (striped) n_cons = std::min(n_cons, 16);
         int stages = plan->exec.stages > 0 ? plan->exec.stages : 3;
