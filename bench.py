@@ -46,7 +46,9 @@ CAP = 1 << 16
 # dram read+write bytes per filter-kernel launch from an ncu capture, keyed by
 # the sha256 of the filter kernel's source it was taken on (null once that
 # source changes)
-NCU_TRAFFIC = {"e447e4d9d8de52fd": 2577.20e6}  # 2*10^6-row capture x 5 rows
+NCU_TRAFFIC = {"e0b00ae8eed0effc": 2575.74e6}  # 2*10^6-row capture x 5 rows
+# the same for the striped filter over compact 16-bit planes (its own source)
+NCU_TRAFFIC_STRIPED = {"bde26c624d67763a": 1295.89e6}  # 2*10^6-row capture x 5 rows
 
 
 def parse():
@@ -108,13 +110,15 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def filter_src_sha():
-    """sha256[:16] of the uint32 join filter's source (FilterArgs through
-    filter_kernel)."""
+def filter_src_sha(striped=False):
+    """sha256[:16] of the join filter's source: FilterArgs through
+    filter_kernel, and for the striped filter on to its end."""
     with open(os.path.join(ROOT, "paper_1805_11254_gb300", "csrc", "query.cu")) as f:
         text = f.read()
     a = text.index("struct FilterArgs {")
     b = text.index("// Join filter over a striped group map")
+    if striped:
+        b = text.index("// Join strategy, part 3")
     return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 
 
@@ -1328,15 +1332,22 @@ def compact_leg(args, off, coll_seed, dq_ids, dq_off, nq, pairs_ref, dev, stream
     ach = alg / (filt / 1e3) / 1e9
     ms_serial = ms
     ms = min(ms, ms2)
+    # lanes_per_row 0 is the library's choice: the striped filter for 16-bit planes
+    striped = best is None or (best.get("strategy", 1) != 0 and
+                               best.get("lanes_per_row", 0) in (0, 32))
     return {"value": nq * args.rows / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "ms_per_step_one_batch_at_a_time": ms_serial,
             "ms_per_step_by_batches_in_flight": ms_in_flight,
             "same_pairs_as_uint32_planes": same, "plane_bytes": args.rows * K * 2,
             "autotune": {"best": best, "ms_by_candidate": tune_ms},
-            "roofline": {"bound": "hbm", "kernel": "filter_kernel (uint16 planes)",
+            "roofline": {"bound": "hbm",
+                         "kernel": ("filter_striped_kernel" if striped else "filter_kernel")
+                         + " (uint16 planes)",
                          "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": alg,
-                         "kernel_ms_per_launch": filt},
+                         "kernel_ms_per_launch": filt,
+                         "traffic": NCU_TRAFFIC_STRIPED.get(filter_src_sha(True))
+                         if striped else None},
             "how": "same collection and query sets; sketch values stored as 16-bit bin offsets "
                    "(empty = 0xFFFF); CUDA graph replays, CUDA events"}
 
