@@ -1379,10 +1379,13 @@ def self_join_leg(off, coll_seed, dev, stream, n_base=1_000_000, n_planted=1000,
         d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
         hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
         base_planes = plan.sketch(d_ids, to_dev(off[:n_base + 1], dev), n_base)
+        base16 = plan.sketch16(d_ids, to_dev(off[:n_base + 1], dev), n_base)
         del d_ids
         pl_planes = plan.sketch(to_dev(p_ids, dev), to_dev(p_off, dev), n_planted)
+        pl16 = plan.sketch16(to_dev(p_ids, dev), to_dev(p_off, dev), n_planted)
         planes = torch.cat([base_planes, pl_planes], dim=1).contiguous()
-        del base_planes, pl_planes
+        planes16 = torch.cat([base16, pl16], dim=1).contiguous()
+        del base_planes, pl_planes, base16, pl16
         plan.check()
         cap = 1 << 20
         out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
@@ -1415,6 +1418,28 @@ def self_join_leg(off, coll_seed, dev, stream, n_base=1_000_000, n_planted=1000,
         pairs = ref
         m = len(ref)
         del planes
+        # the same self-join over compact 16-bit planes (hoph_self_join16:
+        # the striped filter), the result checked against the uint32 one
+        ms16_by_choice, same16 = {}, True
+        for b in batches:
+            for ln in lanes[-2:]:
+                plan.update_exec(join_lanes=ln)
+                hoph.hoph_self_join16(plan.handle, hoph.HOPH_MODE_HOPH, planes16, n, b, out, cap,
+                                      cnt, None, stream)
+                plan.check(stream)
+                m16 = int(cnt.item())
+                got = out[:min(m16, cap)].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+                same16 = same16 and bool(np.array_equal(got, ref))
+                e0.record(stream)
+                for _ in range(reps):
+                    hoph.hoph_self_join16(plan.handle, hoph.HOPH_MODE_HOPH, planes16, n, b, out,
+                                          cap, cnt, None, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                plan.check(stream)
+                ms16_by_choice["%d rows x %d lanes" % (b, ln)] = e0.elapsed_time(e1) / reps
+        best16 = min(ms16_by_choice, key=ms16_by_choice.get)
+        del planes16
         torch.cuda.empty_cache()
     found = {(int(p["query"]), int(p["row"])) for p in pairs}
     want = {(int(src[i]), n_base + i) for i in range(n_planted) if truly[i]}
@@ -1423,6 +1448,12 @@ def self_join_leg(off, coll_seed, dev, stream, n_base=1_000_000, n_planted=1000,
             "value": compared / (ms / 1e3), "unit": UNIT, "accepted": m,
             "ms_by_block_rows_and_lanes": ms_by_choice,
             "planted_truly_similar": len(want), "planted_found": len(want & found),
+            "compact": {"ms": ms16_by_choice[best16],
+                        "value": compared / (ms16_by_choice[best16] / 1e3),
+                        "same_pairs_as_uint32_planes": same16,
+                        "ms_by_block_rows_and_lanes": ms16_by_choice,
+                        "how": "hoph_self_join16 over compact 16-bit planes, blocks of %s"
+                               % best16},
             "how": "hoph_self_join, blocks of %s in flight, each block's rows as queries against "
                    "the rows from the block on; (1:2)HOPH k=256 k'=64, T=0.7, eps=1e-4" % best}
 

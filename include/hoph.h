@@ -309,6 +309,17 @@ int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int
                    hoph_stats *d_stats, void *stream);
 
 /*
+ * hoph_self_join over compact planes (uint16[G][n_rows][k'] from
+ * oph_build_sketches16: each bin's minimum as its offset from the bin's lower
+ * bound, HOPH_EMPTY_VALUE16 for an empty bin; Sec. 3.2 / 4.1).  Same
+ * arguments, pairs, statistics and errors as hoph_self_join on the uint32
+ * planes of the same sets; HOPH_ERR_UNSUPPORTED as for hoph_query_batch16.
+ */
+int hoph_self_join16(hoph_plan *plan, uint32_t mode, const uint16_t *d_planes, int64_t n_rows,
+                     int64_t batch, hoph_pair *d_out, int64_t out_capacity,
+                     int64_t *d_out_count, hoph_stats *d_stats, void *stream);
+
+/*
  * oph_build_sketches without any device allocation.  The paper has no
  * counterpart: this serves callers that may not allocate device memory
  * during the call, such as a serving loop whose device memory is owned by

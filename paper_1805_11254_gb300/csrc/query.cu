@@ -2091,27 +2091,8 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
     return HOPH_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_planes,
-                     int64_t n_queries, const uint32_t *d_coll_planes, int64_t n_rows,
-                     hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
-                     hoph_stats *d_stats, void *stream) {
-    return query_batch_impl<uint32_t>(plan, mode, d_query_planes, n_queries, d_coll_planes, n_rows,
-                                      d_out, out_capacity, d_out_count, d_stats, stream);
-}
-
-int hoph_query_batch16(hoph_plan *plan, uint32_t mode, const uint16_t *d_query_planes,
-                       int64_t n_queries, const uint16_t *d_coll_planes, int64_t n_rows,
-                       hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
-                       hoph_stats *d_stats, void *stream) {
-    return query_batch_impl<uint16_t>(plan, mode, d_query_planes, n_queries, d_coll_planes,
-                                      n_rows, d_out, out_capacity, d_out_count, d_stats, stream);
-}
-
-int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int64_t n_rows,
+template <typename E>
+int self_join_impl(hoph_plan *plan, uint32_t mode, const E *d_planes, int64_t n_rows,
                    int64_t batch, hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
                    hoph_stats *d_stats, void *stream) {
     if (!plan || !d_out_count || n_rows < 0 || batch < 1 || batch > 4096 || out_capacity < 0)
@@ -2152,10 +2133,10 @@ int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int
         const int lane = (int)(blk % lanes);
         cudaStream_t ls = lanes > 1 ? plan->lane_stream[lane] : s;
         // rows q0 .. n_rows-1 against queries q0 .. q0+nb-1, both read in place
-        const uint32_t *bp = d_planes + q0 * kg;
-        rc = query_batch_impl<uint32_t>(plan, mode, bp, nb, bp, n_rows - q0, d_out, out_capacity,
-                                        d_out_count, d_stats, ls, cstride, cstride, q0, false,
-                                        false, lane);
+        const E *bp = d_planes + q0 * kg;
+        rc = query_batch_impl<E>(plan, mode, bp, nb, bp, n_rows - q0, d_out, out_capacity,
+                                 d_out_count, d_stats, ls, cstride, cstride, q0, false, false,
+                                 lane);
     }
     if (lanes > 1) {  // join every lane back, also after an error
         for (int i = 0; i < lanes; ++i) {
@@ -2178,6 +2159,41 @@ int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int
     if (rc2 != HOPH_OK) return rc2;
     plan->launches += sort_launches;
     return HOPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_planes,
+                     int64_t n_queries, const uint32_t *d_coll_planes, int64_t n_rows,
+                     hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
+                     hoph_stats *d_stats, void *stream) {
+    return query_batch_impl<uint32_t>(plan, mode, d_query_planes, n_queries, d_coll_planes, n_rows,
+                                      d_out, out_capacity, d_out_count, d_stats, stream);
+}
+
+int hoph_query_batch16(hoph_plan *plan, uint32_t mode, const uint16_t *d_query_planes,
+                       int64_t n_queries, const uint16_t *d_coll_planes, int64_t n_rows,
+                       hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
+                       hoph_stats *d_stats, void *stream) {
+    return query_batch_impl<uint16_t>(plan, mode, d_query_planes, n_queries, d_coll_planes,
+                                      n_rows, d_out, out_capacity, d_out_count, d_stats, stream);
+}
+
+
+int hoph_self_join(hoph_plan *plan, uint32_t mode, const uint32_t *d_planes, int64_t n_rows,
+                   int64_t batch, hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
+                   hoph_stats *d_stats, void *stream) {
+    return self_join_impl<uint32_t>(plan, mode, d_planes, n_rows, batch, d_out, out_capacity,
+                                    d_out_count, d_stats, stream);
+}
+
+int hoph_self_join16(hoph_plan *plan, uint32_t mode, const uint16_t *d_planes, int64_t n_rows,
+                     int64_t batch, hoph_pair *d_out, int64_t out_capacity,
+                     int64_t *d_out_count, hoph_stats *d_stats, void *stream) {
+    return self_join_impl<uint16_t>(plan, mode, d_planes, n_rows, batch, d_out, out_capacity,
+                                    d_out_count, d_stats, stream);
 }
 
 int hoph_check_bounded_wait(hoph_plan *plan, uint64_t limit_ns, void *stream) {

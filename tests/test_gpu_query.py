@@ -471,6 +471,34 @@ def test_self_join_blocks_in_flight_keep_the_result(self_join_case, lanes):
     assert list(stats.rejected[:len(w["rej"])]) == w["rej"]
 
 
+@pytest.mark.parametrize("knobs", [dict(strategy=1, lanes_per_row=0),
+                                   dict(strategy=1, lanes_per_row=32, consumer_warps=5,
+                                        tile_rows=96),
+                                   dict(strategy=1, lanes_per_row=4),
+                                   dict(strategy=0)])
+def test_compact_self_join_gives_the_oracle_pairs(self_join_case, knobs):
+    """hoph_self_join16 over compact 16-bit planes, blocks of 300 rows on
+    three streams, through the striped filter (the library's choice and
+    forced, ragged tiles), the lanes-over-rows filter and the dense scan: the
+    oracle's upper-triangle pairs in order and its per-group decision
+    counts, as for the uint32 planes."""
+    dev = device()
+    w = self_join_case
+    with hoph.Plan(w["D"], w["k"], w["kg"], *w["ab"], seed=1, thr=T, epsilon=EPS) as plan:
+        c16 = plan.sketch16(to_dev(w["ids"], dev), to_dev(w["off"], dev), w["n"])
+        plan.set_exec(join_lanes=3, **knobs)
+        pairs, m, stats = plan.self_join("hoph", c16, w["n"], batch=300, stats=True)
+        plan.check()
+        got = [(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"]))
+               for p in pairs]
+    assert c16.dtype == torch.int16
+    assert m == len(got)
+    assert got == w["want"]
+    assert stats.entering[0] == w["n"] * (w["n"] - 1) // 2
+    assert list(stats.accepted[:len(w["acc"])]) == w["acc"]
+    assert list(stats.rejected[:len(w["rej"])]) == w["rej"]
+
+
 def test_self_join_with_lanes_replays_from_a_graph(self_join_case):
     """The self-join's fork onto the plan's streams and join back, captured
     in a CUDA graph (after one eager call has created the streams) and
