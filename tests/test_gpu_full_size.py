@@ -153,7 +153,9 @@ def test_full_size_self_join_on_reported_planted_and_random_pairs():
     among them, blocks of 1,536 rows: every reported pair is one the oracle
     accepts, with its groups and matches; every planted pair the oracle
     accepts is reported; so is every accepted pair of 4,000 random pairs;
-    and the statistics cover exactly the n (n - 1) / 2 pairs."""
+    and the statistics cover exactly the n (n - 1) / 2 pairs.  The compact
+    self-join (hoph_self_join16, the striped filter) gives the same pairs and
+    statistics."""
     dev = device()
     n_base, n_pl = 1_000_000, 1000
     off_all = synth.offsets_from_sizes(synth.counter_collection_sizes(10_000_000, COLL_SEED))
@@ -172,10 +174,13 @@ def test_full_size_self_join_on_reported_planted_and_random_pairs():
         d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
         hoph.hoph_synth_ids(COLL_SEED, 0, n_ids, D, 0, None, 0, d_ids)
         base = plan.sketch(d_ids, to_dev(off, dev), n_base)
+        base16 = plan.sketch16(d_ids, to_dev(off, dev), n_base)
         del d_ids
         pl = plan.sketch(to_dev(p_ids, dev), to_dev(p_off, dev), n_pl)
+        pl16 = plan.sketch16(to_dev(p_ids, dev), to_dev(p_off, dev), n_pl)
         planes = torch.cat([base, pl], dim=1).contiguous()
-        del base, pl
+        planes16 = torch.cat([base16, pl16], dim=1).contiguous()
+        del base, pl, base16, pl16
         plan.check()
         cap = 1 << 20
         out = torch.empty((cap, 2), dtype=torch.int64, device=dev)
@@ -188,7 +193,17 @@ def test_full_size_self_join_on_reported_planted_and_random_pairs():
         stats = hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes())
         G = plan.G
         del planes
+        st.zero_()
+        hoph.hoph_self_join16(plan.handle, hoph.HOPH_MODE_HOPH, planes16, n, 1536, out, cap, cnt,
+                              st)
+        plan.check()
+        got16 = out[:int(cnt.item())].cpu().numpy().view(hoph.PAIR_DTYPE).reshape(-1)
+        stats16 = hoph.hoph_stats.from_buffer_copy(st.cpu().numpy().tobytes())
+        del planes16
         torch.cuda.empty_cache()
+    assert np.array_equal(got16, got)
+    for f in ("entering", "accepted", "rejected"):
+        assert list(getattr(stats16, f)) == list(getattr(stats, f))
 
     def ids_of(r):
         return _row_ids(COLL_SEED, off, r) if r < n_base else planted[r - n_base]
