@@ -660,6 +660,39 @@ def test_striped_filter_keeps_the_oracle_pairs(small, k, kg, compact, knobs):
         assert e.value.code == hoph.HOPH_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("lanes_per_row", [0, 32])
+def test_value_join_when_rows_hit_most_queries(lanes_per_row):
+    """Sketches over two values per bin, so every row hits nearly all of 600
+    queries in most bins: the value join passes most rows, and its candidate
+    counting walks long query lists for each of them and drains its
+    survivor list many times; (1:2)HOPH at T = 7/10 rejects pairs after the
+    first group and takes others on.  The oracle's pairs and per-group
+    decision counts."""
+    dev = device()
+    rng = np.random.default_rng(78)
+    D, k, kg, ab, nq, nr = 1 << 16, 256, 64, (1, 2), 600, 1500
+    q_rows = rng.integers(0, 2, (nq, k)).astype(np.uint32)
+    c_rows = rng.integers(0, 2, (nr, k)).astype(np.uint32)
+    c_rows[:40] = q_rows[:40]  # some exact duplicates
+    c_rows[rng.random((nr, k)) < 0.05] = hoph.HOPH_EMPTY_VALUE
+    want = oc.query("hoph", q_rows, c_rows, kg, T[0], T[1], EPS, z=oracle_z(D, k, kg, ab))
+    assert want["count"] >= 40
+    with hoph.Plan(D, k, kg, *ab, seed=1, thr=T, epsilon=EPS) as plan:
+        q, c = rows_to_planes(q_rows, kg, dev), rows_to_planes(c_rows, kg, dev)
+        plan.set_exec(strategy=1, lanes_per_row=lanes_per_row)
+        pairs, n, st = plan.query("hoph", q, nq, c, nr, capacity=1 << 16, stats=True)
+        assert st.strategy == 1
+        assert st.rows_counted > nr // 2
+        assert n == want["count"]
+        got = np.stack([pairs["query"].astype(np.int64), pairs["row"],
+                        pairs["groups"].astype(np.int64), pairs["matches"].astype(np.int64)], 1)
+        assert np.array_equal(got, want["accepted"])
+        hist = want["hist"]
+        for g in range(plan.G):
+            assert st.accepted[g] == hist[g + 1][1] and st.rejected[g] == hist[g + 1][2]
+    assert hist[1][2] > 0 and hist[2:].sum() > 0  # group 1 rejects some pairs, others go on
+
+
 def test_over_a_million_accepted_pairs_come_out_in_order():
     """Over a million accepted pairs (sketches over two values per bin, so about
     half the bins of a pair match; T = 2/5): a capacity above the one-CTA
