@@ -972,10 +972,18 @@ struct CountArgs {
     const uint32_t *n_allempty;
 };
 
-// four warps and about 11 KB of shared memory a CTA (1,024 queries), so that
-// counting CTAs fit on an SM beside a running filter CTA of another batch
+// four warps and about 7 KB of shared memory a CTA (1,024 queries), so that
+// a counting CTA fits on an SM beside a running filter CTA of another batch
 constexpr int kCountThreads = 128;
 constexpr int kCountWarps = kCountThreads / 32;
+
+// a warp's per-query match counters: 8 bits each when a row has fewer than
+// 256 scanned bins (a count never exceeds W), else 16
+__host__ __device__ inline int count_lg(int W) { return W < 256 ? 2 : 1; }  // log2 per word
+__host__ __device__ inline int count_words(int n_q, int W) {
+    const int per = 1 << count_lg(W);
+    return (n_q + per - 1) / per;
+}
 
 struct CountSmem {
     uint32_t thr, woff, counters, rowmask, surv, nsurv, stats, total;
@@ -986,7 +994,7 @@ __host__ __device__ inline CountSmem count_smem(const CountArgs &a) {
     uint32_t o = 0;
     L.thr = o;      o = align_up(o + 3 * (a.p.W + 1) * 2, 16);
     L.woff = o;     o = align_up(o + a.p.W * 8, 16);
-    L.counters = o; o = align_up(o + kCountWarps * ((a.p.n_q + 1) / 2) * 4, 16);
+    L.counters = o; o = align_up(o + kCountWarps * count_words(a.p.n_q, a.p.W) * 4, 16);
     L.rowmask = o;  o = align_up(o + kCountWarps * a.mask_words * 4, 16);
     L.surv = o;     o = align_up(o + kCountWarps * kSurvCap * (uint32_t)sizeof(Survivor), 16);
     L.nsurv = o;    o = align_up(o + kCountWarps * 4, 16);
@@ -1012,7 +1020,10 @@ __global__ void __launch_bounds__(kCountThreads, 6) count_kernel(const __grid_co
     uint32_t *s_nsurv = reinterpret_cast<uint32_t *>(smem + L.nsurv);
     unsigned long long *s_stats = reinterpret_cast<unsigned long long *>(smem + L.stats);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int cwords = (P.n_q + 1) / 2;
+    const int cwords = count_words(P.n_q, P.W);
+    // counter of query q: bits [csh(q), csh(q) + cbits) of word q >> clg
+    const uint32_t clg = (uint32_t)count_lg(P.W), cbits = 32u >> clg;
+    const uint32_t cmask = (1u << cbits) - 1u, csel = (1u << clg) - 1u;
     for (int i = tid; i < 3 * (P.W + 1); i += blockDim.x) s_thr[i] = P.thr[i];
     for (int w = tid; w < P.W; w += blockDim.x) {
         const int g = w / P.kg, b = w - g * P.kg;
@@ -1110,7 +1121,7 @@ __global__ void __launch_bounds__(kCountThreads, 6) count_kernel(const __grid_co
             for (uint32_t e = f[c]; e != kNil; e = __ldg(a.next + e)) {
                 const uint32_t q = e >> a.wshift;
                 if (q < qlim) {
-                    atomicAdd(cnt + (q >> 1), 1u << ((q & 1) * 16));
+                    atomicAdd(cnt + (q >> clg), 1u << ((q & csel) * cbits));
                     ++hits;
                 }
             }
@@ -1136,9 +1147,9 @@ __global__ void __launch_bounds__(kCountThreads, 6) count_kernel(const __grid_co
                 }
                 // (a query at or past qlim was not counted: m = 0 below)
                 const uint32_t q = i >> a.wshift;
-                const uint32_t sh = (q & 1) * 16;
-                const uint32_t old = atomicAnd(cnt + (q >> 1), ~(0xFFFFu << sh));
-                const int m = (int)((old >> sh) & 0xFFFFu);
+                const uint32_t sh = (q & csel) * cbits;
+                const uint32_t old = atomicAnd(cnt + (q >> clg), ~(cmask << sh));
+                const int m = (int)((old >> sh) & cmask);
                 if (m >= need) {
                     int both = 0, one = 0;
                     const uint32_t *qm = a.q_emask + (int64_t)q * a.mask_words;
@@ -1154,7 +1165,7 @@ __global__ void __launch_bounds__(kCountThreads, 6) count_kernel(const __grid_co
                         emit_pair(P, q, row, 1, m);
                     } else if (d == HOPH_CONTINUE) {
                         if (!push_survivor(list, nsurv, q, row, m, K)) {
-                            atomicAdd(cnt + (q >> 1), (uint32_t)m << sh);  // retry later
+                            atomicAdd(cnt + (q >> clg), (uint32_t)m << sh);  // retry later
                             break;
                         }
                     }
