@@ -1036,7 +1036,8 @@ def profile_shingle(args, dev, stream, reps=2):
 def profile_self_join(args, off, coll_seed, dev, stream, batch=1536):
     """One hoph_self_join over the collection's first --rows rows ((1:2)HOPH,
     blocks of 1,536 rows, the library's default blocks in flight), for an ncu
-    launch list."""
+    launch list; with --profile-compact over compact 16-bit planes
+    (hoph_self_join16)."""
     import torch
     from paper_1805_11254_gb300 import hoph
     n = args.rows
@@ -1044,10 +1045,12 @@ def profile_self_join(args, off, coll_seed, dev, stream, batch=1536):
         n_ids = int(off[n])
         d_ids = torch.empty(n_ids, dtype=torch.int32, device=dev)
         hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
-        planes = plan.sketch(d_ids, to_dev(off[:n + 1], dev), n, stream=stream)
+        sketch = plan.sketch16 if args.profile_compact else plan.sketch
+        planes = sketch(d_ids, to_dev(off[:n + 1], dev), n, stream=stream)
         del d_ids
         pairs, m, _ = plan.self_join("hoph", planes, n, batch=batch, stream=stream)
-        print(json.dumps({"self_join_rows": n, "batch": batch, "accepted": m}), flush=True)
+        print(json.dumps({"self_join_rows": n, "batch": batch, "accepted": m,
+                          "compact": bool(args.profile_compact)}), flush=True)
 
 
 def profile_oph1(args, off, coll_seed, dev, stream, launches=3):
