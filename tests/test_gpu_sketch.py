@@ -240,6 +240,16 @@ def test_compact_sketches_need_bins_of_at_most_65535_values():
         with pytest.raises(hoph.HophError) as e:
             hoph.oph_build_sketches16(plan.handle, off, off, 1, out)
         assert e.value.code == hoph.HOPH_ERR_UNSUPPORTED
+        # the compact query and self-join refuse such a plan too
+        pairs = torch.empty((4, 2), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        planes = torch.full((1, 3, 8), -1, dtype=torch.int16, device=dev)
+        with pytest.raises(hoph.HophError) as e:
+            hoph.hoph_query_batch16(plan.handle, "oph_full", planes, 3, planes, 3, pairs, 4, cnt)
+        assert e.value.code == hoph.HOPH_ERR_UNSUPPORTED
+        with pytest.raises(hoph.HophError) as e:
+            hoph.hoph_self_join16(plan.handle, "oph_full", planes, 3, 2, pairs, 4, cnt)
+        assert e.value.code == hoph.HOPH_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("n", [64, 4096, 4097, 16383, 16384])
