@@ -253,7 +253,10 @@ int minwise_build_sketches(hoph_plan *plan, const uint32_t *d_ids, const int64_t
  *   d_stats         nullable; hoph_stats accumulated on the device.
  * Mode GOPH and OPH_FULL need an equal-bin plan (a = b = 0); mode HOPH an
  * (a:b) plan; MINWISE_FULL a plan with minwise_k > 0.
- * Plane pointers must be 16-byte aligned.
+ * Plane pointers must be 16-byte aligned.  Every stored value must be one the
+ * sketch functions of this plan can produce (an offset below its bin's width,
+ * or HOPH_EMPTY_VALUE): the value join indexes shared-memory tables by the
+ * values without a bounds check, so other values are undefined behaviour.
  */
 int hoph_query_batch(hoph_plan *plan, uint32_t mode, const uint32_t *d_query_planes,
                      int64_t n_queries, const uint32_t *d_coll_planes, int64_t n_rows,
