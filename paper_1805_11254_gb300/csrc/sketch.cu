@@ -31,14 +31,16 @@ constexpr int64_t kSplitPhases = 16384;  // from this many sets: one launch per 
 constexpr int64_t kSmallList = 4096;     // up to this many sets: the work list in one CTA
 
 // Hash path: psi-space regions of equal-width bins (the whole space for equal
-// bins, one per group for a:b); a value's bin is first + floor(o * nb / z).
+// bins, one per group for a:b); a value's bin is first + floor(o * nb / z),
+// computed as the high half of o * magic with magic = floor(2^64 nb / z) + 1:
+// o * magic / 2^64 exceeds o nb / z by less than o / 2^64 < 2^-32 <= 1 / z,
+// and o nb / z is at most 1 / z below the next integer, so the floor is the
+// same.  magic = 0 marks bins of one value (nb = z: the bin is the offset).
 struct RegionTable {
     int32_t n;
     uint32_t start[HOPH_MAX_GROUPS];
-    uint64_t size[HOPH_MAX_GROUPS];
-    uint32_t bins[HOPH_MAX_GROUPS];
     uint32_t first[HOPH_MAX_GROUPS];
-    float ratio[HOPH_MAX_GROUPS];  // bins / size
+    uint64_t magic[HOPH_MAX_GROUPS];
 };
 
 struct SketchArgs {
@@ -86,19 +88,17 @@ __device__ __forceinline__ uint32_t hash61(uint64_t x, uint64_t a, uint64_t b) {
 }
 
 // Bin and offset of a hashed psi-value v: the region containing v (a few
-// comparisons against the region starts), then floor(o * nb / z) from a
-// float estimate corrected by one exact integer step each way (the float
-// error is far below one bin), then the offset from the bin's lower bound.
+// comparisons against the region starts), then floor(o * nb / z) by the
+// region's magic multiplier (the high word of o * magic, as o * (magic >> 32)
+// plus the high half of o * (magic & 0xFFFFFFFF)), then the offset from the
+// bin's lower bound.
 __device__ __forceinline__ uint64_t hash_bin(const RegionTable &t, const uint64_t *s_lo, uint32_t v) {
     int r = 0;
     for (int i = 1; i < t.n; ++i) r += v >= t.start[i];
     const uint32_t o = v - t.start[r];
-    const uint64_t ok = (uint64_t)o * t.bins[r];
-    const uint64_t z = t.size[r];
-    uint32_t q = (uint32_t)((float)o * t.ratio[r]);
-    if (q >= t.bins[r]) q = t.bins[r] - 1;
-    if ((uint64_t)q * z > ok) --q;
-    else if ((uint64_t)(q + 1) * z <= ok) ++q;
+    const uint64_t m = t.magic[r];
+    const uint32_t q =
+        m ? (uint32_t)(((uint64_t)o * (uint32_t)(m >> 32) + __umulhi(o, (uint32_t)m)) >> 32) : o;
     const uint32_t bin = t.first[r] + q;
     return ((uint64_t)bin << 32) | (uint32_t)(v - s_lo[bin]);
 }
@@ -541,11 +541,11 @@ SketchArgs sketch_args(hoph_plan *plan, const uint32_t *d_ids, const int64_t *d_
     for (int r = 0; r < a.reg.n; ++r) {
         const uint32_t first = equal ? 0 : (uint32_t)r * P.k_group;
         const uint32_t nb = equal ? P.k : P.k_group;
+        const uint64_t z = plan->lo[first + nb] - plan->lo[first];
         a.reg.start[r] = (uint32_t)plan->lo[first];
-        a.reg.size[r] = plan->lo[first + nb] - plan->lo[first];
-        a.reg.bins[r] = nb;
         a.reg.first[r] = first;
-        a.reg.ratio[r] = (float)((double)nb / (double)a.reg.size[r]);
+        a.reg.magic[r] =
+            nb < z ? (uint64_t)(((unsigned __int128)nb << 64) / z) + 1u : 0u;  // z <= 2^32
     }
     a.status = plan->d_status;
     return a;
