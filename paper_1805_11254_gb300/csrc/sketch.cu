@@ -92,7 +92,7 @@ __device__ __forceinline__ uint32_t hash61(uint64_t x, uint64_t a, uint64_t b) {
 // region's magic multiplier (the high word of o * magic, as o * (magic >> 32)
 // plus the high half of o * (magic & 0xFFFFFFFF)), then the offset from the
 // bin's lower bound.
-__device__ __forceinline__ uint64_t hash_bin(const RegionTable &t, const uint64_t *s_lo, uint32_t v) {
+__device__ __forceinline__ uint64_t hash_bin(const RegionTable &t, const uint32_t *s_lo, uint32_t v) {
     int r = 0;
     for (int i = 1; i < t.n; ++i) r += v >= t.start[i];
     const uint32_t o = v - t.start[r];
@@ -100,7 +100,7 @@ __device__ __forceinline__ uint64_t hash_bin(const RegionTable &t, const uint64_
     const uint32_t q =
         m ? (uint32_t)(((uint64_t)o * (uint32_t)(m >> 32) + __umulhi(o, (uint32_t)m)) >> 32) : o;
     const uint32_t bin = t.first[r] + q;
-    return ((uint64_t)bin << 32) | (uint32_t)(v - s_lo[bin]);
+    return ((uint64_t)bin << 32) | (v - s_lo[bin]);
 }
 
 // Table path: the IDs below kHotIds (the most frequent words of a
@@ -142,7 +142,7 @@ __device__ __forceinline__ void apply_hot(const SketchArgs &a, uint32_t *sk, uin
 // shared-memory operation per ID instead of a read and, when it improves, an
 // atomic).
 template <bool HASH, bool WIDE = true>
-__device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *s_lo,
+__device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint32_t *s_lo,
                                            const RegionTable *s_reg, uint32_t *sk,
                                            const uint32_t *p, int64_t n, int t, int T,
                                            bool &bad, uint32_t &hot) {
@@ -202,7 +202,7 @@ __device__ __forceinline__ void sketch_ids(const SketchArgs &a, const uint64_t *
 // As sketch_ids, with the IDs of elements [first, first + n) of the
 // generator stream produced in registers instead of loaded.
 template <bool HASH>
-__device__ __forceinline__ void sketch_generated(const SketchArgs &a, const uint64_t *s_lo,
+__device__ __forceinline__ void sketch_generated(const SketchArgs &a, const uint32_t *s_lo,
                                                  const RegionTable *s_reg, uint32_t *sk,
                                                  uint64_t first, int64_t n, int t, int T,
                                                  bool &bad, uint32_t &hot) {
@@ -267,12 +267,14 @@ template <bool HASH, int PHASES, bool COMPACT>
 __global__ void __launch_bounds__(kSketchThreads, (!HASH && PHASES != 3) ? 8 : 6)
     oph_sketch_kernel(const SketchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *s_lo = reinterpret_cast<uint64_t *>(smem_raw);  // HASH only
-    uint32_t *s_sk = reinterpret_cast<uint32_t *>(smem_raw + (HASH ? (a.k + 1) * 8 : 0));
+    // HASH only: the bins' lower bounds (below 2^32 for every bin of a universe
+    // of at most 2^32 values)
+    uint32_t *s_lo = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *s_sk = reinterpret_cast<uint32_t *>(smem_raw + (HASH ? (a.k + 3) / 4 * 16 : 0));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ RegionTable s_reg;
     if (HASH) {
-        for (uint32_t i = threadIdx.x; i <= a.k; i += blockDim.x) s_lo[i] = a.lo[i];
+        for (uint32_t i = threadIdx.x; i < a.k; i += blockDim.x) s_lo[i] = (uint32_t)a.lo[i];
         if (threadIdx.x == 0) s_reg = a.reg;
     }
     const uint32_t regions = (PHASES & 2) ? kSketchWarps : 1;
@@ -587,7 +589,7 @@ int build_work_list(hoph_plan *plan, const int64_t *d_offsets, int64_t n_sets, u
 template <bool HASH, int PHASES, bool COMPACT>
 int launch_phases(hoph_plan *plan, const SketchArgs &a, cudaStream_t s) {
     const uint32_t k = a.k;
-    const size_t lo_b = HASH ? (size_t)(k + 1) * 8 : 0;
+    const size_t lo_b = HASH ? (size_t)(k + 3) / 4 * 16 : 0;
     const size_t smem = lo_b + (size_t)((PHASES & 2) ? kSketchWarps : 1) * k * 4;
     auto kern = oph_sketch_kernel<HASH, PHASES, COMPACT>;
     HOPH_CUDA_TRY(hoph_ensure_smem((const void *)kern, (int)smem));
