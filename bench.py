@@ -1589,12 +1589,13 @@ def sweep_leg(dev, stream, reps=5):
             "collection_sketch_ms": sketch_ms, "points": out}
 
 
-# 64-bit multiplies per ID on the hashed-psi sketch path (read off the
-# kernels): the generator's SplitMix64 step (3 low products) and its scaling
-# to [0, D) (1 low), psi = ((a x + b) mod 2^61-1) >> 29 (1 low + 1 high), and
-# the bin arithmetic floor(o nb / z) with its exact correction (2 low)
-ALU_MULS_GENERATED = {"lo": 7, "hi": 1}
-ALU_MULS_STORED = {"lo": 3, "hi": 1}
+# Multiplies per ID on the hashed-psi sketch path (read off the kernels): the
+# generator's SplitMix64 step (3 low 64-bit products) and its scaling to
+# [0, D) (1 low), psi = ((a x + b) mod 2^61-1) >> 29 (1 low + 1 high 64-bit
+# product), and the bin floor(o nb / z) by the region's magic multiplier
+# (2 32-bit multiplies: a wide product and a high half)
+ALU_MULS_GENERATED = {"lo": 5, "hi": 1, "imad32": 2}
+ALU_MULS_STORED = {"lo": 1, "hi": 1, "imad32": 2}
 
 
 def alu_peak_leg(dev, stream, target_ms=30.0):
@@ -1641,13 +1642,14 @@ def alu_peak_leg(dev, stream, target_ms=30.0):
 
 
 def alu_roofline(ids_per_s, muls, peak):
-    """IDs/s against the IDs/s the measured 64-bit multiply rates allow at
-    `muls` low and high products per ID."""
+    """IDs/s against the IDs/s the measured multiply rates allow at `muls`
+    64-bit low and high products and 32-bit multiplies per ID."""
     ideal = 1.0 / (muls["lo"] / peak["mul64_lo"]["ops_per_s"] +
-                   muls["hi"] / peak["mul64_hi"]["ops_per_s"])
+                   muls["hi"] / peak["mul64_hi"]["ops_per_s"] +
+                   muls.get("imad32", 0) / peak["imad32"]["ops_per_s"])
     return {"bound": "alu", "achieved": ids_per_s, "peak": ideal, "unit": "IDs/s",
             "frac": ids_per_s / ideal, "muls_per_id": muls,
-            "peak_source": "measured (hoph_int_probe 64-bit products, this run)"}
+            "peak_source": "measured (hoph_int_probe multiply rates, this run)"}
 
 
 def shingle_leg(args, dev, stream, peaks, q_batch=1024, n_planted=32):
