@@ -377,6 +377,30 @@ def run_native(args):
         hoph.hoph_synth_ids(coll_seed, 0, n_ids, D, 0, None, 0, d_ids)
         planes = plan.sketch(d_ids, d_off, args.rows)
         plan.check()
+        coll_sketch = None
+        if rank == 0 and world == 1 and not args.no_extras:
+            # the same call again, timed: 10^7 sets of uniform IDs over 2^20 (next to
+            # no repeated IDs within a set, unlike the Zipf sketch workload)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                plan.sketch(d_ids, d_off, args.rows, out=planes)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            plan.check()
+            ms = e0.elapsed_time(e1) / 2
+            b = 4 * n_ids + 8 * (args.rows + 1) + 4 * K * args.rows
+            # every ID is one random 4-byte gather from the 4 MiB psi table, and the
+            # L1 serves one cache line per SM clock: a floor for the call
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            gather_ms = n_ids / (sms * 2070e6) * 1e3
+            coll_sketch = {"sets": args.rows, "ids": n_ids, "ms_per_call": ms,
+                           "sets_per_s": args.rows / (ms / 1e3),
+                           "hbm_frac": b / (ms / 1e3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
+                           "gather_floor_ms": gather_ms, "gather_floor_frac": gather_ms / ms,
+                           "how": "the collection's own sketch call (uniform IDs over 2^20), "
+                                  "timed twice after the setup call; gather floor = one L1 "
+                                  "line per ID at one line per SM per clock (2,070 MHz)"}
     del d_ids, d_off
     torch.cuda.empty_cache()
 
@@ -429,6 +453,7 @@ def run_native(args):
     # the other legs are single-GPU studies: rank 0 of a one-GPU run only
     if rank == 0 and world == 1 and not args.no_extras:
         details["sketch"] = sketch_leg(dev, stream, peaks)
+        details["sketch"]["uniform_ids_collection"] = coll_sketch
         rq = recall_queries(off, coll_seed)
         details["oph_full_scan_baseline"], oph_pairs, oph_rq_pairs = oph_baseline_leg(
             args, off, coll_seed, qw, dev, stream, value, rq)
