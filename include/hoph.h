@@ -323,6 +323,25 @@ int hoph_self_join16(hoph_plan *plan, uint32_t mode, const uint16_t *d_planes, i
                      int64_t *d_out_count, hoph_stats *d_stats, void *stream);
 
 /*
+ * One part of a self-join split over `parts` callers (one per GPU, each
+ * holding the whole collection): blocks part, part + parts, part + 2 parts,
+ * ... of the blocks hoph_self_join would run (block b: rows b*batch ..
+ * b*batch+batch-1 as queries against the rows from b*batch on).  The parts'
+ * pairs are disjoint, each part's sorted by (query, row); their union in that
+ * order is hoph_self_join's output and the sum of their statistics its
+ * statistics.  Dealing blocks round-robin gives each part about the same
+ * number of pair comparisons.
+ *   d_planes     uint32 (value_bytes 4) or compact uint16 (value_bytes 2)
+ *                planes [G][n_rows][k'].
+ *   part, parts  0 <= part < parts, else HOPH_ERR_PARAM.
+ * Other arguments and errors as hoph_self_join / hoph_self_join16.
+ */
+int hoph_self_join_part(hoph_plan *plan, uint32_t mode, const void *d_planes,
+                        uint32_t value_bytes, int64_t n_rows, int64_t batch, int64_t part,
+                        int64_t parts, hoph_pair *d_out, int64_t out_capacity,
+                        int64_t *d_out_count, hoph_stats *d_stats, void *stream);
+
+/*
  * oph_build_sketches without any device allocation.  The paper has no
  * counterpart: this serves callers that may not allocate device memory
  * during the call, such as a serving loop whose device memory is owned by

@@ -2105,8 +2105,9 @@ int query_batch_impl(hoph_plan *plan, uint32_t mode, const E *d_query_planes, in
 template <typename E>
 int self_join_impl(hoph_plan *plan, uint32_t mode, const E *d_planes, int64_t n_rows,
                    int64_t batch, hoph_pair *d_out, int64_t out_capacity, int64_t *d_out_count,
-                   hoph_stats *d_stats, void *stream) {
-    if (!plan || !d_out_count || n_rows < 0 || batch < 1 || batch > 4096 || out_capacity < 0)
+                   hoph_stats *d_stats, void *stream, int64_t part = 0, int64_t parts = 1) {
+    if (!plan || !d_out_count || n_rows < 0 || batch < 1 || batch > 4096 || out_capacity < 0 ||
+        parts < 1 || part < 0 || part >= parts)
         return HOPH_ERR_PARAM;
     if (out_capacity > 0 && !d_out) return HOPH_ERR_PARAM;
     if (mode == HOPH_MODE_MINWISE_FULL) return HOPH_ERR_UNSUPPORTED;
@@ -2118,8 +2119,11 @@ int self_join_impl(hoph_plan *plan, uint32_t mode, const E *d_planes, int64_t n_
     const int64_t kg = plan->P.k_group;
     const int64_t cstride = n_rows * kg;
     const int64_t n_blocks = (n_rows - 1 + batch - 1) / batch;
+    // this call's blocks: part, part + parts, ...
+    const int64_t my_blocks = n_blocks > part ? (n_blocks - part + parts - 1) / parts : 0;
+    if (my_blocks == 0) return HOPH_OK;
     const int want = plan->exec.join_lanes > 0 ? plan->exec.join_lanes : 8;
-    const int lanes = (int)std::min<int64_t>(std::min(want, (int)hoph_plan::kMaxLanes), n_blocks);
+    const int lanes = (int)std::min<int64_t>(std::min(want, (int)hoph_plan::kMaxLanes), my_blocks);
     // blocks in flight: block b runs on lane b % lanes, each lane a stream and
     // a scratch of the plan's own, forked from and joined back to `stream`
     if (lanes > 1) {
@@ -2138,10 +2142,11 @@ int self_join_impl(hoph_plan *plan, uint32_t mode, const E *d_planes, int64_t n_
             HOPH_CUDA_TRY(cudaStreamWaitEvent(plan->lane_stream[i], plan->fork_event, 0));
     }
     int rc = HOPH_OK;
-    for (int64_t blk = 0; blk < n_blocks && rc == HOPH_OK; ++blk) {
+    for (int64_t i = 0; i < my_blocks && rc == HOPH_OK; ++i) {
+        const int64_t blk = part + i * parts;
         const int64_t q0 = blk * batch;
         const int64_t nb = std::min(batch, n_rows - 1 - q0);
-        const int lane = (int)(blk % lanes);
+        const int lane = (int)(i % lanes);
         cudaStream_t ls = lanes > 1 ? plan->lane_stream[lane] : s;
         // rows q0 .. n_rows-1 against queries q0 .. q0+nb-1, both read in place
         const E *bp = d_planes + q0 * kg;
@@ -2205,6 +2210,21 @@ int hoph_self_join16(hoph_plan *plan, uint32_t mode, const uint16_t *d_planes, i
                      int64_t *d_out_count, hoph_stats *d_stats, void *stream) {
     return self_join_impl<uint16_t>(plan, mode, d_planes, n_rows, batch, d_out, out_capacity,
                                     d_out_count, d_stats, stream);
+}
+
+int hoph_self_join_part(hoph_plan *plan, uint32_t mode, const void *d_planes,
+                        uint32_t value_bytes, int64_t n_rows, int64_t batch, int64_t part,
+                        int64_t parts, hoph_pair *d_out, int64_t out_capacity,
+                        int64_t *d_out_count, hoph_stats *d_stats, void *stream) {
+    if (value_bytes == 4)
+        return self_join_impl<uint32_t>(plan, mode, static_cast<const uint32_t *>(d_planes),
+                                        n_rows, batch, d_out, out_capacity, d_out_count, d_stats,
+                                        stream, part, parts);
+    if (value_bytes == 2)
+        return self_join_impl<uint16_t>(plan, mode, static_cast<const uint16_t *>(d_planes),
+                                        n_rows, batch, d_out, out_capacity, d_out_count, d_stats,
+                                        stream, part, parts);
+    return HOPH_ERR_PARAM;
 }
 
 int hoph_check_bounded_wait(hoph_plan *plan, uint64_t limit_ns, void *stream) {

@@ -102,7 +102,7 @@ _EXPORTS = ["hoph_plan_create", "hoph_plan_create_with_perm", "hoph_plan_destroy
             "hoph_sync_status", "hoph_status_string", "hoph_plan_enable_timing",
             "hoph_plan_read_timing", "oph_build_sketches_static", "hoph_plan_peek_timing",
             "hoph_check_bounded_wait", "hoph_synth_sketch", "oph_build_sketches16",
-            "hoph_query_batch16", "hoph_self_join", "hoph_self_join16",
+            "hoph_query_batch16", "hoph_self_join", "hoph_self_join16", "hoph_self_join_part",
             "hoph_small_probability_limits",
             "hoph_int_probe"]
 
@@ -144,6 +144,8 @@ def load(path=LIB_PATH):
     lib.hoph_self_join.restype = i32
     lib.hoph_self_join16.argtypes = [P, u32, P, i64, i64, P, i64, P, P, P]
     lib.hoph_self_join16.restype = i32
+    lib.hoph_self_join_part.argtypes = [P, u32, P, u32, i64, i64, i64, i64, P, i64, P, P, P]
+    lib.hoph_self_join_part.restype = i32
     lib.oph_build_sketches16.argtypes = [P, P, P, i64, P, P]
     lib.oph_build_sketches16.restype = i32
     lib.hoph_query_batch16.argtypes = [P, u32, P, i64, P, i64, P, i64, P, P, P]
@@ -282,6 +284,18 @@ def hoph_self_join(plan, mode, d_planes, n_rows, batch, d_out, out_capacity, d_o
                                         int(batch), _ptr(d_out), int(out_capacity),
                                         _ptr(d_out_count), _ptr(d_stats), _stream(stream)),
                   "hoph_self_join")
+
+
+def hoph_self_join_part(plan, mode, d_planes, n_rows, batch, part, parts, d_out, out_capacity,
+                        d_out_count, d_stats=None, stream=None):
+    """Blocks part, part + parts, ... of the self-join (uint32 or compact
+    uint16 planes, told apart by the tensor's element size)."""
+    return _check(load().hoph_self_join_part(plan, MODES.get(mode, mode), _ptr(d_planes),
+                                             int(d_planes.element_size()), int(n_rows),
+                                             int(batch), int(part), int(parts), _ptr(d_out),
+                                             int(out_capacity), _ptr(d_out_count),
+                                             _ptr(d_stats), _stream(stream)),
+                  "hoph_self_join_part")
 
 
 def hoph_self_join16(plan, mode, d_planes, n_rows, batch, d_out, out_capacity, d_out_count,
@@ -469,17 +483,22 @@ class Plan:
         return pairs, n, st_out
 
     def self_join(self, mode, planes, n_rows, batch=1536, capacity=1 << 16, stream=None,
-                  stats=False, check=True):
+                  stats=False, check=True, part=0, parts=1):
         """Run hoph_self_join (hoph_self_join16 for compact 16-bit planes) over
         one collection's planes; returns (pairs structured ndarray with
-        query < row, count, stats)."""
+        query < row, count, stats).  parts > 1: only blocks part, part +
+        parts, ... (hoph_self_join_part)."""
         import torch
         dev = planes.device
         out = torch.empty((max(capacity, 1), 2), dtype=torch.int64, device=dev)
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
         st = torch.zeros(STATS_WORDS, dtype=torch.int64, device=dev) if stats else None
-        call = hoph_self_join16 if planes.element_size() == 2 else hoph_self_join
-        call(self.handle, mode, planes, n_rows, batch, out, capacity, cnt, st, stream)
+        if parts > 1:
+            hoph_self_join_part(self.handle, mode, planes, n_rows, batch, part, parts, out,
+                                capacity, cnt, st, stream)
+        else:
+            call = hoph_self_join16 if planes.element_size() == 2 else hoph_self_join
+            call(self.handle, mode, planes, n_rows, batch, out, capacity, cnt, st, stream)
         if check:
             rc = hoph_sync_status(self.handle, stream)
             if rc not in (HOPH_OK, HOPH_ERR_CAPACITY):

@@ -9,6 +9,11 @@ put back in (query, row) order.  The result equals a one-rank run exactly.
 
 Throughput runs with a fixed collection per rank (weak scaling) need none of
 the exchange; `max_over_ranks` is their only collective, for timing.
+
+A self-join (every pair i < j of one collection) splits by its blocks of
+query rows instead: every rank holds the whole collection, takes the blocks
+b = rank, rank + world, ... (hoph_self_join_part), and the one exchange is
+again the final gather of pairs, whose row indices are global already.
 """
 import numpy as np
 
@@ -66,6 +71,40 @@ def sharded_query(local_query, n_rows, group=None, dst=None):
     import torch.distributed as dist
     r0, r1 = row_range(n_rows, dist.get_rank(group), dist.get_world_size(group))
     return gather_pairs(local_query(r0, r1), r0, group, dst)
+
+
+def self_join_blocks(n_rows, batch, part, parts):
+    """The blocks of a self-join over n_rows rows in blocks of `batch` query
+    rows that part `part` of `parts` runs (hoph_self_join_part's split): block b
+    holds queries b*batch .. b*batch+batch-1 against the rows from b*batch on."""
+    if parts < 1 or not 0 <= part < parts or batch < 1 or n_rows < 0:
+        raise ValueError("bad self-join split: n_rows=%d batch=%d part=%d parts=%d"
+                         % (n_rows, batch, part, parts))
+    n_blocks = (n_rows - 1 + batch - 1) // batch if n_rows > 1 else 0
+    return list(range(part, n_blocks, parts))
+
+
+def sharded_self_join(local_self_join, group=None, dst=None):
+    """This rank's part of a self-join and the gather of every part's pairs.
+    local_self_join(part, parts) returns the pairs (PAIR_DTYPE, global rows) of
+    the blocks self_join_blocks(..., part, parts)."""
+    import torch.distributed as dist
+    mine = local_self_join(dist.get_rank(group), dist.get_world_size(group))
+    return gather_pairs(mine, 0, group, dst)
+
+
+def gpu_local_self_join(plan, mode, planes, n_rows, batch=1536, capacity=1 << 16, stream=None):
+    """local_self_join for sharded_self_join on this rank's GPU: `planes` holds
+    the whole collection ([G][n_rows][k'], uint32 or compact uint16)."""
+    def run(part, parts):
+        cap = capacity
+        while True:
+            pairs, count, _ = plan.self_join(mode, planes, n_rows, batch, cap, stream,
+                                             part=part, parts=parts)
+            if count <= cap:
+                return pairs
+            cap = count
+    return run
 
 
 def gpu_local_query(plan, mode, q_planes, n_queries, local_planes, capacity=1 << 16, stream=None):

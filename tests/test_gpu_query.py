@@ -7,7 +7,7 @@ import pytest
 from gpu_helpers import (device, oracle_rows, oracle_tuples, oracle_z, pairs_tuples,
                          planes_to_rows, rows_to_planes, to_dev, torch)  # noqa: F401
 from oracle import oracle_c as oc
-from paper_1805_11254_gb300 import hoph, synth
+from paper_1805_11254_gb300 import hoph, shard, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -497,6 +497,41 @@ def test_compact_self_join_gives_the_oracle_pairs(self_join_case, knobs):
     assert stats.entering[0] == w["n"] * (w["n"] - 1) // 2
     assert list(stats.accepted[:len(w["acc"])]) == w["acc"]
     assert list(stats.rejected[:len(w["rej"])]) == w["rej"]
+
+
+@pytest.mark.parametrize("compact", [False, True])
+@pytest.mark.parametrize("parts", [2, 3])
+def test_self_join_parts_add_up_to_the_self_join(self_join_case, compact, parts):
+    """hoph_self_join_part, blocks of 300 rows dealt to 2 or 3 parts (as over
+    that many GPUs, each holding the whole collection): every part's pairs
+    in (query, row) order, their union the oracle's upper-triangle pairs and
+    their statistics summing to the oracle's decision counts."""
+    dev = device()
+    w = self_join_case
+    with hoph.Plan(w["D"], w["k"], w["kg"], *w["ab"], seed=1, thr=T, epsilon=EPS) as plan:
+        sk = plan.sketch16 if compact else plan.sketch
+        c = sk(to_dev(w["ids"], dev), to_dev(w["off"], dev), w["n"])
+        plan.update_exec(join_lanes=2)
+        chunks, acc, rej, entering = [], None, None, 0
+        for part in range(parts):
+            pairs, m, st = plan.self_join("hoph", c, w["n"], batch=300, stats=True, part=part,
+                                          parts=parts)
+            got = [(int(p["query"]), int(p["row"])) for p in pairs]
+            assert m == len(got) and got == sorted(got)
+            assert all(q // 300 in shard.self_join_blocks(w["n"], 300, part, parts)
+                       for q, _ in got)
+            chunks.append(pairs)
+            a, r = np.asarray(st.accepted, dtype=np.int64), np.asarray(st.rejected, dtype=np.int64)
+            acc = a if acc is None else acc + a
+            rej = r if rej is None else rej + r
+            entering += st.entering[0]
+        plan.check()
+    merged = shard.merge_pairs(chunks)
+    assert [(int(p["query"]), int(p["row"]), int(p["groups"]), int(p["matches"]))
+            for p in merged] == w["want"]
+    assert entering == w["n"] * (w["n"] - 1) // 2
+    assert list(acc[:len(w["acc"])]) == w["acc"]
+    assert list(rej[:len(w["rej"])]) == w["rej"]
 
 
 def test_self_join_with_lanes_replays_from_a_graph(self_join_case):

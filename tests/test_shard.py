@@ -92,6 +92,72 @@ def _free_port():
         return s.getsockname()[1]
 
 
+@pytest.mark.parametrize("n,batch,parts", [(1201, 100, 2), (1201, 100, 3), (10, 4, 5),
+                                            (2, 1536, 2), (1, 10, 2), (0, 10, 1)])
+def test_self_join_blocks_cover_every_block_once(n, batch, parts):
+    blocks = [shard.self_join_blocks(n, batch, p, parts) for p in range(parts)]
+    flat = sorted(b for bl in blocks for b in bl)
+    n_blocks = (n - 1 + batch - 1) // batch if n > 1 else 0
+    assert flat == list(range(n_blocks))
+    # pair comparisons per part (block b: its queries against the rows from b*batch on)
+    work = [sum(min(batch, n - 1 - b * batch) * (n - b * batch) for b in bl) for bl in blocks]
+    if n_blocks >= 2 * parts:
+        assert max(work) <= 1.6 * min(work)
+
+
+def test_self_join_split_rejects_bad_requests():
+    for args in ((10, 0, 0, 1), (10, 4, 2, 2), (10, 4, -1, 2), (10, 4, 0, 0), (-1, 4, 0, 1)):
+        with pytest.raises(ValueError):
+            shard.self_join_blocks(*args)
+
+
+def _self_join_rows():
+    q_rows, c_rows, z = _workload()
+    return np.concatenate([c_rows, q_rows]), z
+
+
+def _self_join_pairs(rows, z, blocks, batch):
+    """The oracle's accepted pairs i < j whose query row i lies in `blocks`."""
+    allp = _oracle_pairs(rows, rows, z)
+    keep = (allp["query"] < allp["row"]) & np.isin(allp["query"] // batch, blocks)
+    return allp[keep]
+
+
+def _self_join_rank_main(rank, world, port, out_dir, batch):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
+                            world_size=world)
+    try:
+        rows, z = _self_join_rows()
+
+        def local_self_join(part, parts):  # every rank holds the whole collection
+            return _self_join_pairs(rows, z, shard.self_join_blocks(len(rows), batch, part,
+                                                                    parts), batch)
+
+        np.save(os.path.join(out_dir, "sj_%d.npy" % rank), shard.sharded_self_join(local_self_join))
+        np.save(os.path.join(out_dir, "mine_%d.npy" % rank), local_self_join(rank, world))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_sharded_self_join_equals_one_rank():
+    """The self-join split by blocks over 2 gloo ranks (each holding the whole
+    collection, the oracle standing in for the GPU): the gathered pairs equal
+    the one-rank self-join's, and both ranks found some of them."""
+    import torch.multiprocessing as mp
+    world, batch = 2, 100
+    with tempfile.TemporaryDirectory() as tmp:
+        mp.spawn(_self_join_rank_main, args=(world, _free_port(), tmp, batch), nprocs=world,
+                 join=True)
+        rows, z = _self_join_rows()
+        allp = _oracle_pairs(rows, rows, z)
+        want = allp[allp["query"] < allp["row"]]
+        assert len(want) > 0  # the planted near duplicates
+        for r in range(world):
+            assert np.array_equal(np.load(os.path.join(tmp, "sj_%d.npy" % r)), want)
+            assert len(np.load(os.path.join(tmp, "mine_%d.npy" % r))) > 0
+
+
 def test_two_rank_sharded_query_equals_one_rank():
     import torch.multiprocessing as mp
     world = 2
