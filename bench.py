@@ -1616,10 +1616,10 @@ def sweep_leg(dev, stream, reps=5):
 
 # Multiplies per ID on the hashed-psi sketch path (read off the kernels): the
 # generator's SplitMix64 step (3 low 64-bit products) and its scaling to
-# [0, D) (1 low), psi = ((a x + b) mod 2^61-1) >> 29 (1 low + 1 high 64-bit
-# product), and the bin floor(o nb / z) by the region's magic multiplier
-# (2 32-bit multiplies: a wide product and a high half)
-ALU_MULS_GENERATED = {"lo": 5, "hi": 1, "imad32": 2}
+# [0, D) (a 32-bit high half), psi = ((a x + b) mod 2^61-1) >> 29 (1 low + 1
+# high 64-bit product), and the bin floor(o nb / z) by the region's magic
+# multiplier (2 32-bit multiplies: a wide product and a high half)
+ALU_MULS_GENERATED = {"lo": 4, "hi": 1, "imad32": 3}
 ALU_MULS_STORED = {"lo": 1, "hi": 1, "imad32": 2}
 
 

@@ -66,13 +66,16 @@ struct SketchArgs {
 };
 
 // Synthetic ID of element e of stream `seed`: the (e+1)-th SplitMix64 output
-// mapped to [0, D) by a multiply-shift of its top 32 bits (hoph_synth_ids kind 0).
+// mapped to [0, D) by a multiply-shift of its top 32 bits (hoph_synth_ids kind 0):
+// (h D) >> 32 for the top word h, which is h itself for D = 2^32 and the high
+// half of the 32 x 32 product h D below it.
 __device__ __forceinline__ uint32_t synth_id(uint64_t seed, uint64_t e, uint64_t D) {
     uint64_t z = seed + (e + 1) * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z = z ^ (z >> 31);
-    return (uint32_t)(((z >> 32) * D) >> 32);
+    const uint32_t h = (uint32_t)(z >> 32);
+    return (D >> 32) ? h : __umulhi(h, (uint32_t)D);
 }
 
 // psi(x) = ((a x + b) mod (2^61 - 1)) >> 29 with a Mersenne-prime reduction:
