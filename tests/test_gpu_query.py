@@ -500,12 +500,13 @@ def test_compact_self_join_gives_the_oracle_pairs(self_join_case, knobs):
 
 
 @pytest.mark.parametrize("compact", [False, True])
-@pytest.mark.parametrize("parts", [2, 3])
+@pytest.mark.parametrize("parts", [2, 3, 24])
 def test_self_join_parts_add_up_to_the_self_join(self_join_case, compact, parts):
-    """hoph_self_join_part, blocks of 300 rows dealt to 2 or 3 parts (as over
-    that many GPUs, each holding the whole collection): every part's pairs
-    in (query, row) order, their union the oracle's upper-triangle pairs and
-    their statistics summing to the oracle's decision counts."""
+    """hoph_self_join_part, blocks of 300 rows dealt to 2, 3 or 24 parts (as
+    over that many GPUs, each holding the whole collection; with 24, parts
+    beyond the 17 blocks get none): every part's pairs in (query, row) order,
+    their union the oracle's upper-triangle pairs and their statistics
+    summing to the oracle's decision counts."""
     dev = device()
     w = self_join_case
     with hoph.Plan(w["D"], w["k"], w["kg"], *w["ab"], seed=1, thr=T, epsilon=EPS) as plan:
