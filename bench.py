@@ -378,7 +378,7 @@ def run_native(args):
         planes = plan.sketch(d_ids, d_off, args.rows)
         plan.check()
         coll_sketch = None
-        if rank == 0 and world == 1 and not args.no_extras:
+        if rank == 0 and world == 1 and not args.no_extras and not args.profile:
             # the same call again, timed: 10^7 sets of uniform IDs over 2^20 (next to
             # no repeated IDs within a set, unlike the Zipf sketch workload)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
