@@ -809,7 +809,7 @@ __device__ __forceinline__ uint32_t umad(uint32_t a, uint32_t b, uint32_t c) {
 // {v, k'/v, rows, 1}: row r's values are contiguous; tile_rows is a multiple
 // of 32 and the stages start on a multiple of 32 rows' bytes.
 template <typename E, int NW>
-__global__ void __launch_bounds__(32 * 17) filter_striped_kernel(const __grid_constant__ FilterArgs a,
+__global__ void __launch_bounds__(32 * 17, 1) filter_striped_kernel(const __grid_constant__ FilterArgs a,
                                                                const __grid_constant__ CUtensorMap map) {
     constexpr int VPW = 4 / (int)sizeof(E);  // values per 32-bit word
     constexpr int NS = NW * VPW;             // values (map stacks) per lane
