@@ -1476,6 +1476,27 @@ def self_join_leg(off, coll_seed, dev, stream, n_base=1_000_000, n_planted=1000,
                 plan.check(stream)
                 ms16_by_choice["%d rows x %d lanes" % (b, ln)] = e0.elapsed_time(e1) / reps
         best16 = min(ms16_by_choice, key=ms16_by_choice.get)
+        # the same compact self-join split in two parts (hoph_self_join_part, as over
+        # two GPUs each holding the collection): each part timed alone on this GPU
+        b16, ln16 = (int(x) for x in best16.replace(" rows x", "").split()[:2])
+        plan.update_exec(join_lanes=ln16)
+        split_ms, split_pairs = [], []
+        for part in range(2):
+            hoph.hoph_self_join_part(plan.handle, hoph.HOPH_MODE_HOPH, planes16, n, b16, part, 2,
+                                     out, cap, cnt, None, stream)
+            plan.check(stream)
+            mp = int(cnt.item())
+            split_pairs.append(out[:min(mp, cap)].cpu().numpy().view(hoph.PAIR_DTYPE)
+                               .reshape(-1).copy())
+            e0.record(stream)
+            for _ in range(reps):
+                hoph.hoph_self_join_part(plan.handle, hoph.HOPH_MODE_HOPH, planes16, n, b16, part,
+                                         2, out, cap, cnt, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            split_ms.append(e0.elapsed_time(e1) / reps)
+        from paper_1805_11254_gb300 import shard
+        split_same = bool(np.array_equal(shard.merge_pairs(split_pairs), ref))
         del planes16
         torch.cuda.empty_cache()
     found = {(int(p["query"]), int(p["row"])) for p in pairs}
@@ -1490,7 +1511,10 @@ def self_join_leg(off, coll_seed, dev, stream, n_base=1_000_000, n_planted=1000,
                         "same_pairs_as_uint32_planes": same16,
                         "ms_by_block_rows_and_lanes": ms16_by_choice,
                         "how": "hoph_self_join16 over compact 16-bit planes, blocks of %s"
-                               % best16},
+                               % best16,
+                        "split_in_two": {"ms_by_part": split_ms, "same_pairs": split_same,
+                                         "how": "hoph_self_join_part, parts 0 and 1 of 2, "
+                                                "each timed alone on this GPU"}},
             "how": "hoph_self_join, blocks of %s in flight, each block's rows as queries against "
                    "the rows from the block on; (1:2)HOPH k=256 k'=64, T=0.7, eps=1e-4" % best}
 
