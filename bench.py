@@ -50,7 +50,7 @@ NCU_TRAFFIC = {"e0b00ae8eed0effc": 2575.74e6}  # 2*10^6-row capture x 5 rows
 # the same for the striped filter over compact 16-bit planes (its own source)
 NCU_TRAFFIC_STRIPED = {"8fa6ac907bca01c7": 1297.26e6}  # 2*10^6-row capture x 5 rows
 # DRAM bytes of the 10^6-set sketch call (both launches), keyed to sketch.cu's hash
-NCU_TRAFFIC_SKETCH = {"5a88e5b3e53dab7c": 3189e6}
+NCU_TRAFFIC_SKETCH = {"000757fea3813741": 3184.5e6}
 
 
 def parse():
